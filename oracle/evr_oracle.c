@@ -1,0 +1,406 @@
+/*
+ * evr_oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * Reinbacher, Graber, Pock, "Real-Time Intensity-Image Reconstruction for Event
+ * Cameras Using Manifold Regularisation", BMVC 2016.  Each function below follows
+ * one passage of the paper, in the paper's order and notation, with one loop per
+ * step and no blocking or fusion, so that it can be checked against the paper by
+ * eye.  Built with -O2 -ffp-contract=off (no fused multiply-add).
+ *
+ * Readings taken where the paper is silent (all are parameters, shared with the
+ * CUDA library by value, never by code):
+ *  - t(x,y) is the time since the pixel's last event (Sec. 3.1), scaled by
+ *    time_scale and clamped at t_max_us; never-fired pixels count from t_init.
+ *  - L_x, L_y are forward differences whose last column/row is zero; L_g^* is
+ *    the exact adjoint, written here as -div_g.
+ *  - f is the previous reconstruction stepped by c1 or c2 once per event at the
+ *    event's pixel (Eq. intensity_update); pixels without events keep the
+ *    previous reconstruction (data_mode 0), or f persists (data_mode 1).
+ *  - primal step first, then the dual step on 2u_{k+1}-u_k (Eq. cont_iterates),
+ *    warm-started from the previous packet's (u, p).
+ */
+#include "evr_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Discrete derivatives (Sec. 3.1 "Discrete Energy": L_x, L_y are first-order
+ * finite differences after Chambolle 2004: forward difference, zero on the last
+ * column for L_x and on the last row for L_y). */
+void orc_grad(int W, int H, const double* a, double* ax, double* ay) {
+  for (int y = 0; y < H; ++y) {
+    for (int x = 0; x < W; ++x) {
+      int i = y * W + x;
+      ax[i] = (x < W - 1) ? a[i + 1] - a[i] : 0.0;
+      ay[i] = (y < H - 1) ? a[i + W] - a[i] : 0.0;
+    }
+  }
+}
+
+/* Metric of the graph surface phi(x,y) = (x, y, t(x,y)) (Eqs. 1, 2):
+ * phi_x = (1,0,t_x), phi_y = (0,1,t_y), g = [[1+t_x^2, t_x t_y],[t_x t_y, 1+t_y^2]],
+ * G = det g = 1 + t_x^2 + t_y^2, with t_x = L_x t, t_y = L_y t (after Eq. 3). */
+void orc_metric(int W, int H, const double* t, double* tx, double* ty, double* G) {
+  orc_grad(W, H, t, tx, ty);
+  for (int i = 0; i < W * H; ++i) G[i] = 1.0 + tx[i] * tx[i] + ty[i] * ty[i];
+}
+
+/* Eq. 3: the three components of L_g u at each pixel, from L_x t, L_y t, L_x u,
+ * L_y u and G. */
+void orc_Lg(int W, int H, const double* tx, const double* ty, const double* G,
+            const double* u, double* g1, double* g2, double* g3) {
+  int n = W * H;
+  double* ux = (double*)malloc(sizeof(double) * (size_t)n);
+  double* uy = (double*)malloc(sizeof(double) * (size_t)n);
+  orc_grad(W, H, u, ux, uy);
+  for (int i = 0; i < n; ++i) {
+    double a = tx[i], b = ty[i];
+    g1[i] = ((1.0 + b * b) * ux[i] - a * b * uy[i]) / G[i];
+    g2[i] = ((1.0 + a * a) * uy[i] - a * b * ux[i]) / G[i];
+    g3[i] = (a * ux[i] + b * uy[i]) / G[i];
+  }
+  free(ux);
+  free(uy);
+}
+
+/* div_g p = -L_g^* p.  Eq. 3 writes L_g u = M (L_x u, L_y u) with the per-pixel
+ * 3x2 matrix M = (1/G) [[1+t_y^2, -t_x t_y], [-t_x t_y, 1+t_x^2], [t_x, t_y]].
+ * Hence <L_g u, p> = <(L_x u, L_y u), M^T p> = -<u, div(M^T p)>, where div is
+ * the negative adjoint of the forward differences:
+ *   (div q)(x,y) = q1(x,y)[x<W-1] - q1(x-1,y)[x>0] + q2(x,y)[y<H-1] - q2(x,y-1)[y>0]. */
+void orc_divg(int W, int H, const double* tx, const double* ty, const double* G,
+              const double* p1, const double* p2, const double* p3, double* out) {
+  int n = W * H;
+  double* q1 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* q2 = (double*)malloc(sizeof(double) * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    double a = tx[i], b = ty[i];
+    /* column 1 and column 2 of M, dotted with (p1, p2, p3) */
+    q1[i] = ((1.0 + b * b) * p1[i] - a * b * p2[i] + a * p3[i]) / G[i];
+    q2[i] = (-a * b * p1[i] + (1.0 + a * a) * p2[i] + b * p3[i]) / G[i];
+  }
+  for (int y = 0; y < H; ++y) {
+    for (int x = 0; x < W; ++x) {
+      int i = y * W + x;
+      double d = 0.0;
+      if (x < W - 1) d += q1[i];
+      if (x > 0) d -= q1[i - 1];
+      if (y < H - 1) d += q2[i];
+      if (y > 0) d -= q2[i - W];
+      out[i] = d;
+    }
+  }
+  free(q1);
+  free(q2);
+}
+
+/* Eq. update_rules, first line: the minimiser of (u - v)^2/(2 tau) +
+ * tau-scaled KL term is the positive root 1/2 (v - beta + sqrt((v-beta)^2 + 4 beta f)),
+ * beta = tau lambda sqrt(G), clamped to [u_min, u_max]. */
+double orc_prox_kl(double v, double beta, double f, double u_min, double u_max) {
+  double d = v - beta;
+  double r = 0.5 * (d + sqrt(d * d + 4.0 * beta * f));
+  if (r < u_min) r = u_min;
+  if (r > u_max) r = u_max;
+  return r;
+}
+
+/* Eq. update_rules, second line: p / max(1, ||p|| / sqrt(G)). */
+void orc_project(double p1, double p2, double p3, double sqrtG, double* out3) {
+  double nrm = sqrt(p1 * p1 + p2 * p2 + p3 * p3);
+  double den = nrm / sqrtG;
+  if (den < 1.0) den = 1.0;
+  out3[0] = p1 / den;
+  out3[1] = p2 / den;
+  out3[2] = p3 / den;
+}
+
+/* Eq. cont_iterates:
+ *   u_{k+1} = prox_{tau D}(u_k - tau L_g^* p_k) = prox_{tau D}(u_k + tau div_g p_k)
+ *   p_{k+1} = prox_{sigma R^*}(p_k + sigma L_g(2 u_{k+1} - u_k))
+ * with the closed-form proximal maps of Eq. update_rules. */
+void orc_pd_iterations(int W, int H, const double* tx, const double* ty, const double* G,
+                       const double* f, double* u, double* p1, double* p2, double* p3,
+                       int K, double tau, double sigma, double lambda,
+                       double u_min, double u_max) {
+  int n = W * H;
+  size_t bytes = sizeof(double) * (size_t)n;
+  double* dv = (double*)malloc(bytes);
+  double* un = (double*)malloc(bytes);
+  double* ub = (double*)malloc(bytes);
+  double* g1 = (double*)malloc(bytes);
+  double* g2 = (double*)malloc(bytes);
+  double* g3 = (double*)malloc(bytes);
+  for (int k = 0; k < K; ++k) {
+    /* primal: argument u_k - tau L_g^* p_k */
+    orc_divg(W, H, tx, ty, G, p1, p2, p3, dv);
+    for (int i = 0; i < n; ++i) {
+      double v = u[i] + tau * dv[i];
+      double beta = tau * lambda * sqrt(G[i]);
+      un[i] = orc_prox_kl(v, beta, f[i], u_min, u_max);
+    }
+    /* over-relaxation 2 u_{k+1} - u_k */
+    for (int i = 0; i < n; ++i) ub[i] = 2.0 * un[i] - u[i];
+    /* dual: ascent on L_g of the extrapolated primal, then projection */
+    orc_Lg(W, H, tx, ty, G, ub, g1, g2, g3);
+    for (int i = 0; i < n; ++i) {
+      double out[3];
+      orc_project(p1[i] + sigma * g1[i], p2[i] + sigma * g2[i], p3[i] + sigma * g3[i],
+                  sqrt(G[i]), out);
+      p1[i] = out[0];
+      p2[i] = out[1];
+      p3[i] = out[2];
+    }
+    for (int i = 0; i < n; ++i) u[i] = un[i];
+  }
+  free(dv);
+  free(un);
+  free(ub);
+  free(g1);
+  free(g2);
+  free(g3);
+}
+
+/* Primal energy, Eq. 5: ||L_g u||_g + lambda sum (u - f log u) sqrt(G), with the
+ * g-tensor norm ||A||_g = sum_ij sqrt(G_ij sum_l A_ijl^2).
+ * Dual function of Eq. primal_dual_energy for feasible p (R^* = 0):
+ *   min_{u in box} D(u,f) + <L_g u, p> = sum_ij min_{u in box} [a (u - f log u) - u div_g p],
+ * a = lambda sqrt(G).  The per-pixel minimiser is clamp(a f / (a + w)) with
+ * w = -div_g p when a + w > 0, and u_max otherwise (the objective then decreases). */
+void orc_energy(int W, int H, const double* tx, const double* ty, const double* G,
+                const double* f, const double* u, const double* p1, const double* p2,
+                const double* p3, double lambda, double u_min, double u_max,
+                double* primal, double* dual) {
+  int n = W * H;
+  size_t bytes = sizeof(double) * (size_t)n;
+  if (primal) {
+    double* g1 = (double*)malloc(bytes);
+    double* g2 = (double*)malloc(bytes);
+    double* g3 = (double*)malloc(bytes);
+    orc_Lg(W, H, tx, ty, G, u, g1, g2, g3);
+    double reg = 0.0, dat = 0.0;
+    for (int i = 0; i < n; ++i) {
+      reg += sqrt(G[i] * (g1[i] * g1[i] + g2[i] * g2[i] + g3[i] * g3[i]));
+      double lg = (f[i] == 0.0) ? 0.0 : f[i] * log(u[i]);
+      dat += (u[i] - lg) * sqrt(G[i]);
+    }
+    *primal = reg + lambda * dat;
+    free(g1);
+    free(g2);
+    free(g3);
+  }
+  if (dual) {
+    double* dv = (double*)malloc(bytes);
+    orc_divg(W, H, tx, ty, G, p1, p2, p3, dv);
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double a = lambda * sqrt(G[i]);
+      double w = -dv[i];
+      double us = (a + w > 0.0) ? a * f[i] / (a + w) : u_max;
+      if (us < u_min) us = u_min;
+      if (us > u_max) us = u_max;
+      double lg = (f[i] == 0.0) ? 0.0 : f[i] * log(us);
+      acc += a * (us - lg) + w * us;
+    }
+    *dual = acc;
+    free(dv);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Stream: the state carried from packet to packet. */
+struct orc_stream {
+  int W, H;
+  orc_params prm;
+  int64_t* t_last;  /* surface of active events: most recent timestamp per pixel */
+  int32_t* n_pos;   /* positive events at the pixel since the last solve */
+  int32_t* n_neg;   /* negative events at the pixel since the last solve */
+  int64_t t_ref;    /* stream clock: the latest timestamp seen */
+  int64_t t_init;
+  int have_t_init;
+  double *u, *p1, *p2, *p3, *f;
+  double *tau, *tx, *ty, *G; /* last solve's time surface and metric */
+};
+
+static int prm_valid(const orc_params* p) {
+  if (!(p->lambda > 0.0) || !(p->delta_pos > 0.0) || !(p->delta_neg > 0.0)) return 0;
+  if (!(p->u_min > 0.0) || !(p->u_min < p->u_max)) return 0;
+  if (!(p->u_init > 0.0)) return 0;
+  if (!(p->tau > 0.0) || !(p->sigma > 0.0) || !(p->time_scale >= 0.0)) return 0;
+  if (p->data_mode != 0 && p->data_mode != 1) return 0;
+  return 1;
+}
+
+orc_stream* orc_create(int W, int H, const orc_params* prm) {
+  if (W <= 0 || H <= 0 || W > 65536 || H > 65536 || !prm || !prm_valid(prm)) return NULL;
+  orc_stream* s = (orc_stream*)calloc(1, sizeof(orc_stream));
+  if (!s) return NULL;
+  size_t n = (size_t)W * (size_t)H;
+  s->W = W;
+  s->H = H;
+  s->prm = *prm;
+  s->t_last = (int64_t*)malloc(sizeof(int64_t) * n);
+  s->n_pos = (int32_t*)calloc(n, sizeof(int32_t));
+  s->n_neg = (int32_t*)calloc(n, sizeof(int32_t));
+  double** planes[] = {&s->u, &s->p1, &s->p2, &s->p3, &s->f, &s->tau, &s->tx, &s->ty, &s->G};
+  for (int k = 0; k < 9; ++k) *planes[k] = (double*)calloc(n, sizeof(double));
+  if (!s->t_last || !s->n_pos || !s->n_neg || !s->G) {
+    orc_destroy(s);
+    return NULL;
+  }
+  s->have_t_init = prm->t_init_first ? 0 : 1;
+  s->t_init = prm->t_init_first ? 0 : prm->t_init_us;
+  s->t_ref = s->t_init;
+  for (size_t i = 0; i < n; ++i) {
+    s->t_last[i] = s->t_init;
+    s->u[i] = prm->u_init;
+    s->f[i] = prm->u_init;
+    s->G[i] = 1.0;
+  }
+  return s;
+}
+
+void orc_destroy(orc_stream* s) {
+  if (!s) return;
+  free(s->t_last);
+  free(s->n_pos);
+  free(s->n_neg);
+  free(s->u);
+  free(s->p1);
+  free(s->p2);
+  free(s->p3);
+  free(s->f);
+  free(s->tau);
+  free(s->tx);
+  free(s->ty);
+  free(s->G);
+  free(s);
+}
+
+/* Events e^n = {x^n, y^n, theta^n, t^n}, theta in {-1, 1}, timestamps increasing
+ * (Sec. 3, first paragraph; equal timestamps are accepted).  The surface of active
+ * events records the most recent timestamp of each pixel (Sec. 3.1). */
+int orc_push(orc_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t,
+             const int8_t* pol, size_t n) {
+  if (!s) return ORC_ERR_INVALID_ARG;
+  if (n == 0) return ORC_OK;
+  if (!x || !y || !t || !pol) return ORC_ERR_INVALID_ARG;
+  /* validate the whole packet before touching the state */
+  int have_clock = s->have_t_init;
+  int64_t clock = s->t_ref;
+  for (size_t i = 0; i < n; ++i) {
+    if ((int)x[i] >= s->W || (int)y[i] >= s->H) return ORC_ERR_OUT_OF_RANGE;
+    if (pol[i] == 0) return ORC_ERR_BAD_POLARITY;
+    if (have_clock && t[i] < clock) return ORC_ERR_NONMONOTONIC;
+    have_clock = 1;
+    clock = t[i];
+  }
+  /* commit */
+  if (!s->have_t_init) {
+    s->t_init = t[0];
+    s->t_ref = t[0];
+    s->have_t_init = 1;
+    for (int i = 0; i < s->W * s->H; ++i) s->t_last[i] = s->t_init;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    int k = (int)y[i] * s->W + (int)x[i];
+    if (t[i] > s->t_last[k]) s->t_last[k] = t[i];
+    if (pol[i] > 0)
+      s->n_pos[k] += 1;
+    else
+      s->n_neg[k] += 1;
+    if (t[i] > s->t_ref) s->t_ref = t[i];
+  }
+  return ORC_OK;
+}
+
+int orc_solve(orc_stream* s, int K) {
+  if (!s || K < 0) return ORC_ERR_INVALID_ARG;
+  const orc_params* pr = &s->prm;
+  int n = s->W * s->H;
+  /* time surface: time since the pixel's last event (Sec. 3.1), in manifold units */
+  for (int i = 0; i < n; ++i) {
+    if (!pr->manifold) {
+      s->tau[i] = 0.0; /* t = const switches the manifold off (Sec. 4.2) */
+      continue;
+    }
+    int64_t d = s->t_ref - s->t_last[i];
+    if (pr->t_max_us > 0 && d > pr->t_max_us) d = pr->t_max_us;
+    s->tau[i] = pr->time_scale * (double)d;
+  }
+  orc_metric(s->W, s->H, s->tau, s->tx, s->ty, s->G);
+  /* data image: Eq. intensity_update applied once per event, starting from the
+   * previous reconstruction u^{n-1} (data_mode 0) or the previous f (data_mode 1);
+   * c1 = exp(Delta+), c2 = exp(-Delta-). */
+  double c1 = exp(pr->delta_pos), c2 = exp(-pr->delta_neg);
+  for (int i = 0; i < n; ++i) {
+    double v = (pr->data_mode == 0) ? s->u[i] : s->f[i];
+    for (int e = 0; e < s->n_pos[i]; ++e) v = v * c1;
+    for (int e = 0; e < s->n_neg[i]; ++e) v = v * c2;
+    s->f[i] = v;
+    s->n_pos[i] = 0;
+    s->n_neg[i] = 0;
+  }
+  orc_pd_iterations(s->W, s->H, s->tx, s->ty, s->G, s->f, s->u, s->p1, s->p2, s->p3, K,
+                    pr->tau, pr->sigma, pr->lambda, pr->u_min, pr->u_max);
+  return ORC_OK;
+}
+
+static size_t plane_bytes(const orc_stream* s, int which) {
+  size_t n = (size_t)s->W * (size_t)s->H;
+  switch (which) {
+    case ORC_U: case ORC_P1: case ORC_P2: case ORC_P3: case ORC_F: case ORC_TAU:
+    case ORC_G: case ORC_TX: case ORC_TY:
+      return n * sizeof(double);
+    case ORC_TLAST: return n * sizeof(int64_t);
+    case ORC_NPOS: case ORC_NNEG: return n * sizeof(int32_t);
+    case ORC_TREF: case ORC_TINIT: return sizeof(int64_t);
+    default: return 0;
+  }
+}
+
+static void* plane_ptr(const orc_stream* s, int which) {
+  switch (which) {
+    case ORC_U: return s->u;
+    case ORC_P1: return s->p1;
+    case ORC_P2: return s->p2;
+    case ORC_P3: return s->p3;
+    case ORC_F: return s->f;
+    case ORC_TAU: return s->tau;
+    case ORC_G: return s->G;
+    case ORC_TX: return s->tx;
+    case ORC_TY: return s->ty;
+    case ORC_TLAST: return s->t_last;
+    case ORC_NPOS: return s->n_pos;
+    case ORC_NNEG: return s->n_neg;
+    case ORC_TREF: return (void*)&s->t_ref;
+    case ORC_TINIT: return (void*)&s->t_init;
+    default: return NULL;
+  }
+}
+
+int orc_get(const orc_stream* s, int which, void* out) {
+  if (!s || !out) return ORC_ERR_INVALID_ARG;
+  size_t b = plane_bytes(s, which);
+  if (!b) return ORC_ERR_INVALID_ARG;
+  memcpy(out, plane_ptr(s, which), b);
+  return ORC_OK;
+}
+
+int orc_set(orc_stream* s, int which, const void* in) {
+  if (!s || !in) return ORC_ERR_INVALID_ARG;
+  size_t b = plane_bytes(s, which);
+  if (!b) return ORC_ERR_INVALID_ARG;
+  memcpy(plane_ptr(s, which), in, b);
+  if (which == ORC_TINIT) s->have_t_init = 1;
+  return ORC_OK;
+}
+
+int orc_stream_energy(const orc_stream* s, double* primal, double* dual) {
+  if (!s) return ORC_ERR_INVALID_ARG;
+  orc_energy(s->W, s->H, s->tx, s->ty, s->G, s->f, s->u, s->p1, s->p2, s->p3,
+             s->prm.lambda, s->prm.u_min, s->prm.u_max, primal, dual);
+  return ORC_OK;
+}
