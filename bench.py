@@ -1,0 +1,408 @@
+"""Benchmark of the event-manifold reconstruction hot path on GB300.
+
+A step is one event packet through the whole hot path: event validation and
+scatter, packet prologue (time surface, metric, data image) and K primal-dual
+iterations.  Default workload: 346x260 sensor, seeded scene of 200 Gaussian blobs
+(1 rad/s rotation + 100 px/s), 1M events, 1000-event packets, 50 iterations per
+packet, FP32.  With more steps than packets the stream is replayed with its
+timestamps shifted forward, so every packet stays valid.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Rank 0 prints one JSON line.  Under torchrun each rank solves its own independent
+stream (seed + rank): weak scaling, no data-path collective; the timed region is
+bracketed by a barrier and the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "events/s and Gpixel-iter/s per GB300 at stated error vs FP64; batched vs plain"
+B_ALG = 40  # algorithmic bytes per pixel-iteration, FP32 state (read u,p1,p2,p3,f,t; write u,p)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=980)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="blobs346")
+    ap.add_argument("--cpu-budget-s", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solver", type=int, default=0, help="evr_params.solver")
+    ap.add_argument("--tile", type=int, default=0, help="evr_params.tile_config")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload(name, rank):
+    from evsim import CONFIGS, make_stream
+    cfg = CONFIGS[name]
+    if rank:
+        d = dict(cfg.__dict__)
+        d["seed"] = cfg.seed + 7 * rank
+        cfg = type(cfg)(**d)
+    return cfg, make_stream(cfg)
+
+
+def packet_slices(stream, cfg, n_steps):
+    """(start, stop, time shift) of each step; replays the stream shifted in time."""
+    n_pk = cfg.n_packets
+    span = int(stream.t[-1] - stream.t[0]) + 1
+    for k in range(n_steps):
+        rep, j = divmod(k, n_pk)
+        a = j * cfg.packet
+        yield a, min(a + cfg.packet, len(stream)), rep * span
+
+
+def describe(cfg):
+    return (f"{cfg.name}: {cfg.W}x{cfg.H} sensor, {cfg.kind} scene ({cfg.n_objects} objects), "
+            f"{cfg.n_events} events, {cfg.packet}-event packets, {cfg.iters} iterations")
+
+
+# ----------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
+        mhz = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        if mhz:
+            out["sm_mhz"] = statistics.median(mhz)
+        if mx:
+            out["sm_max_mhz"] = max(mx)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower() == "active":
+                    seen.add(nm)
+        out["reasons"] = sorted(seen)
+        return out
+
+
+# ----------------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("evr_kernels.cu", "evr_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1607_06283_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(solver_name):
+    """DRAM bytes per launch of the iteration kernel from the committed ncu summary,
+    if it was taken on the current kernel source and the same tile shape; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    ent = d.get(solver_name)
+    if not ent or ent.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch_full_size")
+
+
+def cpu_baseline(cfg, stream, budget_s, max_packets=None):
+    """The FP64 oracle, as it stands, on this host's cores: packets of the same stream
+    until the time budget is spent."""
+    from oracle import oracle as O
+    o = O.OracleStream(cfg.W, cfg.H)
+    t0 = time.perf_counter()
+    done = ev = 0
+    while True:
+        a = done * cfg.packet
+        if a >= len(stream) or (max_packets and done >= max_packets):
+            break
+        b = min(a + cfg.packet, len(stream))
+        o.push(stream.x[a:b], stream.y[a:b], stream.t[a:b], stream.pol[a:b])
+        o.solve(cfg.iters)
+        done += 1
+        ev += b - a
+        if time.perf_counter() - t0 > budget_s and done >= 3:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": ev / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "gpix_iter_per_s": done * cfg.W * cfg.H * cfg.iters / dt / 1e9,
+            "sample": f"first {done} packets ({ev} events) of the same stream, FP64, "
+                      f"single thread, {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    cfg, stream = workload(args.config, 0)
+    from oracle import oracle as O
+    o = O.OracleStream(cfg.W, cfg.H)
+    steps = list(packet_slices(stream, cfg, args.warmup + args.steps))
+    for a, b, sh in steps[:args.warmup]:
+        o.push(stream.x[a:b], stream.y[a:b], stream.t[a:b] + sh, stream.pol[a:b])
+        o.solve(cfg.iters)
+    budget = 150.0
+    t0 = time.perf_counter()
+    done = ev = 0
+    for a, b, sh in steps[args.warmup:]:
+        o.push(stream.x[a:b], stream.y[a:b], stream.t[a:b] + sh, stream.pol[a:b])
+        o.solve(cfg.iters)
+        done += 1
+        ev += b - a
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    v = ev / dt
+    sample = (f"{done} of {args.steps} timed packets (time budget {budget:.0f} s), "
+              f"after {args.warmup} warm-up packets; FP64 oracle, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "events/s",
+            "n_gpus": 1, "steps": done, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / max(1, done), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "gpix_iter_per_s": done * cfg.W * cfg.H * cfg.iters / dt / 1e9,
+            "config": {"workload": describe(cfg), "sensor": f"{cfg.W}x{cfg.H}",
+                       "packet": cfg.packet, "iters": cfg.iters},
+            "cpu_baseline": {"value": v, "unit": "events/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}), flush=True)
+        return 1
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    from paper_1607_06283_gb300 import build
+    if rank == 0:
+        build.build()
+    if pg:
+        pg.barrier()
+    from paper_1607_06283_gb300 import evr as E
+
+    cfg, stream = workload(args.config, rank)
+    cur = torch.cuda.current_stream()
+    p = E.evr_default_params()
+    p.solver = args.solver
+    p.tile_config = args.tile
+    g = E.Stream(cfg.W, cfg.H, p)
+    E.evr_set_cuda_stream(g.h, cur.cuda_stream)
+
+    n_all = args.warmup + args.steps
+    steps = list(packet_slices(stream, cfg, n_all))
+    # device-resident inputs: the whole (time-shifted) event sequence of the run
+    t_all = np.concatenate([stream.t[a:b] + sh for a, b, sh in steps])
+    idx = np.concatenate([np.arange(a, b) for a, b, _ in steps])
+    dx = torch.from_numpy(stream.x[idx].view(np.int16)).cuda()
+    dy = torch.from_numpy(stream.y[idx].view(np.int16)).cuda()
+    dt_ = torch.from_numpy(t_all).cuda()
+    dp = torch.from_numpy(stream.pol[idx]).cuda()
+    offs = np.concatenate([[0], np.cumsum([b - a for a, b, _ in steps])])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(k):
+        s, e = int(offs[k]), int(offs[k + 1])
+        rc = g.push_device(dx[s:e], dy[s:e], dt_[s:e], dp[s:e])
+        if rc:
+            raise RuntimeError(f"push failed: {rc}")
+        g.solve(cfg.iters)
+
+    for k in range(args.warmup):
+        step(k)
+    assert g.synchronize() == 0
+    torch.cuda.synchronize()
+
+    clk = ClockSampler(local)
+    if rank == 0:
+        clk.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    E.evr_enable_kernel_timing(g.h, True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for j in range(args.steps):
+        flush.fill_(float(j))  # L2 flush between timed steps (outside the events)
+        evs[j][0].record(cur)
+        step(args.warmup + j)
+        evs[j][1].record(cur)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if pg:
+        pg.barrier()
+    clocks = clk.stop() if rank == 0 else None
+    ms_steps = sum(a.elapsed_time(b) for a, b in evs)
+    k_ms, k_launches, k_pixiters = E.evr_kernel_time(g.h)
+    E.evr_enable_kernel_timing(g.h, False)
+    status = g.synchronize()
+    if status:
+        raise RuntimeError(f"device-side rejection during the run: {status}")
+    ev_timed = int(offs[n_all] - offs[args.warmup])
+    t_max = ms_steps
+    if pg:
+        tt = torch.tensor([ms_steps], dtype=torch.float64, device="cuda")
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_max = float(tt.item())
+        ev_t = torch.tensor([ev_timed], dtype=torch.float64, device="cuda")
+        pg.all_reduce(ev_t)
+        ev_total = float(ev_t.item())
+    else:
+        ev_total = float(ev_timed)
+    value = ev_total / (t_max * 1e-3)
+    gpix = world * args.steps * cfg.W * cfg.H * cfg.iters / (t_max * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers (same number of steps)
+    g2 = E.Stream(cfg.W, cfg.H, p)
+    E.evr_set_cuda_stream(g2.h, cur.cuda_stream)
+    img = np.empty((cfg.H, cfg.W), np.float32)
+    hx = stream.x[idx]
+    hy = stream.y[idx]
+    hp = stream.pol[idx]
+
+    def step_host(k):
+        s, e = int(offs[k]), int(offs[k + 1])
+        rc = E.evr_push_events(g2.h, hx[s:e], hy[s:e], t_all[s:e], hp[s:e])
+        if rc:
+            raise RuntimeError(f"push failed: {rc}")
+        E.evr_solve(g2.h, cfg.iters)
+        rc = E.evr_get_image(g2.h, img)
+        if rc:
+            raise RuntimeError(f"get_image: {rc}")
+
+    for k in range(args.warmup):
+        step_host(k)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for j in range(args.steps):
+        step_host(args.warmup + j)
+    e2e_s = time.perf_counter() - e0
+    if pg:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_val = ev_total / e2e_s
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        avg_launch_ms = k_ms / max(1, k_launches)
+        px_per_launch = k_pixiters / max(1, k_launches)
+        achieved = B_ALG * px_per_launch / (avg_launch_ms * 1e-3) / 1e9
+        launches_per_step = 2 + k_launches / args.steps  # push + prologue + iteration kernels
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "gpix_iter_per_s": gpix,
+            "config": {"workload": describe(cfg), "sensor": f"{cfg.W}x{cfg.H}",
+                       "events_per_step": cfg.packet, "iters": cfg.iters,
+                       "solver": g.solver_name, "parallelism": f"{world} independent streams",
+                       "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                       "inputs": "device-resident event arrays (evr_push_events_device)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_traffic(g.solver_name),
+                         "kernel": "iteration kernels (" + g.solver_name + ")",
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "avg_launch_us": avg_launch_ms * 1e3,
+                         "bytes_per_launch": B_ALG * px_per_launch},
+            "e2e": {"value": e2e_val, "unit": "events/s",
+                    "h2d_bytes_per_step": cfg.packet * (2 + 2 + 8 + 1),
+                    "d2h_bytes_per_step": cfg.W * cfg.H * 4},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clocks,
+            "wall_s_timed": wall,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(cfg, stream, args.cpu_budget_s)
+        print(json.dumps(line), flush=True)
+    g.close()
+    g2.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

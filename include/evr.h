@@ -1,0 +1,183 @@
+/*
+ * evr.h -- C ABI of the GB300 event-camera intensity-reconstruction library.
+ *
+ * Method: Reinbacher, Graber, Pock, "Real-Time Intensity-Image Reconstruction for
+ * Event Cameras Using Manifold Regularisation", BMVC 2016 (arXiv:1607.06283).
+ * A stream of events e^n = (x^n, y^n, theta^n, t^n) (Sec. 3) is integrated packet
+ * by packet into the surface of active events t(x,y) (Sec. 3.1) and the data image
+ * f (Eq. intensity_update); each packet then runs warm-started primal-dual
+ * iterations (Eq. cont_iterates, Eq. update_rules) minimising the generalised
+ * Kullback-Leibler data term plus total variation on the event manifold (Eq. 5).
+ *
+ * Conventions
+ *  - Every function returns EVR_OK (0) or a negative EVR_ERR_* code, except
+ *    evr_destroy and evr_strerror.
+ *  - Images are W x H, row-major, index y*W + x with x the column (0 <= x < W) and
+ *    y the row.  Host buffers passed in or out are dense (no padding).
+ *  - The library owns all device state.  Input arrays belong to the caller and may
+ *    be reused as soon as the call returns (host pointers) or as soon as the work
+ *    queued on the handle's CUDA stream has consumed them (device pointers).
+ *  - Work is queued on the handle's CUDA stream (its own stream unless
+ *    evr_set_cuda_stream chose another).  Calls that return data to the host
+ *    synchronise that stream.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - All computation runs in CUDA kernels for sm_103a; there is no CPU fallback.
+ */
+#ifndef EVR_H
+#define EVR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define EVR_OK 0
+#define EVR_ERR_INVALID_ARG (-1)   /* null pointer, bad size, bad parameter */
+#define EVR_ERR_OUT_OF_RANGE (-2)  /* an event with x >= W or y >= H */
+#define EVR_ERR_BAD_POLARITY (-3)  /* an event with polarity 0 (Sec. 3: theta in {-1, 1}) */
+#define EVR_ERR_NONMONOTONIC (-4)  /* a timestamp below its predecessor or the stream clock
+                                      (Sec. 3: timestamps increase; equal ones are accepted) */
+#define EVR_ERR_OOM (-5)           /* device or pinned host allocation failed */
+#define EVR_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+#define EVR_ERR_TIMEOUT (-7)       /* reserved: a bounded device-side wait expired */
+#define EVR_ERR_NOT_SUPPORTED (-8) /* no usable sm_103a device, or option not built */
+
+/* t_init_us value meaning "never-fired pixels take the first pushed timestamp". */
+#define EVR_T_INIT_FIRST INT64_MIN
+
+/* Solver variants (evr_params.solver). */
+#define EVR_SOLVER_AUTO 0      /* pick the tiled solver, tile shape from the autotuner */
+#define EVR_SOLVER_UNFUSED 1   /* two kernels per iteration (primal step, dual step) */
+#define EVR_SOLVER_TILED 2     /* temporally blocked tiles, several iterations per launch */
+
+/* Model and solver parameters.  evr_default_params fills the defaults listed. */
+typedef struct {
+  float lambda;       /* data weight lambda of Eq. 5; default 90 */
+  float delta_pos;    /* Delta+: log step of a positive event (Sec. 3); default 0.15 */
+  float delta_neg;    /* Delta-: log step of a negative event (Sec. 3); default 0.15 */
+  float u_min;        /* box of Eq. data_term; default exp(-3) */
+  float u_max;        /* default exp(3) */
+  float u_init;       /* u^0 (unknown in the paper, Sec. 3); default 1 */
+  float tau;          /* primal step (Sec. 3.2, tau sigma ||L_g||^2 <= 1 with ||L_g||^2 <=
+                         8 + 4 sqrt 2); default (8 + 4 sqrt 2)^-1/2 */
+  float sigma;        /* dual step; default (8 + 4 sqrt 2)^-1/2 */
+  float time_scale;   /* manifold height per microsecond of time since the last event;
+                         default 1e-3 (milliseconds) */
+  int64_t t_max_us;   /* clamp of the time since the last event; <= 0 disables;
+                         default 100000 */
+  int64_t t_init_us;  /* timestamp of never-fired pixels; default EVR_T_INIT_FIRST */
+  int data_mode;      /* 0: f = previous image stepped at event pixels (default);
+                         1: f persists between packets, stepped at event pixels */
+  int manifold;       /* 1: t from the events (default); 0: t = const (Sec. 4.2) */
+  int solver;         /* EVR_SOLVER_*; default EVR_SOLVER_AUTO */
+  int tile_config;    /* tiled solver shape index (0 = let the autotuner choose) */
+} evr_params;
+
+typedef struct evr_stream evr_stream; /* opaque handle */
+
+/* Fill *out with the defaults above.  Errors: EVR_ERR_INVALID_ARG if out is NULL. */
+int evr_default_params(evr_params* out);
+
+/* Create a stream for a W x H sensor (1 <= W, H <= 65536) on the current CUDA
+ * device and allocate its device state: u = u_init, p = 0, no events.
+ * Errors: EVR_ERR_INVALID_ARG (null pointers, bad size, lambda <= 0, Delta <= 0,
+ * u_min <= 0, u_min >= u_max, u_init outside [u_min, u_max], tau or sigma <= 0,
+ * tau sigma (8 + 4 sqrt 2) > 1 + 1e-6, time_scale < 0, bad mode or solver),
+ * EVR_ERR_NOT_SUPPORTED (no sm_103a device), EVR_ERR_OOM, EVR_ERR_CUDA.
+ * On error *out is set to NULL. */
+int evr_create(int W, int H, const evr_params* params, evr_stream** out);
+
+/* Release the device state (synchronises the handle's stream).  NULL is a no-op. */
+void evr_destroy(evr_stream* s);
+
+/* Queue the handle's work on an existing cudaStream_t (NULL: the library's own
+ * stream).  The library does not take ownership. */
+int evr_set_cuda_stream(evr_stream* s, void* cuda_stream);
+
+/* Integrate one packet of n events (Sec. 3 and 3.1): for each event
+ * t_last(x,y) = max(t_last(x,y), t), n+(x,y) or n-(x,y) += 1, clock = max(clock, t).
+ * Host arrays, structure of arrays: x[n], y[n] (uint16), t_us[n] (int64,
+ * microseconds, non-decreasing and not below the stream clock), pol[n] (int8,
+ * > 0 positive, < 0 negative, 0 invalid).  The whole packet is validated before any
+ * state changes; a rejected packet changes nothing and the code is that of its
+ * first invalid event (checked in the order range, polarity, time).  The host
+ * checks what it can at once and returns the code; the device repeats the full
+ * check.  n = 0 is a no-op.  The arrays are copied before the call returns. */
+int evr_push_events(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
+                    const int8_t* pol, size_t n);
+
+/* As evr_push_events, with device pointers; validation runs on the device only, and
+ * a rejection is reported by the next call that synchronises (evr_synchronize,
+ * evr_get_image, evr_get_state, evr_gap).  The arrays must stay valid until the
+ * queued work has run. */
+int evr_push_events_device(evr_stream* s, const uint16_t* x, const uint16_t* y,
+                           const int64_t* t_us, const int8_t* pol, size_t n);
+
+/* Solve the current packet: time surface t = time_scale * min(clock - t_last, t_max)
+ * (Sec. 3.1), metric (Eq. 2, Eq. 3), data image f (Eq. intensity_update, one factor
+ * c1 = exp(Delta+) or c2 = exp(-Delta-) per event, compounded), reset of the event
+ * counts, then `iters` primal-dual iterations (Eq. cont_iterates with Eq.
+ * update_rules) warm-started from the previous (u, p).  Asynchronous.
+ * Errors: EVR_ERR_INVALID_ARG (iters < 0), EVR_ERR_CUDA. */
+int evr_solve(evr_stream* s, int iters);
+
+/* Copy the current image u (W*H floats, row-major) to host memory; synchronises.
+ * len is the capacity of out_host in floats and must be >= W*H.  Returns the first
+ * pending device-side rejection, if any, else EVR_OK. */
+int evr_get_image(evr_stream* s, float* out_host, size_t len);
+
+/* Copy the current image into device memory out_dev (W*H floats, dense row-major);
+ * asynchronous, on the handle's stream. */
+int evr_get_image_device(evr_stream* s, float* out_dev, size_t len);
+
+/* State planes for tests and checkpoints (dense row-major, W*H elements). */
+#define EVR_STATE_U 0       /* float */
+#define EVR_STATE_P1 1      /* float, dual variable p, component 1 */
+#define EVR_STATE_P2 2      /* float */
+#define EVR_STATE_P3 3      /* float */
+#define EVR_STATE_F 4       /* float, data image of the last solve */
+#define EVR_STATE_TLAST 5   /* int64, never-fired pixels report t_init */
+#define EVR_STATE_NPOS 6    /* int32, positive events since the last solve */
+#define EVR_STATE_NNEG 7    /* int32 */
+#define EVR_STATE_CLOCK 8   /* int64[1], latest timestamp */
+#define EVR_STATE_TINIT 9   /* int64[1], timestamp of never-fired pixels (0 if unset) */
+#define EVR_STATE_SQRTG 10  /* float, sqrt(G) of the last solve */
+
+/* Copy a state plane to host memory (bytes = its exact size); synchronises.
+ * Returns the first pending device-side rejection, if any. */
+int evr_get_state(evr_stream* s, int which, void* out_host, size_t bytes);
+
+/* Overwrite a state plane from host memory (u, p1, p2, p3 only; bytes = W*H*4).
+ * Used to restore checkpoints.  Synchronises. */
+int evr_set_state(evr_stream* s, int which, const void* in_host, size_t bytes);
+
+/* Primal energy of Eq. 5 and the dual value of the saddle form (Eq.
+ * primal_dual_energy) of the current (u, p) under the last solve's metric and f,
+ * reduced on the device in FP64 (fixed reduction order: deterministic).  The gap
+ * primal - dual >= 0 is the convergence check.  Synchronises. */
+int evr_gap(evr_stream* s, double* primal, double* dual);
+
+/* Wait for the handle's queued work; returns the first pending device-side
+ * rejection (then clears it), EVR_ERR_CUDA, or EVR_OK. */
+int evr_synchronize(evr_stream* s);
+
+/* Kernel timing with CUDA events on the handle's stream around each solve's
+ * iteration kernels (enable = 1 starts and clears, 0 stops).  evr_kernel_time
+ * synchronises and reports the total milliseconds, the number of iteration-kernel
+ * launches and the pixel-iterations they performed since timing was enabled. */
+int evr_enable_kernel_timing(evr_stream* s, int enable);
+int evr_kernel_time(evr_stream* s, double* ms, int64_t* launches, int64_t* pixel_iters);
+
+/* Description of the solver in use, e.g. "tiled 32x32 R4"; static storage. */
+const char* evr_solver_name(evr_stream* s);
+
+/* Static description of a return code. */
+const char* evr_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,659 @@
+// evr_api.cu -- host runtime and C ABI (include/evr.h).
+//
+// The host side validates arguments, stages host events through pinned memory,
+// owns the device state, captures each packet's iteration launches into a CUDA
+// graph (one per iteration count and buffer parity), picks the tile shape of the
+// tiled solver by timing the candidates on the actual sensor, and reads results
+// back.  Every step of the reconstruction itself runs in evr_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "../../include/evr.h"
+#include "evr_internal.cuh"
+
+using namespace evr;
+
+namespace {
+
+constexpr int kStageSlots = 2;
+constexpr int kMaxTimingPairs = 8192;
+
+struct StageSlot {
+  size_t cap = 0;
+  uint16_t* hx = nullptr;
+  uint16_t* hy = nullptr;
+  long long* ht = nullptr;
+  int8_t* hp = nullptr;
+  cudaEvent_t done = nullptr;  // recorded after the slot's host-to-device copy
+  bool pending = false;
+};
+
+struct GraphKey {
+  int iters, cur;
+  bool operator<(const GraphKey& o) const {
+    return iters != o.iters ? iters < o.iters : cur < o.cur;
+  }
+};
+
+}  // namespace
+
+struct evr_stream {
+  int W = 0, H = 0, pitch = 0, device = 0;
+  evr_params prm{};
+  Planes P{};
+  void* dev_base = nullptr;
+  cudaStream_t stream = nullptr;      // where work is queued
+  cudaStream_t own_stream = nullptr;  // the library's stream
+  cudaStream_t cap_stream = nullptr;  // graph capture
+  int cur = 0;                        // buffer holding the current (u, p)
+  int shape = -1;                     // tiled solver shape, -1 = unfused
+  bool tuned = false;
+  // host-to-device event staging
+  StageSlot slot[kStageSlots];
+  int next_slot = 0;
+  size_t dcap = 0;
+  uint16_t* dx = nullptr;
+  uint16_t* dy = nullptr;
+  long long* dt = nullptr;
+  int8_t* dp = nullptr;
+  // host mirror of the stream clock for immediate checks
+  long long h_clock = 0;
+  bool h_have_clock = false;
+  bool h_clock_valid = true;
+  // results
+  double* d_gap = nullptr;   // 2 doubles on the device
+  double* h_gap = nullptr;   // pinned
+  DevScalars* h_sc = nullptr;  // pinned
+  // graphs of the per-packet iteration launches
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  // kernel timing
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free, ev_used;
+  std::vector<int> ev_launches;
+  std::vector<long long> ev_pixiters;
+  double t_ms = 0.0;
+  long long t_launches = 0, t_pixiters = 0;
+  char name[64] = {0};
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? EVR_OK : EVR_ERR_CUDA; }
+
+SolveConsts solve_consts(const evr_stream* s) {
+  return SolveConsts{s->prm.tau, s->prm.sigma, s->prm.lambda, s->prm.u_min, s->prm.u_max};
+}
+
+PrologueConsts prologue_consts(const evr_stream* s) {
+  return PrologueConsts{s->prm.time_scale, s->prm.delta_pos, s->prm.delta_neg,
+                        (long long)s->prm.t_max_us, s->prm.manifold, s->prm.data_mode};
+}
+
+int params_valid(const evr_params* p) {
+  if (!(p->lambda > 0.f) || !(p->delta_pos > 0.f) || !(p->delta_neg > 0.f)) return 0;
+  if (!(p->u_min > 0.f) || !(p->u_min < p->u_max)) return 0;
+  if (!(p->u_init >= p->u_min && p->u_init <= p->u_max)) return 0;
+  if (!(p->tau > 0.f) || !(p->sigma > 0.f)) return 0;
+  double bound = (double)p->tau * (double)p->sigma * (8.0 + 4.0 * std::sqrt(2.0));
+  if (bound > 1.0 + 1e-6) return 0;
+  if (!(p->time_scale >= 0.f) || !std::isfinite(p->time_scale)) return 0;
+  if (p->data_mode != 0 && p->data_mode != 1) return 0;
+  if (p->manifold != 0 && p->manifold != 1) return 0;
+  if (p->solver < 0 || p->solver > EVR_SOLVER_TILED) return 0;
+  if (p->tile_config < 0 || p->tile_config > kNumTileShapes) return 0;
+  return 1;
+}
+
+void set_name(evr_stream* s) {
+  if (s->shape < 0) {
+    std::snprintf(s->name, sizeof(s->name), "unfused");
+  } else {
+    const TileShape& t = kTileShapes[s->shape];
+    std::snprintf(s->name, sizeof(s->name), "tiled %dx%d R%d (%d threads)", t.EW, t.EH, t.R,
+                  32 * t.NTY);
+  }
+}
+
+void free_stage(evr_stream* s) {
+  for (auto& sl : s->slot) {
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.hx) cudaFreeHost(sl.hx);
+    sl = StageSlot{};
+  }
+  if (s->dx) cudaFree(s->dx);
+  s->dx = nullptr;
+  s->dy = nullptr;
+  s->dt = nullptr;
+  s->dp = nullptr;
+  s->dcap = 0;
+}
+
+// Grow the pinned slot and the device staging buffer to hold n events.
+int ensure_stage(evr_stream* s, StageSlot& sl, size_t n) {
+  if (sl.cap < n) {
+    if (sl.done) cudaEventSynchronize(sl.done);
+    if (sl.hx) cudaFreeHost(sl.hx);
+    size_t cap = ((n < 4096 ? 4096 : n + n / 2) + 63) / 64 * 64;
+    char* h = nullptr;
+    if (cudaMallocHost((void**)&h, cap * (2 + 2 + 8 + 1)) != cudaSuccess) {
+      sl.hx = nullptr;
+      sl.cap = 0;
+      return EVR_ERR_OOM;
+    }
+    // one allocation: x | y | t | pol (hx is the base pointer)
+    sl.hx = (uint16_t*)h;
+    sl.hy = (uint16_t*)(h + cap * 2);
+    sl.ht = (long long*)(h + cap * 4);
+    sl.hp = (int8_t*)(h + cap * 12);
+    sl.cap = cap;
+    if (!sl.done && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
+      return EVR_ERR_CUDA;
+  }
+  if (s->dcap < n) {
+    if (s->dx) {
+      cudaStreamSynchronize(s->stream);
+      cudaFree(s->dx);
+    }
+    size_t cap = ((n < 4096 ? 4096 : n + n / 2) + 63) / 64 * 64;
+    char* d = nullptr;
+    if (cudaMalloc((void**)&d, cap * (2 + 2 + 8 + 1)) != cudaSuccess) {
+      s->dx = nullptr;
+      s->dcap = 0;
+      return EVR_ERR_OOM;
+    }
+    s->dx = (uint16_t*)d;
+    s->dy = (uint16_t*)(d + cap * 2);
+    s->dt = (long long*)(d + cap * 4);
+    s->dp = (int8_t*)(d + cap * 12);
+    s->dcap = cap;
+  }
+  return EVR_OK;
+}
+
+void drop_graphs(evr_stream* s) {
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  s->graphs.clear();
+}
+
+// The iteration launches of one packet: `iters` iterations from buffer `cur`.
+// Returns the buffer that holds the result.
+int enqueue_iterations(evr_stream* s, int iters, int cur, cudaStream_t st, int* launches) {
+  SolveConsts c = solve_consts(s);
+  *launches = 0;
+  if (s->shape < 0) {
+    for (int k = 0; k < iters; ++k) {
+      if (launch_unfused_iteration(s->P, cur, c, st)) return -1;
+      *launches += 2;
+    }
+    return cur;
+  }
+  const int R = kTileShapes[s->shape].R;
+  for (int done = 0; done < iters; done += R) {
+    int it = iters - done < R ? iters - done : R;
+    if (launch_tiled_pass(s->P, s->shape, cur, it, c, st)) return -1;
+    cur = 1 - cur;
+    *launches += 1;
+  }
+  return cur;
+}
+
+// Time each tile shape on this sensor (reads buffer cur, writes the other one,
+// which holds no live state) and keep the fastest per iteration.
+void autotune(evr_stream* s) {
+  SolveConsts c = solve_consts(s);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_shape = 1;
+  for (int sh = 0; sh < kNumTileShapes; ++sh) {
+    const int R = kTileShapes[sh].R;
+    const int reps = 12;
+    for (int w = 0; w < 2; ++w) launch_tiled_pass(s->P, sh, s->cur, R, c, s->stream);
+    cudaEventRecord(e0, s->stream);
+    for (int r = 0; r < reps; ++r) launch_tiled_pass(s->P, sh, s->cur, R, c, s->stream);
+    cudaEventRecord(e1, s->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    float per_iter = ms / (reps * R);
+    if (cudaGetLastError() == cudaSuccess && per_iter < best) {
+      best = per_iter;
+      best_shape = sh;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->shape = best_shape;
+}
+
+int refresh_scalars(evr_stream* s) {
+  cudaError_t e = cudaMemcpyAsync(s->h_sc, s->P.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                                  s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return EVR_ERR_CUDA;
+  s->h_clock = s->h_sc->clock;
+  s->h_have_clock = s->h_sc->t_init_set != 0;
+  s->h_clock_valid = true;
+  return EVR_OK;
+}
+
+// Synchronise, then report (and clear) the first pending device-side rejection.
+int sync_status(evr_stream* s) {
+  int rc = refresh_scalars(s);
+  if (rc) return rc;
+  int st = s->h_sc->status;
+  if (st != 0) {
+    if (cudaMemsetAsync(&s->P.sc->status, 0, sizeof(int), s->stream) != cudaSuccess)
+      return EVR_ERR_CUDA;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return EVR_ERR_CUDA;
+    return st;
+  }
+  return EVR_OK;
+}
+
+void resolve_timing(evr_stream* s) {
+  for (size_t k = 0; k < s->ev_used.size(); ++k) {
+    cudaEventSynchronize(s->ev_used[k].second);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s->ev_used[k].first, s->ev_used[k].second);
+    s->t_ms += ms;
+    s->t_launches += s->ev_launches[k];
+    s->t_pixiters += s->ev_pixiters[k];
+    s->ev_free.push_back(s->ev_used[k]);
+  }
+  s->ev_used.clear();
+  s->ev_launches.clear();
+  s->ev_pixiters.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+int evr_default_params(evr_params* out) {
+  if (!out) return EVR_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->lambda = 90.0f;
+  out->delta_pos = 0.15f;
+  out->delta_neg = 0.15f;
+  out->u_min = (float)std::exp(-3.0);
+  out->u_max = (float)std::exp(3.0);
+  out->u_init = 1.0f;
+  out->tau = (float)(1.0 / std::sqrt(8.0 + 4.0 * std::sqrt(2.0)));
+  out->sigma = out->tau;
+  out->time_scale = 1e-3f;
+  out->t_max_us = 100000;
+  out->t_init_us = EVR_T_INIT_FIRST;
+  out->data_mode = 0;
+  out->manifold = 1;
+  out->solver = EVR_SOLVER_AUTO;
+  out->tile_config = 0;
+  return EVR_OK;
+}
+
+int evr_create(int W, int H, const evr_params* params, evr_stream** out) {
+  if (!out) return EVR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!params || W <= 0 || H <= 0 || W > 65536 || H > 65536) return EVR_ERR_INVALID_ARG;
+  if (!params_valid(params)) return EVR_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return EVR_ERR_NOT_SUPPORTED;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return EVR_ERR_NOT_SUPPORTED;
+  if (!(prop.major == 10 && prop.minor == 3)) return EVR_ERR_NOT_SUPPORTED;
+  evr_stream* s = new (std::nothrow) evr_stream();
+  if (!s) return EVR_ERR_OOM;
+  s->W = W;
+  s->H = H;
+  s->device = dev;
+  s->prm = *params;
+  s->pitch = (W + 31) / 32 * 32;
+  const size_t plane = (size_t)s->pitch * H;
+  // float planes: u[2], p1[2], p2[2], p3[2], ubar, f, tx, ty, iG, sG = 14
+  // int64: t_last; int32: npos, nneg; scalars; gap partials
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t fb = al(plane * 4), lb = al(plane * 8);
+  const size_t total = 14 * fb + lb + 2 * fb + al(sizeof(DevScalars)) +
+                       al(sizeof(double) * 3 * kGapBlocks) + al(sizeof(double) * 2);
+  char* base = nullptr;
+  if (cudaMalloc((void**)&base, total) != cudaSuccess) {
+    delete s;
+    return EVR_ERR_OOM;
+  }
+  s->dev_base = base;
+  char* q = base;
+  auto take = [&](size_t b) {
+    char* r = q;
+    q += b;
+    return r;
+  };
+  Planes& P = s->P;
+  P.W = W;
+  P.H = H;
+  P.pitch = s->pitch;
+  for (int b = 0; b < 2; ++b) {
+    P.u[b] = (float*)take(fb);
+    P.p1[b] = (float*)take(fb);
+    P.p2[b] = (float*)take(fb);
+    P.p3[b] = (float*)take(fb);
+  }
+  P.ubar = (float*)take(fb);
+  P.f = (float*)take(fb);
+  P.tx = (float*)take(fb);
+  P.ty = (float*)take(fb);
+  P.iG = (float*)take(fb);
+  P.sG = (float*)take(fb);
+  P.t_last = (long long*)take(lb);
+  P.npos = (int*)take(fb);
+  P.nneg = (int*)take(fb);
+  P.sc = (DevScalars*)take(al(sizeof(DevScalars)));
+  P.partials = (double*)take(al(sizeof(double) * 3 * kGapBlocks));
+  s->d_gap = (double*)take(al(sizeof(double) * 2));
+  int rc = EVR_OK;
+  if (cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void**)&s->h_gap, sizeof(double) * 2) != cudaSuccess ||
+      cudaMallocHost((void**)&s->h_sc, sizeof(DevScalars)) != cudaSuccess)
+    rc = EVR_ERR_CUDA;
+  s->stream = s->own_stream;
+  const bool first = params->t_init_us == EVR_T_INIT_FIRST;
+  const long long t0 = first ? 0 : (long long)params->t_init_us;
+  if (!rc && launch_init(P, params->u_init, t0, t0, first ? 0 : 1, s->stream)) rc = EVR_ERR_CUDA;
+  if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = EVR_ERR_CUDA;
+  if (rc) {
+    evr_destroy(s);
+    return rc;
+  }
+  s->h_clock = t0;
+  s->h_have_clock = !first;
+  s->h_clock_valid = true;
+  if (params->solver == EVR_SOLVER_UNFUSED) {
+    s->shape = -1;
+    s->tuned = true;
+  } else if (params->tile_config > 0) {
+    s->shape = params->tile_config - 1;
+    s->tuned = true;
+  }
+  set_name(s);
+  *out = s;
+  return EVR_OK;
+}
+
+void evr_destroy(evr_stream* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  drop_graphs(s);
+  resolve_timing(s);
+  for (auto& e : s->ev_free) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  free_stage(s);
+  if (s->h_gap) cudaFreeHost(s->h_gap);
+  if (s->h_sc) cudaFreeHost(s->h_sc);
+  if (s->own_stream) cudaStreamDestroy(s->own_stream);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->dev_base) cudaFree(s->dev_base);
+  delete s;
+}
+
+int evr_set_cuda_stream(evr_stream* s, void* cuda_stream) {
+  if (!s) return EVR_ERR_INVALID_ARG;
+  cudaStream_t ns = cuda_stream ? (cudaStream_t)cuda_stream : s->own_stream;
+  if (ns != s->stream) {
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return EVR_ERR_CUDA;
+    s->stream = ns;
+  }
+  return EVR_OK;
+}
+
+int evr_push_events(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
+                    const int8_t* pol, size_t n) {
+  if (!s) return EVR_ERR_INVALID_ARG;
+  if (n == 0) return EVR_OK;
+  if (!x || !y || !t_us || !pol || n > (size_t)INT_MAX) return EVR_ERR_INVALID_ARG;
+  // immediate checks on the host, in the order the device applies them
+  long long clock = s->h_clock;
+  bool have = s->h_have_clock && s->h_clock_valid;
+  for (size_t i = 0; i < n; ++i) {
+    if ((int)x[i] >= s->W || (int)y[i] >= s->H) return EVR_ERR_OUT_OF_RANGE;
+    if (pol[i] == 0) return EVR_ERR_BAD_POLARITY;
+    if (have && (long long)t_us[i] < clock) return EVR_ERR_NONMONOTONIC;
+    have = true;
+    clock = (long long)t_us[i];
+  }
+  StageSlot& sl = s->slot[s->next_slot];
+  s->next_slot = (s->next_slot + 1) % kStageSlots;
+  if (sl.pending) {
+    if (cudaEventSynchronize(sl.done) != cudaSuccess) return EVR_ERR_CUDA;
+    sl.pending = false;
+  }
+  int rc = ensure_stage(s, sl, n);
+  if (rc) return rc;
+  std::memcpy(sl.hx, x, n * 2);
+  std::memcpy(sl.hy, y, n * 2);
+  std::memcpy(sl.ht, t_us, n * 8);
+  std::memcpy(sl.hp, pol, n);
+  cudaStream_t st = s->stream;
+  cudaError_t e = cudaMemcpyAsync(s->dx, sl.hx, n * 2, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->dy, sl.hy, n * 2, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->dt, sl.ht, n * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->dp, sl.hp, n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(sl.done, st);
+  if (e != cudaSuccess) return EVR_ERR_CUDA;
+  sl.pending = true;
+  if (launch_push(s->P, s->dx, s->dy, s->dt, s->dp, (int)n, st)) return EVR_ERR_CUDA;
+  if (s->h_clock_valid) {
+    s->h_clock = clock;
+    s->h_have_clock = true;
+  }
+  return EVR_OK;
+}
+
+int evr_push_events_device(evr_stream* s, const uint16_t* x, const uint16_t* y,
+                           const int64_t* t_us, const int8_t* pol, size_t n) {
+  if (!s) return EVR_ERR_INVALID_ARG;
+  if (n == 0) return EVR_OK;
+  if (!x || !y || !t_us || !pol || n > (size_t)INT_MAX) return EVR_ERR_INVALID_ARG;
+  if (launch_push(s->P, x, y, (const long long*)t_us, pol, (int)n, s->stream))
+    return EVR_ERR_CUDA;
+  s->h_clock_valid = false;
+  return EVR_OK;
+}
+
+int evr_solve(evr_stream* s, int iters) {
+  if (!s || iters < 0) return EVR_ERR_INVALID_ARG;
+  cudaStream_t st = s->stream;
+  if (launch_prologue(s->P, s->cur, prologue_consts(s), st)) return EVR_ERR_CUDA;
+  if (iters == 0) return EVR_OK;
+  if (!s->tuned) {
+    autotune(s);
+    s->tuned = true;
+    set_name(s);
+  }
+  GraphKey key{iters, s->cur};
+  auto it = s->graphs.find(key);
+  int end_cur = s->cur;
+  int launches = 0;
+  cudaGraphExec_t exec = nullptr;
+  if (it == s->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return EVR_ERR_CUDA;
+    int r = enqueue_iterations(s, iters, s->cur, s->cap_stream, &launches);
+    cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
+    if (r < 0 || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return EVR_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return EVR_ERR_CUDA;
+    s->graphs[key] = exec;
+  } else {
+    exec = it->second;
+  }
+  // the graph's end buffer and launch count follow from the solver shape
+  if (s->shape < 0) {
+    launches = 2 * iters;
+  } else {
+    const int R = kTileShapes[s->shape].R;
+    const int passes = (iters + R - 1) / R;
+    launches = passes;
+    end_cur = (passes % 2) ? 1 - s->cur : s->cur;
+  }
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (s->timing) {
+    if ((int)s->ev_used.size() >= kMaxTimingPairs) resolve_timing(s);
+    if (s->ev_free.empty()) {
+      cudaEventCreate(&ev.first);
+      cudaEventCreate(&ev.second);
+    } else {
+      ev = s->ev_free.back();
+      s->ev_free.pop_back();
+    }
+    cudaEventRecord(ev.first, st);
+  }
+  if (cudaGraphLaunch(exec, st) != cudaSuccess) return EVR_ERR_CUDA;
+  if (s->timing) {
+    cudaEventRecord(ev.second, st);
+    s->ev_used.push_back(ev);
+    s->ev_launches.push_back(launches);
+    s->ev_pixiters.push_back((long long)s->W * s->H * iters);
+  }
+  s->cur = end_cur;
+  return EVR_OK;
+}
+
+int evr_get_image(evr_stream* s, float* out_host, size_t len) {
+  if (!s || !out_host || len < (size_t)s->W * s->H) return EVR_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpy2DAsync(out_host, (size_t)s->W * 4, s->P.u[s->cur],
+                                    (size_t)s->pitch * 4, (size_t)s->W * 4, s->H,
+                                    cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return EVR_ERR_CUDA;
+  return sync_status(s);
+}
+
+int evr_get_image_device(evr_stream* s, float* out_dev, size_t len) {
+  if (!s || !out_dev || len < (size_t)s->W * s->H) return EVR_ERR_INVALID_ARG;
+  return cuda_err(cudaMemcpy2DAsync(out_dev, (size_t)s->W * 4, s->P.u[s->cur],
+                                    (size_t)s->pitch * 4, (size_t)s->W * 4, s->H,
+                                    cudaMemcpyDeviceToDevice, s->stream));
+}
+
+static void* plane_ptr(evr_stream* s, int which, size_t* elem) {
+  *elem = 4;
+  switch (which) {
+    case EVR_STATE_U: return s->P.u[s->cur];
+    case EVR_STATE_P1: return s->P.p1[s->cur];
+    case EVR_STATE_P2: return s->P.p2[s->cur];
+    case EVR_STATE_P3: return s->P.p3[s->cur];
+    case EVR_STATE_F: return s->P.f;
+    case EVR_STATE_SQRTG: return s->P.sG;
+    case EVR_STATE_NPOS: return s->P.npos;
+    case EVR_STATE_NNEG: return s->P.nneg;
+    case EVR_STATE_TLAST: *elem = 8; return s->P.t_last;
+    default: return nullptr;
+  }
+}
+
+int evr_get_state(evr_stream* s, int which, void* out_host, size_t bytes) {
+  if (!s || !out_host) return EVR_ERR_INVALID_ARG;
+  if (which == EVR_STATE_CLOCK || which == EVR_STATE_TINIT) {
+    if (bytes != 8) return EVR_ERR_INVALID_ARG;
+    int rc = sync_status(s);
+    long long v = which == EVR_STATE_CLOCK ? s->h_sc->clock
+                                           : (s->h_sc->t_init_set ? s->h_sc->t_init : 0);
+    std::memcpy(out_host, &v, 8);
+    return rc;
+  }
+  size_t elem = 0;
+  void* src = plane_ptr(s, which, &elem);
+  if (!src || bytes != elem * s->W * s->H) return EVR_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpy2DAsync(out_host, elem * s->W, src, elem * s->pitch, elem * s->W,
+                                    s->H, cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return EVR_ERR_CUDA;
+  int rc = sync_status(s);
+  if (which == EVR_STATE_TLAST) {
+    long long t_init = s->h_sc->t_init_set ? s->h_sc->t_init : s->h_sc->clock;
+    long long* v = (long long*)out_host;
+    for (size_t i = 0; i < (size_t)s->W * s->H; ++i)
+      if (v[i] == kNeverFired) v[i] = t_init;
+  }
+  return rc;
+}
+
+int evr_set_state(evr_stream* s, int which, const void* in_host, size_t bytes) {
+  if (!s || !in_host) return EVR_ERR_INVALID_ARG;
+  if (which < EVR_STATE_U || which > EVR_STATE_P3) return EVR_ERR_INVALID_ARG;
+  size_t elem = 0;
+  void* dst = plane_ptr(s, which, &elem);
+  if (bytes != elem * s->W * s->H) return EVR_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpy2DAsync(dst, elem * s->pitch, in_host, elem * s->W, elem * s->W,
+                                    s->H, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_err(e);
+}
+
+int evr_gap(evr_stream* s, double* primal, double* dual) {
+  if (!s || !primal || !dual) return EVR_ERR_INVALID_ARG;
+  if (launch_gap(s->P, s->cur, solve_consts(s), s->d_gap, s->stream)) return EVR_ERR_CUDA;
+  if (cudaMemcpyAsync(s->h_gap, s->d_gap, 16, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+    return EVR_ERR_CUDA;
+  int rc = sync_status(s);
+  *primal = s->h_gap[0];
+  *dual = s->h_gap[1];
+  return rc;
+}
+
+int evr_synchronize(evr_stream* s) {
+  if (!s) return EVR_ERR_INVALID_ARG;
+  return sync_status(s);
+}
+
+int evr_enable_kernel_timing(evr_stream* s, int enable) {
+  if (!s) return EVR_ERR_INVALID_ARG;
+  resolve_timing(s);
+  s->t_ms = 0.0;
+  s->t_launches = 0;
+  s->t_pixiters = 0;
+  s->timing = enable != 0;
+  return EVR_OK;
+}
+
+int evr_kernel_time(evr_stream* s, double* ms, int64_t* launches, int64_t* pixel_iters) {
+  if (!s || !ms || !launches || !pixel_iters) return EVR_ERR_INVALID_ARG;
+  resolve_timing(s);
+  *ms = s->t_ms;
+  *launches = s->t_launches;
+  *pixel_iters = s->t_pixiters;
+  return cuda_err(cudaGetLastError());
+}
+
+const char* evr_solver_name(evr_stream* s) { return s ? s->name : ""; }
+
+const char* evr_strerror(int code) {
+  switch (code) {
+    case EVR_OK: return "ok";
+    case EVR_ERR_INVALID_ARG: return "invalid argument";
+    case EVR_ERR_OUT_OF_RANGE: return "event outside the sensor";
+    case EVR_ERR_BAD_POLARITY: return "event with polarity 0";
+    case EVR_ERR_NONMONOTONIC: return "event timestamp decreases";
+    case EVR_ERR_OOM: return "out of memory";
+    case EVR_ERR_CUDA: return "CUDA error";
+    case EVR_ERR_TIMEOUT: return "device wait timed out";
+    case EVR_ERR_NOT_SUPPORTED: return "no sm_103a device or option not built";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,565 @@
+// evr_kernels.cu -- sm_103a kernels of the event-manifold reconstruction.
+//
+// Reinbacher, Graber, Pock, BMVC 2016.  Per packet: event scatter (Sec. 3, Sec. 3.1),
+// prologue (time surface, metric of Eq. 2 / Eq. 3, data image of Eq.
+// intensity_update), then primal-dual iterations (Eq. cont_iterates, Eq.
+// update_rules).  FP32 arithmetic with IEEE division and square root; FP64 only in
+// the gap reduction.
+#include <cuda_runtime.h>
+
+#include <climits>
+
+#include "evr_internal.cuh"
+
+namespace evr {
+
+// codes as in include/evr.h
+constexpr int kErrOutOfRange = -2;
+constexpr int kErrBadPolarity = -3;
+constexpr int kErrNonmonotonic = -4;
+
+const TileShape kTileShapes[kNumTileShapes] = {
+    {32, 32, 8, 2}, {32, 32, 8, 4}, {64, 32, 16, 2}, {64, 32, 16, 4},
+    {64, 64, 16, 4}, {64, 64, 16, 6}, {32, 32, 8, 6}, {64, 64, 32, 4},
+};
+
+// ---------------------------------------------------------------- pointwise maps
+// L_g u at one pixel from the forward differences (ux, uy) (Eq. 3), with
+// a = L_x t, b = L_y t, iG = 1/G.  Written as M (ux, uy) with
+// M = (1/G) [[1+b^2, -ab], [-ab, 1+a^2], [a, b]].
+__device__ __forceinline__ void apply_M(float a, float b, float iG, float ux, float uy, float& g1,
+                                        float& g2, float& g3) {
+  float w = b * ux - a * uy;
+  g1 = iG * (ux + b * w);
+  g2 = iG * (uy - a * w);
+  g3 = iG * (a * ux + b * uy);
+}
+
+// M^T p: the vector field whose ordinary divergence is div_g p = -L_g^* p.
+__device__ __forceinline__ void apply_MT(float a, float b, float iG, float p1, float p2, float p3,
+                                         float& q1, float& q2) {
+  float z = b * p1 - a * p2;
+  q1 = iG * (p1 + b * z + a * p3);
+  q2 = iG * (p2 - a * z + b * p3);
+}
+
+// Closed-form KL proximal root with clamping (Eq. update_rules, first line):
+// 1/2 (v - beta + sqrt((v - beta)^2 + 4 beta f)).  For v - beta < 0 the same root is
+// evaluated as 2 beta f / (sqrt(...) - (v - beta)), which avoids the cancellation of
+// two nearly equal terms when beta >> v.
+__device__ __forceinline__ float prox_kl(float v, float beta, float f, float umin, float umax) {
+  float d = v - beta;
+  float bf = beta * f;
+  float disc = sqrtf(d * d + 4.0f * bf);
+  float r = (d >= 0.0f) ? 0.5f * (d + disc) : (2.0f * bf) / (disc - d);
+  return fminf(fmaxf(r, umin), umax);
+}
+
+// Projection onto the metric ball |p| <= sqrt(G) (Eq. update_rules, second line).
+__device__ __forceinline__ void project(float& p1, float& p2, float& p3, float sG) {
+  float nrm = sqrtf(p1 * p1 + p2 * p2 + p3 * p3);
+  float den = fmaxf(1.0f, nrm / sG);
+  p1 = p1 / den;
+  p2 = p2 / den;
+  p3 = p3 / den;
+}
+
+// ---------------------------------------------------------------- initialisation
+__global__ void k_init(Planes P, float u_init, long long clock0, long long t_init, int t_init_set) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x == 0 && y == 0) {
+    P.sc->clock = clock0;
+    P.sc->t_init = t_init;
+    P.sc->t_init_set = t_init_set;
+    P.sc->status = 0;
+    P.sc->first_bad = INT_MAX;
+  }
+  if (x >= P.pitch || y >= P.H) return;
+  size_t i = (size_t)y * P.pitch + x;
+  for (int b = 0; b < 2; ++b) {
+    P.u[b][i] = u_init;
+    P.p1[b][i] = 0.0f;
+    P.p2[b][i] = 0.0f;
+    P.p3[b][i] = 0.0f;
+  }
+  P.ubar[i] = u_init;
+  P.f[i] = u_init;
+  P.tx[i] = 0.0f;
+  P.ty[i] = 0.0f;
+  P.iG[i] = 1.0f;
+  P.sG[i] = 1.0f;
+  P.t_last[i] = kNeverFired;
+  P.npos[i] = 0;
+  P.nneg[i] = 0;
+}
+
+int launch_init(const Planes& P, float u_init, long long clock0, long long t_init, int t_init_set,
+                void* stream) {
+  dim3 blk(32, 8), grd((P.pitch + 31) / 32, (P.H + 7) / 8);
+  k_init<<<grd, blk, 0, (cudaStream_t)stream>>>(P, u_init, clock0, t_init, t_init_set);
+  return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- event scatter
+// Code of event i when all events before it are valid (then the running clock is
+// t[i-1], or the stream clock for i = 0): range, then polarity, then time.
+__device__ __forceinline__ int event_code(const uint16_t* x, const uint16_t* y,
+                                          const long long* t, const int8_t* pol, int i, int W,
+                                          int H, long long clock, int have_clock) {
+  if ((int)x[i] >= W || (int)y[i] >= H) return kErrOutOfRange;
+  if (pol[i] == 0) return kErrBadPolarity;
+  if (i > 0) {
+    if (t[i] < t[i - 1]) return kErrNonmonotonic;
+  } else if (have_clock && t[0] < clock) {
+    return kErrNonmonotonic;
+  }
+  return 0;
+}
+
+// Warp-aggregated commit of events [base, n) with stride `stride`: lanes holding
+// the same pixel elect the highest lane (it carries the latest timestamp because
+// the packet is sorted), which issues one atomicMax on t_last and one atomicAdd per
+// polarity.  max and + commute, so the result is independent of scheduling.
+__device__ __forceinline__ void commit_events(const Planes& P, const uint16_t* x, const uint16_t* y,
+                                              const long long* t, const int8_t* pol, int n,
+                                              int first, int stride) {
+  const int lane = threadIdx.x & 31;
+  for (int base = first - lane; base < n; base += stride) {
+    int i = base + lane;
+    bool ok = i < n;
+    unsigned act = __ballot_sync(0xffffffffu, ok);
+    if (!ok) continue;
+    int idx = (int)y[i] * P.pitch + (int)x[i];
+    unsigned peers = __match_any_sync(act, idx);
+    unsigned posm = __ballot_sync(act, pol[i] > 0);
+    int leader = 31 - __clz(peers);
+    if (lane == leader) {
+      atomicMax(&P.t_last[idx], t[i]);
+      int np = __popc(peers & posm);
+      int nn = __popc(peers & ~posm);
+      if (np) atomicAdd(&P.npos[idx], np);
+      if (nn) atomicAdd(&P.nneg[idx], nn);
+    }
+  }
+}
+
+// One CTA validates the whole packet, then commits it: a rejected packet changes
+// nothing (Sec. 3 requires theta in {-1,1}, pixels on the sensor, increasing t).
+__global__ void __launch_bounds__(1024) k_push_one_cta(Planes P, const uint16_t* __restrict__ x,
+                                                       const uint16_t* __restrict__ y,
+                                                       const long long* __restrict__ t,
+                                                       const int8_t* __restrict__ pol, int n) {
+  __shared__ int s_bad;
+  __shared__ long long s_clock;
+  __shared__ int s_have;
+  if (threadIdx.x == 0) {
+    s_bad = n;
+    s_clock = P.sc->clock;
+    s_have = P.sc->t_init_set;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (event_code(x, y, t, pol, i, P.W, P.H, s_clock, s_have) != 0) atomicMin(&s_bad, i);
+  __syncthreads();
+  int bad = s_bad;
+  if (bad < n) {
+    if (threadIdx.x == 0)
+      atomicCAS(&P.sc->status, 0, event_code(x, y, t, pol, bad, P.W, P.H, s_clock, s_have));
+    return;
+  }
+  const int warp_base = threadIdx.x & ~31;
+  commit_events(P, x, y, t, pol, n, warp_base + (threadIdx.x & 31), blockDim.x);
+  if (threadIdx.x == 0) {
+    if (!s_have) {
+      P.sc->t_init = t[0];
+      P.sc->t_init_set = 1;
+    }
+    P.sc->clock = t[n - 1] > s_clock ? t[n - 1] : s_clock;
+  }
+}
+
+// Large packets: grid-wide validation, then a commit kernel that checks the result.
+__global__ void k_push_validate(Planes P, const uint16_t* __restrict__ x,
+                                const uint16_t* __restrict__ y, const long long* __restrict__ t,
+                                const int8_t* __restrict__ pol, int n) {
+  long long clock = P.sc->clock;
+  int have = P.sc->t_init_set;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (event_code(x, y, t, pol, i, P.W, P.H, clock, have) != 0) atomicMin(&P.sc->first_bad, i);
+}
+
+__global__ void k_push_commit(Planes P, const uint16_t* __restrict__ x,
+                              const uint16_t* __restrict__ y, const long long* __restrict__ t,
+                              const int8_t* __restrict__ pol, int n) {
+  int bad = P.sc->first_bad;
+  if (bad < n) return;
+  int first = blockIdx.x * blockDim.x + threadIdx.x;
+  commit_events(P, x, y, t, pol, n, first, gridDim.x * blockDim.x);
+}
+
+// Finishes a large push: records the rejection, or advances the clock; re-arms
+// first_bad for the next push.
+__global__ void k_push_finish(Planes P, const uint16_t* __restrict__ x,
+                              const uint16_t* __restrict__ y, const long long* __restrict__ t,
+                              const int8_t* __restrict__ pol, int n) {
+  int bad = P.sc->first_bad;
+  long long clock = P.sc->clock;
+  int have = P.sc->t_init_set;
+  if (bad < n) {
+    atomicCAS(&P.sc->status, 0, event_code(x, y, t, pol, bad, P.W, P.H, clock, have));
+  } else {
+    if (!have) {
+      P.sc->t_init = t[0];
+      P.sc->t_init_set = 1;
+    }
+    P.sc->clock = t[n - 1] > clock ? t[n - 1] : clock;
+  }
+  P.sc->first_bad = INT_MAX;
+}
+
+int launch_push(const Planes& P, const uint16_t* x, const uint16_t* y, const long long* t,
+                const int8_t* pol, int n, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n <= 0) return 0;
+  if (n <= 32768) {
+    k_push_one_cta<<<1, 1024, 0, st>>>(P, x, y, t, pol, n);
+  } else {
+    int blocks = (n + 255) / 256;
+    if (blocks > 1216) blocks = 1216;
+    k_push_validate<<<blocks, 256, 0, st>>>(P, x, y, t, pol, n);
+    k_push_commit<<<blocks, 256, 0, st>>>(P, x, y, t, pol, n);
+    k_push_finish<<<1, 1, 0, st>>>(P, x, y, t, pol, n);
+  }
+  return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- packet prologue
+// Time surface (time since the pixel's last event, Sec. 3.1), scaled and clamped.
+__device__ __forceinline__ float time_surface(long long tl, long long clock, long long t_init,
+                                              const PrologueConsts& c) {
+  if (!c.manifold) return 0.0f;
+  long long last = (tl == kNeverFired) ? t_init : tl;
+  long long d = clock - last;
+  if (c.t_max_us > 0 && d > c.t_max_us) d = c.t_max_us;
+  return (float)d * c.time_scale;
+}
+
+// Per pixel: L_x t, L_y t (forward differences, zero on the last column/row), G,
+// 1/G, sqrt G (Eq. 2, text after Eq. 3), and the data image
+// f = base * exp(Delta+ n+ - Delta- n-) (Eq. intensity_update, one factor per event);
+// the counts are then cleared.
+__global__ void k_prologue(Planes P, int cur, PrologueConsts c) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.W || y >= P.H) return;
+  long long clock = P.sc->clock;
+  long long t_init = P.sc->t_init_set ? P.sc->t_init : clock;
+  size_t i = (size_t)y * P.pitch + x;
+  float t0 = time_surface(P.t_last[i], clock, t_init, c);
+  float a = (x < P.W - 1) ? time_surface(P.t_last[i + 1], clock, t_init, c) - t0 : 0.0f;
+  float b = (y < P.H - 1) ? time_surface(P.t_last[i + P.pitch], clock, t_init, c) - t0 : 0.0f;
+  float G = 1.0f + a * a + b * b;
+  P.tx[i] = a;
+  P.ty[i] = b;
+  P.iG[i] = 1.0f / G;
+  P.sG[i] = sqrtf(G);
+  int np = P.npos[i], nn = P.nneg[i];
+  float base = (c.data_mode == 0) ? P.u[cur][i] : P.f[i];
+  float e = c.delta_pos * (float)np - c.delta_neg * (float)nn;
+  P.f[i] = base * expf(e);
+  P.npos[i] = 0;
+  P.nneg[i] = 0;
+}
+
+int launch_prologue(const Planes& P, int cur, const PrologueConsts& c, void* stream) {
+  dim3 blk(32, 8), grd((P.W + 31) / 32, (P.H + 7) / 8);
+  k_prologue<<<grd, blk, 0, (cudaStream_t)stream>>>(P, cur, c);
+  return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- unfused iteration
+// Primal step at every pixel: v = u + tau div_g p, u+ = prox(v), ubar = 2u+ - u.
+__global__ void k_primal(Planes P, int cur, SolveConsts c) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.W || y >= P.H) return;
+  size_t i = (size_t)y * P.pitch + x;
+  const float *p1 = P.p1[cur], *p2 = P.p2[cur], *p3 = P.p3[cur];
+  float q1, q2, q1m = 0.0f, q2m = 0.0f, d1, d2;
+  apply_MT(P.tx[i], P.ty[i], P.iG[i], p1[i], p2[i], p3[i], q1, q2);
+  if (x > 0) apply_MT(P.tx[i - 1], P.ty[i - 1], P.iG[i - 1], p1[i - 1], p2[i - 1], p3[i - 1], q1m, d2);
+  if (y > 0) {
+    size_t j = i - P.pitch;
+    apply_MT(P.tx[j], P.ty[j], P.iG[j], p1[j], p2[j], p3[j], d1, q2m);
+  }
+  float div = ((x < P.W - 1) ? q1 : 0.0f) - q1m + ((y < P.H - 1) ? q2 : 0.0f) - q2m;
+  float u = P.u[cur][i];
+  float v = u + c.tau * div;
+  float beta = c.tau * c.lambda * P.sG[i];
+  float un = prox_kl(v, beta, P.f[i], c.u_min, c.u_max);
+  P.u[cur][i] = un;
+  P.ubar[i] = 2.0f * un - u;
+}
+
+// Dual step at every pixel: p = proj(p + sigma L_g ubar).
+__global__ void k_dual(Planes P, int cur, SolveConsts c) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.W || y >= P.H) return;
+  size_t i = (size_t)y * P.pitch + x;
+  float ub = P.ubar[i];
+  float ux = (x < P.W - 1) ? P.ubar[i + 1] - ub : 0.0f;
+  float uy = (y < P.H - 1) ? P.ubar[i + P.pitch] - ub : 0.0f;
+  float g1, g2, g3;
+  apply_M(P.tx[i], P.ty[i], P.iG[i], ux, uy, g1, g2, g3);
+  float p1 = P.p1[cur][i] + c.sigma * g1;
+  float p2 = P.p2[cur][i] + c.sigma * g2;
+  float p3 = P.p3[cur][i] + c.sigma * g3;
+  project(p1, p2, p3, P.sG[i]);
+  P.p1[cur][i] = p1;
+  P.p2[cur][i] = p2;
+  P.p3[cur][i] = p3;
+}
+
+int launch_unfused_iteration(const Planes& P, int cur, const SolveConsts& c, void* stream) {
+  dim3 blk(32, 8), grd((P.W + 31) / 32, (P.H + 7) / 8);
+  k_primal<<<grd, blk, 0, (cudaStream_t)stream>>>(P, cur, c);
+  k_dual<<<grd, blk, 0, (cudaStream_t)stream>>>(P, cur, c);
+  return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- tiled iterations
+// One launch = `iters` (<= R) iterations.  CTA b owns an OW x OH tile (OW = EW - 2R)
+// and loads it with an R-pixel halo: after j iterations the values are exact on the
+// tile grown by R - j pixels (each iteration reads one neighbour in each direction),
+// so the owned pixels are exact after R.  Pixel-local state (u, p, f, metric) lives
+// in registers; the fields neighbours read (q = M^T p for the divergence, ubar for
+// the forward differences) go through shared memory.  State is read from buffer src
+// and the owned pixels are written to buffer 1 - src, so no CTA reads a halo that a
+// neighbour has already advanced.
+template <int EW, int EH, int NTY, int R>
+__global__ void __launch_bounds__(32 * NTY) k_tiled(Planes P, int src, int iters, SolveConsts c,
+                                                    int tiles_x) {
+  constexpr int KX = EW / 32, KY = EH / NTY, K = KX * KY;
+  constexpr int OW = EW - 2 * R, OH = EH - 2 * R;
+  __shared__ float s_q1[EH][EW];
+  __shared__ float s_q2[EH][EW];
+  __shared__ float s_ub[EH][EW];
+  const int W = P.W, H = P.H;
+  const int gx0 = (int)(blockIdx.x % tiles_x) * OW - R;
+  const int gy0 = (int)(blockIdx.x / tiles_x) * OH - R;
+  const int tx0 = threadIdx.x, ty0 = threadIdx.y;
+  float u[K], p1[K], p2[K], p3[K], f[K], ta[K], tb[K], iG[K], sG[K];
+  const float *U = P.u[src], *P1 = P.p1[src], *P2 = P.p2[src], *P3 = P.p3[src];
+#pragma unroll
+  for (int ky = 0; ky < KY; ++ky) {
+#pragma unroll
+    for (int kx = 0; kx < KX; ++kx) {
+      const int k = ky * KX + kx;
+      const int gx = gx0 + tx0 + 32 * kx, gy = gy0 + ty0 + NTY * ky;
+      if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+        size_t i = (size_t)gy * P.pitch + gx;
+        u[k] = U[i];
+        p1[k] = P1[i];
+        p2[k] = P2[i];
+        p3[k] = P3[i];
+        f[k] = P.f[i];
+        ta[k] = P.tx[i];
+        tb[k] = P.ty[i];
+        iG[k] = P.iG[i];
+        sG[k] = P.sG[i];
+      } else {  // off the sensor: finite filler, never read by on-sensor pixels
+        u[k] = 1.0f;
+        p1[k] = p2[k] = p3[k] = 0.0f;
+        f[k] = 1.0f;
+        ta[k] = tb[k] = 0.0f;
+        iG[k] = sG[k] = 1.0f;
+      }
+    }
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int ky = 0; ky < KY; ++ky) {
+#pragma unroll
+      for (int kx = 0; kx < KX; ++kx) {
+        const int k = ky * KX + kx;
+        float q1, q2;
+        apply_MT(ta[k], tb[k], iG[k], p1[k], p2[k], p3[k], q1, q2);
+        s_q1[ty0 + NTY * ky][tx0 + 32 * kx] = q1;
+        s_q2[ty0 + NTY * ky][tx0 + 32 * kx] = q2;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ky = 0; ky < KY; ++ky) {
+#pragma unroll
+      for (int kx = 0; kx < KX; ++kx) {
+        const int k = ky * KX + kx;
+        const int lx = tx0 + 32 * kx, ly = ty0 + NTY * ky;
+        const int gx = gx0 + lx, gy = gy0 + ly;
+        float div = 0.0f;
+        if (gx < W - 1) div += s_q1[ly][lx];
+        if (gx > 0 && lx > 0) div -= s_q1[ly][lx - 1];
+        if (gy < H - 1) div += s_q2[ly][lx];
+        if (gy > 0 && ly > 0) div -= s_q2[ly - 1][lx];
+        float v = u[k] + c.tau * div;
+        float beta = c.tau * c.lambda * sG[k];
+        float un = prox_kl(v, beta, f[k], c.u_min, c.u_max);
+        s_ub[ly][lx] = 2.0f * un - u[k];
+        u[k] = un;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ky = 0; ky < KY; ++ky) {
+#pragma unroll
+      for (int kx = 0; kx < KX; ++kx) {
+        const int k = ky * KX + kx;
+        const int lx = tx0 + 32 * kx, ly = ty0 + NTY * ky;
+        const int gx = gx0 + lx, gy = gy0 + ly;
+        float ub = s_ub[ly][lx];
+        float ux = (gx < W - 1 && lx < EW - 1) ? s_ub[ly][lx + 1] - ub : 0.0f;
+        float uy = (gy < H - 1 && ly < EH - 1) ? s_ub[ly + 1][lx] - ub : 0.0f;
+        float g1, g2, g3;
+        apply_M(ta[k], tb[k], iG[k], ux, uy, g1, g2, g3);
+        float a1 = p1[k] + c.sigma * g1;
+        float a2 = p2[k] + c.sigma * g2;
+        float a3 = p3[k] + c.sigma * g3;
+        project(a1, a2, a3, sG[k]);
+        p1[k] = a1;
+        p2[k] = a2;
+        p3[k] = a3;
+      }
+    }
+  }
+  const int dst = 1 - src;
+  float *Ud = P.u[dst], *P1d = P.p1[dst], *P2d = P.p2[dst], *P3d = P.p3[dst];
+#pragma unroll
+  for (int ky = 0; ky < KY; ++ky) {
+#pragma unroll
+    for (int kx = 0; kx < KX; ++kx) {
+      const int k = ky * KX + kx;
+      const int lx = tx0 + 32 * kx, ly = ty0 + NTY * ky;
+      const int gx = gx0 + lx, gy = gy0 + ly;
+      if (lx >= R && lx < R + OW && ly >= R && ly < R + OH && gx < W && gy < H) {
+        size_t i = (size_t)gy * P.pitch + gx;
+        Ud[i] = u[k];
+        P1d[i] = p1[k];
+        P2d[i] = p2[k];
+        P3d[i] = p3[k];
+      }
+    }
+  }
+}
+
+template <int EW, int EH, int NTY, int R>
+static int run_tiled(const Planes& P, int src, int iters, const SolveConsts& c, cudaStream_t st) {
+  constexpr int OW = EW - 2 * R, OH = EH - 2 * R;
+  int tiles_x = (P.W + OW - 1) / OW, tiles_y = (P.H + OH - 1) / OH;
+  k_tiled<EW, EH, NTY, R><<<tiles_x * tiles_y, dim3(32, NTY), 0, st>>>(P, src, iters, c, tiles_x);
+  return (int)cudaGetLastError();
+}
+
+int tiled_pass_blocks(const Planes& P, int shape) {
+  const TileShape& s = kTileShapes[shape];
+  int OW = s.EW - 2 * s.R, OH = s.EH - 2 * s.R;
+  return ((P.W + OW - 1) / OW) * ((P.H + OH - 1) / OH);
+}
+
+int launch_tiled_pass(const Planes& P, int shape, int src, int iters, const SolveConsts& c,
+                      void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (shape) {
+    case 0: return run_tiled<32, 32, 8, 2>(P, src, iters, c, st);
+    case 1: return run_tiled<32, 32, 8, 4>(P, src, iters, c, st);
+    case 2: return run_tiled<64, 32, 16, 2>(P, src, iters, c, st);
+    case 3: return run_tiled<64, 32, 16, 4>(P, src, iters, c, st);
+    case 4: return run_tiled<64, 64, 16, 4>(P, src, iters, c, st);
+    case 5: return run_tiled<64, 64, 16, 6>(P, src, iters, c, st);
+    case 6: return run_tiled<32, 32, 8, 6>(P, src, iters, c, st);
+    case 7: return run_tiled<64, 64, 32, 4>(P, src, iters, c, st);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------- FP64 gap
+// Per pixel, in FP64 from the FP32 state: the g-tensor norm term sqrt(G) |L_g u|,
+// the data term sqrt(G)(u - f log u) (Eq. 5), and the dual term
+// min_{u in box} a (u - f log u) + w u with a = lambda sqrt(G), w = -div_g p, whose
+// minimiser is clamp(a f / (a + w)) for a + w > 0 and u_max otherwise.
+__device__ __forceinline__ void mt64(const Planes& P, size_t i, int cur, double& q1, double& q2) {
+  double a = P.tx[i], b = P.ty[i];
+  double G = 1.0 + a * a + b * b;
+  double p1 = P.p1[cur][i], p2 = P.p2[cur][i], p3 = P.p3[cur][i];
+  q1 = ((1.0 + b * b) * p1 - a * b * p2 + a * p3) / G;
+  q2 = (-a * b * p1 + (1.0 + a * a) * p2 + b * p3) / G;
+}
+
+__global__ void __launch_bounds__(kGapThreads) k_gap_partial(Planes P, int cur, SolveConsts c) {
+  __shared__ double s[3][kGapThreads];
+  double reg = 0.0, dat = 0.0, dua = 0.0;
+  const int n = P.W * P.H;
+  const double lam = c.lambda, umin = c.u_min, umax = c.u_max;
+  for (int k = blockIdx.x * kGapThreads + threadIdx.x; k < n; k += kGapBlocks * kGapThreads) {
+    int x = k % P.W, y = k / P.W;
+    size_t i = (size_t)y * P.pitch + x;
+    const float* U = P.u[cur];
+    double a = P.tx[i], b = P.ty[i];
+    double G = 1.0 + a * a + b * b, sG = sqrt(G);
+    double u = U[i], f = P.f[i];
+    double ux = (x < P.W - 1) ? (double)U[i + 1] - u : 0.0;
+    double uy = (y < P.H - 1) ? (double)U[i + P.pitch] - u : 0.0;
+    double g1 = ((1.0 + b * b) * ux - a * b * uy) / G;
+    double g2 = ((1.0 + a * a) * uy - a * b * ux) / G;
+    double g3 = (a * ux + b * uy) / G;
+    reg += sqrt(G * (g1 * g1 + g2 * g2 + g3 * g3));
+    dat += (u - (f == 0.0 ? 0.0 : f * log(u))) * sG;
+    double q1, q2, q1m = 0.0, q2m = 0.0, d;
+    mt64(P, i, cur, q1, q2);
+    if (x > 0) mt64(P, i - 1, cur, q1m, d);
+    if (y > 0) mt64(P, i - P.pitch, cur, d, q2m);
+    double div = ((x < P.W - 1) ? q1 : 0.0) - q1m + ((y < P.H - 1) ? q2 : 0.0) - q2m;
+    double aa = lam * sG, w = -div;
+    double us = (aa + w > 0.0) ? aa * f / (aa + w) : umax;
+    us = fmin(fmax(us, umin), umax);
+    dua += aa * (us - (f == 0.0 ? 0.0 : f * log(us))) + w * us;
+  }
+  s[0][threadIdx.x] = reg;
+  s[1][threadIdx.x] = dat;
+  s[2][threadIdx.x] = dua;
+  __syncthreads();
+  for (int h = kGapThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int j = 0; j < 3; ++j) s[j][threadIdx.x] += s[j][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 3; ++j) P.partials[3 * blockIdx.x + j] = s[j][0];
+}
+
+__global__ void __launch_bounds__(512) k_gap_final(Planes P, SolveConsts c, double* out2) {
+  __shared__ double s[3][512];
+  for (int j = 0; j < 3; ++j)
+    s[j][threadIdx.x] = (threadIdx.x < kGapBlocks) ? P.partials[3 * threadIdx.x + j] : 0.0;
+  __syncthreads();
+  for (int h = 256; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int j = 0; j < 3; ++j) s[j][threadIdx.x] += s[j][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out2[0] = s[0][0] + (double)c.lambda * s[1][0];
+    out2[1] = s[2][0];
+  }
+}
+
+int launch_gap(const Planes& P, int cur, const SolveConsts& c, double* out2, void* stream) {
+  static_assert(kGapBlocks <= 512, "final reduction covers all partials");
+  cudaStream_t st = (cudaStream_t)stream;
+  k_gap_partial<<<kGapBlocks, kGapThreads, 0, st>>>(P, cur, c);
+  k_gap_final<<<1, 512, 0, st>>>(P, c, out2);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace evr

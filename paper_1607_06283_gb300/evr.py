@@ -1,0 +1,283 @@
+"""Thin ctypes binding of libevr (include/evr.h), names as in the C ABI.
+
+Argument marshalling only: numpy arrays and torch CUDA tensors are turned into
+pointers and sizes, and return codes into exceptions.  Every step of the
+reconstruction runs in the library's CUDA kernels.  Importing this module loads
+paper_1607_06283_gb300/_build/libevr.so and fails loudly if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libevr.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "evr.h")
+
+EVR_OK = 0
+EVR_ERR_INVALID_ARG = -1
+EVR_ERR_OUT_OF_RANGE = -2
+EVR_ERR_BAD_POLARITY = -3
+EVR_ERR_NONMONOTONIC = -4
+EVR_ERR_OOM = -5
+EVR_ERR_CUDA = -6
+EVR_ERR_TIMEOUT = -7
+EVR_ERR_NOT_SUPPORTED = -8
+EVR_T_INIT_FIRST = -(2 ** 63)
+EVR_SOLVER_AUTO, EVR_SOLVER_UNFUSED, EVR_SOLVER_TILED = 0, 1, 2
+(EVR_STATE_U, EVR_STATE_P1, EVR_STATE_P2, EVR_STATE_P3, EVR_STATE_F, EVR_STATE_TLAST,
+ EVR_STATE_NPOS, EVR_STATE_NNEG, EVR_STATE_CLOCK, EVR_STATE_TINIT, EVR_STATE_SQRTG) = range(11)
+
+
+class EvrError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {evr_strerror(code)} ({code})")
+        self.code = code
+
+
+class evr_params(ctypes.Structure):
+    _fields_ = [
+        ("lambda_", ctypes.c_float),
+        ("delta_pos", ctypes.c_float),
+        ("delta_neg", ctypes.c_float),
+        ("u_min", ctypes.c_float),
+        ("u_max", ctypes.c_float),
+        ("u_init", ctypes.c_float),
+        ("tau", ctypes.c_float),
+        ("sigma", ctypes.c_float),
+        ("time_scale", ctypes.c_float),
+        ("t_max_us", ctypes.c_int64),
+        ("t_init_us", ctypes.c_int64),
+        ("data_mode", ctypes.c_int),
+        ("manifold", ctypes.c_int),
+        ("solver", ctypes.c_int),
+        ("tile_config", ctypes.c_int),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libevr.so is not built ({LIB_PATH}); run paper_1607_06283_gb300.build.build() "
+            "(nvcc, sm_103a).  There is no CPU fallback.")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    sig = {
+        "evr_default_params": ([vp], i),
+        "evr_create": ([i, i, vp, vp], i),
+        "evr_destroy": ([vp], None),
+        "evr_set_cuda_stream": ([vp, vp], i),
+        "evr_push_events": ([vp, vp, vp, vp, vp, sz], i),
+        "evr_push_events_device": ([vp, vp, vp, vp, vp, sz], i),
+        "evr_solve": ([vp, i], i),
+        "evr_get_image": ([vp, vp, sz], i),
+        "evr_get_image_device": ([vp, vp, sz], i),
+        "evr_get_state": ([vp, i, vp, sz], i),
+        "evr_set_state": ([vp, i, vp, sz], i),
+        "evr_gap": ([vp, vp, vp], i),
+        "evr_synchronize": ([vp], i),
+        "evr_enable_kernel_timing": ([vp, i], i),
+        "evr_kernel_time": ([vp, vp, vp, vp], i),
+        "evr_solver_name": ([vp], ctypes.c_char_p),
+        "evr_strerror": ([i], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def header_functions() -> list:
+    """Names of the functions include/evr.h declares."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(evr_[a-z_]+)\s*\(", text)))
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != EVR_OK:
+        raise EvrError(rc, what)
+
+
+def evr_strerror(code: int) -> str:
+    return _lib.evr_strerror(int(code)).decode()
+
+
+def evr_default_params() -> evr_params:
+    p = evr_params()
+    _check(_lib.evr_default_params(ctypes.byref(p)), "evr_default_params")
+    return p
+
+
+def evr_create(W: int, H: int, params: evr_params | None = None):
+    params = params or evr_default_params()
+    h = ctypes.c_void_p()
+    _check(_lib.evr_create(int(W), int(H), ctypes.byref(params), ctypes.byref(h)), "evr_create")
+    return h
+
+
+def evr_destroy(h) -> None:
+    _lib.evr_destroy(h)
+
+
+def evr_set_cuda_stream(h, stream_handle: int | None) -> None:
+    _check(_lib.evr_set_cuda_stream(h, stream_handle or None), "evr_set_cuda_stream")
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+def evr_push_events(h, x, y, t_us, pol) -> int:
+    """Host arrays; returns the library's code (0 or a negative EVR_ERR_*)."""
+    x, px = _host(x, np.uint16)
+    y, py = _host(y, np.uint16)
+    t, pt = _host(t_us, np.int64)
+    p, pp = _host(pol, np.int8)
+    n = len(x)
+    if not (len(y) == len(t) == len(p) == n):
+        raise ValueError("event arrays differ in length")
+    return _lib.evr_push_events(h, px, py, pt, pp, n)
+
+
+def evr_push_events_device(h, x, y, t_us, pol) -> int:
+    """torch CUDA tensors (uint16/int32 x,y are accepted as uint16 views), int64 t, int8 pol."""
+    n = int(x.numel())
+    for a in (x, y, t_us, pol):
+        if not a.is_cuda or not a.is_contiguous() or int(a.numel()) != n:
+            raise ValueError("device events must be contiguous CUDA tensors of equal length")
+    return _lib.evr_push_events_device(h, x.data_ptr(), y.data_ptr(), t_us.data_ptr(),
+                                       pol.data_ptr(), n)
+
+
+def evr_solve(h, iters: int) -> None:
+    _check(_lib.evr_solve(h, int(iters)), "evr_solve")
+
+
+def evr_get_image(h, out: np.ndarray) -> int:
+    """Fills a float32 host array of W*H elements; returns the pending device status."""
+    assert out.dtype == np.float32 and out.flags["C_CONTIGUOUS"]
+    rc = _lib.evr_get_image(h, out.ctypes.data, out.size)
+    if rc in (EVR_ERR_INVALID_ARG, EVR_ERR_CUDA):
+        _check(rc, "evr_get_image")
+    return rc
+
+
+def evr_get_image_device(h, out) -> None:
+    _check(_lib.evr_get_image_device(h, out.data_ptr(), int(out.numel())), "evr_get_image_device")
+
+
+_STATE_DT = {EVR_STATE_U: np.float32, EVR_STATE_P1: np.float32, EVR_STATE_P2: np.float32,
+             EVR_STATE_P3: np.float32, EVR_STATE_F: np.float32, EVR_STATE_SQRTG: np.float32,
+             EVR_STATE_TLAST: np.int64, EVR_STATE_NPOS: np.int32, EVR_STATE_NNEG: np.int32}
+
+
+def evr_get_state(h, which: int, W: int, H: int):
+    if which in (EVR_STATE_CLOCK, EVR_STATE_TINIT):
+        out = np.zeros(1, np.int64)
+    else:
+        out = np.empty((H, W), _STATE_DT[which])
+    rc = _lib.evr_get_state(h, int(which), out.ctypes.data, out.nbytes)
+    if rc in (EVR_ERR_INVALID_ARG, EVR_ERR_CUDA):
+        _check(rc, "evr_get_state")
+    return (out[0] if out.size == 1 and which in (EVR_STATE_CLOCK, EVR_STATE_TINIT) else out), rc
+
+
+def evr_set_state(h, which: int, arr: np.ndarray) -> None:
+    a = np.ascontiguousarray(arr, dtype=np.float32)
+    _check(_lib.evr_set_state(h, int(which), a.ctypes.data, a.nbytes), "evr_set_state")
+
+
+def evr_gap(h):
+    pr, du = ctypes.c_double(), ctypes.c_double()
+    rc = _lib.evr_gap(h, ctypes.byref(pr), ctypes.byref(du))
+    if rc in (EVR_ERR_INVALID_ARG, EVR_ERR_CUDA):
+        _check(rc, "evr_gap")
+    return pr.value, du.value
+
+
+def evr_synchronize(h) -> int:
+    rc = _lib.evr_synchronize(h)
+    if rc == EVR_ERR_CUDA:
+        _check(rc, "evr_synchronize")
+    return rc
+
+
+def evr_enable_kernel_timing(h, enable: bool) -> None:
+    _check(_lib.evr_enable_kernel_timing(h, 1 if enable else 0), "evr_enable_kernel_timing")
+
+
+def evr_kernel_time(h):
+    ms, la, pi = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.evr_kernel_time(h, ctypes.byref(ms), ctypes.byref(la), ctypes.byref(pi)),
+           "evr_kernel_time")
+    return ms.value, la.value, pi.value
+
+
+def evr_solver_name(h) -> str:
+    return _lib.evr_solver_name(h).decode()
+
+
+class Stream:
+    """Owning wrapper of one evr_stream handle for a W x H sensor."""
+
+    def __init__(self, W: int, H: int, params: evr_params | None = None, **overrides):
+        p = params or evr_default_params()
+        for k, v in overrides.items():
+            setattr(p, "lambda_" if k == "lam" else k, v)
+        self.W, self.H, self.params = int(W), int(H), p
+        self.h = evr_create(W, H, p)
+
+    def close(self):
+        if getattr(self, "h", None):
+            evr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, x, y, t, pol) -> int:
+        return evr_push_events(self.h, x, y, t, pol)
+
+    def push_device(self, x, y, t, pol) -> int:
+        return evr_push_events_device(self.h, x, y, t, pol)
+
+    def solve(self, iters: int) -> None:
+        evr_solve(self.h, iters)
+
+    def image(self) -> np.ndarray:
+        out = np.empty((self.H, self.W), np.float32)
+        rc = evr_get_image(self.h, out)
+        if rc:
+            raise EvrError(rc, "pending device-side rejection")
+        return out
+
+    def state(self, which: int):
+        v, rc = evr_get_state(self.h, which, self.W, self.H)
+        return v
+
+    def p(self) -> np.ndarray:
+        return np.stack([self.state(EVR_STATE_P1), self.state(EVR_STATE_P2),
+                         self.state(EVR_STATE_P3)])
+
+    def gap(self):
+        return evr_gap(self.h)
+
+    def synchronize(self) -> int:
+        return evr_synchronize(self.h)
+
+    @property
+    def solver_name(self) -> str:
+        return evr_solver_name(self.h)

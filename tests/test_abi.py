@@ -1,0 +1,68 @@
+"""The C-ABI library builds for sm_103a, loads, and exports what include/evr.h declares.
+
+No compute calls: these run without a GPU.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1607_06283_gb300 import build
+
+
+@pytest.fixture(scope="module")
+def evr():
+    build.build()
+    from paper_1607_06283_gb300 import evr as E
+    return E
+
+
+def test_every_declared_function_is_exported(evr):
+    names = evr.header_functions()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(evr._lib, n), n
+
+
+def test_default_params(evr):
+    p = evr.evr_default_params()
+    assert p.lambda_ == pytest.approx(90.0)
+    assert p.tau == pytest.approx(1.0 / np.sqrt(8 + 4 * np.sqrt(2)), rel=1e-7)
+    assert p.tau * p.sigma * (8 + 4 * np.sqrt(2)) <= 1 + 1e-6
+    assert p.t_init_us == evr.EVR_T_INIT_FIRST
+    assert p.u_min == pytest.approx(np.exp(-3), rel=1e-7)
+
+
+def test_struct_layout_matches_header(evr):
+    # 9 floats, 2 int64 (8-byte aligned), 4 ints
+    assert ctypes.sizeof(evr.evr_params) == 9 * 4 + 4 + 2 * 8 + 4 * 4
+
+
+def test_argument_errors_need_no_gpu(evr):
+    E = evr
+    h = ctypes.c_void_p()
+    p = E.evr_default_params()
+    assert E._lib.evr_create(0, 5, ctypes.byref(p), ctypes.byref(h)) == E.EVR_ERR_INVALID_ARG
+    assert E._lib.evr_create(5, 5, None, ctypes.byref(h)) == E.EVR_ERR_INVALID_ARG
+    bad = E.evr_default_params()
+    bad.tau = 1.0
+    bad.sigma = 1.0
+    assert E._lib.evr_create(5, 5, ctypes.byref(bad), ctypes.byref(h)) == E.EVR_ERR_INVALID_ARG
+    bad = E.evr_default_params()
+    bad.u_min = 0.0
+    assert E._lib.evr_create(5, 5, ctypes.byref(bad), ctypes.byref(h)) == E.EVR_ERR_INVALID_ARG
+    assert E._lib.evr_solve(None, 3) == E.EVR_ERR_INVALID_ARG
+    assert E._lib.evr_push_events(None, None, None, None, None, 0) == E.EVR_ERR_INVALID_ARG
+    assert E.evr_strerror(E.EVR_ERR_NONMONOTONIC) == "event timestamp decreases"
+
+
+def test_ptxas_reports_no_spills_in_the_iteration_kernels(evr):
+    """Register pressure check on the built kernels (from nvcc -Xptxas -v)."""
+    import os
+    log = os.path.join(os.path.dirname(build.LIB), "evr_kernels.ptxas.txt")
+    text = open(log).read()
+    blocks = text.split("Compiling entry function")
+    for b in blocks[1:]:
+        name = b.split("'")[1]
+        if "k_tiled" in name and "Li32ELi4EE" not in name:  # the 1024-thread shape is capped at 64 regs
+            assert "0 bytes spill stores" in b, name
