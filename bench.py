@@ -252,7 +252,8 @@ def run_ours(args):
     from paper_1607_06283_gb300 import evr as E
 
     cfg, stream = workload(args.config, rank)
-    cur = torch.cuda.current_stream()
+    cur = torch.cuda.Stream()  # one non-default stream for the library and the timing events
+    torch.cuda.set_stream(cur)
     p = E.evr_default_params()
     p.solver = args.solver
     p.tile_config = args.tile

@@ -93,8 +93,14 @@ int evr_create(int W, int H, const evr_params* params, evr_stream** out);
 /* Release the device state (synchronises the handle's stream).  NULL is a no-op. */
 void evr_destroy(evr_stream* s);
 
-/* Queue the handle's work on an existing cudaStream_t (NULL: the library's own
- * stream).  The library does not take ownership. */
+/* Stream selector for evr_set_cuda_stream: the library's own non-blocking stream,
+ * which every handle uses until another stream is chosen. */
+#define EVR_OWN_STREAM ((void*)(intptr_t)-1)
+
+/* Queue the handle's work on an existing cudaStream_t.  NULL (0) is the legacy
+ * default stream (the stream PyTorch calls its default stream); EVR_OWN_STREAM
+ * returns to the library's own stream.  Work already queued is waited for first.
+ * The library does not take ownership. */
 int evr_set_cuda_stream(evr_stream* s, void* cuda_stream);
 
 /* Integrate one packet of n events (Sec. 3 and 3.1): for each event

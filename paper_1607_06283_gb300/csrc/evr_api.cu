@@ -408,7 +408,7 @@ void evr_destroy(evr_stream* s) {
 
 int evr_set_cuda_stream(evr_stream* s, void* cuda_stream) {
   if (!s) return EVR_ERR_INVALID_ARG;
-  cudaStream_t ns = cuda_stream ? (cudaStream_t)cuda_stream : s->own_stream;
+  cudaStream_t ns = cuda_stream == EVR_OWN_STREAM ? s->own_stream : (cudaStream_t)cuda_stream;
   if (ns != s->stream) {
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return EVR_ERR_CUDA;
     s->stream = ns;

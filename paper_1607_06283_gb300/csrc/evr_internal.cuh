@@ -60,7 +60,7 @@ struct TileShape {
   int EW, EH, NTY, R;
 };
 
-constexpr int kNumTileShapes = 8;
+constexpr int kNumTileShapes = 16;
 extern const TileShape kTileShapes[kNumTileShapes];
 
 constexpr int kGapBlocks = 304;   // fixed: the reduction order does not depend on W, H

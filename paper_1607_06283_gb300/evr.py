@@ -128,8 +128,15 @@ def evr_destroy(h) -> None:
     _lib.evr_destroy(h)
 
 
-def evr_set_cuda_stream(h, stream_handle: int | None) -> None:
-    _check(_lib.evr_set_cuda_stream(h, stream_handle or None), "evr_set_cuda_stream")
+EVR_OWN_STREAM = ctypes.c_void_p(-1 & 0xFFFFFFFFFFFFFFFF)
+
+
+def evr_set_cuda_stream(h, stream_handle) -> None:
+    """stream_handle: a cudaStream_t as an int (torch's ``Stream.cuda_stream``; 0 is the
+    legacy default stream) or EVR_OWN_STREAM."""
+    arg = stream_handle if isinstance(stream_handle, ctypes.c_void_p) else ctypes.c_void_p(
+        int(stream_handle))
+    _check(_lib.evr_set_cuda_stream(h, arg), "evr_set_cuda_stream")
 
 
 def _host(a, dtype):

@@ -64,5 +64,5 @@ def test_ptxas_reports_no_spills_in_the_iteration_kernels(evr):
     blocks = text.split("Compiling entry function")
     for b in blocks[1:]:
         name = b.split("'")[1]
-        if "k_tiled" in name and "Li32ELi4EE" not in name:  # the 1024-thread shape is capped at 64 regs
+        if "k_tiled" in name or "k_prologue" in name or "k_push" in name:
             assert "0 bytes spill stores" in b, name
