@@ -1,10 +1,11 @@
 // evr_api.cu -- host runtime and C ABI (include/evr.h).
 //
 // The host side validates arguments, stages host events through pinned memory,
-// owns the device state, captures each packet's iteration launches into a CUDA
-// graph (one per iteration count and buffer parity), picks the tile shape of the
-// tiled solver by timing the candidates on the actual sensor, and reads results
-// back.  Every step of the reconstruction itself runs in evr_kernels.cu.
+// owns the device state, picks the solver configuration by timing the candidates
+// on the actual sensor (autotuner), captures the multi-launch tiled solver's
+// launches into a CUDA graph (one per iteration count and buffer parity), and reads
+// results back.  Every step of the reconstruction itself runs in the kernels of
+// evr_kernels.cu and evr_solvers.cu.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -54,8 +55,9 @@ struct evr_stream {
   cudaStream_t own_stream = nullptr;  // the library's stream
   cudaStream_t cap_stream = nullptr;  // graph capture
   int cur = 0;                        // buffer holding the current (u, p)
-  int shape = -1;                     // tiled solver shape, -1 = unfused
+  int cfg = -1;                       // index into kSolverCfgs, -1 = unfused
   bool tuned = false;
+  int flag_base = 0;                  // persistent solver: progress-flag count
   // host-to-device event staging
   StageSlot slot[kStageSlots];
   int next_slot = 0;
@@ -108,17 +110,19 @@ int params_valid(const evr_params* p) {
   if (p->data_mode != 0 && p->data_mode != 1) return 0;
   if (p->manifold != 0 && p->manifold != 1) return 0;
   if (p->solver < 0 || p->solver > EVR_SOLVER_TILED) return 0;
-  if (p->tile_config < 0 || p->tile_config > kNumTileShapes) return 0;
+  if (p->tile_config < 0 || p->tile_config > kNumSolverCfgs) return 0;
   return 1;
 }
 
 void set_name(evr_stream* s) {
-  if (s->shape < 0) {
+  if (s->cfg < 0) {
     std::snprintf(s->name, sizeof(s->name), "unfused");
   } else {
-    const TileShape& t = kTileShapes[s->shape];
-    std::snprintf(s->name, sizeof(s->name), "tiled %dx%d R%d (%d threads)", t.EW, t.EH, t.R,
-                  32 * t.NTY);
+    const SolverCfg& c = kSolverCfgs[s->cfg];
+    const TileShape& t = kTileShapes[c.shape];
+    std::snprintf(s->name, sizeof(s->name), "%s %dx%d R%d (%d threads, %d CTAs)",
+                  c.kind == 2 ? "persistent" : "tiled", t.EW, t.EH, c.R, 32 * t.NTY,
+                  solver_cfg_ctas(s->P, c));
   }
 }
 
@@ -183,56 +187,107 @@ void drop_graphs(evr_stream* s) {
   s->graphs.clear();
 }
 
-// The iteration launches of one packet: `iters` iterations from buffer `cur`.
-// Returns the buffer that holds the result.
+// Clear the persistent solver's progress flags (required whenever the set of CTAs
+// changes and after an aborted launch).
+int clear_flags(evr_stream* s) {
+  s->flag_base = 0;
+  cudaError_t e = cudaMemsetAsync(s->P.flags, 0, sizeof(int) * kMaxCtas, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&s->P.sc->abort, 0, sizeof(int), s->stream);
+  return cuda_err(e);
+}
+
+// The multi-launch iteration launches of one packet (unfused or kind 1):
+// `iters` iterations from buffer `cur`.  Returns the buffer holding the result.
 int enqueue_iterations(evr_stream* s, int iters, int cur, cudaStream_t st, int* launches) {
   SolveConsts c = solve_consts(s);
   *launches = 0;
-  if (s->shape < 0) {
+  if (s->cfg < 0) {
     for (int k = 0; k < iters; ++k) {
       if (launch_unfused_iteration(s->P, cur, c, st)) return -1;
       *launches += 2;
     }
     return cur;
   }
-  const int R = kTileShapes[s->shape].R;
-  for (int done = 0; done < iters; done += R) {
-    int it = iters - done < R ? iters - done : R;
-    if (launch_tiled_pass(s->P, s->shape, cur, it, c, st)) return -1;
+  const SolverCfg& cfg = kSolverCfgs[s->cfg];
+  for (int done = 0; done < iters; done += cfg.R) {
+    int it = iters - done < cfg.R ? iters - done : cfg.R;
+    if (launch_tiled_pass(s->P, cfg, cur, it, c, st)) return -1;
     cur = 1 - cur;
     *launches += 1;
   }
   return cur;
 }
 
-// Time each tile shape on this sensor (reads buffer cur, writes the other one,
-// which holds no live state) and keep the fastest per iteration.
-void autotune(evr_stream* s) {
+// Run one packet's iterations with configuration index `ci` (kind 1 or 2) directly
+// on the handle's stream; updates s->cur.
+int run_cfg_direct(evr_stream* s, int ci, int iters) {
+  const SolverCfg& cfg = kSolverCfgs[ci];
   SolveConsts c = solve_consts(s);
+  if (cfg.kind == 2) {
+    if (launch_persistent(s->P, cfg, s->cur, iters, s->flag_base, c, s->stream)) return -1;
+    const int passes = (iters + cfg.R - 1) / cfg.R;
+    s->flag_base += passes - 1;
+    s->cur ^= passes & 1;
+    return 0;
+  }
+  int launches = 0;
+  int r = enqueue_iterations(s, iters, s->cur, s->stream, &launches);
+  if (r < 0) return -1;
+  s->cur = r;
+  return 0;
+}
+
+// Time every usable configuration on this sensor with the packet's iteration count
+// and keep the fastest.  The live (u, p) is saved first and restored afterwards.
+void autotune(evr_stream* s, int iters) {
+  const size_t plane = (size_t)s->pitch * s->H * sizeof(float);
+  float* save = nullptr;
+  if (cudaMalloc((void**)&save, 4 * plane) != cudaSuccess) {
+    s->cfg = 0;
+    return;
+  }
+  const int cur0 = s->cur;
+  float* src[4] = {s->P.u[cur0], s->P.p1[cur0], s->P.p2[cur0], s->P.p3[cur0]};
+  for (int k = 0; k < 4; ++k)
+    cudaMemcpyAsync((char*)save + k * plane, src[k], plane, cudaMemcpyDeviceToDevice, s->stream);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int best_shape = 1;
-  for (int sh = 0; sh < kNumTileShapes; ++sh) {
-    const int R = kTileShapes[sh].R;
-    const int reps = 12;
-    for (int w = 0; w < 2; ++w) launch_tiled_pass(s->P, sh, s->cur, R, c, s->stream);
+  int best_cfg = 0;
+  for (int ci = 0; ci < kNumSolverCfgs; ++ci) {
+    if (!solver_cfg_usable(s->P, kSolverCfgs[ci])) continue;
+    s->cfg = ci;
+    clear_flags(s);
+    bool ok = run_cfg_direct(s, ci, iters) == 0;  // warm-up (module load)
     cudaEventRecord(e0, s->stream);
-    for (int r = 0; r < reps; ++r) launch_tiled_pass(s->P, sh, s->cur, R, c, s->stream);
+    const int reps = 3;
+    for (int r = 0; r < reps && ok; ++r) ok = run_cfg_direct(s, ci, iters) == 0;
     cudaEventRecord(e1, s->stream);
-    cudaEventSynchronize(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    float per_iter = ms / (reps * R);
-    if (cudaGetLastError() == cudaSuccess && per_iter < best) {
-      best = per_iter;
-      best_shape = sh;
+    int st = 0;
+    cudaMemcpy(&st, &s->P.sc->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (st != 0) {  // a timed-out trial disqualifies the configuration
+      ok = false;
+      cudaMemset(&s->P.sc->status, 0, sizeof(int));
+    }
+    if (cudaGetLastError() == cudaSuccess && ok && ms < best) {
+      best = ms;
+      best_cfg = ci;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  s->shape = best_shape;
+  float* dst[4] = {s->P.u[cur0], s->P.p1[cur0], s->P.p2[cur0], s->P.p3[cur0]};
+  for (int k = 0; k < 4; ++k)
+    cudaMemcpyAsync(dst[k], (char*)save + k * plane, plane, cudaMemcpyDeviceToDevice, s->stream);
+  cudaStreamSynchronize(s->stream);
+  cudaFree(save);
+  s->cur = cur0;
+  s->cfg = best_cfg;
+  clear_flags(s);
 }
 
 int refresh_scalars(evr_stream* s) {
@@ -254,6 +309,7 @@ int sync_status(evr_stream* s) {
   if (st != 0) {
     if (cudaMemsetAsync(&s->P.sc->status, 0, sizeof(int), s->stream) != cudaSuccess)
       return EVR_ERR_CUDA;
+    if (st == EVR_ERR_TIMEOUT && clear_flags(s) != EVR_OK) return EVR_ERR_CUDA;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return EVR_ERR_CUDA;
     return st;
   }
@@ -323,7 +379,8 @@ int evr_create(int W, int H, const evr_params* params, evr_stream** out) {
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t fb = al(plane * 4), lb = al(plane * 8);
   const size_t total = 14 * fb + lb + 2 * fb + al(sizeof(DevScalars)) +
-                       al(sizeof(double) * 3 * kGapBlocks) + al(sizeof(double) * 2);
+                       al(sizeof(double) * 3 * kGapBlocks) + al(sizeof(double) * 2) +
+                       al(sizeof(int) * kMaxCtas);
   char* base = nullptr;
   if (cudaMalloc((void**)&base, total) != cudaSuccess) {
     delete s;
@@ -358,6 +415,7 @@ int evr_create(int W, int H, const evr_params* params, evr_stream** out) {
   P.sc = (DevScalars*)take(al(sizeof(DevScalars)));
   P.partials = (double*)take(al(sizeof(double) * 3 * kGapBlocks));
   s->d_gap = (double*)take(al(sizeof(double) * 2));
+  P.flags = (int*)take(al(sizeof(int) * kMaxCtas));
   int rc = EVR_OK;
   if (cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -377,10 +435,14 @@ int evr_create(int W, int H, const evr_params* params, evr_stream** out) {
   s->h_have_clock = !first;
   s->h_clock_valid = true;
   if (params->solver == EVR_SOLVER_UNFUSED) {
-    s->shape = -1;
+    s->cfg = -1;
     s->tuned = true;
   } else if (params->tile_config > 0) {
-    s->shape = params->tile_config - 1;
+    s->cfg = params->tile_config - 1;
+    if (!solver_cfg_usable(s->P, kSolverCfgs[s->cfg])) {
+      evr_destroy(s);
+      return EVR_ERR_NOT_SUPPORTED;
+    }
     s->tuned = true;
   }
   set_name(s);
@@ -476,40 +538,9 @@ int evr_solve(evr_stream* s, int iters) {
   if (launch_prologue(s->P, s->cur, prologue_consts(s), st)) return EVR_ERR_CUDA;
   if (iters == 0) return EVR_OK;
   if (!s->tuned) {
-    autotune(s);
+    autotune(s, iters);
     s->tuned = true;
     set_name(s);
-  }
-  GraphKey key{iters, s->cur};
-  auto it = s->graphs.find(key);
-  int end_cur = s->cur;
-  int launches = 0;
-  cudaGraphExec_t exec = nullptr;
-  if (it == s->graphs.end()) {
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-      return EVR_ERR_CUDA;
-    int r = enqueue_iterations(s, iters, s->cur, s->cap_stream, &launches);
-    cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
-    if (r < 0 || e != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      return EVR_ERR_CUDA;
-    }
-    e = cudaGraphInstantiate(&exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return EVR_ERR_CUDA;
-    s->graphs[key] = exec;
-  } else {
-    exec = it->second;
-  }
-  // the graph's end buffer and launch count follow from the solver shape
-  if (s->shape < 0) {
-    launches = 2 * iters;
-  } else {
-    const int R = kTileShapes[s->shape].R;
-    const int passes = (iters + R - 1) / R;
-    launches = passes;
-    end_cur = (passes % 2) ? 1 - s->cur : s->cur;
   }
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (s->timing) {
@@ -523,14 +554,48 @@ int evr_solve(evr_stream* s, int iters) {
     }
     cudaEventRecord(ev.first, st);
   }
-  if (cudaGraphLaunch(exec, st) != cudaSuccess) return EVR_ERR_CUDA;
+  int launches = 0;
+  if (s->cfg >= 0 && kSolverCfgs[s->cfg].kind == 2) {
+    if (run_cfg_direct(s, s->cfg, iters)) return EVR_ERR_CUDA;
+    launches = 1;
+  } else {
+    GraphKey key{iters, s->cur};
+    auto it = s->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    int end_cur = s->cur;
+    if (it == s->graphs.end()) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return EVR_ERR_CUDA;
+      int r = enqueue_iterations(s, iters, s->cur, s->cap_stream, &launches);
+      cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
+      if (r < 0 || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return EVR_ERR_CUDA;
+      }
+      e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return EVR_ERR_CUDA;
+      s->graphs[key] = exec;
+    } else {
+      exec = it->second;
+    }
+    if (s->cfg < 0) {
+      launches = 2 * iters;
+    } else {
+      const int passes = (iters + kSolverCfgs[s->cfg].R - 1) / kSolverCfgs[s->cfg].R;
+      launches = passes;
+      end_cur = (passes % 2) ? 1 - s->cur : s->cur;
+    }
+    if (cudaGraphLaunch(exec, st) != cudaSuccess) return EVR_ERR_CUDA;
+    s->cur = end_cur;
+  }
   if (s->timing) {
     cudaEventRecord(ev.second, st);
     s->ev_used.push_back(ev);
     s->ev_launches.push_back(launches);
     s->ev_pixiters.push_back((long long)s->W * s->H * iters);
   }
-  s->cur = end_cur;
   return EVR_OK;
 }
 

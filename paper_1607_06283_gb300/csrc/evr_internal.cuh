@@ -20,10 +20,13 @@ struct DevScalars {
   long long clock;   // latest timestamp seen (stream clock)
   long long t_init;  // timestamp of never-fired pixels (valid when t_init_set)
   int t_init_set;
-  int status;        // first device-side rejection code, 0 if none
+  int status;        // first device-side error code (rejection or timeout), 0 if none
   int first_bad;     // multi-CTA validation: lowest index of an invalid event
-  int pad;
+  int abort;         // persistent solver: set by a CTA whose neighbour wait timed out
 };
+
+// Persistent solver: at most this many CTAs (one progress flag each).
+constexpr int kMaxCtas = 1024;
 
 struct Planes {
   int W, H, pitch;
@@ -42,6 +45,7 @@ struct Planes {
   int* nneg;
   DevScalars* sc;
   double* partials;
+  int* flags;  // persistent solver: passes completed by each CTA (monotonic)
 };
 
 struct SolveConsts {
@@ -54,14 +58,22 @@ struct PrologueConsts {
   int manifold, data_mode;
 };
 
-// Tiled-solver shapes: extended tile EW x EH (owned tile plus an R-pixel halo on
-// every side), 32 x NTY threads, R iterations per launch.
+// Tiled solvers.  A tile template is an extended tile of EW x EH pixels (an owned
+// tile plus an R-pixel halo on every side) processed by 32 x NTY threads.  A solver
+// configuration is a template, a halo width R and a kind:
+//   kind 1: one launch per R iterations (state in HBM/L2 between launches);
+//   kind 2: one cooperative launch per packet, state in registers, R-wide halo bands
+//           exchanged with the 8 neighbouring CTAs through L2 every R iterations.
 struct TileShape {
-  int EW, EH, NTY, R;
+  int EW, EH, NTY;
 };
-
-constexpr int kNumTileShapes = 16;
+struct SolverCfg {
+  int kind, shape, R;
+};
+constexpr int kNumTileShapes = 6;
 extern const TileShape kTileShapes[kNumTileShapes];
+constexpr int kNumSolverCfgs = 24;
+extern const SolverCfg kSolverCfgs[kNumSolverCfgs];
 
 constexpr int kGapBlocks = 304;   // fixed: the reduction order does not depend on W, H
 constexpr int kGapThreads = 256;
@@ -73,9 +85,18 @@ int launch_push(const Planes& P, const uint16_t* x, const uint16_t* y, const lon
                 const int8_t* pol, int n, void* stream);
 int launch_prologue(const Planes& P, int cur, const PrologueConsts& c, void* stream);
 int launch_unfused_iteration(const Planes& P, int cur, const SolveConsts& c, void* stream);
-int launch_tiled_pass(const Planes& P, int shape, int src, int iters, const SolveConsts& c,
-                      void* stream);
-int tiled_pass_blocks(const Planes& P, int shape);
+// kind 1: `iters` <= R iterations from buffer src into buffer 1 - src.
+int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters,
+                      const SolveConsts& c, void* stream);
+// kind 2: all `iters` iterations from buffer cur; the result lands in buffer
+// cur ^ (ceil(iters / R) & 1).  `base` is the value of every CTA's progress flag at
+// launch (flags cleared by the host start at 0; each launch adds passes - 1).
+// Returns cudaErrorCooperativeLaunchTooLarge when the grid cannot be co-resident.
+int launch_persistent(const Planes& P, const SolverCfg& cfg, int cur, int iters, int base,
+                      const SolveConsts& c, void* stream);
+// Whether the configuration can run on this sensor (tile fits, grid co-resident).
+bool solver_cfg_usable(const Planes& P, const SolverCfg& cfg);
+int solver_cfg_ctas(const Planes& P, const SolverCfg& cfg);
 int launch_gap(const Planes& P, int cur, const SolveConsts& c, double* out2, void* stream);
 
 }  // namespace evr

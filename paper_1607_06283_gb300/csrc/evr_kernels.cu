@@ -1,10 +1,11 @@
-// evr_kernels.cu -- sm_103a kernels of the event-manifold reconstruction.
+// evr_kernels.cu -- sm_103a kernels of the event-manifold reconstruction, except
+// the tiled solvers (evr_solvers.cu).
 //
 // Reinbacher, Graber, Pock, BMVC 2016.  Per packet: event scatter (Sec. 3, Sec. 3.1),
 // prologue (time surface, metric of Eq. 2 / Eq. 3, data image of Eq.
 // intensity_update), then primal-dual iterations (Eq. cont_iterates, Eq.
-// update_rules).  FP32 arithmetic with IEEE division and square root; FP64 only in
-// the gap reduction.
+// update_rules).  The unfused iteration here uses IEEE division and square root in
+// FP32; the FP64 gap reduction is the convergence check.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -17,14 +18,6 @@ namespace evr {
 constexpr int kErrOutOfRange = -2;
 constexpr int kErrBadPolarity = -3;
 constexpr int kErrNonmonotonic = -4;
-
-// {EW, EH, NTY, R}: the tile templates of k_tiled, each with a few halo widths.
-const TileShape kTileShapes[kNumTileShapes] = {
-    {32, 32, 8, 2},  {32, 32, 8, 3},  {32, 32, 8, 4},  {32, 32, 8, 6},
-    {32, 32, 16, 2}, {32, 32, 16, 3}, {32, 32, 16, 4}, {32, 32, 16, 6},
-    {32, 64, 16, 3}, {32, 64, 16, 4}, {32, 64, 16, 6}, {32, 64, 16, 8},
-    {64, 32, 8, 3},  {64, 32, 8, 4},  {64, 32, 16, 3}, {64, 32, 16, 4},
-};
 
 // ---------------------------------------------------------------- pointwise maps
 // L_g u at one pixel from the forward differences (ux, uy) (Eq. 3), with
@@ -77,7 +70,9 @@ __global__ void k_init(Planes P, float u_init, long long clock0, long long t_ini
     P.sc->t_init_set = t_init_set;
     P.sc->status = 0;
     P.sc->first_bad = INT_MAX;
+    P.sc->abort = 0;
   }
+  if (y == 0 && x < kMaxCtas) P.flags[x] = 0;
   if (x >= P.pitch || y >= P.H) return;
   size_t i = (size_t)y * P.pitch + x;
   for (int b = 0; b < 2; ++b) {
@@ -99,7 +94,8 @@ __global__ void k_init(Planes P, float u_init, long long clock0, long long t_ini
 
 int launch_init(const Planes& P, float u_init, long long clock0, long long t_init, int t_init_set,
                 void* stream) {
-  dim3 blk(32, 8), grd((P.pitch + 31) / 32, (P.H + 7) / 8);
+  int gx = (P.pitch > kMaxCtas ? P.pitch : kMaxCtas);
+  dim3 blk(32, 8), grd((gx + 31) / 32, (P.H + 7) / 8);
   k_init<<<grd, blk, 0, (cudaStream_t)stream>>>(P, u_init, clock0, t_init, t_init_set);
   return (int)cudaGetLastError();
 }
@@ -330,219 +326,6 @@ int launch_unfused_iteration(const Planes& P, int cur, const SolveConsts& c, voi
   k_primal<<<grd, blk, 0, (cudaStream_t)stream>>>(P, cur, c);
   k_dual<<<grd, blk, 0, (cudaStream_t)stream>>>(P, cur, c);
   return (int)cudaGetLastError();
-}
-
-// ---------------------------------------------------------------- tiled iterations
-// Fast forms of the two proximal maps used by the tiled solver.  The square roots
-// and the quotient use the MUFU reciprocal-square-root and reciprocal (a few ulp);
-// the KL root takes the cancellation-free branch for v < beta (same value as
-// Eq. update_rules).  beta = tau lambda sqrt(G) and fb4 = 4 beta f are per-pixel
-// constants of the packet.
-__device__ __forceinline__ float prox_kl_fast(float v, float beta, float fb4, float umin,
-                                             float umax) {
-  float d = v - beta;
-  float disc = fmaf(d, d, fb4);  // > 0: beta, f > 0
-  float sq = disc * rsqrtf(disc);
-  float rp = 0.5f * (d + sq);
-  float rn = __fdividef(0.5f * fb4, sq - d);
-  float r = (d >= 0.0f) ? rp : rn;
-  return fminf(fmaxf(r, umin), umax);
-}
-
-__device__ __forceinline__ void project_fast(float& p1, float& p2, float& p3, float sG) {
-  float n2 = fmaf(p1, p1, fmaf(p2, p2, p3 * p3));
-  float sc = (n2 > sG * sG) ? sG * rsqrtf(n2) : 1.0f;
-  p1 *= sc;
-  p2 *= sc;
-  p3 *= sc;
-}
-
-// One launch = `iters` (<= R) iterations.  CTA b owns an OW x OH tile (OW = EW - 2R)
-// and loads it with an R-pixel halo.  One iteration reads each pixel's neighbours
-// within Chebyshev distance 1 (the divergence reads q at x-1 and y-1, the forward
-// differences read ubar at x+1 and y+1, and ubar(x+1, y) depends on q(x+1, y-1)),
-// so after j iterations the values are exact on the extended tile shrunk by j:
-// after R, on the owned tile.  Thread (tx, ty) holds the pixels
-// (tx + 32 kx, KY ty + ky): pixel-local state lives in registers, vertical
-// neighbours inside the strip are registers too, and only q1 (read at x-1),
-// ubar (read at x+1) and the strip ends go through shared memory.  The image-border
-// rules (zero last column/row of the forward differences, the matching divergence)
-// are folded into two per-pixel masks: q is stored as zero where the difference
-// does not exist and off the sensor, so the divergence needs no tests.  Padded
-// shared arrays (zero) stand in for neighbours beyond the extended tile; they only
-// reach pixels outside the exact region.  State is read from buffer src and the
-// owned pixels are written to buffer 1 - src, so no CTA reads a halo that a
-// neighbour has already advanced.
-template <int KX, int KY, int NTY>
-__global__ void __launch_bounds__(32 * NTY) k_tiled(Planes P, int src, int iters, int R,
-                                                    SolveConsts c, int tiles_x) {
-  constexpr int EW = 32 * KX, EH = NTY * KY, K = KX * KY;
-  __shared__ float s_q1[EH][EW + 1];      // column 0: left pad
-  __shared__ float s_ub[EH][EW + 1];      // column EW: right pad
-  __shared__ float s_q2last[NTY + 1][EW]; // row ty+1: q2 of strip ty's last pixel; row 0 pad
-  __shared__ float s_ubfirst[NTY + 1][EW];// row ty: ubar of strip ty's first pixel; row NTY pad
-  const int W = P.W, H = P.H;
-  const int OW = EW - 2 * R, OH = EH - 2 * R;
-  const int gx0 = (int)(blockIdx.x % tiles_x) * OW - R;
-  const int gy0 = (int)(blockIdx.x / tiles_x) * OH - R;
-  const int tx0 = threadIdx.x, ty0 = threadIdx.y;
-  const int tid = ty0 * 32 + tx0;
-  for (int i = tid; i < EH; i += 32 * NTY) {
-    s_q1[i][0] = 0.0f;
-    s_ub[i][EW] = 0.0f;
-  }
-  for (int i = tid; i < EW; i += 32 * NTY) {
-    s_q2last[0][i] = 0.0f;
-    s_ubfirst[NTY][i] = 0.0f;
-  }
-  float u[K], p1[K], p2[K], p3[K], ta[K], tb[K], iG[K], sG[K], bt[K], fb4[K];
-  unsigned mx = 0, my = 0;  // bit k: forward difference in x (y) exists at pixel k
-  const float *U = P.u[src], *P1 = P.p1[src], *P2 = P.p2[src], *P3 = P.p3[src];
-  const float tl = c.tau * c.lambda;
-#pragma unroll
-  for (int kx = 0; kx < KX; ++kx) {
-#pragma unroll
-    for (int ky = 0; ky < KY; ++ky) {
-      const int k = kx * KY + ky;
-      const int gx = gx0 + tx0 + 32 * kx, gy = gy0 + KY * ty0 + ky;
-      if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-        size_t i = (size_t)gy * P.pitch + gx;
-        u[k] = U[i];
-        p1[k] = P1[i];
-        p2[k] = P2[i];
-        p3[k] = P3[i];
-        ta[k] = P.tx[i];
-        tb[k] = P.ty[i];
-        iG[k] = P.iG[i];
-        sG[k] = P.sG[i];
-        bt[k] = tl * sG[k];
-        fb4[k] = 4.0f * bt[k] * P.f[i];
-        if (gx < W - 1) mx |= 1u << k;
-        if (gy < H - 1) my |= 1u << k;
-      } else {  // off the sensor: finite filler, masked out of every neighbour term
-        u[k] = 1.0f;
-        p1[k] = p2[k] = p3[k] = 0.0f;
-        ta[k] = tb[k] = 0.0f;
-        iG[k] = sG[k] = 1.0f;
-        bt[k] = tl;
-        fb4[k] = 4.0f * tl;
-      }
-    }
-  }
-  float q1r[K], q2r[K];
-  for (int it = 0; it < iters; ++it) {
-    // q = M^T p, stored as zero where the matching difference does not exist
-#pragma unroll
-    for (int kx = 0; kx < KX; ++kx) {
-#pragma unroll
-      for (int ky = 0; ky < KY; ++ky) {
-        const int k = kx * KY + ky;
-        const int lx = tx0 + 32 * kx, ly = KY * ty0 + ky;
-        float q1, q2;
-        apply_MT(ta[k], tb[k], iG[k], p1[k], p2[k], p3[k], q1, q2);
-        q1r[k] = (mx >> k & 1u) ? q1 : 0.0f;
-        q2r[k] = (my >> k & 1u) ? q2 : 0.0f;
-        s_q1[ly][lx + 1] = q1r[k];
-        if (ky == KY - 1) s_q2last[ty0 + 1][lx] = q2r[k];
-      }
-    }
-    __syncthreads();
-    // primal step: v = u + tau div(M^T p), u+ = prox(v), ubar = 2 u+ - u
-#pragma unroll
-    for (int kx = 0; kx < KX; ++kx) {
-#pragma unroll
-      for (int ky = 0; ky < KY; ++ky) {
-        const int k = kx * KY + ky;
-        const int lx = tx0 + 32 * kx, ly = KY * ty0 + ky;
-        float q1m = s_q1[ly][lx];
-        float q2m = (ky == 0) ? s_q2last[ty0][lx] : q2r[k - 1];
-        float div = (q1r[k] - q1m) + (q2r[k] - q2m);
-        float v = fmaf(c.tau, div, u[k]);
-        float un = prox_kl_fast(v, bt[k], fb4[k], c.u_min, c.u_max);
-        float ub = 2.0f * un - u[k];
-        u[k] = un;
-        q1r[k] = ub;  // reuse: ubar of pixel k
-        s_ub[ly][lx] = ub;
-        if (ky == 0) s_ubfirst[ty0][lx] = ub;
-      }
-    }
-    __syncthreads();
-    // dual step: p = proj(p + sigma M (D_x ubar, D_y ubar))
-#pragma unroll
-    for (int kx = 0; kx < KX; ++kx) {
-#pragma unroll
-      for (int ky = 0; ky < KY; ++ky) {
-        const int k = kx * KY + ky;
-        const int lx = tx0 + 32 * kx, ly = KY * ty0 + ky;
-        const float ub = q1r[k];
-        float ubx = s_ub[ly][lx + 1];
-        float uby = (ky == KY - 1) ? s_ubfirst[ty0 + 1][lx] : q1r[k + 1];
-        float ux = (mx >> k & 1u) ? ubx - ub : 0.0f;
-        float uy = (my >> k & 1u) ? uby - ub : 0.0f;
-        float g1, g2, g3;
-        apply_M(ta[k], tb[k], iG[k], ux, uy, g1, g2, g3);
-        float a1 = fmaf(c.sigma, g1, p1[k]);
-        float a2 = fmaf(c.sigma, g2, p2[k]);
-        float a3 = fmaf(c.sigma, g3, p3[k]);
-        project_fast(a1, a2, a3, sG[k]);
-        p1[k] = a1;
-        p2[k] = a2;
-        p3[k] = a3;
-      }
-    }
-  }
-  const int dst = 1 - src;
-  float *Ud = P.u[dst], *P1d = P.p1[dst], *P2d = P.p2[dst], *P3d = P.p3[dst];
-#pragma unroll
-  for (int kx = 0; kx < KX; ++kx) {
-#pragma unroll
-    for (int ky = 0; ky < KY; ++ky) {
-      const int k = kx * KY + ky;
-      const int lx = tx0 + 32 * kx, ly = KY * ty0 + ky;
-      const int gx = gx0 + lx, gy = gy0 + ly;
-      if (lx >= R && lx < R + OW && ly >= R && ly < R + OH && gx < W && gy < H) {
-        size_t i = (size_t)gy * P.pitch + gx;
-        Ud[i] = u[k];
-        P1d[i] = p1[k];
-        P2d[i] = p2[k];
-        P3d[i] = p3[k];
-      }
-    }
-  }
-}
-
-template <int KX, int KY, int NTY>
-static int run_tiled(const Planes& P, int R, int src, int iters, const SolveConsts& c,
-                     cudaStream_t st) {
-  constexpr int EW = 32 * KX, EH = NTY * KY;
-  const int OW = EW - 2 * R, OH = EH - 2 * R;
-  if (OW < 1 || OH < 1 || iters > R) return (int)cudaErrorInvalidValue;
-  int tiles_x = (P.W + OW - 1) / OW, tiles_y = (P.H + OH - 1) / OH;
-  k_tiled<KX, KY, NTY><<<tiles_x * tiles_y, dim3(32, NTY), 0, st>>>(P, src, iters, R, c,
-                                                                    tiles_x);
-  return (int)cudaGetLastError();
-}
-
-int tiled_pass_blocks(const Planes& P, int shape) {
-  const TileShape& s = kTileShapes[shape];
-  int OW = s.EW - 2 * s.R, OH = s.EH - 2 * s.R;
-  return ((P.W + OW - 1) / OW) * ((P.H + OH - 1) / OH);
-}
-
-int launch_tiled_pass(const Planes& P, int shape, int src, int iters, const SolveConsts& c,
-                      void* stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  if (shape < 0 || shape >= kNumTileShapes) return (int)cudaErrorInvalidValue;
-  const TileShape& s = kTileShapes[shape];
-  const int key = s.EW * 10000 + s.EH * 10 + (s.NTY == 16 ? 1 : 0);
-  switch (key) {
-    case 320320: return run_tiled<1, 4, 8>(P, s.R, src, iters, c, st);     // 32x32, 256 thr
-    case 320321: return run_tiled<1, 2, 16>(P, s.R, src, iters, c, st);    // 32x32, 512 thr
-    case 320641: return run_tiled<1, 4, 16>(P, s.R, src, iters, c, st);    // 32x64, 512 thr
-    case 640320: return run_tiled<2, 4, 8>(P, s.R, src, iters, c, st);     // 64x32, 256 thr
-    case 640321: return run_tiled<2, 2, 16>(P, s.R, src, iters, c, st);    // 64x32, 512 thr
-    default: return (int)cudaErrorInvalidValue;
-  }
 }
 
 // ---------------------------------------------------------------- FP64 gap

@@ -1,0 +1,450 @@
+// evr_solvers.cu -- tiled primal-dual solvers (Eq. cont_iterates with Eq.
+// update_rules) for sm_103a.
+//
+// Both solvers give every CTA an owned tile plus an R-pixel halo.  One iteration
+// reads each pixel's neighbours within Chebyshev distance 1 (the divergence reads
+// q = M^T p at x-1 and y-1, the forward differences read ubar at x+1 and y+1, and
+// ubar(x+1, y) itself depends on q(x+1, y-1)), so after j local iterations the
+// values are exact on the extended tile shrunk by j pixels, and after R on the
+// owned tile.
+//   kind 1 (k_tiled): one launch per R iterations; state in HBM/L2 between launches.
+//   kind 2 (k_persist): one cooperative launch per packet; the tile stays in
+//     registers for all iterations, and every R iterations each CTA publishes the
+//     R-wide band along its owned border and reads its halo from the 8 neighbouring
+//     CTAs' bands through L2, synchronised by per-CTA progress flags.  Every wait is
+//     bounded; a wait that runs out sets an abort flag and EVR_ERR_TIMEOUT and the
+//     kernel returns.
+#include <cuda_runtime.h>
+
+#include "evr_internal.cuh"
+
+namespace evr {
+
+constexpr int kErrTimeout = -7;  // as in include/evr.h
+
+const TileShape kTileShapes[kNumTileShapes] = {
+    {32, 32, 8},   // 0: 256 threads, 4 px each
+    {32, 32, 16},  // 1: 512 threads, 2 px each
+    {32, 64, 16},  // 2: 512 threads, 4 px each
+    {64, 32, 8},   // 3: 256 threads, 8 px each
+    {64, 32, 16},  // 4: 512 threads, 4 px each
+    {32, 16, 8},   // 5: 256 threads, 2 px each
+};
+
+// {kind, shape, R}
+const SolverCfg kSolverCfgs[kNumSolverCfgs] = {
+    {1, 0, 2}, {1, 0, 4}, {1, 0, 6}, {1, 1, 2}, {1, 1, 4}, {1, 2, 4}, {1, 2, 6}, {1, 2, 8},
+    {1, 3, 3}, {1, 4, 4},
+    {2, 0, 1}, {2, 0, 2}, {2, 0, 3}, {2, 0, 4}, {2, 1, 1}, {2, 1, 2}, {2, 1, 3}, {2, 2, 2},
+    {2, 2, 4}, {2, 3, 2}, {2, 4, 2}, {2, 5, 1}, {2, 5, 2}, {2, 5, 3},
+};
+
+// ---------------------------------------------------------------- pointwise maps
+// L_g u at one pixel (Eq. 3) as M (ux, uy), M = (1/G)[[1+b^2, -ab], [-ab, 1+a^2], [a, b]],
+// a = L_x t, b = L_y t, iG = 1/G.
+__device__ __forceinline__ void tile_M(float a, float b, float iG, float ux, float uy,
+                                       float& g1, float& g2, float& g3) {
+  float w = b * ux - a * uy;
+  g1 = iG * (ux + b * w);
+  g2 = iG * (uy - a * w);
+  g3 = iG * (a * ux + b * uy);
+}
+
+// M^T p, whose ordinary divergence is div_g p = -L_g^* p.
+__device__ __forceinline__ void tile_MT(float a, float b, float iG, float p1, float p2,
+                                        float p3, float& q1, float& q2) {
+  float z = b * p1 - a * p2;
+  q1 = iG * (p1 + b * z + a * p3);
+  q2 = iG * (p2 - a * z + b * p3);
+}
+
+// KL proximal root with clamping (Eq. update_rules, first line) with the MUFU
+// reciprocal square root and reciprocal (a few ulp); for v < beta the root is
+// evaluated as 2 beta f / (sqrt(.) - (v - beta)), free of cancellation.
+// beta = tau lambda sqrt(G) and fb4 = 4 beta f are per-pixel constants of the packet.
+__device__ __forceinline__ float tile_prox(float v, float beta, float fb4, float umin,
+                                           float umax) {
+  float d = v - beta;
+  float disc = fmaf(d, d, fb4);  // > 0 since beta, f > 0
+  float sq = disc * rsqrtf(disc);
+  float rp = 0.5f * (d + sq);
+  float rn = __fdividef(0.5f * fb4, sq - d);
+  float r = (d >= 0.0f) ? rp : rn;
+  return fminf(fmaxf(r, umin), umax);
+}
+
+// Projection onto the metric ball |p| <= sqrt(G) (Eq. update_rules, second line).
+__device__ __forceinline__ void tile_project(float& p1, float& p2, float& p3, float sG) {
+  float n2 = fmaf(p1, p1, fmaf(p2, p2, p3 * p3));
+  float sc = (n2 > sG * sG) ? sG * rsqrtf(n2) : 1.0f;
+  p1 *= sc;
+  p2 *= sc;
+  p3 *= sc;
+}
+
+// ---------------------------------------------------------------- one tile
+template <int KX, int KY, int NTY>
+struct TileSmem {
+  static constexpr int EW = 32 * KX, EH = NTY * KY;
+  float q1[EH][EW + 1];       // column 0: left pad (zero)
+  float ub[EH][EW + 1];       // column EW: right pad (zero)
+  float q2last[NTY + 1][EW];  // row ty + 1: q2 of strip ty's last pixel; row 0 pad
+  float ubfirst[NTY + 1][EW]; // row ty: ubar of strip ty's first pixel; row NTY pad
+};
+
+// The extended tile held by one CTA.  Thread (tx, ty) holds pixels
+// (tx + 32 kx, KY ty + ky): pixel-local state in registers, vertical neighbours
+// inside the strip in registers, and only q1 (read at x-1), ubar (read at x+1) and
+// the strip ends in shared memory.  The image-border rules (forward differences
+// zero on the last column/row, the matching divergence) are two per-pixel masks:
+// q is stored as zero where its difference does not exist and off the sensor, so
+// the divergence needs no tests.
+template <int KX, int KY, int NTY>
+struct Tile {
+  static constexpr int EW = 32 * KX, EH = NTY * KY, K = KX * KY;
+  float u[K], p1[K], p2[K], p3[K], ta[K], tb[K], iG[K], sG[K], bt[K], fb4[K];
+  unsigned mx, my;  // bit k: forward difference in x (y) exists at pixel k
+  int gx0, gy0, R, OW, OH;
+
+  __device__ __forceinline__ int lx(int k) const { return threadIdx.x + 32 * (k / KY); }
+  __device__ __forceinline__ int ly(int k) const { return KY * threadIdx.y + (k % KY); }
+
+  __device__ __forceinline__ void setup(int tile, int tiles_x, int R_) {
+    R = R_;
+    OW = EW - 2 * R;
+    OH = EH - 2 * R;
+    gx0 = (tile % tiles_x) * OW - R;
+    gy0 = (tile / tiles_x) * OH - R;
+  }
+
+  __device__ __forceinline__ static void zero_pads(TileSmem<KX, KY, NTY>& sm) {
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int i = tid; i < EH; i += 32 * NTY) {
+      sm.q1[i][0] = 0.0f;
+      sm.ub[i][EW] = 0.0f;
+    }
+    for (int i = tid; i < EW; i += 32 * NTY) {
+      sm.q2last[0][i] = 0.0f;
+      sm.ubfirst[NTY][i] = 0.0f;
+    }
+  }
+
+  __device__ __forceinline__ bool on(int k, int W, int H) const {
+    const int gx = gx0 + lx(k), gy = gy0 + ly(k);
+    return gx >= 0 && gx < W && gy >= 0 && gy < H;
+  }
+  __device__ __forceinline__ bool owned(int k) const {
+    const int x = lx(k), y = ly(k);
+    return x >= R && x < R + OW && y >= R && y < R + OH;
+  }
+  __device__ __forceinline__ bool band(int k) const {  // owned, within R of the owned border
+    const int x = lx(k), y = ly(k);
+    return owned(k) && (x < 2 * R || x >= OW || y < 2 * R || y >= OH);
+  }
+  __device__ __forceinline__ size_t gidx(const Planes& P, int k) const {
+    return (size_t)(gy0 + ly(k)) * P.pitch + (gx0 + lx(k));
+  }
+
+  __device__ __forceinline__ void load(const Planes& P, int buf, const SolveConsts& c) {
+    const float tl = c.tau * c.lambda;
+    const float *U = P.u[buf], *P1 = P.p1[buf], *P2 = P.p2[buf], *P3 = P.p3[buf];
+    mx = my = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (on(k, P.W, P.H)) {
+        const size_t i = gidx(P, k);
+        u[k] = U[i];
+        p1[k] = P1[i];
+        p2[k] = P2[i];
+        p3[k] = P3[i];
+        ta[k] = P.tx[i];
+        tb[k] = P.ty[i];
+        iG[k] = P.iG[i];
+        sG[k] = P.sG[i];
+        bt[k] = tl * sG[k];
+        fb4[k] = 4.0f * bt[k] * P.f[i];
+        if (gx0 + lx(k) < P.W - 1) mx |= 1u << k;
+        if (gy0 + ly(k) < P.H - 1) my |= 1u << k;
+      } else {  // off the sensor: finite filler, masked out of every neighbour term
+        u[k] = 1.0f;
+        p1[k] = p2[k] = p3[k] = 0.0f;
+        ta[k] = tb[k] = 0.0f;
+        iG[k] = sG[k] = 1.0f;
+        bt[k] = tl;
+        fb4[k] = 4.0f * tl;
+      }
+    }
+  }
+
+  // One primal-dual iteration over the extended tile (two CTA barriers).
+  __device__ __forceinline__ void iterate(TileSmem<KX, KY, NTY>& sm, const SolveConsts& c) {
+    float q1r[K], q2r[K];
+    const int ty0 = threadIdx.y;
+    // q = M^T p, zero where the matching forward difference does not exist
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int ky = k % KY;
+      float q1, q2;
+      tile_MT(ta[k], tb[k], iG[k], p1[k], p2[k], p3[k], q1, q2);
+      q1r[k] = (mx >> k & 1u) ? q1 : 0.0f;
+      q2r[k] = (my >> k & 1u) ? q2 : 0.0f;
+      sm.q1[ly(k)][lx(k) + 1] = q1r[k];
+      if (ky == KY - 1) sm.q2last[ty0 + 1][lx(k)] = q2r[k];
+    }
+    __syncthreads();
+    // primal step: v = u + tau div(M^T p), u+ = prox(v), ubar = 2 u+ - u
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int ky = k % KY;
+      float q1m = sm.q1[ly(k)][lx(k)];
+      float q2m = (ky == 0) ? sm.q2last[ty0][lx(k)] : q2r[k - 1];
+      float div = (q1r[k] - q1m) + (q2r[k] - q2m);
+      float v = fmaf(c.tau, div, u[k]);
+      float un = tile_prox(v, bt[k], fb4[k], c.u_min, c.u_max);
+      float ub = 2.0f * un - u[k];
+      u[k] = un;
+      q1r[k] = ub;  // from here on: ubar of pixel k
+      sm.ub[ly(k)][lx(k)] = ub;
+      if (ky == 0) sm.ubfirst[ty0][lx(k)] = ub;
+    }
+    __syncthreads();
+    // dual step: p = proj(p + sigma M (D_x ubar, D_y ubar))
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int ky = k % KY;
+      const float ub = q1r[k];
+      float ubx = sm.ub[ly(k)][lx(k) + 1];
+      float uby = (ky == KY - 1) ? sm.ubfirst[ty0 + 1][lx(k)] : q1r[k + 1];
+      float ux = (mx >> k & 1u) ? ubx - ub : 0.0f;
+      float uy = (my >> k & 1u) ? uby - ub : 0.0f;
+      float g1, g2, g3;
+      tile_M(ta[k], tb[k], iG[k], ux, uy, g1, g2, g3);
+      float a1 = fmaf(c.sigma, g1, p1[k]);
+      float a2 = fmaf(c.sigma, g2, p2[k]);
+      float a3 = fmaf(c.sigma, g3, p3[k]);
+      tile_project(a1, a2, a3, sG[k]);
+      p1[k] = a1;
+      p2[k] = a2;
+      p3[k] = a3;
+    }
+  }
+
+  // Write (u, p) of the owned pixels (all of them, or only the border band).
+  __device__ __forceinline__ void store(const Planes& P, int buf, bool band_only) const {
+    float *U = P.u[buf], *P1 = P.p1[buf], *P2 = P.p2[buf], *P3 = P.p3[buf];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if ((band_only ? band(k) : owned(k)) && on(k, P.W, P.H)) {
+        const size_t i = gidx(P, k);
+        U[i] = u[k];
+        P1[i] = p1[k];
+        P2[i] = p2[k];
+        P3[i] = p3[k];
+      }
+    }
+  }
+
+  // Read (u, p) of the halo pixels from the neighbours' bands, through L2.
+  __device__ __forceinline__ void reload_halo(const Planes& P, int buf) {
+    const float *U = P.u[buf], *P1 = P.p1[buf], *P2 = P.p2[buf], *P3 = P.p3[buf];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (!owned(k) && on(k, P.W, P.H)) {
+        const size_t i = gidx(P, k);
+        u[k] = __ldcg(U + i);
+        p1[k] = __ldcg(P1 + i);
+        p2[k] = __ldcg(P2 + i);
+        p3[k] = __ldcg(P3 + i);
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------- kind 1
+template <int KX, int KY, int NTY>
+__global__ void __launch_bounds__(32 * NTY) k_tiled(Planes P, int src, int iters, int R,
+                                                    SolveConsts c, int tiles_x) {
+  __shared__ TileSmem<KX, KY, NTY> sm;
+  Tile<KX, KY, NTY> T;
+  T.setup(blockIdx.x, tiles_x, R);
+  Tile<KX, KY, NTY>::zero_pads(sm);
+  T.load(P, src, c);
+  for (int it = 0; it < iters; ++it) T.iterate(sm, c);
+  T.store(P, 1 - src, false);
+}
+
+// ---------------------------------------------------------------- kind 2
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr unsigned kSpinLimit = 1u << 21;  // polls of ~100 ns: a wait gives up after ~0.2 s
+
+template <int KX, int KY, int NTY>
+__global__ void __launch_bounds__(32 * NTY) k_persist(Planes P, int cur, int iters, int R,
+                                                      SolveConsts c, int tiles_x, int tiles_y,
+                                                      int base) {
+  __shared__ TileSmem<KX, KY, NTY> sm;
+  __shared__ int s_bail;
+  Tile<KX, KY, NTY> T;
+  const int cta = blockIdx.x;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  T.setup(cta, tiles_x, R);
+  Tile<KX, KY, NTY>::zero_pads(sm);
+  T.load(P, cur, c);
+  // progress flags count exchanges since the host last cleared them; `base` is the
+  // count every CTA reached at the end of the previous launch
+  const int passes = (iters + R - 1) / R;
+  const int bx = cta % tiles_x, by = cta / tiles_x;
+  for (int j = 0; j < passes; ++j) {
+    const int r = min(R, iters - j * R);
+    for (int it = 0; it < r; ++it) T.iterate(sm, c);
+    const int buf = cur ^ ((j + 1) & 1);
+    if (j == passes - 1) {
+      T.store(P, buf, false);
+      break;
+    }
+    T.store(P, buf, true);
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release(&P.flags[cta], base + j + 1);
+    }
+    if (tid < 32) {  // lanes 0..7 wait for one neighbour each
+      bool ok = true;
+      if (tid < 8) {
+        const int d = tid < 4 ? tid : tid + 1;  // 3x3 neighbourhood without the centre
+        const int nx = bx + d % 3 - 1, ny = by + d / 3 - 1;
+        if (nx >= 0 && nx < tiles_x && ny >= 0 && ny < tiles_y) {
+          const int* f = &P.flags[ny * tiles_x + nx];
+          const volatile int* ab = &P.sc->abort;
+          unsigned n = 0;
+          while (ld_acquire(f) < base + j + 1) {
+            if (*ab || ++n > kSpinLimit) {
+              ok = false;
+              break;
+            }
+            __nanosleep(64);
+          }
+        }
+      }
+      ok = __all_sync(0xffffffffu, ok);
+      if (tid == 0) {
+        s_bail = ok ? 0 : 1;
+        if (!ok) {
+          atomicExch(&P.sc->abort, 1);
+          atomicCAS(&P.sc->status, 0, kErrTimeout);
+        }
+      }
+    }
+    __syncthreads();
+    if (s_bail) return;
+    T.reload_halo(P, buf);
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <int KX, int KY, int NTY>
+static int tiles_of(const Planes& P, int R, int* tx, int* ty) {
+  const int OW = 32 * KX - 2 * R, OH = NTY * KY - 2 * R;
+  if (R < 1 || OW < R || OH < R) return 0;
+  *tx = (P.W + OW - 1) / OW;
+  *ty = (P.H + OH - 1) / OH;
+  return 1;
+}
+
+template <int KX, int KY, int NTY>
+static int run_tiled(const Planes& P, int R, int src, int iters, const SolveConsts& c,
+                     cudaStream_t st) {
+  int tx, ty;
+  if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters > R || iters < 1)
+    return (int)cudaErrorInvalidValue;
+  k_tiled<KX, KY, NTY><<<tx * ty, dim3(32, NTY), 0, st>>>(P, src, iters, R, c, tx);
+  return (int)cudaGetLastError();
+}
+
+template <int KX, int KY, int NTY>
+static bool persist_fits(const Planes& P, int R, int* nctas) {
+  int tx, ty;
+  if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty)) return false;
+  *nctas = tx * ty;
+  if (tx * ty > kMaxCtas) return false;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<KX, KY, NTY>, 32 * NTY,
+                                                    0) != cudaSuccess)
+    return false;
+  return tx * ty <= sms * per_sm;
+}
+
+template <int KX, int KY, int NTY>
+static int run_persist(const Planes& P, int R, int cur, int iters, int base,
+                       const SolveConsts& c, cudaStream_t st) {
+  int tx, ty, n;
+  if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters < 1) return (int)cudaErrorInvalidValue;
+  if (!persist_fits<KX, KY, NTY>(P, R, &n)) return (int)cudaErrorCooperativeLaunchTooLarge;
+  Planes Pc = P;
+  SolveConsts cc = c;
+  void* args[] = {&Pc, &cur, &iters, &R, &cc, &tx, &ty, &base};
+  return (int)cudaLaunchCooperativeKernel((const void*)k_persist<KX, KY, NTY>, dim3(tx * ty),
+                                          dim3(32, NTY), args, 0, st);
+}
+
+#define EVR_SHAPE_DISPATCH(FN, ...)                                  \
+  switch (cfg.shape) {                                               \
+    case 0: return FN<1, 4, 8>(__VA_ARGS__);                         \
+    case 1: return FN<1, 2, 16>(__VA_ARGS__);                        \
+    case 2: return FN<1, 4, 16>(__VA_ARGS__);                        \
+    case 3: return FN<2, 4, 8>(__VA_ARGS__);                         \
+    case 4: return FN<2, 2, 16>(__VA_ARGS__);                        \
+    case 5: return FN<1, 2, 8>(__VA_ARGS__);                         \
+    default: break;                                                  \
+  }
+
+int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters,
+                      const SolveConsts& c, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  EVR_SHAPE_DISPATCH(run_tiled, P, cfg.R, src, iters, c, st)
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_persistent(const Planes& P, const SolverCfg& cfg, int cur, int iters, int base,
+                      const SolveConsts& c, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  EVR_SHAPE_DISPATCH(run_persist, P, cfg.R, cur, iters, base, c, st)
+  return (int)cudaErrorInvalidValue;
+}
+
+template <int KX, int KY, int NTY>
+static bool usable(const Planes& P, const SolverCfg& cfg) {
+  int tx, ty, n;
+  if (cfg.kind == 1) return tiles_of<KX, KY, NTY>(P, cfg.R, &tx, &ty) != 0;
+  if (cfg.kind == 2) return persist_fits<KX, KY, NTY>(P, cfg.R, &n);
+  return false;
+}
+
+template <int KX, int KY, int NTY>
+static int ctas(const Planes& P, const SolverCfg& cfg) {
+  int tx = 0, ty = 0;
+  tiles_of<KX, KY, NTY>(P, cfg.R, &tx, &ty);
+  return tx * ty;
+}
+
+bool solver_cfg_usable(const Planes& P, const SolverCfg& cfg) {
+  EVR_SHAPE_DISPATCH(usable, P, cfg)
+  return false;
+}
+
+int solver_cfg_ctas(const Planes& P, const SolverCfg& cfg) {
+  EVR_SHAPE_DISPATCH(ctas, P, cfg)
+  return 0;
+}
+
+}  // namespace evr

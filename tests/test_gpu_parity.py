@@ -37,7 +37,8 @@ def oracle_params(p, **kw):
         data_mode=int(p.data_mode), manifold=int(p.manifold), **kw)
 
 
-SOLVERS = [("unfused", 1, 0)] + [(f"tiled{k}", 2, k) for k in range(1, 17)]
+N_CFGS = 24  # solver configurations selectable with evr_params.tile_config = 1..N_CFGS
+SOLVERS = [("unfused", 1, 0)] + [(f"cfg{k}", 2, k) for k in range(1, N_CFGS + 1)]
 
 
 def make_pair(E, W, H, solver=2, tile=0, **over):
@@ -177,7 +178,7 @@ def test_free_running_drift_rects128(E, rects128):
 
 @pytest.mark.parametrize("W,H", [(1, 1), (1, 9), (9, 1), (2, 2), (33, 17), (65, 31), (100, 3),
                                  (3, 100), (57, 57)])
-@pytest.mark.parametrize("name,solver,tile", [SOLVERS[0], SOLVERS[1], SOLVERS[12], SOLVERS[13]])
+@pytest.mark.parametrize("name,solver,tile", [SOLVERS[0], SOLVERS[1], SOLVERS[11], SOLVERS[20], SOLVERS[24]])
 def test_ragged_sizes(E, W, H, name, solver, tile):
     rng = np.random.default_rng(W * 1000 + H)
     g, o = make_pair(E, W, H, solver=solver, tile=tile)
