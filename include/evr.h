@@ -151,6 +151,8 @@ int evr_get_image_device(evr_stream* s, float* out_dev, size_t len);
 #define EVR_STATE_CLOCK 8   /* int64[1], latest timestamp */
 #define EVR_STATE_TINIT 9   /* int64[1], timestamp of never-fired pixels (0 if unset) */
 #define EVR_STATE_SQRTG 10  /* float, sqrt(G) of the last solve */
+#define EVR_STATE_TX 11     /* float, L_x t of the last solve (Eq. 3) */
+#define EVR_STATE_TY 12     /* float, L_y t of the last solve */
 
 /* Copy a state plane to host memory (bytes = its exact size); synchronises.
  * Returns the first pending device-side rejection, if any. */

@@ -624,6 +624,8 @@ static void* plane_ptr(evr_stream* s, int which, size_t* elem) {
     case EVR_STATE_P3: return s->P.p3[s->cur];
     case EVR_STATE_F: return s->P.f;
     case EVR_STATE_SQRTG: return s->P.sG;
+    case EVR_STATE_TX: return s->P.tx;
+    case EVR_STATE_TY: return s->P.ty;
     case EVR_STATE_NPOS: return s->P.npos;
     case EVR_STATE_NNEG: return s->P.nneg;
     case EVR_STATE_TLAST: *elem = 8; return s->P.t_last;

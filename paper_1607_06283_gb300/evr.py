@@ -29,7 +29,8 @@ EVR_ERR_NOT_SUPPORTED = -8
 EVR_T_INIT_FIRST = -(2 ** 63)
 EVR_SOLVER_AUTO, EVR_SOLVER_UNFUSED, EVR_SOLVER_TILED = 0, 1, 2
 (EVR_STATE_U, EVR_STATE_P1, EVR_STATE_P2, EVR_STATE_P3, EVR_STATE_F, EVR_STATE_TLAST,
- EVR_STATE_NPOS, EVR_STATE_NNEG, EVR_STATE_CLOCK, EVR_STATE_TINIT, EVR_STATE_SQRTG) = range(11)
+ EVR_STATE_NPOS, EVR_STATE_NNEG, EVR_STATE_CLOCK, EVR_STATE_TINIT, EVR_STATE_SQRTG,
+ EVR_STATE_TX, EVR_STATE_TY) = range(13)
 
 
 class EvrError(RuntimeError):
@@ -185,6 +186,7 @@ def evr_get_image_device(h, out) -> None:
 
 _STATE_DT = {EVR_STATE_U: np.float32, EVR_STATE_P1: np.float32, EVR_STATE_P2: np.float32,
              EVR_STATE_P3: np.float32, EVR_STATE_F: np.float32, EVR_STATE_SQRTG: np.float32,
+             EVR_STATE_TX: np.float32, EVR_STATE_TY: np.float32,
              EVR_STATE_TLAST: np.int64, EVR_STATE_NPOS: np.int32, EVR_STATE_NNEG: np.int32}
 
 

@@ -108,6 +108,8 @@ def test_scatter_bit_exact(E, path, W, H, per, dense):
     np.testing.assert_array_equal(g.state(E.EVR_STATE_NPOS), 0)
     np.testing.assert_allclose(g.state(E.EVR_STATE_F), o.get(O.F), rtol=2e-6)
     np.testing.assert_allclose(g.state(E.EVR_STATE_SQRTG), np.sqrt(o.get(O.G)), rtol=2e-6)
+    np.testing.assert_allclose(g.state(E.EVR_STATE_TX), o.get(O.TX), rtol=2e-6, atol=1e-5)
+    np.testing.assert_allclose(g.state(E.EVR_STATE_TY), o.get(O.TY), rtol=2e-6, atol=1e-5)
 
 
 @pytest.mark.parametrize("bad,code", [("x", -2), ("y", -2), ("pol", -3), ("t", -4), ("clock", -4)])
