@@ -168,6 +168,29 @@ int evr_set_state(evr_stream* s, int which, const void* in_host, size_t bytes);
  * primal - dual >= 0 is the convergence check.  Synchronises. */
 int evr_gap(evr_stream* s, double* primal, double* dual);
 
+/* Largest image (W*H pixels) that evr_gap_static accepts. */
+#define EVR_GAP_STATIC_MAX_PIXELS 4194304
+
+/* The FP64 primal energy and dual value of evr_gap, computed from caller-provided
+ * device planes without allocating any device memory.  The paper has no counterpart:
+ * it exists for callers that may not allocate once they are running -- a real-time
+ * loop that cannot afford cudaMalloc's implicit device synchronisation, or a host
+ * application that owns all device memory through its own pool.
+ *   u, p1, p2, p3, f, tx, ty: device planes of H rows of `pitch` floats (pitch >= W,
+ *     row-major, x the column), as read back from a stream (u, p, f, L_x t, L_y t);
+ *   lambda, u_min, u_max: the model's parameters;
+ *   out_dev: device memory for 2 doubles, receives {primal, dual};
+ *   cuda_stream: cudaStream_t to queue on (NULL: the legacy default stream).
+ * Asynchronous.  The reduction's scratch is one fixed 24 KiB device array inside the
+ * library (held by every GPU that loads it until the process exits) and shared by
+ * all calls: calls whose work overlaps on the GPU race on it.  The first call on a
+ * device looks up the array's address; make that first call before any stream
+ * capture.  Errors: EVR_ERR_INVALID_ARG (null pointer, W or H <= 0, pitch < W,
+ * W*H > EVR_GAP_STATIC_MAX_PIXELS, lambda <= 0, bad box), EVR_ERR_CUDA. */
+int evr_gap_static(const float* u, const float* p1, const float* p2, const float* p3,
+                   const float* f, const float* tx, const float* ty, int W, int H, int pitch,
+                   float lambda, float u_min, float u_max, double* out_dev, void* cuda_stream);
+
 /* Wait for the handle's queued work; returns the first pending device-side
  * rejection (then clears it), EVR_ERR_CUDA, or EVR_OK. */
 int evr_synchronize(evr_stream* s);

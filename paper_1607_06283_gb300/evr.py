@@ -84,6 +84,8 @@ def _load():
         "evr_kernel_time": ([vp, vp, vp, vp], i),
         "evr_solver_name": ([vp], ctypes.c_char_p),
         "evr_strerror": ([i], ctypes.c_char_p),
+        "evr_gap_static": ([vp] * 7 + [i, i, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                       vp, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -212,6 +214,19 @@ def evr_gap(h):
     if rc in (EVR_ERR_INVALID_ARG, EVR_ERR_CUDA):
         _check(rc, "evr_gap")
     return pr.value, du.value
+
+
+EVR_GAP_STATIC_MAX_PIXELS = 4194304
+
+
+def evr_gap_static(u, p1, p2, p3, f, tx, ty, W: int, H: int, pitch: int, lam: float,
+                   u_min: float, u_max: float, out, stream_handle: int = 0) -> int:
+    """Gap of caller-provided device planes (torch CUDA tensors) into `out`
+    (a CUDA float64 tensor of 2 elements); allocates no device memory.  Returns the
+    library's code."""
+    ptrs = [a.data_ptr() for a in (u, p1, p2, p3, f, tx, ty)]
+    return _lib.evr_gap_static(*ptrs, int(W), int(H), int(pitch), float(lam), float(u_min),
+                               float(u_max), out.data_ptr(), ctypes.c_void_p(int(stream_handle)))
 
 
 def evr_synchronize(h) -> int:
