@@ -57,10 +57,11 @@ def dist_env():
 
 def workload(name, rank):
     from evsim import CONFIGS, make_stream
+    from paper_1607_06283_gb300.shard import stream_seed
     cfg = CONFIGS[name]
     if rank:
         d = dict(cfg.__dict__)
-        d["seed"] = cfg.seed + 7 * rank
+        d["seed"] = stream_seed(cfg.seed, rank)
         cfg = type(cfg)(**d)
     return cfg, make_stream(cfg)
 
@@ -311,16 +312,8 @@ def run_ours(args):
     if status:
         raise RuntimeError(f"device-side rejection during the run: {status}")
     ev_timed = int(offs[n_all] - offs[args.warmup])
-    t_max = ms_steps
-    if pg:
-        tt = torch.tensor([ms_steps], dtype=torch.float64, device="cuda")
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_max = float(tt.item())
-        ev_t = torch.tensor([ev_timed], dtype=torch.float64, device="cuda")
-        pg.all_reduce(ev_t)
-        ev_total = float(ev_t.item())
-    else:
-        ev_total = float(ev_timed)
+    from paper_1607_06283_gb300.shard import reduce_timing
+    t_max, ev_total = reduce_timing(ms_steps, ev_timed, pg, "cuda")
     value = ev_total / (t_max * 1e-3)
     gpix = world * args.steps * cfg.W * cfg.H * cfg.iters / (t_max * 1e-3) / 1e9
 
@@ -351,10 +344,7 @@ def run_ours(args):
     for j in range(args.steps):
         step_host(args.warmup + j)
     e2e_s = time.perf_counter() - e0
-    if pg:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s, _ = reduce_timing(e2e_s, 0.0, pg, "cuda")
     e2e_val = ev_total / e2e_s
 
     if rank == 0:

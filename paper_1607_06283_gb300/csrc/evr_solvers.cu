@@ -145,18 +145,14 @@ struct Tile {
     return (size_t)(gy0 + ly(k)) * P.pitch + (gx0 + lx(k));
   }
 
-  __device__ __forceinline__ void load(const Planes& P, int buf, const SolveConsts& c) {
+  // Packet constants: metric, beta = tau lambda sqrt(G), 4 beta f, border masks.
+  __device__ __forceinline__ void load_consts(const Planes& P, const SolveConsts& c) {
     const float tl = c.tau * c.lambda;
-    const float *U = P.u[buf], *P1 = P.p1[buf], *P2 = P.p2[buf], *P3 = P.p3[buf];
     mx = my = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (on(k, P.W, P.H)) {
         const size_t i = gidx(P, k);
-        u[k] = U[i];
-        p1[k] = P1[i];
-        p2[k] = P2[i];
-        p3[k] = P3[i];
         ta[k] = P.tx[i];
         tb[k] = P.ty[i];
         iG[k] = P.iG[i];
@@ -166,14 +162,35 @@ struct Tile {
         if (gx0 + lx(k) < P.W - 1) mx |= 1u << k;
         if (gy0 + ly(k) < P.H - 1) my |= 1u << k;
       } else {  // off the sensor: finite filler, masked out of every neighbour term
-        u[k] = 1.0f;
-        p1[k] = p2[k] = p3[k] = 0.0f;
         ta[k] = tb[k] = 0.0f;
         iG[k] = sG[k] = 1.0f;
         bt[k] = tl;
         fb4[k] = 4.0f * tl;
       }
     }
+  }
+
+  // Iterated state (u, p) from buffer buf.
+  __device__ __forceinline__ void load_state(const Planes& P, int buf) {
+    const float *U = P.u[buf], *P1 = P.p1[buf], *P2 = P.p2[buf], *P3 = P.p3[buf];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (on(k, P.W, P.H)) {
+        const size_t i = gidx(P, k);
+        u[k] = U[i];
+        p1[k] = P1[i];
+        p2[k] = P2[i];
+        p3[k] = P3[i];
+      } else {
+        u[k] = 1.0f;
+        p1[k] = p2[k] = p3[k] = 0.0f;
+      }
+    }
+  }
+
+  __device__ __forceinline__ void load(const Planes& P, int buf, const SolveConsts& c) {
+    load_consts(P, c);
+    load_state(P, buf);
   }
 
   // One primal-dual iteration over the extended tile (two CTA barriers).
@@ -261,6 +278,11 @@ struct Tile {
 };
 
 // ---------------------------------------------------------------- kind 1
+// Launched with programmatic stream serialisation: a pass may start while the
+// previous one drains.  It first loads the packet constants (written by the
+// prologue, which finished before the previous pass got past its own wait), then
+// waits for the previous pass to complete before reading (u, p), and only then lets
+// the next pass launch -- so no pass can run ahead of the prologue.
 template <int KX, int KY, int NTY>
 __global__ void __launch_bounds__(32 * NTY) k_tiled(Planes P, int src, int iters, int R,
                                                     SolveConsts c, int tiles_x) {
@@ -268,7 +290,10 @@ __global__ void __launch_bounds__(32 * NTY) k_tiled(Planes P, int src, int iters
   Tile<KX, KY, NTY> T;
   T.setup(blockIdx.x, tiles_x, R);
   Tile<KX, KY, NTY>::zero_pads(sm);
-  T.load(P, src, c);
+  T.load_consts(P, c);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+  T.load_state(P, src);
   for (int it = 0; it < iters; ++it) T.iterate(sm, c);
   T.store(P, 1 - src, false);
 }
@@ -364,8 +389,16 @@ static int run_tiled(const Planes& P, int R, int src, int iters, const SolveCons
   int tx, ty;
   if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters > R || iters < 1)
     return (int)cudaErrorInvalidValue;
-  k_tiled<KX, KY, NTY><<<tx * ty, dim3(32, NTY), 0, st>>>(P, src, iters, R, c, tx);
-  return (int)cudaGetLastError();
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(tx * ty);
+  lc.blockDim = dim3(32, NTY);
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&lc, k_tiled<KX, KY, NTY>, P, src, iters, R, c, tx);
 }
 
 template <int KX, int KY, int NTY>
