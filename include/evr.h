@@ -191,6 +191,52 @@ int evr_gap_static(const float* u, const float* p1, const float* p2, const float
                    const float* f, const float* tx, const float* ty, int W, int H, int pitch,
                    float lambda, float u_min, float u_max, double* out_dev, void* cuda_stream);
 
+/* ---- differentiation of one packet's solve (no counterpart in the paper's text:
+ * the adjoint of its iteration, Eq. cont_iterates with Eq. update_rules) ----
+ * The solve is u_K = S(u_0, p_0, f, lambda) with the metric fixed: K unrolled
+ * iterations.  The calls below are stateless and allocate nothing: every plane is
+ * caller-owned device memory of H rows of `pitch` floats (pitch >= W, x the column);
+ * a dual variable p is 3 such planes back to back (plane stride pitch*H).  tx, ty are
+ * L_x t, L_y t of the packet (evr_get_state EVR_STATE_TX / EVR_STATE_TY).  All work is
+ * queued on cuda_stream (NULL: legacy default stream).  Errors: EVR_ERR_INVALID_ARG
+ * (null pointer, W or H <= 0, pitch < W, K < 1, every < 1), EVR_ERR_CUDA. */
+
+/* Workspace bytes for evr_unrolled_forward/backward (0 for invalid sizes). */
+size_t evr_unrolled_workspace_bytes(int W, int H, int pitch, int K, int every);
+
+/* K iterations from (u0, p0) (FP32, IEEE division and square root), storing (u, p)
+ * checkpoints every `every` iterations in `workspace`; result in u_out, p_out. */
+int evr_unrolled_forward(const float* tx, const float* ty, const float* f, const float* u0,
+                         const float* p0, int W, int H, int pitch, float lambda, float tau,
+                         float sigma, float u_min, float u_max, int K, int every,
+                         void* workspace, float* u_out, float* p_out, void* cuda_stream);
+
+/* Reverse mode after evr_unrolled_forward with the same arguments and workspace:
+ * from gu_K = dL/du_K and gp_K = dL/dp_K (3 planes; NULL means 0), recompute each
+ * checkpoint segment and walk the adjoint back: gu0 = dL/du0 and gp0 = dL/dp0
+ * (either may be NULL), gf = dL/df, and glambda_dev[0] = dL/dlambda (device double,
+ * FP64 reduction).  Clamped pixels and the projection are differentiated on their
+ * active side. */
+int evr_unrolled_backward(const float* tx, const float* ty, const float* f, int W, int H,
+                          int pitch, float lambda, float tau, float sigma, float u_min,
+                          float u_max, int K, int every, void* workspace, const float* gu_K,
+                          const float* gp_K, float* gu0, float* gp0, float* gf,
+                          double* glambda_dev, void* cuda_stream);
+
+/* Data image f = u_prev exp(Delta+ n+ - Delta- n-) (Eq. intensity_update, one factor
+ * per event, compounded) from the packet's event counts. */
+int evr_data_image(const float* u_prev, const int32_t* npos, const int32_t* nneg, int W, int H,
+                   int pitch, float delta_pos, float delta_neg, float* f_out,
+                   void* cuda_stream);
+
+/* Its backward: g_uprev = dL/du_prev (may be NULL) and g_delta_dev[0..1] =
+ * (dL/dDelta+, dL/dDelta-) in FP64 from gf = dL/df.  scratch: caller-owned device
+ * memory of 2*pitch*H + 1024 doubles. */
+int evr_data_image_backward(const float* f, const float* u_prev, const int32_t* npos,
+                            const int32_t* nneg, int W, int H, int pitch, float delta_pos,
+                            float delta_neg, const float* gf, float* g_uprev, double* scratch,
+                            double* g_delta_dev, void* cuda_stream);
+
 /* Wait for the handle's queued work; returns the first pending device-side
  * rejection (then clears it), EVR_ERR_CUDA, or EVR_OK. */
 int evr_synchronize(evr_stream* s);

@@ -163,6 +163,127 @@ void orc_pd_iterations(int W, int H, const double* tx, const double* ty, const d
   free(g3);
 }
 
+/* Reverse mode through Eq. cont_iterates.  One forward iteration maps (u, p) to
+ *   d  = div_g p = div(M^T p)             (= -L_g^T p)
+ *   v  = u + tau d
+ *   r  = 1/2 (v - beta + sqrt((v - beta)^2 + 4 beta f)),  beta = tau lambda sqrt(G)
+ *   u' = clamp(r, u_min, u_max)
+ *   ub = 2 u' - u
+ *   pt = p + sigma L_g ub
+ *   p' = pt / max(1, |pt| / sqrt(G))
+ * and the adjoint walks these steps backwards with the chain rule:
+ *   a_pt = J_proj a_p'   (J = identity inside the ball, else
+ *                         (sqrt G/|pt|)(I - pt pt^T/|pt|^2))
+ *   a_p += a_pt;  a_ub = L_g^T (sigma a_pt) = -div_g(sigma a_pt)
+ *   a_u' += 2 a_ub;  a_u = -a_ub
+ *   a_r = a_u' [clamp inactive];  a_v = a_r dr/dv;  a_beta = a_r dr/dbeta;
+ *   a_f += a_r dr/df;  a_lambda += a_beta tau sqrt(G)
+ *   a_u += a_v;  a_p += -L_g (tau a_v)     (d = -L_g^T p)
+ * with dr/dv = (1 + (v-beta)/s)/2, dr/dbeta = (-1 + (2f - v + beta)/s)/2,
+ * dr/df = beta/s, s = sqrt((v-beta)^2 + 4 beta f). */
+void orc_pd_grad(int W, int H, const double* tx, const double* ty, const double* G,
+                 const double* f, const double* u0, const double* p0, int K, double tau,
+                 double sigma, double lambda, double u_min, double u_max, const double* gu_K,
+                 double* gu0, double* gp0, double* gf, double* glambda) {
+  int n = W * H;
+  size_t bytes = sizeof(double) * (size_t)n;
+  /* tape: (u_k, p_k) for k = 0..K */
+  double* tu = (double*)malloc(bytes * (size_t)(K + 1));
+  double* tp = (double*)malloc(3 * bytes * (size_t)(K + 1));
+  memcpy(tu, u0, bytes);
+  memcpy(tp, p0, 3 * bytes);
+  for (int k = 0; k < K; ++k) {
+    memcpy(tu + (size_t)(k + 1) * n, tu + (size_t)k * n, bytes);
+    memcpy(tp + (size_t)(k + 1) * 3 * n, tp + (size_t)k * 3 * n, 3 * bytes);
+    double* pk = tp + (size_t)(k + 1) * 3 * n;
+    orc_pd_iterations(W, H, tx, ty, G, f, tu + (size_t)(k + 1) * n, pk, pk + n, pk + 2 * n, 1,
+                      tau, sigma, lambda, u_min, u_max);
+  }
+  double* au = (double*)malloc(bytes);
+  double* ap = (double*)malloc(3 * bytes);
+  double* d = (double*)malloc(bytes);
+  double* v = (double*)malloc(bytes);
+  double* un = (double*)malloc(bytes);
+  double* ub = (double*)malloc(bytes);
+  double* g = (double*)malloc(3 * bytes);
+  double* apt = (double*)malloc(3 * bytes);
+  double* aub = (double*)malloc(bytes);
+  double* av = (double*)malloc(bytes);
+  double* lv = (double*)malloc(3 * bytes);
+  memcpy(au, gu_K, bytes);
+  memset(ap, 0, 3 * bytes);
+  memset(gf, 0, bytes);
+  double gl = 0.0;
+  for (int k = K - 1; k >= 0; --k) {
+    const double* u = tu + (size_t)k * n;
+    const double* p = tp + (size_t)k * 3 * n;
+    /* recompute the iteration's intermediates */
+    orc_divg(W, H, tx, ty, G, p, p + n, p + 2 * n, d);
+    for (int i = 0; i < n; ++i) {
+      v[i] = u[i] + tau * d[i];
+      un[i] = orc_prox_kl(v[i], tau * lambda * sqrt(G[i]), f[i], u_min, u_max);
+      ub[i] = 2.0 * un[i] - u[i];
+    }
+    orc_Lg(W, H, tx, ty, G, ub, g, g + n, g + 2 * n);
+    /* dual step backwards */
+    for (int i = 0; i < n; ++i) {
+      double pt[3] = {p[i] + sigma * g[i], p[n + i] + sigma * g[n + i],
+                      p[2 * n + i] + sigma * g[2 * n + i]};
+      double nrm = sqrt(pt[0] * pt[0] + pt[1] * pt[1] + pt[2] * pt[2]);
+      double sG = sqrt(G[i]);
+      double a[3] = {ap[i], ap[n + i], ap[2 * n + i]};
+      if (nrm > sG) {
+        double dot = (pt[0] * a[0] + pt[1] * a[1] + pt[2] * a[2]) / (nrm * nrm);
+        for (int c = 0; c < 3; ++c) a[c] = (sG / nrm) * (a[c] - pt[c] * dot);
+      }
+      for (int c = 0; c < 3; ++c) {
+        apt[c * n + i] = a[c];
+        ap[c * n + i] = a[c]; /* a_p (from pt = p + ...) */
+        lv[c * n + i] = sigma * a[c];
+      }
+    }
+    orc_divg(W, H, tx, ty, G, lv, lv + n, lv + 2 * n, aub); /* div_g(sigma a_pt) */
+    for (int i = 0; i < n; ++i) aub[i] = -aub[i];            /* L_g^T = -div_g */
+    /* over-relaxation and primal step backwards */
+    for (int i = 0; i < n; ++i) {
+      double aun = au[i] + 2.0 * aub[i];
+      double anew_u = -aub[i];
+      double beta = tau * lambda * sqrt(G[i]);
+      double dd = v[i] - beta;
+      double s = sqrt(dd * dd + 4.0 * beta * f[i]);
+      double r = 0.5 * (dd + s);
+      double ar = (r < u_min || r > u_max) ? 0.0 : aun;
+      double drdv = 0.5 * (1.0 + dd / s);
+      double drdb = 0.5 * (-1.0 + (2.0 * f[i] - v[i] + beta) / s);
+      double drdf = beta / s;
+      av[i] = ar * drdv;
+      gf[i] += ar * drdf;
+      gl += ar * drdb * tau * sqrt(G[i]);
+      au[i] = anew_u + av[i];
+      lv[i] = tau * av[i];
+    }
+    orc_Lg(W, H, tx, ty, G, lv, g, g + n, g + 2 * n); /* L_g(tau a_v) */
+    for (int c = 0; c < 3; ++c)
+      for (int i = 0; i < n; ++i) ap[c * n + i] -= g[c * n + i];
+  }
+  memcpy(gu0, au, bytes);
+  memcpy(gp0, ap, 3 * bytes);
+  *glambda = gl;
+  free(tu);
+  free(tp);
+  free(au);
+  free(ap);
+  free(d);
+  free(v);
+  free(un);
+  free(ub);
+  free(g);
+  free(apt);
+  free(aub);
+  free(av);
+  free(lv);
+}
+
 /* Primal energy, Eq. 5: ||L_g u||_g + lambda sum (u - f log u) sqrt(G), with the
  * g-tensor norm ||A||_g = sum_ij sqrt(G_ij sum_l A_ijl^2).
  * Dual function of Eq. primal_dual_energy for feasible p (R^* = 0):

@@ -87,6 +87,17 @@ void orc_energy(int W, int H, const double* tx, const double* ty, const double* 
                 const double* p3, double lambda, double u_min, double u_max,
                 double* primal, double* dual);
 
+/* Reverse-mode derivative of orc_pd_iterations (K iterations from (u0, p0) with
+ * fixed metric and f) for a loss L with given dL/du_K (gu_K[W*H]).  Outputs:
+ * gu0[W*H] = dL/du0, gp0[3*W*H] = dL/dp0 (planes p1, p2, p3), gf[W*H] = dL/df,
+ * *glambda = dL/dlambda.  Clamped pixels and the projection's kink are
+ * differentiated on their active side (derivative 0 through an active clamp).
+ * Every intermediate (u, p) is kept (plain full tape). */
+void orc_pd_grad(int W, int H, const double* tx, const double* ty, const double* G,
+                 const double* f, const double* u0, const double* p0, int K, double tau,
+                 double sigma, double lambda, double u_min, double u_max, const double* gu_K,
+                 double* gu0, double* gp0, double* gf, double* glambda);
+
 /* ---- a stream: events in, one image per packet out ---- */
 typedef struct orc_stream orc_stream;
 

@@ -87,6 +87,8 @@ def _lib_handle():
             lib.orc_project.argtypes = [d, d, d, d, _D]
             lib.orc_pd_iterations.argtypes = [i, i, _D, _D, _D, _D, _D, _D, _D, _D,
                                               i, d, d, d, d, d]
+            lib.orc_pd_grad.argtypes = [i, i, _D, _D, _D, _D, _D, _D, i, d, d, d, d, d, _D,
+                                        _D, _D, _D, _D]
             lib.orc_energy.argtypes = [i, i, _D, _D, _D, _D, _D, _D, _D, _D, d, d, d, _D, _D]
             lib.orc_create.argtypes = [i, i, ctypes.POINTER(_Params)]
             lib.orc_create.restype = vp
@@ -171,6 +173,20 @@ def pd_iterations(tx, ty, G, f, u, p, K, tau, sigma, lam, u_min, u_max):
                                     _dp(p[0]), _dp(p[1]), _dp(p[2]), int(K), float(tau),
                                     float(sigma), float(lam), float(u_min), float(u_max))
     return u, p
+
+
+def pd_grad(tx, ty, G, f, u0, p0, K, tau, sigma, lam, u_min, u_max, gu_K):
+    """Reverse-mode derivative of pd_iterations for dL/du_K = gu_K:
+    returns (dL/du0, dL/dp0 (3,H,W), dL/df, dL/dlambda)."""
+    tx, ty, G, f, u0, gu_K = (_f64(a) for a in (tx, ty, G, f, u0, gu_K))
+    p0 = _f64(p0)
+    H, W = u0.shape
+    gu0, gp0, gf = np.empty_like(u0), np.empty((3, H, W)), np.empty_like(u0)
+    gl = ctypes.c_double()
+    _lib_handle().orc_pd_grad(W, H, _dp(tx), _dp(ty), _dp(G), _dp(f), _dp(u0), _dp(p0), int(K),
+                              float(tau), float(sigma), float(lam), float(u_min), float(u_max),
+                              _dp(gu_K), _dp(gu0), _dp(gp0), _dp(gf), ctypes.byref(gl))
+    return gu0, gp0, gf, gl.value
 
 
 def energy(tx, ty, G, f, u, p, lam, u_min, u_max):

@@ -1,0 +1,435 @@
+// evr_grad.cu -- differentiation of one packet's solve (K unrolled iterations of
+// Eq. cont_iterates with Eq. update_rules) by a hand-written adjoint, with (u, p)
+// checkpoints every `every` iterations.  FP32 kernels with IEEE division and square
+// root; the lambda gradient and the contrast-threshold sums are reduced in FP64.
+//
+// All memory (inputs, outputs and the workspace) belongs to the caller; nothing here
+// allocates.  Planes are H rows of `pitch` floats; a dual variable is 3 such planes
+// back to back (plane stride pitch * H).
+#include <cuda_runtime.h>
+
+#include "../../include/evr.h"
+
+namespace {
+
+constexpr int kRedBlocks = 256;
+constexpr int kRedThreads = 256;
+
+struct Geo {
+  int W, H, pitch;
+  size_t plane;  // pitch * H
+};
+
+struct Coef {
+  float tau, sigma, lambda, u_min, u_max;
+};
+
+// metric at pixel i from L_x t, L_y t: M = (1/G)[[1+b^2,-ab],[-ab,1+a^2],[a,b]] (Eq. 3)
+__device__ __forceinline__ void metric(const float* tx, const float* ty, size_t i, float& a,
+                                       float& b, float& iG, float& sG) {
+  a = tx[i];
+  b = ty[i];
+  float G = 1.0f + a * a + b * b;
+  iG = 1.0f / G;
+  sG = sqrtf(G);
+}
+
+__device__ __forceinline__ void MT(float a, float b, float iG, float p1, float p2, float p3,
+                                   float& q1, float& q2) {
+  float z = b * p1 - a * p2;
+  q1 = iG * (p1 + b * z + a * p3);
+  q2 = iG * (p2 - a * z + b * p3);
+}
+
+__device__ __forceinline__ void Mg(float a, float b, float iG, float ux, float uy, float& g1,
+                                   float& g2, float& g3) {
+  float w = b * ux - a * uy;
+  g1 = iG * (ux + b * w);
+  g2 = iG * (uy - a * w);
+  g3 = iG * (a * ux + b * uy);
+}
+
+// div(M^T q) at (x, y) for a 3-plane field q (div_g q = -L_g^T q)
+__device__ __forceinline__ float div_g(const Geo& g, const float* tx, const float* ty,
+                                       const float* q, int x, int y) {
+  const size_t i = (size_t)y * g.pitch + x;
+  float a, b, iG, sG, q1, q2, q1m = 0.0f, q2m = 0.0f, d;
+  metric(tx, ty, i, a, b, iG, sG);
+  MT(a, b, iG, q[i], q[g.plane + i], q[2 * g.plane + i], q1, q2);
+  if (x > 0) {
+    metric(tx, ty, i - 1, a, b, iG, sG);
+    MT(a, b, iG, q[i - 1], q[g.plane + i - 1], q[2 * g.plane + i - 1], q1m, d);
+  }
+  if (y > 0) {
+    const size_t j = i - g.pitch;
+    metric(tx, ty, j, a, b, iG, sG);
+    MT(a, b, iG, q[j], q[g.plane + j], q[2 * g.plane + j], d, q2m);
+  }
+  return ((x < g.W - 1) ? q1 : 0.0f) - q1m + ((y < g.H - 1) ? q2 : 0.0f) - q2m;
+}
+
+// L_g w at (x, y) for a scalar plane w
+__device__ __forceinline__ void Lg(const Geo& g, const float* tx, const float* ty,
+                                   const float* w, int x, int y, float& g1, float& g2,
+                                   float& g3) {
+  const size_t i = (size_t)y * g.pitch + x;
+  float a, b, iG, sG;
+  metric(tx, ty, i, a, b, iG, sG);
+  float wx = (x < g.W - 1) ? w[i + 1] - w[i] : 0.0f;
+  float wy = (y < g.H - 1) ? w[i + g.pitch] - w[i] : 0.0f;
+  Mg(a, b, iG, wx, wy, g1, g2, g3);
+}
+
+#define PIXEL                                             \
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;     \
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;     \
+  if (x >= g.W || y >= g.H) return;                        \
+  const size_t i = (size_t)y * g.pitch + x;
+
+// ---- forward iteration (reads state k, writes state k+1 and ubar) ----
+__global__ void k_f_primal(Geo g, Coef c, const float* tx, const float* ty, const float* f,
+                           const float* u, const float* p, float* u_out, float* ub) {
+  PIXEL
+  float a, b, iG, sG;
+  metric(tx, ty, i, a, b, iG, sG);
+  float v = u[i] + c.tau * div_g(g, tx, ty, p, x, y);
+  float beta = c.tau * c.lambda * sG;
+  float d = v - beta;
+  float r = 0.5f * (d + sqrtf(d * d + 4.0f * beta * f[i]));
+  float un = fminf(fmaxf(r, c.u_min), c.u_max);
+  u_out[i] = un;
+  ub[i] = 2.0f * un - u[i];
+}
+
+__global__ void k_f_dual(Geo g, Coef c, const float* tx, const float* ty, const float* ub,
+                         const float* p, float* p_out) {
+  PIXEL
+  float a, b, iG, sG, g1, g2, g3;
+  metric(tx, ty, i, a, b, iG, sG);
+  Lg(g, tx, ty, ub, x, y, g1, g2, g3);
+  float p1 = p[i] + c.sigma * g1, p2 = p[g.plane + i] + c.sigma * g2,
+        p3 = p[2 * g.plane + i] + c.sigma * g3;
+  float den = fmaxf(1.0f, sqrtf(p1 * p1 + p2 * p2 + p3 * p3) / sG);
+  p_out[i] = p1 / den;
+  p_out[g.plane + i] = p2 / den;
+  p_out[2 * g.plane + i] = p3 / den;
+}
+
+// ---- backward of one iteration from state (u, p) ----
+// step 1: ubar (recomputed) and the adjoint through the projection:
+//   apt = J_proj ap_next, written scaled by sigma (it is what L_g^T acts on)
+__global__ void k_b_dual(Geo g, Coef c, const float* tx, const float* ty, const float* ub,
+                         const float* p, const float* ap_next, float* sapt) {
+  PIXEL
+  float a, b, iG, sG, g1, g2, g3;
+  metric(tx, ty, i, a, b, iG, sG);
+  Lg(g, tx, ty, ub, x, y, g1, g2, g3);
+  float t1 = p[i] + c.sigma * g1, t2 = p[g.plane + i] + c.sigma * g2,
+        t3 = p[2 * g.plane + i] + c.sigma * g3;
+  float a1 = ap_next[i], a2 = ap_next[g.plane + i], a3 = ap_next[2 * g.plane + i];
+  float nrm = sqrtf(t1 * t1 + t2 * t2 + t3 * t3);
+  if (nrm > sG) {
+    float dot = (t1 * a1 + t2 * a2 + t3 * a3) / (nrm * nrm);
+    float s = sG / nrm;
+    a1 = s * (a1 - t1 * dot);
+    a2 = s * (a2 - t2 * dot);
+    a3 = s * (a3 - t3 * dot);
+  }
+  sapt[i] = c.sigma * a1;
+  sapt[g.plane + i] = c.sigma * a2;
+  sapt[2 * g.plane + i] = c.sigma * a3;
+}
+
+// step 2: a_ub = -div_g(sigma apt); primal step backwards.  Writes the new au (in
+// place), tau * a_v, and accumulates df and the lambda gradient per pixel.
+__global__ void k_b_primal(Geo g, Coef c, const float* tx, const float* ty, const float* f,
+                           const float* u, const float* p, const float* sapt, float* au,
+                           float* tav, float* gf, double* glam_px) {
+  PIXEL
+  float a, b, iG, sG;
+  metric(tx, ty, i, a, b, iG, sG);
+  float aub = -div_g(g, tx, ty, sapt, x, y);
+  float v = u[i] + c.tau * div_g(g, tx, ty, p, x, y);
+  float beta = c.tau * c.lambda * sG;
+  float d = v - beta;
+  float s = sqrtf(d * d + 4.0f * beta * f[i]);
+  float r = 0.5f * (d + s);
+  float aun = au[i] + 2.0f * aub;
+  float ar = (r < c.u_min || r > c.u_max) ? 0.0f : aun;
+  float av = ar * 0.5f * (1.0f + d / s);
+  gf[i] += ar * (beta / s);
+  glam_px[i] += (double)(ar * 0.5f * (-1.0f + (2.0f * f[i] - v + beta) / s)) *
+                ((double)c.tau * (double)sG);
+  au[i] = -aub + av;
+  tav[i] = c.tau * av;
+}
+
+// step 3: ap = apt - L_g(tau a_v)   (apt = sapt / sigma)
+__global__ void k_b_pupdate(Geo g, Coef c, const float* tx, const float* ty, const float* sapt,
+                            const float* tav, float* ap) {
+  PIXEL
+  float g1, g2, g3;
+  Lg(g, tx, ty, tav, x, y, g1, g2, g3);
+  ap[i] = sapt[i] / c.sigma - g1;
+  ap[g.plane + i] = sapt[g.plane + i] / c.sigma - g2;
+  ap[2 * g.plane + i] = sapt[2 * g.plane + i] / c.sigma - g3;
+}
+
+__global__ void k_zero(Geo g, float* a, int planes) {
+  PIXEL
+  for (int k = 0; k < planes; ++k) a[k * g.plane + i] = 0.0f;
+}
+
+__global__ void k_zero_d(Geo g, double* a) {
+  PIXEL
+  a[i] = 0.0;
+}
+
+__global__ void k_copy(Geo g, const float* src, float* dst, int planes) {
+  PIXEL
+  for (int k = 0; k < planes; ++k) dst[k * g.plane + i] = src[k * g.plane + i];
+}
+
+// Fixed-order FP64 reduction of up to 4 per-pixel double planes into out[0..n-1].
+__global__ void __launch_bounds__(kRedThreads) k_red_partial(Geo g, const double* a, int n,
+                                                            double* partials) {
+  __shared__ double s[4][kRedThreads];
+  double acc[4] = {0, 0, 0, 0};
+  const int N = g.W * g.H;
+  for (int k = blockIdx.x * kRedThreads + threadIdx.x; k < N; k += kRedBlocks * kRedThreads) {
+    const size_t i = (size_t)(k / g.W) * g.pitch + (k % g.W);
+    for (int j = 0; j < n; ++j) acc[j] += a[j * g.plane + i];
+  }
+  for (int j = 0; j < 4; ++j) s[j][threadIdx.x] = acc[j];
+  __syncthreads();
+  for (int h = kRedThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int j = 0; j < 4; ++j) s[j][threadIdx.x] += s[j][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 4; ++j) partials[4 * blockIdx.x + j] = s[j][0];
+}
+
+__global__ void __launch_bounds__(kRedBlocks) k_red_final(const double* partials, int n,
+                                                         double* out) {
+  __shared__ double s[4][kRedBlocks];
+  for (int j = 0; j < 4; ++j) s[j][threadIdx.x] = partials[4 * threadIdx.x + j];
+  __syncthreads();
+  for (int h = kRedBlocks / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int j = 0; j < 4; ++j) s[j][threadIdx.x] += s[j][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int j = 0; j < n; ++j) out[j] = s[j][0];
+}
+
+// Data image f = u_prev exp(Delta+ n+ - Delta- n-) (Eq. intensity_update, compounded).
+__global__ void k_data_image(Geo g, const float* u_prev, const int* npos, const int* nneg,
+                             float dpos, float dneg, float* f) {
+  PIXEL
+  f[i] = u_prev[i] * expf(dpos * (float)npos[i] - dneg * (float)nneg[i]);
+}
+
+// Its backward: g_uprev = gf exp(...), per-pixel terms of dL/dDelta+ = sum gf f n+ and
+// dL/dDelta- = -sum gf f n-.
+__global__ void k_data_image_bwd(Geo g, const float* f, const float* u_prev, const int* npos,
+                                 const int* nneg, float dpos, float dneg, const float* gf,
+                                 float* g_uprev, double* terms) {
+  PIXEL
+  float e = expf(dpos * (float)npos[i] - dneg * (float)nneg[i]);
+  if (g_uprev) g_uprev[i] = gf[i] * e;
+  terms[i] = (double)gf[i] * (double)f[i] * (double)npos[i];
+  terms[g.plane + i] = -(double)gf[i] * (double)f[i] * (double)nneg[i];
+}
+
+struct Workspace {
+  float* ck;       // n_ck checkpoints x 4 planes
+  float* tape;     // max(every, 2) states x 4 planes
+  float* ub;       // 1 plane
+  float* sapt;     // 3 planes
+  float* au;       // 1 plane
+  float* ap;       // 3 planes
+  float* tav;      // 1 plane
+  double* glam;    // 1 double plane
+  double* partials;  // 4 * kRedBlocks doubles
+};
+
+size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspace* w) {
+  const size_t plane = (size_t)pitch * H;
+  const size_t fpl = (plane * 4 + 255) / 256 * 256;
+  const size_t dpl = (plane * 8 + 255) / 256 * 256;
+  const int n_ck = (K + every - 1) / every;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += b;
+    return base ? base + o : nullptr;
+  };
+  Workspace t;
+  t.ck = (float*)take(fpl * 4 * (size_t)(n_ck > 0 ? n_ck : 1));
+  t.tape = (float*)take(fpl * 4 * (size_t)(every > 2 ? every : 2));  // >= 2: forward ping-pong
+  t.ub = (float*)take(fpl);
+  t.sapt = (float*)take(fpl * 3);
+  t.au = (float*)take(fpl);
+  t.ap = (float*)take(fpl * 3);
+  t.tav = (float*)take(fpl);
+  t.glam = (double*)take(dpl);
+  t.partials = (double*)take(sizeof(double) * 4 * kRedBlocks);
+  if (w) *w = t;
+  (void)W;
+  return off;
+}
+
+// A state in the workspace is u | p1 | p2 | p3 with the 256-byte-aligned plane size.
+int check_args(int W, int H, int pitch, int K, int every) {
+  if (W <= 0 || H <= 0 || pitch < W || K < 1 || every < 1) return EVR_ERR_INVALID_ARG;
+  return EVR_OK;
+}
+
+}  // namespace
+
+extern "C" size_t evr_unrolled_workspace_bytes(int W, int H, int pitch, int K, int every) {
+  if (check_args(W, H, pitch, K, every)) return 0;
+  return ws_layout(W, H, pitch, K, every, nullptr, nullptr);
+}
+
+// Forward with checkpoints.  u0, p0 (3 planes) are read; u_out, p_out written.
+extern "C" int evr_unrolled_forward(const float* tx, const float* ty, const float* f,
+                                    const float* u0, const float* p0, int W, int H, int pitch,
+                                    float lambda, float tau, float sigma, float u_min,
+                                    float u_max, int K, int every, void* workspace,
+                                    float* u_out, float* p_out, void* cuda_stream) {
+  if (check_args(W, H, pitch, K, every)) return EVR_ERR_INVALID_ARG;
+  if (!tx || !ty || !f || !u0 || !p0 || !workspace || !u_out || !p_out)
+    return EVR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Workspace w;
+  ws_layout(W, H, pitch, K, every, (char*)workspace, &w);
+  Geo g{W, H, pitch, (size_t)pitch * H};
+  Coef c{tau, sigma, lambda, u_min, u_max};
+  const size_t fpl = ((size_t)pitch * H * 4 + 255) / 256 * 256 / 4;  // floats per plane slot
+  dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
+  // state buffers: two ping-pong states in the tape area (u | p1 p2 p3)
+  float* su[2] = {w.tape, w.tape + 4 * fpl};
+  Geo g4 = g;
+  g4.plane = fpl;  // states use the aligned plane stride
+  // copy (u0, p0) into state 0
+  {
+    Geo gi = g;  // caller planes: stride pitch * H
+    k_copy<<<grd, blk, 0, st>>>(gi, u0, su[0], 1);
+    for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(gi, p0 + k * gi.plane, su[0] + (1 + k) * fpl, 1);
+  }
+  int cur = 0;
+  for (int k = 0; k < K; ++k) {
+    if (k % every == 0) {
+      float* dst = w.ck + (size_t)(k / every) * 4 * fpl;
+      k_copy<<<grd, blk, 0, st>>>(g4, su[cur], dst, 4);
+    }
+    float* s0 = su[cur];
+    float* s1 = su[1 - cur];
+    k_f_primal<<<grd, blk, 0, st>>>(g4, c, tx, ty, f, s0, s0 + fpl, s1, w.ub);
+    k_f_dual<<<grd, blk, 0, st>>>(g4, c, tx, ty, w.ub, s0 + fpl, s1 + fpl);
+    cur = 1 - cur;
+  }
+  {
+    Geo go = g;
+    k_copy<<<grd, blk, 0, st>>>(go, su[cur], u_out, 1);
+    for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(go, su[cur] + (1 + k) * fpl, p_out + k * go.plane, 1);
+  }
+  return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}
+
+// Backward from dL/du_K (gu_K) and dL/dp_K (gp_K, NULL = 0).  Outputs dL/du0, dL/dp0
+// (3 planes), dL/df and glambda_dev[0] = dL/dlambda.  gu0, gp0 may be NULL.
+extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const float* f, int W,
+                                     int H, int pitch, float lambda, float tau, float sigma,
+                                     float u_min, float u_max, int K, int every,
+                                     void* workspace, const float* gu_K, const float* gp_K,
+                                     float* gu0, float* gp0, float* gf, double* glambda_dev,
+                                     void* cuda_stream) {
+  if (check_args(W, H, pitch, K, every)) return EVR_ERR_INVALID_ARG;
+  if (!tx || !ty || !f || !workspace || !gu_K || !gf || !glambda_dev) return EVR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Workspace w;
+  ws_layout(W, H, pitch, K, every, (char*)workspace, &w);
+  Geo g{W, H, pitch, (size_t)pitch * H};
+  Coef c{tau, sigma, lambda, u_min, u_max};
+  const size_t fpl = ((size_t)pitch * H * 4 + 255) / 256 * 256 / 4;
+  Geo g4 = g;
+  g4.plane = fpl;
+  dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
+  // adjoint of the final state: au = gu_K, ap = 0; gf = 0; glam = 0
+  k_copy<<<grd, blk, 0, st>>>(g, gu_K, w.au, 1);
+  if (gp_K) {
+    for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, gp_K + k * g.plane, w.ap + k * fpl, 1);
+  } else {
+    k_zero<<<grd, blk, 0, st>>>(g4, w.ap, 3);
+  }
+  k_zero<<<grd, blk, 0, st>>>(g, gf, 1);
+  k_zero_d<<<grd, blk, 0, st>>>(g, w.glam);
+  const int n_ck = (K + every - 1) / every;
+  for (int cseg = n_ck - 1; cseg >= 0; --cseg) {
+    const int k0 = cseg * every, k1 = (k0 + every < K) ? k0 + every : K;
+    // recompute states k0 .. k1-1 into the tape (slot j = state k0 + j)
+    k_copy<<<grd, blk, 0, st>>>(g4, w.ck + (size_t)cseg * 4 * fpl, w.tape, 4);
+    for (int k = k0; k + 1 < k1; ++k) {
+      float* s0 = w.tape + (size_t)(k - k0) * 4 * fpl;
+      float* s1 = s0 + 4 * fpl;
+      k_f_primal<<<grd, blk, 0, st>>>(g4, c, tx, ty, f, s0, s0 + fpl, s1, w.ub);
+      k_f_dual<<<grd, blk, 0, st>>>(g4, c, tx, ty, w.ub, s0 + fpl, s1 + fpl);
+    }
+    for (int k = k1 - 1; k >= k0; --k) {
+      float* s0 = w.tape + (size_t)(k - k0) * 4 * fpl;
+      float* tmp_u = w.tav;  // u' of this iteration is not needed: recompute ubar only
+      k_f_primal<<<grd, blk, 0, st>>>(g4, c, tx, ty, f, s0, s0 + fpl, tmp_u, w.ub);
+      k_b_dual<<<grd, blk, 0, st>>>(g4, c, tx, ty, w.ub, s0 + fpl, w.ap, w.sapt);
+      k_b_primal<<<grd, blk, 0, st>>>(g4, c, tx, ty, f, s0, s0 + fpl, w.sapt, w.au, w.tav, gf,
+                                      w.glam);
+      k_b_pupdate<<<grd, blk, 0, st>>>(g4, c, tx, ty, w.sapt, w.tav, w.ap);
+    }
+  }
+  if (gu0) k_copy<<<grd, blk, 0, st>>>(g, w.au, gu0, 1);
+  if (gp0)
+    for (int k = 0; k < 3; ++k) {
+      Geo go = g;
+      k_copy<<<grd, blk, 0, st>>>(go, w.ap + k * fpl, gp0 + k * go.plane, 1);
+    }
+  Geo gd = g;
+  gd.plane = 0;
+  k_red_partial<<<kRedBlocks, kRedThreads, 0, st>>>(gd, w.glam, 1, w.partials);
+  k_red_final<<<1, kRedBlocks, 0, st>>>(w.partials, 1, glambda_dev);
+  return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}
+
+extern "C" int evr_data_image(const float* u_prev, const int32_t* npos, const int32_t* nneg,
+                              int W, int H, int pitch, float delta_pos, float delta_neg,
+                              float* f_out, void* cuda_stream) {
+  if (!u_prev || !npos || !nneg || !f_out || W <= 0 || H <= 0 || pitch < W)
+    return EVR_ERR_INVALID_ARG;
+  Geo g{W, H, pitch, (size_t)pitch * H};
+  dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
+  k_data_image<<<grd, blk, 0, (cudaStream_t)cuda_stream>>>(g, u_prev, npos, nneg, delta_pos,
+                                                           delta_neg, f_out);
+  return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}
+
+// scratch: 2 double planes (pitch * H each) + 4 * 256 doubles, caller-owned.
+extern "C" int evr_data_image_backward(const float* f, const float* u_prev, const int32_t* npos,
+                                       const int32_t* nneg, int W, int H, int pitch,
+                                       float delta_pos, float delta_neg, const float* gf,
+                                       float* g_uprev, double* scratch, double* g_delta_dev,
+                                       void* cuda_stream) {
+  if (!f || !u_prev || !npos || !nneg || !gf || !scratch || !g_delta_dev || W <= 0 || H <= 0 ||
+      pitch < W)
+    return EVR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Geo g{W, H, pitch, (size_t)pitch * H};
+  dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
+  k_data_image_bwd<<<grd, blk, 0, st>>>(g, f, u_prev, npos, nneg, delta_pos, delta_neg, gf,
+                                        g_uprev, scratch);
+  k_red_partial<<<kRedBlocks, kRedThreads, 0, st>>>(g, scratch, 2, scratch + 2 * g.plane);
+  k_red_final<<<1, kRedBlocks, 0, st>>>(scratch + 2 * g.plane, 2, g_delta_dev);
+  return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}

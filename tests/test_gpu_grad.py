@@ -1,0 +1,158 @@
+"""Differentiation of one packet's solve on the GPU (adjoint kernels through the C ABI,
+behind torch.autograd.Function), against the FP64 oracle's adjoint and FP64 central
+finite differences of the oracle's forward iterations."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TAU = float(np.float32(1.0 / math.sqrt(8.0 + 4.0 * math.sqrt(2.0))))
+UMIN, UMAX = float(np.float32(math.exp(-3.0))), float(np.float32(math.exp(3.0)))
+# FP32 forward/adjoint through K iterations against FP64: relative to the largest entry
+GRAD_RTOL = 2e-3
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_06283_gb300 import build
+    build.build()
+    from paper_1607_06283_gb300 import autograd, evr
+    return torch, autograd, evr
+
+
+def problem(seed, H, W, tscale=3.0):
+    rng = np.random.default_rng(seed)
+    t = rng.uniform(0, tscale, (H, W)).astype(np.float32)
+    tx = np.zeros((H, W), np.float32)
+    ty = np.zeros((H, W), np.float32)
+    tx[:, :-1] = np.diff(t, axis=1)
+    ty[:-1, :] = np.diff(t, axis=0)
+    f = rng.uniform(0.5, 2.0, (H, W)).astype(np.float32)
+    u0 = rng.uniform(0.5, 2.0, (H, W)).astype(np.float32)
+    p0 = (rng.normal(scale=0.3, size=(3, H, W))).astype(np.float32)
+    w = rng.normal(size=(H, W)).astype(np.float32)
+    return tx, ty, f, u0, p0, w
+
+
+def oracle_metric(tx, ty):
+    tx = tx.astype(np.float64)
+    ty = ty.astype(np.float64)
+    return tx, ty, 1.0 + tx * tx + ty * ty
+
+
+def cuda(torch, *arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / max(1e-30, np.max(np.abs(b))))
+
+
+@pytest.mark.parametrize("H,W,K,every,lam", [(23, 37, 30, 10, 9.0), (40, 33, 30, 7, 90.0),
+                                             (1, 50, 12, 5, 20.0), (17, 1, 9, 2, 20.0)])
+def test_forward_and_gradients_match_oracle(T, H, W, K, every, lam):
+    torch, AG, E = T
+    tx, ty, f, u0, p0, w = problem(H * 100 + W, H, W)
+    ttx, tty, tf, tu0, tp0, tw = cuda(torch, tx, ty, f, u0, p0, w)
+    tf.requires_grad_(True)
+    tu0.requires_grad_(True)
+    tp0.requires_grad_(True)
+    tlam = torch.tensor(lam, dtype=torch.float32, device="cuda", requires_grad=True)
+    u, p = AG.packet_solve(tf, tlam, tu0, tp0, ttx, tty, K, every)
+    loss = (u * tw).sum()
+    loss.backward()
+    otx, oty, oG = oracle_metric(tx, ty)
+    uo, po = O.pd_iterations(otx, oty, oG, f, u0, p0, K, TAU, TAU, lam, UMIN, UMAX)
+    assert np.max(np.abs(u.detach().cpu().numpy() - uo)) <= 1e-4
+    gu0, gp0, gf, gl = O.pd_grad(otx, oty, oG, f, u0, p0, K, TAU, TAU, lam, UMIN, UMAX, w)
+    assert rel_err(tf.grad.cpu().numpy(), gf) <= GRAD_RTOL
+    assert rel_err(tu0.grad.cpu().numpy(), gu0) <= GRAD_RTOL
+    assert rel_err(tp0.grad.cpu().numpy(), gp0) <= GRAD_RTOL
+    assert float(tlam.grad) == pytest.approx(gl, rel=GRAD_RTOL, abs=1e-6)
+
+
+def test_checkpoint_spacing_does_not_change_gradients(T):
+    torch, AG, E = T
+    H, W, K = 31, 29, 24
+    tx, ty, f, u0, p0, w = problem(5, H, W)
+    ttx, tty, tu0, tp0, tw = cuda(torch, tx, ty, u0, p0, w)
+    grads = []
+    for every in (1, 3, 8, 24, 100):
+        tf = torch.from_numpy(f).cuda().requires_grad_(True)
+        tlam = torch.tensor(30.0, device="cuda", requires_grad=True)
+        u, _ = AG.packet_solve(tf, tlam, tu0, tp0, ttx, tty, K, every)
+        (u * tw).sum().backward()
+        grads.append((tf.grad.cpu().numpy(), float(tlam.grad)))
+    for gf, gl in grads[1:]:
+        np.testing.assert_array_equal(gf, grads[0][0])
+        assert gl == grads[0][1]
+
+
+def test_contrast_threshold_and_lambda_against_finite_differences(T):
+    """dL/dC and dL/dlambda of L = sum w * u_K with f = u_prev exp(C (n+ - n-)), against
+    FP64 central differences of the oracle forward."""
+    torch, AG, E = T
+    H, W, K = 24, 30, 30
+    rng = np.random.default_rng(9)
+    tx, ty, _, u0, p0, w = problem(9, H, W)
+    u_prev = rng.uniform(0.5, 2.0, (H, W)).astype(np.float32)
+    npos = rng.poisson(0.6, (H, W)).astype(np.int32)
+    nneg = rng.poisson(0.6, (H, W)).astype(np.int32)
+    C0, lam0 = 0.15, 40.0
+    ttx, tty, tu0, tp0, tw, tup, tnp, tnn = cuda(torch, tx, ty, u0, p0, w, u_prev, npos, nneg)
+    tC = torch.tensor(C0, device="cuda", requires_grad=True)
+    tlam = torch.tensor(lam0, device="cuda", requires_grad=True)
+    f = AG.data_image(tup, tnp, tnn, tC, tC)
+    u, _ = AG.packet_solve(f, tlam, tu0, tp0, ttx, tty, K, 10)
+    (u * tw).sum().backward()
+    otx, oty, oG = oracle_metric(tx, ty)
+
+    def L(C, lam):
+        fo = u_prev.astype(np.float64) * np.exp(C * (npos - nneg))
+        uo, _ = O.pd_iterations(otx, oty, oG, fo, u0, p0, K, TAU, TAU, lam, UMIN, UMAX)
+        return float(np.sum(w * uo))
+
+    h = 1e-5
+    dC = (L(C0 + h, lam0) - L(C0 - h, lam0)) / (2 * h)
+    dl = (L(C0, lam0 + h) - L(C0, lam0 - h)) / (2 * h)
+    assert float(tC.grad) == pytest.approx(dC, rel=GRAD_RTOL)
+    assert float(tlam.grad) == pytest.approx(dl, rel=GRAD_RTOL, abs=1e-6)
+
+
+def test_fit_lambda_and_threshold_to_target(T):
+    """Gradient descent through the GPU adjoint moves (lambda, C) towards the values
+    that produced a target image and lowers the loss."""
+    torch, AG, E = T
+    H, W, K = 32, 40, 30
+    rng = np.random.default_rng(21)
+    tx, ty, _, u0, _, _ = problem(21, H, W, tscale=1.0)
+    u_prev = rng.uniform(0.6, 1.6, (H, W)).astype(np.float32)
+    npos = rng.poisson(1.0, (H, W)).astype(np.int32)
+    nneg = rng.poisson(1.0, (H, W)).astype(np.int32)
+    p0 = np.zeros((3, H, W), np.float32)
+    ttx, tty, tu0, tp0, tup, tnp, tnn = cuda(torch, tx, ty, u0, p0, u_prev, npos, nneg)
+    with torch.no_grad():
+        target, _ = AG.packet_solve(AG.data_image(tup, tnp, tnn, 0.2, 0.2), 25.0, tu0, tp0, ttx,
+                                    tty, K, 10)
+    logl = torch.tensor(math.log(60.0), device="cuda", requires_grad=True)
+    C = torch.tensor(0.1, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([logl, C], lr=0.05)
+    losses = []
+    for _ in range(60):
+        opt.zero_grad()
+        u, _ = AG.packet_solve(AG.data_image(tup, tnp, tnn, C, C), logl.exp(), tu0, tp0, ttx,
+                               tty, K, 10)
+        loss = ((u - target) ** 2).mean()
+        loss.backward()
+        opt.step()
+        losses.append(float(loss))
+    assert losses[-1] < 0.05 * losses[0]
+    assert abs(float(C) - 0.2) < abs(0.1 - 0.2) * 0.5
+    assert abs(math.log(float(logl.exp()) / 25.0)) < abs(math.log(60.0 / 25.0))
