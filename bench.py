@@ -146,24 +146,26 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("evr_kernels.cu", "evr_internal.cuh"):
+    for f in ("evr_kernels.cu", "evr_solvers.cu", "evr_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1607_06283_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(solver_name):
-    """DRAM bytes per launch of the iteration kernel from the committed ncu summary,
-    if it was taken on the current kernel source and the same tile shape; else None."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch of the iteration kernel from the committed ncu summary
+    (profiles/k_tiled_blobs346.md), if it was taken on the current kernel source and
+    the same solver configuration; else None."""
+    p = os.path.join(ROOT, "profiles", "k_tiled_blobs346.md")
     if not os.path.exists(p):
         return None
+    import re
     with open(p) as fh:
-        d = json.load(fh)
-    ent = d.get(solver_name)
-    if not ent or ent.get("kernel_source_sha") != kernel_source_hash():
+        text = fh.read()
+    m = re.search(r"traffic_bytes_per_launch: (\d+) kernel_source_sha: (\w+) solver: (.+)", text)
+    if not m or m.group(2) != kernel_source_hash() or m.group(3).strip() != solver_name:
         return None
-    return ent.get("dram_bytes_per_launch_full_size")
+    return int(m.group(1))
 
 
 def cpu_baseline(cfg, stream, budget_s, max_packets=None):

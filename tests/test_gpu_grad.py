@@ -152,7 +152,7 @@ def test_fit_lambda_and_threshold_to_target(T):
         loss = ((u - target) ** 2).mean()
         loss.backward()
         opt.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     assert losses[-1] < 0.05 * losses[0]
     assert abs(float(C) - 0.2) < abs(0.1 - 0.2) * 0.5
     assert abs(math.log(float(logl.exp()) / 25.0)) < abs(math.log(60.0 / 25.0))
