@@ -191,6 +191,57 @@ int evr_gap_static(const float* u, const float* p1, const float* p2, const float
                    const float* f, const float* tx, const float* ty, int W, int H, int pitch,
                    float lambda, float u_min, float u_max, double* out_dev, void* cuda_stream);
 
+/* ---- batching: many independent streams solved together ----
+ * A batch holds n streams of possibly different sizes sharing one evr_params.  A step
+ * takes at most one packet per stream (streams with no events in the step are left
+ * untouched), validates and integrates every packet (one CTA per stream), then runs
+ * the packet prologue and `iters` iterations for every stream that had events, as one
+ * CUDA graph over a (stream, tile) work list.  Each stream's results are bit-identical
+ * to a single stream (evr_create) fed the same packets with the same tile_config; the
+ * tiled configuration is autotuned over the whole batch at the first step unless
+ * tile_config selects one (multi-launch configurations only).  Per-stream packets
+ * above 32768 events are rejected with EVR_ERR_INVALID_ARG. */
+typedef struct evr_batch evr_batch; /* opaque handle */
+
+/* Create n streams of sizes W[s] x H[s].  Errors as evr_create; EVR_ERR_NOT_SUPPORTED
+ * for the unfused solver or a persistent tile_config. */
+int evr_batch_create(int n, const int* W, const int* H, const evr_params* params,
+                     evr_batch** out);
+void evr_batch_destroy(evr_batch* b);
+int evr_batch_set_cuda_stream(evr_batch* b, void* cuda_stream);
+
+/* One step.  Events of all streams concatenated (structure of arrays, device
+ * pointers); stream s owns events [offsets[s], offsets[s+1]) (offsets: device int64
+ * array of n+1 entries, offsets[0] = 0, non-decreasing).  Validation is per stream
+ * and device-side: a rejected packet changes nothing of its stream and is reported by
+ * evr_batch_synchronize.  Asynchronous. */
+int evr_batch_step_device(evr_batch* b, const uint16_t* x, const uint16_t* y,
+                          const int64_t* t_us, const int8_t* pol, const int64_t* offsets,
+                          int iters);
+
+/* As evr_batch_step_device with host arrays (offsets on the host); the events are
+ * copied before the call returns. */
+int evr_batch_step(evr_batch* b, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
+                   const int8_t* pol, const int64_t* offsets, int iters);
+
+/* Image / state plane of stream s (as evr_get_image / evr_get_state); synchronise. */
+int evr_batch_get_image(evr_batch* b, int s, float* out_host, size_t len);
+/* All images, stream after stream, each W[s]*H[s] floats row-major; synchronises.
+ * len is the capacity of out_host in floats. */
+int evr_batch_get_images(evr_batch* b, float* out_host, size_t len);
+int evr_batch_get_state(evr_batch* b, int s, int which, void* out_host, size_t bytes);
+
+/* Wait; return the first pending rejection (lowest stream index, written to
+ * *stream_out if not NULL, -1 if none) and clear all pending rejections. */
+int evr_batch_synchronize(evr_batch* b, int* stream_out);
+
+/* Kernel timing of the steps' graphs (prologue + iteration passes), as
+ * evr_enable_kernel_timing / evr_kernel_time; pixel_iters counts every stream as
+ * active in every timed step. */
+int evr_batch_enable_kernel_timing(evr_batch* b, int enable);
+int evr_batch_kernel_time(evr_batch* b, double* ms, int64_t* launches, int64_t* pixel_iters);
+const char* evr_batch_solver_name(evr_batch* b);
+
 /* ---- differentiation of one packet's solve (no counterpart in the paper's text:
  * the adjoint of its iteration, Eq. cont_iterates with Eq. update_rules) ----
  * The solve is u_K = S(u_0, p_0, f, lambda) with the metric fixed: K unrolled

@@ -333,6 +333,78 @@ void resolve_timing(evr_stream* s) {
 
 }  // namespace
 
+namespace evr {
+
+static size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Device bytes of one stream's state (see the layout in evr_internal.cuh); `solo`
+// adds the gap partials, the gap result and the persistent solver's flags.
+size_t state_bytes(int W, int H, bool solo) {
+  const size_t plane = (size_t)((W + 31) / 32 * 32) * H;
+  const size_t fb = al256(plane * 4), lb = al256(plane * 8);
+  size_t total = 16 * fb + lb + al256(sizeof(DevScalars));
+  if (solo)
+    total += al256(sizeof(double) * 3 * kGapBlocks) + al256(sizeof(double) * 2) +
+             al256(sizeof(int) * kMaxCtas);
+  return total;
+}
+
+// Lay one stream's planes out from `base`; returns the first byte after them (for a
+// solo stream: the 2-double gap result, followed by nothing else).
+char* carve_state(char* base, int W, int H, bool solo, Planes* out) {
+  Planes P{};
+  P.W = W;
+  P.H = H;
+  P.pitch = (W + 31) / 32 * 32;
+  const size_t plane = (size_t)P.pitch * H;
+  const size_t fb = al256(plane * 4), lb = al256(plane * 8);
+  char* q = base;
+  auto take = [&](size_t b) {
+    char* r = q;
+    q += b;
+    return r;
+  };
+  for (int b = 0; b < 2; ++b) {
+    P.u[b] = (float*)take(fb);
+    P.p1[b] = (float*)take(fb);
+    P.p2[b] = (float*)take(fb);
+    P.p3[b] = (float*)take(fb);
+  }
+  P.ubar = (float*)take(fb);
+  P.f = (float*)take(fb);
+  P.tx = (float*)take(fb);
+  P.ty = (float*)take(fb);
+  P.iG = (float*)take(fb);
+  P.sG = (float*)take(fb);
+  P.t_last = (long long*)take(lb);
+  P.npos = (int*)take(fb);
+  P.nneg = (int*)take(fb);
+  P.sc = (DevScalars*)take(al256(sizeof(DevScalars)));
+  P.partials = nullptr;
+  P.flags = nullptr;
+  char* gap = nullptr;
+  if (solo) {
+    P.partials = (double*)take(al256(sizeof(double) * 3 * kGapBlocks));
+    gap = take(al256(sizeof(double) * 2));
+    P.flags = (int*)take(al256(sizeof(int) * kMaxCtas));
+  }
+  *out = P;
+  return solo ? gap : q;
+}
+
+int check_params(const evr_params* p) { return params_valid(p); }
+
+int check_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return EVR_ERR_NOT_SUPPORTED;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return EVR_ERR_NOT_SUPPORTED;
+  if (!(prop.major == 10 && prop.minor == 3)) return EVR_ERR_NOT_SUPPORTED;
+  return EVR_OK;
+}
+
+}  // namespace evr
+
 extern "C" {
 
 int evr_default_params(evr_params* out) {
@@ -373,49 +445,16 @@ int evr_create(int W, int H, const evr_params* params, evr_stream** out) {
   s->device = dev;
   s->prm = *params;
   s->pitch = (W + 31) / 32 * 32;
-  const size_t plane = (size_t)s->pitch * H;
-  // float planes: u[2], p1[2], p2[2], p3[2], ubar, f, tx, ty, iG, sG = 14
-  // int64: t_last; int32: npos, nneg; scalars; gap partials
-  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t fb = al(plane * 4), lb = al(plane * 8);
-  const size_t total = 14 * fb + lb + 2 * fb + al(sizeof(DevScalars)) +
-                       al(sizeof(double) * 3 * kGapBlocks) + al(sizeof(double) * 2) +
-                       al(sizeof(int) * kMaxCtas);
+  const size_t total = evr::state_bytes(W, H, true);
   char* base = nullptr;
   if (cudaMalloc((void**)&base, total) != cudaSuccess) {
     delete s;
     return EVR_ERR_OOM;
   }
   s->dev_base = base;
-  char* q = base;
-  auto take = [&](size_t b) {
-    char* r = q;
-    q += b;
-    return r;
-  };
+  char* q = evr::carve_state(base, W, H, true, &s->P);
+  s->d_gap = (double*)q;
   Planes& P = s->P;
-  P.W = W;
-  P.H = H;
-  P.pitch = s->pitch;
-  for (int b = 0; b < 2; ++b) {
-    P.u[b] = (float*)take(fb);
-    P.p1[b] = (float*)take(fb);
-    P.p2[b] = (float*)take(fb);
-    P.p3[b] = (float*)take(fb);
-  }
-  P.ubar = (float*)take(fb);
-  P.f = (float*)take(fb);
-  P.tx = (float*)take(fb);
-  P.ty = (float*)take(fb);
-  P.iG = (float*)take(fb);
-  P.sG = (float*)take(fb);
-  P.t_last = (long long*)take(lb);
-  P.npos = (int*)take(fb);
-  P.nneg = (int*)take(fb);
-  P.sc = (DevScalars*)take(al(sizeof(DevScalars)));
-  P.partials = (double*)take(al(sizeof(double) * 3 * kGapBlocks));
-  s->d_gap = (double*)take(al(sizeof(double) * 2));
-  P.flags = (int*)take(al(sizeof(int) * kMaxCtas));
   int rc = EVR_OK;
   if (cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||

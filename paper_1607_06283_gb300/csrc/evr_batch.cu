@@ -1,0 +1,518 @@
+// evr_batch.cu -- many independent event streams solved together.
+//
+// Every stream keeps the state layout of a single stream (evr_internal.cuh); the
+// device holds an array of their plane descriptors.  A step takes one packet per
+// stream (streams without events in the step are left alone): one launch validates
+// and scatters all packets (one CTA per stream), then a CUDA graph runs the packet
+// prologue over every stream's pixel blocks and the tiled iteration passes over a
+// work list of (stream, tile) pairs.  The tiled kernel is the same instantiation the
+// single-stream solver uses, so each stream's result is bit-identical to solving it
+// alone with the same solver configuration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "../../include/evr.h"
+#include "evr_internal.cuh"
+
+namespace evr {
+int check_params(const evr_params* p);
+}
+
+using namespace evr;
+
+struct evr_batch {
+  int n = 0;
+  evr_params prm{};
+  std::vector<Planes> planes;  // host copies of the descriptors
+  char* dev = nullptr;         // all device memory of the batch
+  Planes* d_descs = nullptr;
+  int* d_curs = nullptr;
+  int* d_active = nullptr;
+  int2* d_work_pro = nullptr;
+  int n_work_pro = 0;
+  int2* d_work_tile = nullptr;
+  int n_work_tile = 0;
+  int cfg = -1;
+  bool tuned = false;
+  cudaStream_t stream = nullptr, own_stream = nullptr, cap_stream = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;  // by iteration count
+  // host-pointer steps: device staging
+  size_t stage_cap = 0;
+  char* d_stage = nullptr;
+  long long* d_offsets = nullptr;
+  DevScalars* h_sc = nullptr;  // pinned, one per stream
+  int* h_curs = nullptr;       // pinned
+  // kernel timing
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
+  std::vector<int> ev_launches;
+  std::vector<long long> ev_pixiters;
+  double t_ms = 0.0;
+  long long t_launches = 0, t_pixiters = 0;
+  long long px_total = 0;
+  char name[96] = {0};
+};
+
+namespace {
+
+SolveConsts consts(const evr_batch* b) {
+  return SolveConsts{b->prm.tau, b->prm.sigma, b->prm.lambda, b->prm.u_min, b->prm.u_max};
+}
+
+PrologueConsts pconsts(const evr_batch* b) {
+  return PrologueConsts{b->prm.time_scale, b->prm.delta_pos, b->prm.delta_neg,
+                        (long long)b->prm.t_max_us, b->prm.manifold, b->prm.data_mode};
+}
+
+BatchRef bref(const evr_batch* b, bool tiles) {
+  return BatchRef{b->d_descs, tiles ? b->d_work_tile : b->d_work_pro, b->d_curs, b->d_active};
+}
+
+// (stream, tile) work items of configuration ci for every stream.
+int build_tile_work(evr_batch* b, int ci) {
+  const SolverCfg& c = kSolverCfgs[ci];
+  const TileShape& t = kTileShapes[c.shape];
+  const int OW = t.EW - 2 * c.R, OH = t.EH - 2 * c.R;
+  std::vector<int2> w;
+  for (int s = 0; s < b->n; ++s) {
+    const int tx = (b->planes[s].W + OW - 1) / OW, ty = (b->planes[s].H + OH - 1) / OH;
+    for (int k = 0; k < tx * ty; ++k) w.push_back(make_int2(s, k));
+  }
+  if (b->d_work_tile) cudaFree(b->d_work_tile);
+  b->d_work_tile = nullptr;
+  if (cudaMalloc((void**)&b->d_work_tile, sizeof(int2) * w.size()) != cudaSuccess)
+    return EVR_ERR_OOM;
+  if (cudaMemcpy(b->d_work_tile, w.data(), sizeof(int2) * w.size(), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return EVR_ERR_CUDA;
+  b->n_work_tile = (int)w.size();
+  return EVR_OK;
+}
+
+void drop_graphs(evr_batch* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+void set_name(evr_batch* b) {
+  if (b->cfg < 0) {
+    std::snprintf(b->name, sizeof(b->name), "batch: untuned");
+    return;
+  }
+  const SolverCfg& c = kSolverCfgs[b->cfg];
+  const TileShape& t = kTileShapes[c.shape];
+  std::snprintf(b->name, sizeof(b->name), "batch of %d: tiled %dx%d R%d (%d threads, %d CTAs)",
+                b->n, t.EW, t.EH, c.R, 32 * t.NTY, b->n_work_tile);
+}
+
+// Time each multi-launch tiled configuration over the whole batch: single passes that
+// read each stream's current buffer and write the other one (no live state changes).
+void autotune(evr_batch* b) {
+  SolveConsts c = consts(b);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_cfg = -1;
+  for (int ci = 0; ci < kNumSolverCfgs; ++ci) {
+    if (kSolverCfgs[ci].kind != 1) continue;
+    if (build_tile_work(b, ci)) continue;
+    const int R = kSolverCfgs[ci].R;
+    BatchRef B = bref(b, true);
+    launch_tiled_pass_batch(B, b->n_work_tile, kSolverCfgs[ci], 0, R, c, b->stream);
+    cudaEventRecord(e0, b->stream);
+    const int reps = 4;
+    for (int r = 0; r < reps; ++r)
+      launch_tiled_pass_batch(B, b->n_work_tile, kSolverCfgs[ci], 0, R, c, b->stream);
+    cudaEventRecord(e1, b->stream);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaGetLastError() == cudaSuccess) {
+      cudaEventElapsedTime(&ms, e0, e1);
+      float per_iter = ms / (reps * R);
+      if (per_iter < best) {
+        best = per_iter;
+        best_cfg = ci;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->cfg = best_cfg < 0 ? 0 : best_cfg;
+  build_tile_work(b, b->cfg);
+}
+
+void resolve_timing(evr_batch* b) {
+  for (size_t k = 0; k < b->ev_used.size(); ++k) {
+    cudaEventSynchronize(b->ev_used[k].second);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->ev_used[k].first, b->ev_used[k].second);
+    b->t_ms += ms;
+    b->t_launches += b->ev_launches[k];
+    b->t_pixiters += b->ev_pixiters[k];
+    b->ev_free.push_back(b->ev_used[k]);
+  }
+  b->ev_used.clear();
+  b->ev_launches.clear();
+  b->ev_pixiters.clear();
+}
+
+// Graph of one step after the push: prologue over all streams, the passes, the flip.
+int step_graph(evr_batch* b, int iters, cudaGraphExec_t* out) {
+  auto it = b->graphs.find(iters);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return EVR_OK;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return EVR_ERR_CUDA;
+  int bad = launch_prologue_batch(bref(b, false), b->n_work_pro, pconsts(b), b->cap_stream);
+  int passes = 0;
+  if (iters > 0) {
+    const SolverCfg& cfg = kSolverCfgs[b->cfg];
+    SolveConsts c = consts(b);
+    for (int done = 0; done < iters; done += cfg.R, ++passes) {
+      int k = iters - done < cfg.R ? iters - done : cfg.R;
+      bad |= launch_tiled_pass_batch(bref(b, true), b->n_work_tile, cfg, passes, k, c,
+                                     b->cap_stream);
+    }
+    bad |= launch_batch_flip(b->d_curs, b->d_active, b->n, passes, b->cap_stream);
+  }
+  cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+  if (bad || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return EVR_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return EVR_ERR_CUDA;
+  b->graphs[iters] = exec;
+  *out = exec;
+  return EVR_OK;
+}
+
+int read_back(evr_batch* b) {
+  cudaError_t e = cudaMemcpyAsync(b->h_curs, b->d_curs, sizeof(int) * b->n,
+                                  cudaMemcpyDeviceToHost, b->stream);
+  for (int s = 0; s < b->n && e == cudaSuccess; ++s)
+    e = cudaMemcpyAsync(&b->h_sc[s], b->planes[s].sc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int evr_batch_create(int n, const int* W, const int* H, const evr_params* params,
+                     evr_batch** out) {
+  if (!out) return EVR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n <= 0 || !W || !H || !params || !check_params(params)) return EVR_ERR_INVALID_ARG;
+  if (params->solver == EVR_SOLVER_UNFUSED) return EVR_ERR_NOT_SUPPORTED;
+  if (params->tile_config > 0 && kSolverCfgs[params->tile_config - 1].kind != 1)
+    return EVR_ERR_NOT_SUPPORTED;
+  for (int s = 0; s < n; ++s)
+    if (W[s] <= 0 || H[s] <= 0 || W[s] > 65536 || H[s] > 65536) return EVR_ERR_INVALID_ARG;
+  int rc = check_device();
+  if (rc) return rc;
+  evr_batch* b = new (std::nothrow) evr_batch();
+  if (!b) return EVR_ERR_OOM;
+  b->n = n;
+  b->prm = *params;
+  size_t total = 0;
+  std::vector<size_t> off(n);
+  for (int s = 0; s < n; ++s) {
+    off[s] = total;
+    total += state_bytes(W[s], H[s], false);
+  }
+  const size_t tail = total;
+  total += sizeof(Planes) * n + 256 + 2 * sizeof(int) * n + 256;
+  if (cudaMalloc((void**)&b->dev, total) != cudaSuccess) {
+    delete b;
+    return EVR_ERR_OOM;
+  }
+  b->planes.resize(n);
+  std::vector<int2> pro;
+  for (int s = 0; s < n; ++s) {
+    carve_state(b->dev + off[s], W[s], H[s], false, &b->planes[s]);
+    const int nb = ((W[s] + 31) / 32) * ((H[s] + 7) / 8);
+    for (int k = 0; k < nb; ++k) pro.push_back(make_int2(s, k));
+    b->px_total += (long long)W[s] * H[s];
+  }
+  b->d_descs = (Planes*)(b->dev + tail);
+  b->d_curs = (int*)(b->dev + tail + (sizeof(Planes) * n + 255) / 256 * 256);
+  b->d_active = b->d_curs + n;
+  cudaError_t e = cudaMemcpy(b->d_descs, b->planes.data(), sizeof(Planes) * n,
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->d_curs, 0, 2 * sizeof(int) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_work_pro, sizeof(int2) * pro.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_work_pro, pro.data(), sizeof(int2) * pro.size(), cudaMemcpyHostToDevice);
+  b->n_work_pro = (int)pro.size();
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_sc, sizeof(DevScalars) * n);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_curs, sizeof(int) * n);
+  b->stream = b->own_stream;
+  const bool first = params->t_init_us == EVR_T_INIT_FIRST;
+  const long long t0 = first ? 0 : (long long)params->t_init_us;
+  for (int s = 0; s < n && e == cudaSuccess; ++s)
+    if (launch_init(b->planes[s], params->u_init, t0, t0, first ? 0 : 1, b->stream))
+      e = cudaErrorUnknown;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    evr_batch_destroy(b);
+    return EVR_ERR_CUDA;
+  }
+  if (params->tile_config > 0) {
+    b->cfg = params->tile_config - 1;
+    if (build_tile_work(b, b->cfg)) {
+      evr_batch_destroy(b);
+      return EVR_ERR_OOM;
+    }
+    b->tuned = true;
+  }
+  set_name(b);
+  *out = b;
+  return EVR_OK;
+}
+
+void evr_batch_destroy(evr_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graphs(b);
+  resolve_timing(b);
+  for (auto& e : b->ev_free) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  if (b->d_work_pro) cudaFree(b->d_work_pro);
+  if (b->d_work_tile) cudaFree(b->d_work_tile);
+  if (b->d_stage) cudaFree(b->d_stage);
+  if (b->h_sc) cudaFreeHost(b->h_sc);
+  if (b->h_curs) cudaFreeHost(b->h_curs);
+  if (b->own_stream) cudaStreamDestroy(b->own_stream);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->dev) cudaFree(b->dev);
+  delete b;
+}
+
+int evr_batch_set_cuda_stream(evr_batch* b, void* cuda_stream) {
+  if (!b) return EVR_ERR_INVALID_ARG;
+  cudaStream_t ns = cuda_stream == EVR_OWN_STREAM ? b->own_stream : (cudaStream_t)cuda_stream;
+  if (ns != b->stream) {
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return EVR_ERR_CUDA;
+    b->stream = ns;
+  }
+  return EVR_OK;
+}
+
+int evr_batch_step_device(evr_batch* b, const uint16_t* x, const uint16_t* y,
+                          const int64_t* t_us, const int8_t* pol, const int64_t* offsets,
+                          int iters) {
+  if (!b || !offsets || iters < 0) return EVR_ERR_INVALID_ARG;
+  if (!x || !y || !t_us || !pol) return EVR_ERR_INVALID_ARG;
+  cudaStream_t st = b->stream;
+  if (launch_push_batch(b->d_descs, b->n, x, y, (const long long*)t_us, pol,
+                        (const long long*)offsets, b->d_active, st))
+    return EVR_ERR_CUDA;
+  if (iters > 0 && !b->tuned) {
+    autotune(b);
+    drop_graphs(b);  // the tile work list may have moved
+    b->tuned = true;
+    set_name(b);
+  }
+  if (b->cfg < 0) {  // iters == 0 before any tuning: prologue only
+    b->cfg = 0;
+    if (build_tile_work(b, 0)) return EVR_ERR_OOM;
+  }
+  cudaGraphExec_t exec = nullptr;
+  int rc = step_graph(b, iters, &exec);
+  if (rc) return rc;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (b->timing) {
+    if (b->ev_free.empty()) {
+      cudaEventCreate(&ev.first);
+      cudaEventCreate(&ev.second);
+    } else {
+      ev = b->ev_free.back();
+      b->ev_free.pop_back();
+    }
+    cudaEventRecord(ev.first, st);
+  }
+  if (cudaGraphLaunch(exec, st) != cudaSuccess) return EVR_ERR_CUDA;
+  if (b->timing) {
+    cudaEventRecord(ev.second, st);
+    b->ev_used.push_back(ev);
+    const int R = kSolverCfgs[b->cfg].R;
+    b->ev_launches.push_back(iters > 0 ? (iters + R - 1) / R : 0);
+    b->ev_pixiters.push_back(b->px_total * iters);  // upper bound: every stream active
+  }
+  return EVR_OK;
+}
+
+int evr_batch_step(evr_batch* b, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
+                   const int8_t* pol, const int64_t* offsets, int iters) {
+  if (!b || !offsets || iters < 0) return EVR_ERR_INVALID_ARG;
+  const long long n_ev = offsets[b->n];
+  for (int s = 0; s < b->n; ++s)
+    if (offsets[s + 1] < offsets[s] || offsets[0] != 0) return EVR_ERR_INVALID_ARG;
+  if (n_ev > 0 && (!x || !y || !t_us || !pol)) return EVR_ERR_INVALID_ARG;
+  const size_t need = (size_t)n_ev * 13 + sizeof(long long) * (b->n + 1) + 1024;
+  if (b->stage_cap < need) {
+    if (b->d_stage) {
+      cudaStreamSynchronize(b->stream);
+      cudaFree(b->d_stage);
+    }
+    b->d_stage = nullptr;
+    b->stage_cap = 0;
+    if (cudaMalloc((void**)&b->d_stage, need * 2) != cudaSuccess) return EVR_ERR_OOM;
+    b->stage_cap = need * 2;
+  }
+  char* q = b->d_stage;
+  long long* doff = (long long*)q;
+  q += (sizeof(long long) * (b->n + 1) + 255) / 256 * 256;
+  long long* dt = (long long*)q;
+  q += ((size_t)n_ev * 8 + 255) / 256 * 256;
+  uint16_t* dx = (uint16_t*)q;
+  q += ((size_t)n_ev * 2 + 255) / 256 * 256;
+  uint16_t* dy = (uint16_t*)q;
+  q += ((size_t)n_ev * 2 + 255) / 256 * 256;
+  int8_t* dp = (int8_t*)q;
+  cudaStream_t st = b->stream;
+  cudaError_t e = cudaMemcpyAsync(doff, offsets, sizeof(long long) * (b->n + 1),
+                                  cudaMemcpyHostToDevice, st);
+  if (n_ev > 0) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, t_us, n_ev * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, n_ev * 2, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, n_ev * 2, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, pol, n_ev, cudaMemcpyHostToDevice, st);
+  }
+  if (e != cudaSuccess) return EVR_ERR_CUDA;
+  // pageable sources: the copies above complete before returning to the caller
+  return evr_batch_step_device(b, dx, dy, (const int64_t*)dt, dp, (const int64_t*)doff, iters);
+}
+
+int evr_batch_get_image(evr_batch* b, int s, float* out_host, size_t len) {
+  if (!b || s < 0 || s >= b->n || !out_host) return EVR_ERR_INVALID_ARG;
+  const Planes& P = b->planes[s];
+  if (len < (size_t)P.W * P.H) return EVR_ERR_INVALID_ARG;
+  if (read_back(b)) return EVR_ERR_CUDA;
+  cudaError_t e = cudaMemcpy2DAsync(out_host, (size_t)P.W * 4, P.u[b->h_curs[s]],
+                                    (size_t)P.pitch * 4, (size_t)P.W * 4, P.H,
+                                    cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}
+
+int evr_batch_get_images(evr_batch* b, float* out_host, size_t len) {
+  if (!b || !out_host) return EVR_ERR_INVALID_ARG;
+  size_t need = 0;
+  for (int s = 0; s < b->n; ++s) need += (size_t)b->planes[s].W * b->planes[s].H;
+  if (len < need) return EVR_ERR_INVALID_ARG;
+  if (read_back(b)) return EVR_ERR_CUDA;
+  cudaError_t e = cudaSuccess;
+  float* q = out_host;
+  for (int s = 0; s < b->n && e == cudaSuccess; ++s) {
+    const Planes& P = b->planes[s];
+    e = cudaMemcpy2DAsync(q, (size_t)P.W * 4, P.u[b->h_curs[s]], (size_t)P.pitch * 4,
+                          (size_t)P.W * 4, P.H, cudaMemcpyDeviceToHost, b->stream);
+    q += (size_t)P.W * P.H;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}
+
+int evr_batch_get_state(evr_batch* b, int s, int which, void* out_host, size_t bytes) {
+  if (!b || s < 0 || s >= b->n || !out_host) return EVR_ERR_INVALID_ARG;
+  if (read_back(b)) return EVR_ERR_CUDA;
+  const Planes& P = b->planes[s];
+  const int cur = b->h_curs[s];
+  if (which == EVR_STATE_CLOCK || which == EVR_STATE_TINIT) {
+    if (bytes != 8) return EVR_ERR_INVALID_ARG;
+    long long v = which == EVR_STATE_CLOCK ? b->h_sc[s].clock
+                                           : (b->h_sc[s].t_init_set ? b->h_sc[s].t_init : 0);
+    std::memcpy(out_host, &v, 8);
+    return EVR_OK;
+  }
+  const void* src = nullptr;
+  size_t elem = 4;
+  switch (which) {
+    case EVR_STATE_U: src = P.u[cur]; break;
+    case EVR_STATE_P1: src = P.p1[cur]; break;
+    case EVR_STATE_P2: src = P.p2[cur]; break;
+    case EVR_STATE_P3: src = P.p3[cur]; break;
+    case EVR_STATE_F: src = P.f; break;
+    case EVR_STATE_SQRTG: src = P.sG; break;
+    case EVR_STATE_TX: src = P.tx; break;
+    case EVR_STATE_TY: src = P.ty; break;
+    case EVR_STATE_NPOS: src = P.npos; break;
+    case EVR_STATE_NNEG: src = P.nneg; break;
+    case EVR_STATE_TLAST: src = P.t_last; elem = 8; break;
+    default: return EVR_ERR_INVALID_ARG;
+  }
+  if (bytes != elem * P.W * P.H) return EVR_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpy2DAsync(out_host, elem * P.W, src, elem * P.pitch, elem * P.W, P.H,
+                                    cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return EVR_ERR_CUDA;
+  if (which == EVR_STATE_TLAST) {
+    long long t_init = b->h_sc[s].t_init_set ? b->h_sc[s].t_init : b->h_sc[s].clock;
+    long long* v = (long long*)out_host;
+    for (size_t i = 0; i < (size_t)P.W * P.H; ++i)
+      if (v[i] == kNeverFired) v[i] = t_init;
+  }
+  return EVR_OK;
+}
+
+int evr_batch_synchronize(evr_batch* b, int* stream_out) {
+  if (!b) return EVR_ERR_INVALID_ARG;
+  if (stream_out) *stream_out = -1;
+  if (read_back(b)) return EVR_ERR_CUDA;
+  int code = EVR_OK;
+  for (int s = 0; s < b->n; ++s) {
+    if (b->h_sc[s].status != 0) {
+      if (code == EVR_OK) {
+        code = b->h_sc[s].status;
+        if (stream_out) *stream_out = s;
+      }
+      if (cudaMemsetAsync(&b->planes[s].sc->status, 0, sizeof(int), b->stream) != cudaSuccess)
+        return EVR_ERR_CUDA;
+    }
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return EVR_ERR_CUDA;
+  return code;
+}
+
+int evr_batch_enable_kernel_timing(evr_batch* b, int enable) {
+  if (!b) return EVR_ERR_INVALID_ARG;
+  resolve_timing(b);
+  b->t_ms = 0.0;
+  b->t_launches = 0;
+  b->t_pixiters = 0;
+  b->timing = enable != 0;
+  return EVR_OK;
+}
+
+int evr_batch_kernel_time(evr_batch* b, double* ms, int64_t* launches, int64_t* pixel_iters) {
+  if (!b || !ms || !launches || !pixel_iters) return EVR_ERR_INVALID_ARG;
+  resolve_timing(b);
+  *ms = b->t_ms;
+  *launches = b->t_launches;
+  *pixel_iters = b->t_pixiters;
+  return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}
+
+const char* evr_batch_solver_name(evr_batch* b) { return b ? b->name : ""; }
+
+}  // extern "C"

@@ -48,6 +48,15 @@ struct Planes {
   int* flags;  // persistent solver: passes completed by each CTA (monotonic)
 };
 
+// Batched streams: per-stream plane descriptors and work items on the device.  A
+// kernel given a null `descs` works on the single stream passed by value.
+struct BatchRef {
+  const Planes* descs;  // per-stream planes, or null
+  const int2* work;     // work item per CTA: (stream, tile or block index)
+  const int* curs;      // per-stream buffer holding the current (u, p)
+  const int* active;    // per-stream: 1 when the stream has a packet in this step
+};
+
 struct SolveConsts {
   float tau, sigma, lambda, u_min, u_max;
 };
@@ -78,16 +87,35 @@ extern const SolverCfg kSolverCfgs[kNumSolverCfgs];
 constexpr int kGapBlocks = 304;   // fixed: the reduction order does not depend on W, H
 constexpr int kGapThreads = 256;
 
+// host helpers shared by the single-stream and batched runtimes (evr_api.cu)
+size_t state_bytes(int W, int H, bool solo);
+char* carve_state(char* base, int W, int H, bool solo, Planes* out);
+int check_device();
+
 // kernel launchers (evr_kernels.cu); all return cudaError_t as int
 int launch_init(const Planes& P, float u_init, long long clock0, long long t_init, int t_init_set,
                 void* stream);
 int launch_push(const Planes& P, const uint16_t* x, const uint16_t* y, const long long* t,
                 const int8_t* pol, int n, void* stream);
 int launch_prologue(const Planes& P, int cur, const PrologueConsts& c, void* stream);
+// Batched: one CTA of 32 x 8 threads per work item (stream, block); blocks of a W x H
+// stream are numbered by = b / ceil(W/32), bx = b % ceil(W/32).
+int launch_prologue_batch(const BatchRef& B, int n_work, const PrologueConsts& c, void* stream);
+// Batched push: CTA s validates and commits stream s's events
+// [offsets[s], offsets[s+1]) and sets active[s] = (count > 0).
+int launch_push_batch(const Planes* descs, int n_streams, const uint16_t* x, const uint16_t* y,
+                      const long long* t, const int8_t* pol, const long long* offsets,
+                      int* active, void* stream);
+// Batched buffer flip after `passes` tiled passes: curs[s] ^= passes & 1 for active s.
+int launch_batch_flip(int* curs, const int* active, int n_streams, int passes, void* stream);
 int launch_unfused_iteration(const Planes& P, int cur, const SolveConsts& c, void* stream);
 // kind 1: `iters` <= R iterations from buffer src into buffer 1 - src.
 int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters,
                       const SolveConsts& c, void* stream);
+// kind 1 over a batch: one CTA per work item (stream, tile); pass j of a step reads
+// buffer curs[s] ^ (j & 1).  Inactive streams are skipped.
+int launch_tiled_pass_batch(const BatchRef& B, int n_work, const SolverCfg& cfg, int pass,
+                            int iters, const SolveConsts& c, void* stream);
 // kind 2: all `iters` iterations from buffer cur; the result lands in buffer
 // cur ^ (ceil(iters / R) & 1).  `base` is the value of every CTA's progress flag at
 // launch (flags cleared by the host start at 0; each launch adds passes - 1).

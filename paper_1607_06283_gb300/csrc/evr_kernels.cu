@@ -72,7 +72,7 @@ __global__ void k_init(Planes P, float u_init, long long clock0, long long t_ini
     P.sc->first_bad = INT_MAX;
     P.sc->abort = 0;
   }
-  if (y == 0 && x < kMaxCtas) P.flags[x] = 0;
+  if (P.flags && y == 0 && x < kMaxCtas) P.flags[x] = 0;  // solo streams only
   if (x >= P.pitch || y >= P.H) return;
   size_t i = (size_t)y * P.pitch + x;
   for (int b = 0; b < 2; ++b) {
@@ -145,10 +145,10 @@ __device__ __forceinline__ void commit_events(const Planes& P, const uint16_t* x
 
 // One CTA validates the whole packet, then commits it: a rejected packet changes
 // nothing (Sec. 3 requires theta in {-1,1}, pixels on the sensor, increasing t).
-__global__ void __launch_bounds__(1024) k_push_one_cta(Planes P, const uint16_t* __restrict__ x,
-                                                       const uint16_t* __restrict__ y,
-                                                       const long long* __restrict__ t,
-                                                       const int8_t* __restrict__ pol, int n) {
+__device__ __forceinline__ void push_cta(const Planes& P, const uint16_t* __restrict__ x,
+                                         const uint16_t* __restrict__ y,
+                                         const long long* __restrict__ t,
+                                         const int8_t* __restrict__ pol, int n) {
   __shared__ int s_bad;
   __shared__ long long s_clock;
   __shared__ int s_have;
@@ -176,6 +176,58 @@ __global__ void __launch_bounds__(1024) k_push_one_cta(Planes P, const uint16_t*
     }
     P.sc->clock = t[n - 1] > s_clock ? t[n - 1] : s_clock;
   }
+}
+
+__global__ void __launch_bounds__(1024) k_push_one_cta(Planes P, const uint16_t* __restrict__ x,
+                                                       const uint16_t* __restrict__ y,
+                                                       const long long* __restrict__ t,
+                                                       const int8_t* __restrict__ pol, int n) {
+  push_cta(P, x, y, t, pol, n);
+}
+
+constexpr int kErrInvalidArg = -1;
+constexpr int kMaxBatchPacket = 32768;
+
+// Batched push: CTA s handles stream s.  Packets above kMaxBatchPacket events are
+// rejected with EVR_ERR_INVALID_ARG (state unchanged).
+__global__ void __launch_bounds__(1024) k_push_batch(const Planes* __restrict__ descs,
+                                                     const uint16_t* __restrict__ x,
+                                                     const uint16_t* __restrict__ y,
+                                                     const long long* __restrict__ t,
+                                                     const int8_t* __restrict__ pol,
+                                                     const long long* __restrict__ offsets,
+                                                     int* active) {
+  const int s = blockIdx.x;
+  const long long a = offsets[s], b = offsets[s + 1];
+  const Planes& P = descs[s];
+  if (threadIdx.x == 0) active[s] = b > a ? 1 : 0;
+  if (b <= a) return;
+  if (b - a > kMaxBatchPacket) {
+    if (threadIdx.x == 0) atomicCAS(&P.sc->status, 0, kErrInvalidArg);
+    return;
+  }
+  push_cta(P, x + a, y + a, t + a, pol + a, (int)(b - a));
+}
+
+int launch_push_batch(const Planes* descs, int n_streams, const uint16_t* x, const uint16_t* y,
+                      const long long* t, const int8_t* pol, const long long* offsets,
+                      int* active, void* stream) {
+  if (n_streams <= 0) return 0;
+  k_push_batch<<<n_streams, 1024, 0, (cudaStream_t)stream>>>(descs, x, y, t, pol, offsets,
+                                                             active);
+  return (int)cudaGetLastError();
+}
+
+__global__ void k_batch_flip(int* curs, const int* active, int n, int passes) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n && active[s] && (passes & 1)) curs[s] ^= 1;
+}
+
+int launch_batch_flip(int* curs, const int* active, int n_streams, int passes, void* stream) {
+  if (n_streams <= 0) return 0;
+  k_batch_flip<<<(n_streams + 255) / 256, 256, 0, (cudaStream_t)stream>>>(curs, active,
+                                                                          n_streams, passes);
+  return (int)cudaGetLastError();
 }
 
 // Large packets: grid-wide validation, then a commit kernel that checks the result.
@@ -247,10 +299,21 @@ __device__ __forceinline__ float time_surface(long long tl, long long clock, lon
 // Per pixel: L_x t, L_y t (forward differences, zero on the last column/row), G,
 // 1/G, sqrt G (Eq. 2, text after Eq. 3), and the data image
 // f = base * exp(Delta+ n+ - Delta- n-) (Eq. intensity_update, one factor per event);
-// the counts are then cleared.
-__global__ void k_prologue(Planes P, int cur, PrologueConsts c) {
-  int x = blockIdx.x * blockDim.x + threadIdx.x;
-  int y = blockIdx.y * blockDim.y + threadIdx.y;
+// the counts are then cleared.  One kernel serves a single stream (B.descs null,
+// blocks numbered over its image) and a batch (one work item per CTA).
+__global__ void __launch_bounds__(256) k_prologue(Planes P, int cur, PrologueConsts c,
+                                                  BatchRef B) {
+  int blk = blockIdx.x;
+  if (B.descs) {
+    const int2 w = B.work[blockIdx.x];
+    if (!B.active[w.x]) return;
+    P = B.descs[w.x];
+    cur = B.curs[w.x];
+    blk = w.y;
+  }
+  const int nbx = (P.W + 31) / 32;
+  const int x = (blk % nbx) * 32 + threadIdx.x;
+  const int y = (blk / nbx) * 8 + threadIdx.y;
   if (x >= P.W || y >= P.H) return;
   long long clock = P.sc->clock;
   long long t_init = P.sc->t_init_set ? P.sc->t_init : clock;
@@ -272,8 +335,17 @@ __global__ void k_prologue(Planes P, int cur, PrologueConsts c) {
 }
 
 int launch_prologue(const Planes& P, int cur, const PrologueConsts& c, void* stream) {
-  dim3 blk(32, 8), grd((P.W + 31) / 32, (P.H + 7) / 8);
-  k_prologue<<<grd, blk, 0, (cudaStream_t)stream>>>(P, cur, c);
+  const int nb = ((P.W + 31) / 32) * ((P.H + 7) / 8);
+  k_prologue<<<nb, dim3(32, 8), 0, (cudaStream_t)stream>>>(P, cur, c,
+                                                            BatchRef{nullptr, nullptr, nullptr,
+                                                                     nullptr});
+  return (int)cudaGetLastError();
+}
+
+int launch_prologue_batch(const BatchRef& B, int n_work, const PrologueConsts& c, void* stream) {
+  if (n_work <= 0) return 0;
+  Planes dummy{};
+  k_prologue<<<n_work, dim3(32, 8), 0, (cudaStream_t)stream>>>(dummy, 0, c, B);
   return (int)cudaGetLastError();
 }
 

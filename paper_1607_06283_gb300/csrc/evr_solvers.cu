@@ -285,10 +285,20 @@ struct Tile {
 // the next pass launch -- so no pass can run ahead of the prologue.
 template <int KX, int KY, int NTY>
 __global__ void __launch_bounds__(32 * NTY) k_tiled(Planes P, int src, int iters, int R,
-                                                    SolveConsts c, int tiles_x) {
+                                                    SolveConsts c, int tiles_x, BatchRef B,
+                                                    int pass) {
   __shared__ TileSmem<KX, KY, NTY> sm;
+  int tile = blockIdx.x;
+  if (B.descs) {  // batch: this CTA's (stream, tile); one code path for both uses
+    const int2 w = B.work[blockIdx.x];
+    if (!B.active[w.x]) return;
+    P = B.descs[w.x];
+    src = B.curs[w.x] ^ (pass & 1);
+    tiles_x = (P.W + (32 * KX - 2 * R) - 1) / (32 * KX - 2 * R);
+    tile = w.y;
+  }
   Tile<KX, KY, NTY> T;
-  T.setup(blockIdx.x, tiles_x, R);
+  T.setup(tile, tiles_x, R);
   Tile<KX, KY, NTY>::zero_pads(sm);
   T.load_consts(P, c);
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -384,13 +394,11 @@ static int tiles_of(const Planes& P, int R, int* tx, int* ty) {
 }
 
 template <int KX, int KY, int NTY>
-static int run_tiled(const Planes& P, int R, int src, int iters, const SolveConsts& c,
-                     cudaStream_t st) {
-  int tx, ty;
-  if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters > R || iters < 1)
-    return (int)cudaErrorInvalidValue;
+static int launch_k_tiled(int blocks, const Planes& P, int src, int iters, int R,
+                          const SolveConsts& c, int tx, const BatchRef& B, int pass,
+                          cudaStream_t st) {
   cudaLaunchConfig_t lc = {};
-  lc.gridDim = dim3(tx * ty);
+  lc.gridDim = dim3(blocks);
   lc.blockDim = dim3(32, NTY);
   lc.stream = st;
   cudaLaunchAttribute at[1];
@@ -398,7 +406,27 @@ static int run_tiled(const Planes& P, int R, int src, int iters, const SolveCons
   at[0].val.programmaticStreamSerializationAllowed = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  return (int)cudaLaunchKernelEx(&lc, k_tiled<KX, KY, NTY>, P, src, iters, R, c, tx);
+  return (int)cudaLaunchKernelEx(&lc, k_tiled<KX, KY, NTY>, P, src, iters, R, c, tx, B, pass);
+}
+
+template <int KX, int KY, int NTY>
+static int run_tiled(const Planes& P, int R, int src, int iters, const SolveConsts& c,
+                     cudaStream_t st) {
+  int tx, ty;
+  if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters > R || iters < 1)
+    return (int)cudaErrorInvalidValue;
+  return launch_k_tiled<KX, KY, NTY>(tx * ty, P, src, iters, R, c, tx,
+                                     BatchRef{nullptr, nullptr, nullptr, nullptr}, 0, st);
+}
+
+template <int KX, int KY, int NTY>
+static int run_tiled_batch(const BatchRef& B, int n_work, int R, int pass, int iters,
+                           const SolveConsts& c, cudaStream_t st) {
+  const int OW = 32 * KX - 2 * R, OH = NTY * KY - 2 * R;
+  if (R < 1 || OW < R || OH < R || iters > R || iters < 1) return (int)cudaErrorInvalidValue;
+  if (n_work <= 0) return 0;
+  Planes dummy{};
+  return launch_k_tiled<KX, KY, NTY>(n_work, dummy, 0, iters, R, c, 0, B, pass, st);
 }
 
 template <int KX, int KY, int NTY>
@@ -445,6 +473,14 @@ int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters,
                       const SolveConsts& c, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   EVR_SHAPE_DISPATCH(run_tiled, P, cfg.R, src, iters, c, st)
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_tiled_pass_batch(const BatchRef& B, int n_work, const SolverCfg& cfg, int pass,
+                            int iters, const SolveConsts& c, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cfg.kind != 1) return (int)cudaErrorInvalidValue;
+  EVR_SHAPE_DISPATCH(run_tiled_batch, B, n_work, cfg.R, pass, iters, c, st)
   return (int)cudaErrorInvalidValue;
 }
 

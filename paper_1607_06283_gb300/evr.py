@@ -92,6 +92,18 @@ def _load():
         "evr_unrolled_backward": ([vp] * 3 + [i, i, i] + [ctypes.c_float] * 5 + [i, i] +
                                   [vp] * 8, i),
         "evr_data_image": ([vp] * 3 + [i, i, i, ctypes.c_float, ctypes.c_float, vp, vp], i),
+        "evr_batch_create": ([i, vp, vp, vp, vp], i),
+        "evr_batch_destroy": ([vp], None),
+        "evr_batch_set_cuda_stream": ([vp, vp], i),
+        "evr_batch_step_device": ([vp] * 6 + [i], i),
+        "evr_batch_step": ([vp] * 6 + [i], i),
+        "evr_batch_get_image": ([vp, i, vp, sz], i),
+        "evr_batch_get_state": ([vp, i, i, vp, sz], i),
+        "evr_batch_get_images": ([vp, vp, sz], i),
+        "evr_batch_synchronize": ([vp, vp], i),
+        "evr_batch_enable_kernel_timing": ([vp, i], i),
+        "evr_batch_kernel_time": ([vp, vp, vp, vp], i),
+        "evr_batch_solver_name": ([vp], ctypes.c_char_p),
         "evr_data_image_backward": ([vp] * 4 + [i, i, i, ctypes.c_float, ctypes.c_float] +
                                     [vp] * 5, i),
     }
@@ -313,3 +325,100 @@ class Stream:
     @property
     def solver_name(self) -> str:
         return evr_solver_name(self.h)
+
+
+class Batch:
+    """Owning wrapper of an evr_batch handle: n streams of sizes (W[s], H[s])."""
+
+    def __init__(self, sizes, params: evr_params | None = None, **overrides):
+        p = params or evr_default_params()
+        for k, v in overrides.items():
+            setattr(p, "lambda_" if k == "lam" else k, v)
+        self.sizes = [(int(w), int(h)) for w, h in sizes]
+        self.n = len(self.sizes)
+        self.params = p
+        W = (ctypes.c_int * self.n)(*[w for w, _ in self.sizes])
+        H = (ctypes.c_int * self.n)(*[h for _, h in self.sizes])
+        h = ctypes.c_void_p()
+        _check(_lib.evr_batch_create(self.n, W, H, ctypes.byref(p), ctypes.byref(h)),
+               "evr_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.evr_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_cuda_stream(self, handle) -> None:
+        arg = handle if isinstance(handle, ctypes.c_void_p) else ctypes.c_void_p(int(handle))
+        _check(_lib.evr_batch_set_cuda_stream(self.h, arg), "evr_batch_set_cuda_stream")
+
+    def step(self, x, y, t, pol, offsets, iters: int) -> None:
+        """Host arrays: all streams' events concatenated; offsets (n+1) int64."""
+        x, px = _host(x, np.uint16)
+        y, py = _host(y, np.uint16)
+        t, pt = _host(t, np.int64)
+        p, pp = _host(pol, np.int8)
+        o, po = _host(offsets, np.int64)
+        if len(o) != self.n + 1:
+            raise ValueError("offsets must have n + 1 entries")
+        _check(_lib.evr_batch_step(self.h, px, py, pt, pp, po, int(iters)), "evr_batch_step")
+
+    def step_device(self, x, y, t, pol, offsets, iters: int) -> None:
+        """torch CUDA tensors; offsets int64 of n + 1 entries on the device."""
+        _check(_lib.evr_batch_step_device(self.h, x.data_ptr(), y.data_ptr(), t.data_ptr(),
+                                          pol.data_ptr(), offsets.data_ptr(), int(iters)),
+               "evr_batch_step_device")
+
+    def image(self, s: int) -> np.ndarray:
+        W, H = self.sizes[s]
+        out = np.empty((H, W), np.float32)
+        _check(_lib.evr_batch_get_image(self.h, int(s), out.ctypes.data, out.size),
+               "evr_batch_get_image")
+        return out
+
+    def images(self, out: np.ndarray | None = None) -> np.ndarray:
+        """All images concatenated (float32, sum of W*H)."""
+        n = sum(w * h for w, h in self.sizes)
+        if out is None:
+            out = np.empty(n, np.float32)
+        _check(_lib.evr_batch_get_images(self.h, out.ctypes.data, out.size),
+               "evr_batch_get_images")
+        return out
+
+    def state(self, s: int, which: int):
+        W, H = self.sizes[s]
+        if which in (EVR_STATE_CLOCK, EVR_STATE_TINIT):
+            out = np.zeros(1, np.int64)
+        else:
+            out = np.empty((H, W), _STATE_DT[which])
+        _check(_lib.evr_batch_get_state(self.h, int(s), int(which), out.ctypes.data, out.nbytes),
+               "evr_batch_get_state")
+        return out[0] if which in (EVR_STATE_CLOCK, EVR_STATE_TINIT) else out
+
+    def synchronize(self):
+        s = ctypes.c_int(-1)
+        rc = _lib.evr_batch_synchronize(self.h, ctypes.byref(s))
+        if rc == EVR_ERR_CUDA:
+            _check(rc, "evr_batch_synchronize")
+        return rc, s.value
+
+    def enable_kernel_timing(self, on: bool) -> None:
+        _check(_lib.evr_batch_enable_kernel_timing(self.h, 1 if on else 0),
+               "evr_batch_enable_kernel_timing")
+
+    def kernel_time(self):
+        ms, la, pi = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.evr_batch_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(la),
+                                          ctypes.byref(pi)), "evr_batch_kernel_time")
+        return ms.value, la.value, pi.value
+
+    @property
+    def solver_name(self) -> str:
+        return _lib.evr_batch_solver_name(self.h).decode()

@@ -1,0 +1,128 @@
+"""Batched streams (evr_batch_*) through the C ABI: every stream bit-identical to the
+same stream solved alone with the same solver configuration, per-stream validation,
+idle streams untouched, and one stream checked against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from evsim import CONFIGS, make_stream
+from evsim.configs import StreamConfig, batch_step_arrays, make_batch
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(33, 17), (64, 48), (128, 128), (17, 33), (1, 1), (100, 3), (57, 57), (240, 180),
+         (3, 100), (80, 64)]
+COUNTS = [6, 3, 8, 1, 5, 7, 2, 6, 4, 8]
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_06283_gb300 import build
+    build.build()
+    from paper_1607_06283_gb300 import evr
+    return evr
+
+
+@pytest.fixture(scope="module")
+def streams():
+    cfgs = []
+    for s, ((W, H), cnt) in enumerate(zip(SIZES, COUNTS)):
+        kind = "rects" if s % 2 == 0 else "blobs"
+        cfgs.append(StreamConfig(f"t{s}", W, H, kind, 12, 500 + s, cnt * 300, 300, 30,
+                                 speed=150.0, omega=0.5, noise=0.02))
+    return make_batch(cfgs)
+
+
+def run_batch(E, streams, tile, steps, iters=30):
+    b = E.Batch(SIZES, tile_config=tile)
+    for k in range(steps):
+        x, y, t, p, off = batch_step_arrays(streams, 300, k)
+        b.step(x, y, t, p, off, iters)
+    return b
+
+
+def run_solo(E, st, tile, steps, iters=30):
+    g = E.Stream(st.W, st.H, solver=2, tile_config=tile)
+    for k in range(steps):
+        a = k * 300
+        if a >= len(st):
+            continue
+        s = st.slice(a, a + 300)
+        assert g.push(s.x, s.y, s.t, s.pol) == 0
+        g.solve(iters)
+    return g
+
+
+PLANES = None
+
+
+@pytest.mark.parametrize("tile", [1, 6, 10])
+def test_batch_equals_solo_bit_for_bit(E, streams, tile):
+    steps = max(COUNTS)
+    b = run_batch(E, streams, tile, steps)
+    rc, bad = b.synchronize()
+    assert rc == 0 and bad == -1
+    for s, st in enumerate(streams):
+        g = run_solo(E, st, tile, steps)
+        for w in (E.EVR_STATE_U, E.EVR_STATE_P1, E.EVR_STATE_P2, E.EVR_STATE_P3,
+                  E.EVR_STATE_F, E.EVR_STATE_TLAST, E.EVR_STATE_SQRTG):
+            np.testing.assert_array_equal(b.state(s, w), g.state(w), err_msg=f"stream {s} {w}")
+        assert int(b.state(s, E.EVR_STATE_CLOCK)) == int(g.state(E.EVR_STATE_CLOCK))
+        g.close()
+    b.close()
+
+
+def test_autotuned_batch_runs_and_matches_oracle(E, streams):
+    """Autotuned configuration; stream 2 (128x128) teacher-forced against the oracle on
+    its last packet."""
+    b = E.Batch(SIZES)
+    s_idx = 2
+    st = streams[s_idx]
+    steps = COUNTS[s_idx]
+    p = b.params
+    o = O.OracleStream(st.W, st.H, O.OracleParams(
+        lam=float(p.lambda_), delta_pos=float(p.delta_pos), delta_neg=float(p.delta_neg),
+        u_min=float(p.u_min), u_max=float(p.u_max), u_init=float(p.u_init), tau=float(p.tau),
+        sigma=float(p.sigma), time_scale=float(np.float32(p.time_scale))))
+    for k in range(steps):
+        x, y, t, pol, off = batch_step_arrays(streams, 300, k)
+        s = st.slice(k * 300, k * 300 + 300)
+        if k == steps - 1:
+            o.set_up(b.state(s_idx, E.EVR_STATE_U).astype(np.float64),
+                     np.stack([b.state(s_idx, w) for w in (E.EVR_STATE_P1, E.EVR_STATE_P2,
+                                                           E.EVR_STATE_P3)]).astype(np.float64))
+            o.set(O.TLAST, b.state(s_idx, E.EVR_STATE_TLAST))
+            o.set(O.TREF, int(b.state(s_idx, E.EVR_STATE_CLOCK)))
+            o.set(O.TINIT, int(b.state(s_idx, E.EVR_STATE_TINIT)))
+            assert o.push(s.x, s.y, s.t, s.pol) == 0
+            o.solve(30)
+        b.step(x, y, t, pol, off, 30)
+    assert "batch of 10" in b.solver_name
+    d = np.max(np.abs(b.image(s_idx).astype(np.float64) - o.u))
+    assert d <= 1e-4, d
+    b.close()
+
+
+def test_rejection_is_per_stream_and_idle_streams_are_untouched(E, streams):
+    b = run_batch(E, streams, 1, 2)
+    before = [b.state(s, E.EVR_STATE_U).copy() for s in range(len(SIZES))]
+    x, y, t, p, off = batch_step_arrays(streams, 300, 2)
+    # stream 4 (1x1, still has packets) gets an out-of-range event; stream 1 (3 packets)
+    # stays idle this step by removing its events
+    a4, b4 = off[4], off[5]
+    x = x.copy()
+    x[a4] = 1
+    keep = np.ones(len(x), bool)
+    keep[off[1]:off[2]] = False
+    cnt = np.diff(off)
+    cnt[1] = 0
+    off2 = np.concatenate([[0], np.cumsum(cnt)])
+    b.step(x[keep], y[keep], t[keep], p[keep], off2, 30)
+    rc, bad = b.synchronize()
+    assert rc == E.EVR_ERR_OUT_OF_RANGE and bad == 4
+    np.testing.assert_array_equal(b.state(1, E.EVR_STATE_U), before[1])
+    assert b.synchronize() == (0, -1)
+    b.close()
