@@ -4,8 +4,8 @@ idle streams untouched, and one stream checked against the FP64 oracle."""
 import numpy as np
 import pytest
 
-from evsim import CONFIGS, make_stream
-from evsim.configs import StreamConfig, batch_step_arrays, make_batch
+from evsim.configs import batch_step_arrays
+from evsim.events import EventStream
 from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -28,12 +28,18 @@ def E():
 
 @pytest.fixture(scope="module")
 def streams():
-    cfgs = []
+    """Random packets (uniform pixels, increasing timestamps with repeats, +-1) for
+    sensors down to 1 x 1, with uneven packet counts."""
+    out = []
     for s, ((W, H), cnt) in enumerate(zip(SIZES, COUNTS)):
-        kind = "rects" if s % 2 == 0 else "blobs"
-        cfgs.append(StreamConfig(f"t{s}", W, H, kind, 12, 500 + s, cnt * 300, 300, 30,
-                                 speed=150.0, omega=0.5, noise=0.02))
-    return make_batch(cfgs)
+        rng = np.random.default_rng(500 + s)
+        n = cnt * 300
+        x = rng.integers(0, W, n).astype(np.uint16)
+        y = rng.integers(0, H, n).astype(np.uint16)
+        t = (1000 + np.sort(rng.integers(0, 40 * n, n))).astype(np.int64)
+        p = rng.choice(np.array([-1, 1], np.int8), n)
+        out.append(EventStream(W, H, x, y, t, p))
+    return out
 
 
 def run_batch(E, streams, tile, steps, iters=30):
@@ -54,9 +60,6 @@ def run_solo(E, st, tile, steps, iters=30):
         assert g.push(s.x, s.y, s.t, s.pol) == 0
         g.solve(iters)
     return g
-
-
-PLANES = None
 
 
 @pytest.mark.parametrize("tile", [1, 6, 10])

@@ -154,5 +154,6 @@ def test_fit_lambda_and_threshold_to_target(T):
         opt.step()
         losses.append(float(loss.detach()))
     assert losses[-1] < 0.05 * losses[0]
-    assert abs(float(C) - 0.2) < abs(0.1 - 0.2) * 0.5
-    assert abs(math.log(float(logl.exp()) / 25.0)) < abs(math.log(60.0 / 25.0))
+    c_fit, l_fit = float(C.detach()), float(logl.detach().exp())
+    assert abs(c_fit - 0.2) < abs(0.1 - 0.2) * 0.5
+    assert abs(math.log(l_fit / 25.0)) < abs(math.log(60.0 / 25.0))
