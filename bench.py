@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solver", type=int, default=0, help="evr_params.solver")
     ap.add_argument("--tile", type=int, default=0, help="evr_params.tile_config")
+    ap.add_argument("--storage", type=int, default=0, help="evr_params.storage (0 FP32, 1 FP16, "
+                    "2 BF16)")
+    ap.add_argument("--check-error", action="store_true",
+                    help="also state the max-abs error vs the FP64 oracle on one packet")
     return ap.parse_args()
 
 
@@ -55,10 +59,12 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def workload(name, rank):
+def workload(name, rank, max_packets=None):
     from evsim import CONFIGS, make_stream
     from paper_1607_06283_gb300.shard import stream_seed
     cfg = CONFIGS[name]
+    if max_packets is not None and cfg.n_packets > max_packets:
+        cfg = cfg.with_events(max_packets * cfg.packet)  # only the packets the run uses
     if rank:
         d = dict(cfg.__dict__)
         d["seed"] = stream_seed(cfg.seed, rank)
@@ -193,12 +199,45 @@ def cpu_baseline(cfg, stream, budget_s, max_packets=None):
                       f"single thread, {dt:.1f} s"}
 
 
+def error_vs_oracle(E, cfg, stream, p):
+    """Max |u_gpu - u_oracle| on the third packet, teacher-forced (the oracle starts
+    from the GPU's state), with the run's parameters."""
+    from oracle import oracle as O
+    g = E.Stream(cfg.W, cfg.H, p)
+    o = O.OracleStream(cfg.W, cfg.H, O.OracleParams(
+        lam=float(p.lambda_), delta_pos=float(p.delta_pos), delta_neg=float(p.delta_neg),
+        u_min=float(p.u_min), u_max=float(p.u_max), u_init=float(p.u_init), tau=float(p.tau),
+        sigma=float(p.sigma), time_scale=float(np.float32(p.time_scale)),
+        t_max_us=int(p.t_max_us)))
+    for k in range(2):
+        a = k * cfg.packet
+        g.push(stream.x[a:a + cfg.packet], stream.y[a:a + cfg.packet],
+               stream.t[a:a + cfg.packet], stream.pol[a:a + cfg.packet])
+        g.solve(cfg.iters)
+    o.set_up(g.state(E.EVR_STATE_U).astype(np.float64), g.p().astype(np.float64))
+    o.set(O.TLAST, g.state(E.EVR_STATE_TLAST))
+    o.set(O.TREF, int(g.state(E.EVR_STATE_CLOCK)))
+    o.set(O.TINIT, int(g.state(E.EVR_STATE_TINIT)))
+    a = 2 * cfg.packet
+    sl = slice(a, a + cfg.packet)
+    g.push(stream.x[sl], stream.y[sl], stream.t[sl], stream.pol[sl])
+    o.push(stream.x[sl], stream.y[sl], stream.t[sl], stream.pol[sl])
+    g.solve(cfg.iters)
+    o.solve(cfg.iters)
+    d = np.abs(g.image().astype(np.float64) - o.u)
+    g.close()
+    return {"max_abs": float(d.max()), "p99_9": float(np.percentile(d, 99.9)),
+            "sample": "packet 3, teacher-forced, FP64 oracle"}
+
+
 # ----------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    cfg, stream = workload(args.config, 0)
+    big = args.config != "blobs346"
+    cfg, stream = workload(args.config, 0,
+                           max_packets=args.warmup + args.steps if big else None)
     from oracle import oracle as O
     o = O.OracleStream(cfg.W, cfg.H)
     steps = list(packet_slices(stream, cfg, args.warmup + args.steps))
@@ -254,12 +293,15 @@ def run_ours(args):
         pg.barrier()
     from paper_1607_06283_gb300 import evr as E
 
-    cfg, stream = workload(args.config, rank)
+    big = args.config != "blobs346"
+    cfg, stream = workload(args.config, rank,
+                           max_packets=args.warmup + args.steps if big else None)
     cur = torch.cuda.Stream()  # one non-default stream for the library and the timing events
     torch.cuda.set_stream(cur)
     p = E.evr_default_params()
     p.solver = args.solver
     p.tile_config = args.tile
+    p.storage = args.storage
     g = E.Stream(cfg.W, cfg.H, p)
     E.evr_set_cuda_stream(g.h, cur.cuda_stream)
 
@@ -359,7 +401,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": ["f32", "f32 (p, ubar stored f16)",
+                                           "f32 (p, ubar stored bf16)"][args.storage],
+            "data": "synthetic",
             "gpix_iter_per_s": gpix,
             "config": {"workload": describe(cfg), "sensor": f"{cfg.W}x{cfg.H}",
                        "events_per_step": cfg.packet, "iters": cfg.iters,
@@ -381,6 +425,8 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(cfg, stream, args.cpu_budget_s)
+        if args.check_error:
+            line["error_vs_fp64"] = error_vs_oracle(E, cfg, stream, p)
         print(json.dumps(line), flush=True)
     g.close()
     g2.close()

@@ -52,7 +52,7 @@ CONFIGS = {
     # 1280x720, 1000 blobs in 8 layers with velocities in a 500 px/s disc, mild rotation
     "blobs1280": StreamConfig("blobs1280", 1280, 720, "blobs", 1000, 1004, 10_000_000, 5000,
                               100, speed=500.0, omega=0.2, noise=0.02, layers=8,
-                              speed_disc=True, dt_us=100.0),
+                              speed_disc=True, dt_us=400.0),
 }
 
 

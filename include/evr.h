@@ -73,7 +73,12 @@ typedef struct {
                          1: f persists between packets, stepped at event pixels */
   int manifold;       /* 1: t from the events (default); 0: t = const (Sec. 4.2) */
   int solver;         /* EVR_SOLVER_*; default EVR_SOLVER_AUTO */
-  int tile_config;    /* tiled solver shape index (0 = let the autotuner choose) */
+  int tile_config;    /* solver configuration index (0 = let the autotuner choose) */
+  int storage;        /* format of the dual variable p (between launches) and of the
+                         over-relaxed ubar (shared memory): 0 FP32 (default), 1 FP16,
+                         2 BF16; arithmetic stays FP32 and both are rounded to the format
+                         every iteration.  16-bit formats need the multi-launch tiled
+                         solver (not the unfused or persistent ones). */
 } evr_params;
 
 typedef struct evr_stream evr_stream; /* opaque handle */

@@ -111,6 +111,11 @@ int params_valid(const evr_params* p) {
   if (p->manifold != 0 && p->manifold != 1) return 0;
   if (p->solver < 0 || p->solver > EVR_SOLVER_TILED) return 0;
   if (p->tile_config < 0 || p->tile_config > kNumSolverCfgs) return 0;
+  if (p->storage < 0 || p->storage > 2) return 0;
+  if (p->storage != 0) {
+    if (p->solver == EVR_SOLVER_UNFUSED) return 0;
+    if (p->tile_config > 0 && kSolverCfgs[p->tile_config - 1].kind != 1) return 0;
+  }
   return 1;
 }
 
@@ -257,6 +262,7 @@ void autotune(evr_stream* s, int iters) {
   int best_cfg = 0;
   for (int ci = 0; ci < kNumSolverCfgs; ++ci) {
     if (!solver_cfg_usable(s->P, kSolverCfgs[ci])) continue;
+    if (s->P.storage != 0 && kSolverCfgs[ci].kind != 1) continue;  // 16-bit p: kind 1 only
     s->cfg = ci;
     clear_flags(s);
     bool ok = run_cfg_direct(s, ci, iters) == 0;  // warm-up (module load)
@@ -453,6 +459,7 @@ int evr_create(int W, int H, const evr_params* params, evr_stream** out) {
   }
   s->dev_base = base;
   char* q = evr::carve_state(base, W, H, true, &s->P);
+  s->P.storage = params->storage;
   s->d_gap = (double*)q;
   Planes& P = s->P;
   int rc = EVR_OK;
@@ -685,6 +692,11 @@ int evr_get_state(evr_stream* s, int which, void* out_host, size_t bytes) {
   size_t elem = 0;
   void* src = plane_ptr(s, which, &elem);
   if (!src || bytes != elem * s->W * s->H) return EVR_ERR_INVALID_ARG;
+  if (s->P.storage != 0 && which >= EVR_STATE_P1 && which <= EVR_STATE_P3) {
+    // 16-bit p: widen into the (otherwise unused) ubar plane first
+    if (launch_p_convert(s->P, src, s->P.ubar, 1, s->stream)) return EVR_ERR_CUDA;
+    src = s->P.ubar;
+  }
   cudaError_t e = cudaMemcpy2DAsync(out_host, elem * s->W, src, elem * s->pitch, elem * s->W,
                                     s->H, cudaMemcpyDeviceToHost, s->stream);
   if (e != cudaSuccess) return EVR_ERR_CUDA;
@@ -704,8 +716,12 @@ int evr_set_state(evr_stream* s, int which, const void* in_host, size_t bytes) {
   size_t elem = 0;
   void* dst = plane_ptr(s, which, &elem);
   if (bytes != elem * s->W * s->H) return EVR_ERR_INVALID_ARG;
-  cudaError_t e = cudaMemcpy2DAsync(dst, elem * s->pitch, in_host, elem * s->W, elem * s->W,
-                                    s->H, cudaMemcpyHostToDevice, s->stream);
+  const bool narrow = s->P.storage != 0 && which != EVR_STATE_U;
+  cudaError_t e = cudaMemcpy2DAsync(narrow ? (void*)s->P.ubar : dst, elem * s->pitch, in_host,
+                                    elem * s->W, elem * s->W, s->H, cudaMemcpyHostToDevice,
+                                    s->stream);
+  if (e == cudaSuccess && narrow && launch_p_convert(s->P, dst, s->P.ubar, 0, s->stream))
+    e = cudaErrorUnknown;
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   return cuda_err(e);
 }

@@ -126,11 +126,13 @@ void autotune(evr_batch* b) {
     if (build_tile_work(b, ci)) continue;
     const int R = kSolverCfgs[ci].R;
     BatchRef B = bref(b, true);
-    launch_tiled_pass_batch(B, b->n_work_tile, kSolverCfgs[ci], 0, R, c, b->stream);
+    launch_tiled_pass_batch(B, b->n_work_tile, kSolverCfgs[ci], 0, R, c, b->prm.storage,
+                            b->stream);
     cudaEventRecord(e0, b->stream);
     const int reps = 4;
     for (int r = 0; r < reps; ++r)
-      launch_tiled_pass_batch(B, b->n_work_tile, kSolverCfgs[ci], 0, R, c, b->stream);
+      launch_tiled_pass_batch(B, b->n_work_tile, kSolverCfgs[ci], 0, R, c, b->prm.storage,
+                              b->stream);
     cudaEventRecord(e1, b->stream);
     float ms = 0.f;
     if (cudaEventSynchronize(e1) == cudaSuccess && cudaGetLastError() == cudaSuccess) {
@@ -181,7 +183,7 @@ int step_graph(evr_batch* b, int iters, cudaGraphExec_t* out) {
     for (int done = 0; done < iters; done += cfg.R, ++passes) {
       int k = iters - done < cfg.R ? iters - done : cfg.R;
       bad |= launch_tiled_pass_batch(bref(b, true), b->n_work_tile, cfg, passes, k, c,
-                                     b->cap_stream);
+                                     b->prm.storage, b->cap_stream);
     }
     bad |= launch_batch_flip(b->d_curs, b->d_active, b->n, passes, b->cap_stream);
   }
@@ -245,6 +247,7 @@ int evr_batch_create(int n, const int* W, const int* H, const evr_params* params
   std::vector<int2> pro;
   for (int s = 0; s < n; ++s) {
     carve_state(b->dev + off[s], W[s], H[s], false, &b->planes[s]);
+    b->planes[s].storage = params->storage;
     const int nb = ((W[s] + 31) / 32) * ((H[s] + 7) / 8);
     for (int k = 0; k < nb; ++k) pro.push_back(make_int2(s, k));
     b->px_total += (long long)W[s] * H[s];
@@ -462,6 +465,10 @@ int evr_batch_get_state(evr_batch* b, int s, int which, void* out_host, size_t b
     default: return EVR_ERR_INVALID_ARG;
   }
   if (bytes != elem * P.W * P.H) return EVR_ERR_INVALID_ARG;
+  if (P.storage != 0 && which >= EVR_STATE_P1 && which <= EVR_STATE_P3) {
+    if (launch_p_convert(P, (void*)src, P.ubar, 1, b->stream)) return EVR_ERR_CUDA;
+    src = P.ubar;
+  }
   cudaError_t e = cudaMemcpy2DAsync(out_host, elem * P.W, src, elem * P.pitch, elem * P.W, P.H,
                                     cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

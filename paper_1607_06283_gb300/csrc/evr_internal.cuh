@@ -46,6 +46,7 @@ struct Planes {
   DevScalars* sc;
   double* partials;
   int* flags;  // persistent solver: passes completed by each CTA (monotonic)
+  int storage; // format of the p planes: 0 FP32, 1 FP16, 2 BF16 (tiled solver only)
 };
 
 // Batched streams: per-stream plane descriptors and work items on the device.  A
@@ -115,7 +116,7 @@ int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters,
 // kind 1 over a batch: one CTA per work item (stream, tile); pass j of a step reads
 // buffer curs[s] ^ (j & 1).  Inactive streams are skipped.
 int launch_tiled_pass_batch(const BatchRef& B, int n_work, const SolverCfg& cfg, int pass,
-                            int iters, const SolveConsts& c, void* stream);
+                            int iters, const SolveConsts& c, int storage, void* stream);
 // kind 2: all `iters` iterations from buffer cur; the result lands in buffer
 // cur ^ (ceil(iters / R) & 1).  `base` is the value of every CTA's progress flag at
 // launch (flags cleared by the host start at 0; each launch adds passes - 1).
@@ -126,5 +127,8 @@ int launch_persistent(const Planes& P, const SolverCfg& cfg, int cur, int iters,
 bool solver_cfg_usable(const Planes& P, const SolverCfg& cfg);
 int solver_cfg_ctas(const Planes& P, const SolverCfg& cfg);
 int launch_gap(const Planes& P, int cur, const SolveConsts& c, double* out2, void* stream);
+// Convert one pitched plane between the p storage format (P.storage) and FP32:
+// to_f32 = 1 widens p_plane into f_plane, 0 narrows f_plane into p_plane.
+int launch_p_convert(const Planes& P, void* p_plane, float* f_plane, int to_f32, void* stream);
 
 }  // namespace evr

@@ -6,6 +6,8 @@
 // intensity_update), then primal-dual iterations (Eq. cont_iterates, Eq.
 // update_rules).  The unfused iteration here uses IEEE division and square root in
 // FP32; the FP64 gap reduction is the convergence check.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -296,21 +298,9 @@ __device__ __forceinline__ float time_surface(long long tl, long long clock, lon
   return (float)d * c.time_scale;
 }
 
-// Per pixel: L_x t, L_y t (forward differences, zero on the last column/row), G,
-// 1/G, sqrt G (Eq. 2, text after Eq. 3), and the data image
-// f = base * exp(Delta+ n+ - Delta- n-) (Eq. intensity_update, one factor per event);
-// the counts are then cleared.  One kernel serves a single stream (B.descs null,
-// blocks numbered over its image) and a batch (one work item per CTA).
-__global__ void __launch_bounds__(256) k_prologue(Planes P, int cur, PrologueConsts c,
-                                                  BatchRef B) {
-  int blk = blockIdx.x;
-  if (B.descs) {
-    const int2 w = B.work[blockIdx.x];
-    if (!B.active[w.x]) return;
-    P = B.descs[w.x];
-    cur = B.curs[w.x];
-    blk = w.y;
-  }
+// One pixel of the prologue (block `blk` of the stream's 32 x 8 blocks).
+__device__ __forceinline__ void prologue_px_body(const Planes& P, int cur, const PrologueConsts& c,
+                                                 int blk) {
   const int nbx = (P.W + 31) / 32;
   const int x = (blk % nbx) * 32 + threadIdx.x;
   const int y = (blk / nbx) * 8 + threadIdx.y;
@@ -332,6 +322,28 @@ __global__ void __launch_bounds__(256) k_prologue(Planes P, int cur, PrologueCon
   P.f[i] = base * expf(e);
   P.npos[i] = 0;
   P.nneg[i] = 0;
+}
+
+// Per pixel: L_x t, L_y t (forward differences, zero on the last column/row), G,
+// 1/G, sqrt G (Eq. 2, text after Eq. 3), and the data image
+// f = base * exp(Delta+ n+ - Delta- n-) (Eq. intensity_update, one factor per event);
+// the counts are then cleared.  One kernel serves a single stream (B.descs null,
+// blocks numbered over its image) and a batch (one work item per CTA).
+__global__ void __launch_bounds__(256) k_prologue(Planes P, int cur, PrologueConsts c,
+                                                  BatchRef B) {
+  __shared__ Planes sP;  // this CTA's stream, staged once
+  int blk = blockIdx.x;
+  if (B.descs) {
+    const int2 w = B.work[blockIdx.x];
+    if (!B.active[w.x]) return;
+    cur = B.curs[w.x];
+    blk = w.y;
+    if (threadIdx.x == 0 && threadIdx.y == 0) sP = B.descs[w.x];
+  } else if (threadIdx.x == 0 && threadIdx.y == 0) {
+    sP = P;
+  }
+  __syncthreads();
+  prologue_px_body(sP, cur, c, blk);
 }
 
 int launch_prologue(const Planes& P, int cur, const PrologueConsts& c, void* stream) {
@@ -405,10 +417,17 @@ int launch_unfused_iteration(const Planes& P, int cur, const SolveConsts& c, voi
 // the data term sqrt(G)(u - f log u) (Eq. 5), and the dual term
 // min_{u in box} a (u - f log u) + w u with a = lambda sqrt(G), w = -div_g p, whose
 // minimiser is clamp(a f / (a + w)) for a + w > 0 and u_max otherwise.
+// p component at pixel i in the stream's storage format, widened
+__device__ __forceinline__ float ld_p(const Planes& P, const float* plane, size_t i) {
+  if (P.storage == 1) return __half2float(((const __half*)plane)[i]);
+  if (P.storage == 2) return __bfloat162float(((const __nv_bfloat16*)plane)[i]);
+  return plane[i];
+}
+
 __device__ __forceinline__ void mt64(const Planes& P, size_t i, int cur, double& q1, double& q2) {
   double a = P.tx[i], b = P.ty[i];
   double G = 1.0 + a * a + b * b;
-  double p1 = P.p1[cur][i], p2 = P.p2[cur][i], p3 = P.p3[cur][i];
+  double p1 = ld_p(P, P.p1[cur], i), p2 = ld_p(P, P.p2[cur], i), p3 = ld_p(P, P.p3[cur], i);
   q1 = ((1.0 + b * b) * p1 - a * b * p2 + a * p3) / G;
   q2 = (-a * b * p1 + (1.0 + a * a) * p2 + b * p3) / G;
 }
@@ -469,6 +488,28 @@ __global__ void __launch_bounds__(512) k_gap_final(Planes P, SolveConsts c, doub
     out2[0] = s[0][0] + (double)c.lambda * s[1][0];
     out2[1] = s[2][0];
   }
+}
+
+__global__ void k_p_convert(Planes P, void* pp, float* fp, int to_f32) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.W || y >= P.H) return;
+  size_t i = (size_t)y * P.pitch + x;
+  if (to_f32) {
+    fp[i] = ld_p(P, (const float*)pp, i);
+  } else if (P.storage == 1) {
+    ((__half*)pp)[i] = __float2half_rn(fp[i]);
+  } else if (P.storage == 2) {
+    ((__nv_bfloat16*)pp)[i] = __float2bfloat16_rn(fp[i]);
+  } else {
+    ((float*)pp)[i] = fp[i];
+  }
+}
+
+int launch_p_convert(const Planes& P, void* p_plane, float* f_plane, int to_f32, void* stream) {
+  dim3 blk(32, 8), grd((P.W + 31) / 32, (P.H + 7) / 8);
+  k_p_convert<<<grd, blk, 0, (cudaStream_t)stream>>>(P, p_plane, f_plane, to_f32);
+  return (int)cudaGetLastError();
 }
 
 int launch_gap(const Planes& P, int cur, const SolveConsts& c, double* out2, void* stream) {

@@ -14,6 +14,8 @@
 //     CTAs' bands through L2, synchronised by per-CTA progress flags.  Every wait is
 //     bounded; a wait that runs out sets an abort flag and EVR_ERR_TIMEOUT and the
 //     kernel returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "evr_internal.cuh"
@@ -82,14 +84,54 @@ __device__ __forceinline__ void tile_project(float& p1, float& p2, float& p3, fl
   p3 *= sc;
 }
 
+// ---------------------------------------------------------------- storage formats
+// p (between launches, in HBM/L2) and ubar (in shared memory) are stored as ST; all
+// arithmetic is FP32.  With a 16-bit ST both are rounded to ST every iteration (p
+// after the projection, ubar when formed), so the result does not depend on how the
+// iterations are split into launches.
+template <typename ST>
+struct Stor;
+template <>
+struct Stor<float> {
+  static __device__ __forceinline__ float ld(const float* a, size_t i) { return a[i]; }
+  static __device__ __forceinline__ float ldcg(const float* a, size_t i) { return __ldcg(a + i); }
+  static __device__ __forceinline__ float enc(float v) { return v; }
+  static __device__ __forceinline__ float dec(float v) { return v; }
+  static __device__ __forceinline__ float rnd(float v) { return v; }
+};
+template <>
+struct Stor<__half> {
+  static __device__ __forceinline__ float ld(const __half* a, size_t i) { return __half2float(a[i]); }
+  static __device__ __forceinline__ float ldcg(const __half* a, size_t i) {
+    return __half2float(__ldcg(a + i));
+  }
+  static __device__ __forceinline__ __half enc(float v) { return __float2half_rn(v); }
+  static __device__ __forceinline__ float dec(__half v) { return __half2float(v); }
+  static __device__ __forceinline__ float rnd(float v) { return __half2float(__float2half_rn(v)); }
+};
+template <>
+struct Stor<__nv_bfloat16> {
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* a, size_t i) {
+    return __bfloat162float(a[i]);
+  }
+  static __device__ __forceinline__ float ldcg(const __nv_bfloat16* a, size_t i) {
+    return __bfloat162float(__ldcg(a + i));
+  }
+  static __device__ __forceinline__ __nv_bfloat16 enc(float v) { return __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ float dec(__nv_bfloat16 v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ float rnd(float v) {
+    return __bfloat162float(__float2bfloat16_rn(v));
+  }
+};
+
 // ---------------------------------------------------------------- one tile
-template <int KX, int KY, int NTY>
+template <int KX, int KY, int NTY, typename ST = float>
 struct TileSmem {
   static constexpr int EW = 32 * KX, EH = NTY * KY;
-  float q1[EH][EW + 1];       // column 0: left pad (zero)
-  float ub[EH][EW + 1];       // column EW: right pad (zero)
+  float q1[EH][EW + 1];    // column 0: left pad (zero)
+  ST ub[EH][EW + 1];       // column EW: right pad (zero)
   float q2last[NTY + 1][EW];  // row ty + 1: q2 of strip ty's last pixel; row 0 pad
-  float ubfirst[NTY + 1][EW]; // row ty: ubar of strip ty's first pixel; row NTY pad
+  ST ubfirst[NTY + 1][EW];    // row ty: ubar of strip ty's first pixel; row NTY pad
 };
 
 // The extended tile held by one CTA.  Thread (tx, ty) holds pixels
@@ -99,9 +141,10 @@ struct TileSmem {
 // zero on the last column/row, the matching divergence) are two per-pixel masks:
 // q is stored as zero where its difference does not exist and off the sensor, so
 // the divergence needs no tests.
-template <int KX, int KY, int NTY>
+template <int KX, int KY, int NTY, typename ST = float>
 struct Tile {
   static constexpr int EW = 32 * KX, EH = NTY * KY, K = KX * KY;
+  using S = Stor<ST>;
   float u[K], p1[K], p2[K], p3[K], ta[K], tb[K], iG[K], sG[K], bt[K], fb4[K];
   unsigned mx, my;  // bit k: forward difference in x (y) exists at pixel k
   int gx0, gy0, R, OW, OH;
@@ -117,15 +160,15 @@ struct Tile {
     gy0 = (tile / tiles_x) * OH - R;
   }
 
-  __device__ __forceinline__ static void zero_pads(TileSmem<KX, KY, NTY>& sm) {
+  __device__ __forceinline__ static void zero_pads(TileSmem<KX, KY, NTY, ST>& sm) {
     const int tid = threadIdx.y * 32 + threadIdx.x;
     for (int i = tid; i < EH; i += 32 * NTY) {
       sm.q1[i][0] = 0.0f;
-      sm.ub[i][EW] = 0.0f;
+      sm.ub[i][EW] = S::enc(0.0f);
     }
     for (int i = tid; i < EW; i += 32 * NTY) {
       sm.q2last[0][i] = 0.0f;
-      sm.ubfirst[NTY][i] = 0.0f;
+      sm.ubfirst[NTY][i] = S::enc(0.0f);
     }
   }
 
@@ -172,15 +215,16 @@ struct Tile {
 
   // Iterated state (u, p) from buffer buf.
   __device__ __forceinline__ void load_state(const Planes& P, int buf) {
-    const float *U = P.u[buf], *P1 = P.p1[buf], *P2 = P.p2[buf], *P3 = P.p3[buf];
+    const float* U = P.u[buf];
+    const ST *P1 = (const ST*)P.p1[buf], *P2 = (const ST*)P.p2[buf], *P3 = (const ST*)P.p3[buf];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (on(k, P.W, P.H)) {
         const size_t i = gidx(P, k);
         u[k] = U[i];
-        p1[k] = P1[i];
-        p2[k] = P2[i];
-        p3[k] = P3[i];
+        p1[k] = S::ld(P1, i);
+        p2[k] = S::ld(P2, i);
+        p3[k] = S::ld(P3, i);
       } else {
         u[k] = 1.0f;
         p1[k] = p2[k] = p3[k] = 0.0f;
@@ -194,7 +238,7 @@ struct Tile {
   }
 
   // One primal-dual iteration over the extended tile (two CTA barriers).
-  __device__ __forceinline__ void iterate(TileSmem<KX, KY, NTY>& sm, const SolveConsts& c) {
+  __device__ __forceinline__ void iterate(TileSmem<KX, KY, NTY, ST>& sm, const SolveConsts& c) {
     float q1r[K], q2r[K];
     const int ty0 = threadIdx.y;
     // q = M^T p, zero where the matching forward difference does not exist
@@ -218,11 +262,11 @@ struct Tile {
       float div = (q1r[k] - q1m) + (q2r[k] - q2m);
       float v = fmaf(c.tau, div, u[k]);
       float un = tile_prox(v, bt[k], fb4[k], c.u_min, c.u_max);
-      float ub = 2.0f * un - u[k];
+      float ub = S::rnd(2.0f * un - u[k]);
       u[k] = un;
       q1r[k] = ub;  // from here on: ubar of pixel k
-      sm.ub[ly(k)][lx(k)] = ub;
-      if (ky == 0) sm.ubfirst[ty0][lx(k)] = ub;
+      sm.ub[ly(k)][lx(k)] = S::enc(ub);
+      if (ky == 0) sm.ubfirst[ty0][lx(k)] = S::enc(ub);
     }
     __syncthreads();
     // dual step: p = proj(p + sigma M (D_x ubar, D_y ubar))
@@ -230,8 +274,8 @@ struct Tile {
     for (int k = 0; k < K; ++k) {
       const int ky = k % KY;
       const float ub = q1r[k];
-      float ubx = sm.ub[ly(k)][lx(k) + 1];
-      float uby = (ky == KY - 1) ? sm.ubfirst[ty0 + 1][lx(k)] : q1r[k + 1];
+      float ubx = S::dec(sm.ub[ly(k)][lx(k) + 1]);
+      float uby = (ky == KY - 1) ? S::dec(sm.ubfirst[ty0 + 1][lx(k)]) : q1r[k + 1];
       float ux = (mx >> k & 1u) ? ubx - ub : 0.0f;
       float uy = (my >> k & 1u) ? uby - ub : 0.0f;
       float g1, g2, g3;
@@ -240,38 +284,40 @@ struct Tile {
       float a2 = fmaf(c.sigma, g2, p2[k]);
       float a3 = fmaf(c.sigma, g3, p3[k]);
       tile_project(a1, a2, a3, sG[k]);
-      p1[k] = a1;
-      p2[k] = a2;
-      p3[k] = a3;
+      p1[k] = S::rnd(a1);
+      p2[k] = S::rnd(a2);
+      p3[k] = S::rnd(a3);
     }
   }
 
   // Write (u, p) of the owned pixels (all of them, or only the border band).
   __device__ __forceinline__ void store(const Planes& P, int buf, bool band_only) const {
-    float *U = P.u[buf], *P1 = P.p1[buf], *P2 = P.p2[buf], *P3 = P.p3[buf];
+    float* U = P.u[buf];
+    ST *P1 = (ST*)P.p1[buf], *P2 = (ST*)P.p2[buf], *P3 = (ST*)P.p3[buf];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if ((band_only ? band(k) : owned(k)) && on(k, P.W, P.H)) {
         const size_t i = gidx(P, k);
         U[i] = u[k];
-        P1[i] = p1[k];
-        P2[i] = p2[k];
-        P3[i] = p3[k];
+        P1[i] = S::enc(p1[k]);
+        P2[i] = S::enc(p2[k]);
+        P3[i] = S::enc(p3[k]);
       }
     }
   }
 
   // Read (u, p) of the halo pixels from the neighbours' bands, through L2.
   __device__ __forceinline__ void reload_halo(const Planes& P, int buf) {
-    const float *U = P.u[buf], *P1 = P.p1[buf], *P2 = P.p2[buf], *P3 = P.p3[buf];
+    const float* U = P.u[buf];
+    const ST *P1 = (const ST*)P.p1[buf], *P2 = (const ST*)P.p2[buf], *P3 = (const ST*)P.p3[buf];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (!owned(k) && on(k, P.W, P.H)) {
         const size_t i = gidx(P, k);
         u[k] = __ldcg(U + i);
-        p1[k] = __ldcg(P1 + i);
-        p2[k] = __ldcg(P2 + i);
-        p3[k] = __ldcg(P3 + i);
+        p1[k] = S::ldcg(P1, i);
+        p2[k] = S::ldcg(P2, i);
+        p3[k] = S::ldcg(P3, i);
       }
     }
   }
@@ -283,29 +329,33 @@ struct Tile {
 // prologue, which finished before the previous pass got past its own wait), then
 // waits for the previous pass to complete before reading (u, p), and only then lets
 // the next pass launch -- so no pass can run ahead of the prologue.
-template <int KX, int KY, int NTY>
+template <int KX, int KY, int NTY, typename ST>
 __global__ void __launch_bounds__(32 * NTY) k_tiled(Planes P, int src, int iters, int R,
                                                     SolveConsts c, int tiles_x, BatchRef B,
                                                     int pass) {
-  __shared__ TileSmem<KX, KY, NTY> sm;
+  __shared__ TileSmem<KX, KY, NTY, ST> sm;
+  __shared__ Planes sP;  // this CTA's stream, staged once (no per-thread local copy)
   int tile = blockIdx.x;
   if (B.descs) {  // batch: this CTA's (stream, tile); one code path for both uses
     const int2 w = B.work[blockIdx.x];
     if (!B.active[w.x]) return;
-    P = B.descs[w.x];
     src = B.curs[w.x] ^ (pass & 1);
-    tiles_x = (P.W + (32 * KX - 2 * R) - 1) / (32 * KX - 2 * R);
     tile = w.y;
+    if (threadIdx.x == 0 && threadIdx.y == 0) sP = B.descs[w.x];
+  } else if (threadIdx.x == 0 && threadIdx.y == 0) {
+    sP = P;
   }
-  Tile<KX, KY, NTY> T;
+  __syncthreads();
+  if (B.descs) tiles_x = (sP.W + (32 * KX - 2 * R) - 1) / (32 * KX - 2 * R);
+  Tile<KX, KY, NTY, ST> T;
   T.setup(tile, tiles_x, R);
-  Tile<KX, KY, NTY>::zero_pads(sm);
-  T.load_consts(P, c);
+  Tile<KX, KY, NTY, ST>::zero_pads(sm);
+  T.load_consts(sP, c);
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" :::);
-  T.load_state(P, src);
+  T.load_state(sP, src);
   for (int it = 0; it < iters; ++it) T.iterate(sm, c);
-  T.store(P, 1 - src, false);
+  T.store(sP, 1 - src, false);
 }
 
 // ---------------------------------------------------------------- kind 2
@@ -396,7 +446,7 @@ static int tiles_of(const Planes& P, int R, int* tx, int* ty) {
 template <int KX, int KY, int NTY>
 static int launch_k_tiled(int blocks, const Planes& P, int src, int iters, int R,
                           const SolveConsts& c, int tx, const BatchRef& B, int pass,
-                          cudaStream_t st) {
+                          int storage, cudaStream_t st) {
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(blocks);
   lc.blockDim = dim3(32, NTY);
@@ -406,7 +456,19 @@ static int launch_k_tiled(int blocks, const Planes& P, int src, int iters, int R
   at[0].val.programmaticStreamSerializationAllowed = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  return (int)cudaLaunchKernelEx(&lc, k_tiled<KX, KY, NTY>, P, src, iters, R, c, tx, B, pass);
+  switch (storage) {
+    case 0:
+      return (int)cudaLaunchKernelEx(&lc, k_tiled<KX, KY, NTY, float>, P, src, iters, R, c, tx,
+                                     B, pass);
+    case 1:
+      return (int)cudaLaunchKernelEx(&lc, k_tiled<KX, KY, NTY, __half>, P, src, iters, R, c, tx,
+                                     B, pass);
+    case 2:
+      return (int)cudaLaunchKernelEx(&lc, k_tiled<KX, KY, NTY, __nv_bfloat16>, P, src, iters, R,
+                                     c, tx, B, pass);
+    default:
+      return (int)cudaErrorInvalidValue;
+  }
 }
 
 template <int KX, int KY, int NTY>
@@ -416,17 +478,18 @@ static int run_tiled(const Planes& P, int R, int src, int iters, const SolveCons
   if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters > R || iters < 1)
     return (int)cudaErrorInvalidValue;
   return launch_k_tiled<KX, KY, NTY>(tx * ty, P, src, iters, R, c, tx,
-                                     BatchRef{nullptr, nullptr, nullptr, nullptr}, 0, st);
+                                     BatchRef{nullptr, nullptr, nullptr, nullptr}, 0, P.storage,
+                                     st);
 }
 
 template <int KX, int KY, int NTY>
 static int run_tiled_batch(const BatchRef& B, int n_work, int R, int pass, int iters,
-                           const SolveConsts& c, cudaStream_t st) {
+                           const SolveConsts& c, int storage, cudaStream_t st) {
   const int OW = 32 * KX - 2 * R, OH = NTY * KY - 2 * R;
   if (R < 1 || OW < R || OH < R || iters > R || iters < 1) return (int)cudaErrorInvalidValue;
   if (n_work <= 0) return 0;
   Planes dummy{};
-  return launch_k_tiled<KX, KY, NTY>(n_work, dummy, 0, iters, R, c, 0, B, pass, st);
+  return launch_k_tiled<KX, KY, NTY>(n_work, dummy, 0, iters, R, c, 0, B, pass, storage, st);
 }
 
 template <int KX, int KY, int NTY>
@@ -477,10 +540,10 @@ int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters,
 }
 
 int launch_tiled_pass_batch(const BatchRef& B, int n_work, const SolverCfg& cfg, int pass,
-                            int iters, const SolveConsts& c, void* stream) {
+                            int iters, const SolveConsts& c, int storage, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (cfg.kind != 1) return (int)cudaErrorInvalidValue;
-  EVR_SHAPE_DISPATCH(run_tiled_batch, B, n_work, cfg.R, pass, iters, c, st)
+  EVR_SHAPE_DISPATCH(run_tiled_batch, B, n_work, cfg.R, pass, iters, c, storage, st)
   return (int)cudaErrorInvalidValue;
 }
 

@@ -56,6 +56,7 @@ class evr_params(ctypes.Structure):
         ("manifold", ctypes.c_int),
         ("solver", ctypes.c_int),
         ("tile_config", ctypes.c_int),
+        ("storage", ctypes.c_int),
     ]
 
 

@@ -34,8 +34,8 @@ def test_default_params(evr):
 
 
 def test_struct_layout_matches_header(evr):
-    # 9 floats, 2 int64 (8-byte aligned), 4 ints
-    assert ctypes.sizeof(evr.evr_params) == 9 * 4 + 4 + 2 * 8 + 4 * 4
+    # 9 floats, pad, 2 int64 (8-byte aligned), 5 ints, tail pad to 8
+    assert ctypes.sizeof(evr.evr_params) == 9 * 4 + 4 + 2 * 8 + 5 * 4 + 4
 
 
 def test_argument_errors_need_no_gpu(evr):

@@ -1,0 +1,134 @@
+"""Reduced-precision storage of p and ubar (FP16 / BF16, FP32 arithmetic) against the
+FP64 oracle.  The error of each variant is measured teacher-forced per packet (the
+oracle starts every packet from the GPU's state) and held to the bound stated in the
+design notes."""
+import numpy as np
+import pytest
+
+from evsim import CONFIGS, make_stream
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+# stated max-abs error bounds on u per packet (u in [e^-3, e^3]), per storage format
+BOUND = {0: 1e-4, 1: 2e-3, 2: 2e-2}
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_06283_gb300 import build
+    build.build()
+    from paper_1607_06283_gb300 import evr
+    return evr
+
+
+def oracle_params(p):
+    return O.OracleParams(
+        lam=float(p.lambda_), delta_pos=float(p.delta_pos), delta_neg=float(p.delta_neg),
+        u_min=float(p.u_min), u_max=float(p.u_max), u_init=float(p.u_init), tau=float(p.tau),
+        sigma=float(p.sigma), time_scale=float(np.float32(p.time_scale)),
+        t_max_us=int(p.t_max_us))
+
+
+def teacher_forced(E, g, o, s, K):
+    o.set_up(g.state(E.EVR_STATE_U).astype(np.float64), g.p().astype(np.float64))
+    o.set(O.TLAST, g.state(E.EVR_STATE_TLAST))
+    o.set(O.TREF, int(g.state(E.EVR_STATE_CLOCK)))
+    if int(g.state(E.EVR_STATE_TINIT)):
+        o.set(O.TINIT, int(g.state(E.EVR_STATE_TINIT)))
+    assert g.push(s.x, s.y, s.t, s.pol) == 0 and o.push(s.x, s.y, s.t, s.pol) == 0
+    g.solve(K)
+    o.solve(K)
+    return float(np.max(np.abs(g.image().astype(np.float64) - o.u)))
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_storage_error_rects128(E, storage):
+    cfg = CONFIGS["rects128"]
+    st = make_stream(cfg)
+    g = E.Stream(cfg.W, cfg.H, storage=storage)
+    o = O.OracleStream(cfg.W, cfg.H, oracle_params(g.params))
+    errs = [teacher_forced(E, g, o, st.slice(a, a + cfg.packet), cfg.iters)
+            for a in range(0, len(st), cfg.packet)]
+    assert max(errs) <= BOUND[storage], (storage, max(errs))
+    assert "tiled" in g.solver_name
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_p_readback_is_in_the_storage_format(E, storage):
+    cfg = CONFIGS["rects128"].with_events(2000)
+    st = make_stream(cfg)
+    g = E.Stream(cfg.W, cfg.H, storage=storage)
+    for a in range(0, len(st), cfg.packet):
+        s = st.slice(a, a + cfg.packet)
+        g.push(s.x, s.y, s.t, s.pol)
+        g.solve(20)
+    p = g.p()
+    import torch
+    dt = torch.float16 if storage == 1 else torch.bfloat16
+    t = torch.from_numpy(p)
+    np.testing.assert_array_equal(t.to(dt).to(torch.float32).numpy(), p)  # exactly representable
+    assert np.max(np.abs(p)) > 0
+    # set_state round trip of a p plane
+    E.evr_set_state(g.h, E.EVR_STATE_P1, p[0])
+    np.testing.assert_array_equal(g.state(E.EVR_STATE_P1), p[0])
+
+
+def test_storage_rejected_for_unfused_and_persistent(E):
+    with pytest.raises(E.EvrError):
+        E.Stream(32, 32, storage=1, solver=1)
+    with pytest.raises(E.EvrError):
+        E.Stream(32, 32, storage=2, solver=2, tile_config=12)  # a persistent configuration
+    with pytest.raises(E.EvrError):
+        E.Stream(32, 32, storage=3)
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_full_size_blobs1280_sampled_packet(E, storage):
+    """1280 x 720, 5000-event packets, 100 iterations: the error of each storage variant
+    against the FP64 oracle on a sampled packet (the third) of the stream."""
+    cfg = CONFIGS["blobs1280"].with_events(15000)
+    st = make_stream(cfg)
+    g = E.Stream(cfg.W, cfg.H, storage=storage)
+    o = O.OracleStream(cfg.W, cfg.H, oracle_params(g.params))
+    for k in range(2):
+        s = st.slice(k * cfg.packet, (k + 1) * cfg.packet)
+        assert g.push(s.x, s.y, s.t, s.pol) == 0
+        g.solve(cfg.iters)
+    err = teacher_forced(E, g, o, st.slice(2 * cfg.packet, 3 * cfg.packet), cfg.iters)
+    print(f"storage {storage}: max |u - u_fp64| = {err:.3e}")
+    assert err <= BOUND[storage], (storage, err)
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_batch_equals_solo_with_16bit_storage(E, storage):
+    rng = np.random.default_rng(7)
+    sizes = [(40, 30), (77, 19), (128, 64)]
+    streams = []
+    for W, H in sizes:
+        n = 4 * 400
+        x = rng.integers(0, W, n).astype(np.uint16)
+        y = rng.integers(0, H, n).astype(np.uint16)
+        t = (100 + np.sort(rng.integers(0, 30 * n, n))).astype(np.int64)
+        p = rng.choice(np.array([-1, 1], np.int8), n)
+        streams.append((x, y, t, p))
+    b = E.Batch(sizes, storage=storage, tile_config=2)
+    for k in range(4):
+        xs, ys, ts, ps, off = [], [], [], [], [0]
+        for (x, y, t, p) in streams:
+            sl = slice(k * 400, (k + 1) * 400)
+            xs.append(x[sl]); ys.append(y[sl]); ts.append(t[sl]); ps.append(p[sl])
+            off.append(off[-1] + 400)
+        b.step(np.concatenate(xs), np.concatenate(ys), np.concatenate(ts), np.concatenate(ps),
+               np.array(off, np.int64), 25)
+    for s, ((W, H), (x, y, t, p)) in enumerate(zip(sizes, streams)):
+        g = E.Stream(W, H, storage=storage, solver=2, tile_config=2)
+        for k in range(4):
+            sl = slice(k * 400, (k + 1) * 400)
+            assert g.push(x[sl], y[sl], t[sl], p[sl]) == 0
+            g.solve(25)
+        np.testing.assert_array_equal(b.state(s, E.EVR_STATE_U), g.state(E.EVR_STATE_U))
+        np.testing.assert_array_equal(b.state(s, E.EVR_STATE_P3), g.state(E.EVR_STATE_P3))
