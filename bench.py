@@ -453,7 +453,7 @@ def run_batch_bench(args):
     sizes = [(c.W, c.H) for c in cfgs]
     cur = torch.cuda.Stream()
     torch.cuda.set_stream(cur)
-    b = E.Batch(sizes)
+    b = E.Batch(sizes, storage=args.storage)
     b.set_cuda_stream(cur.cuda_stream)
     steps = [batch_step_arrays(streams, packet, k) for k in range(n_steps)]
     dev = []
@@ -489,7 +489,7 @@ def run_batch_bench(args):
         pxit += sum(w * h for (w, h), c in zip(sizes, cnt) if c > 0) * iters
     value = ev / (ms * 1e-3)
     # end to end: host arrays in, all images out, every step
-    b2 = E.Batch(sizes, tile_config=0)
+    b2 = E.Batch(sizes, storage=args.storage)
     b2.set_cuda_stream(cur.cuda_stream)
     img = np.empty(sum(w * h for w, h in sizes), np.float32)
     for k in range(args.warmup):
@@ -504,7 +504,9 @@ def run_batch_bench(args):
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ["f32", "f32 (p, ubar stored f16)", "f32 (p, ubar stored bf16)"][args.storage],
+        "data": "synthetic",
         "gpix_iter_per_s": pxit / (ms * 1e-3) / 1e9,
         "config": {"workload": "batch256: 256 streams (96 x 128x128, 96 x 240x180, "
                                "64 x 346x260), rects/blobs scenes, packets U[20,400], "
