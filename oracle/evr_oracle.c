@@ -18,6 +18,8 @@
  *    previous reconstruction (data_mode 0), or f persists (data_mode 1).
  *  - primal step first, then the dual step on 2u_{k+1}-u_k (Eq. cont_iterates),
  *    warm-started from the previous packet's (u, p).
+ *  - optional: the L2 data term of Eq. 7 instead of the KL term, and anisotropic
+ *    TV-L1 denoising of the time surface before the metric (Sec. 4).
  */
 #include "evr_oracle.h"
 
@@ -117,6 +119,56 @@ void orc_project(double p1, double p2, double p3, double sqrtG, double* out3) {
   out3[2] = p3 / den;
 }
 
+/* Eq. 7 data term: (u - v)^2/(2 tau) + (lambda/2) sqrt(G)(u - f)^2 is minimal at
+ * (v + beta f)/(1 + beta), beta = tau lambda sqrt(G). */
+double orc_prox_l2(double v, double beta, double f) { return (v + beta * f) / (1.0 + beta); }
+
+/* TV-L1 on the time surface (Sec. 4), anisotropic: min_s sum |L_x s| + |L_y s| +
+ * lam sum |s - t0|, Chambolle-Pock with tau = sigma = 1/sqrt(8) (||grad||^2 <= 8):
+ *   s_{k+1} = t0 + shrink(s_k + tau div q_k - t0, tau lam)
+ *   q_{k+1} = clip(q_k + sigma grad(2 s_{k+1} - s_k), -1, 1)   (each component)
+ * shrink(d, a) = sign(d) max(|d| - a, 0); div is the negative adjoint of grad. */
+void orc_tvl1(int W, int H, const double* t0, int K, double lam, double* out) {
+  int n = W * H;
+  size_t bytes = sizeof(double) * (size_t)n;
+  double st = 1.0 / sqrt(8.0);
+  double* q1 = (double*)calloc((size_t)n, sizeof(double));
+  double* q2 = (double*)calloc((size_t)n, sizeof(double));
+  double* sb = (double*)malloc(bytes);
+  double* gx = (double*)malloc(bytes);
+  double* gy = (double*)malloc(bytes);
+  memcpy(out, t0, bytes);
+  for (int k = 0; k < K; ++k) {
+    for (int y = 0; y < H; ++y) {
+      for (int x = 0; x < W; ++x) {
+        int i = y * W + x;
+        double div = 0.0;
+        if (x < W - 1) div += q1[i];
+        if (x > 0) div -= q1[i - 1];
+        if (y < H - 1) div += q2[i];
+        if (y > 0) div -= q2[i - W];
+        double d = out[i] + st * div - t0[i];
+        double a = st * lam;
+        double sh = (d > a) ? d - a : ((d < -a) ? d + a : 0.0);
+        double s_new = t0[i] + sh;
+        sb[i] = 2.0 * s_new - out[i];
+        out[i] = s_new;
+      }
+    }
+    orc_grad(W, H, sb, gx, gy);
+    for (int i = 0; i < n; ++i) {
+      double a = q1[i] + st * gx[i], b = q2[i] + st * gy[i];
+      q1[i] = a > 1.0 ? 1.0 : (a < -1.0 ? -1.0 : a);
+      q2[i] = b > 1.0 ? 1.0 : (b < -1.0 ? -1.0 : b);
+    }
+  }
+  free(q1);
+  free(q2);
+  free(sb);
+  free(gx);
+  free(gy);
+}
+
 /* Eq. cont_iterates:
  *   u_{k+1} = prox_{tau D}(u_k - tau L_g^* p_k) = prox_{tau D}(u_k + tau div_g p_k)
  *   p_{k+1} = prox_{sigma R^*}(p_k + sigma L_g(2 u_{k+1} - u_k))
@@ -125,6 +177,14 @@ void orc_pd_iterations(int W, int H, const double* tx, const double* ty, const d
                        const double* f, double* u, double* p1, double* p2, double* p3,
                        int K, double tau, double sigma, double lambda,
                        double u_min, double u_max) {
+  orc_pd_iterations_dt(W, H, tx, ty, G, f, u, p1, p2, p3, K, tau, sigma, lambda, u_min, u_max,
+                       0);
+}
+
+void orc_pd_iterations_dt(int W, int H, const double* tx, const double* ty, const double* G,
+                          const double* f, double* u, double* p1, double* p2, double* p3,
+                          int K, double tau, double sigma, double lambda, double u_min,
+                          double u_max, int data_term) {
   int n = W * H;
   size_t bytes = sizeof(double) * (size_t)n;
   double* dv = (double*)malloc(bytes);
@@ -139,7 +199,7 @@ void orc_pd_iterations(int W, int H, const double* tx, const double* ty, const d
     for (int i = 0; i < n; ++i) {
       double v = u[i] + tau * dv[i];
       double beta = tau * lambda * sqrt(G[i]);
-      un[i] = orc_prox_kl(v, beta, f[i], u_min, u_max);
+      un[i] = data_term ? orc_prox_l2(v, beta, f[i]) : orc_prox_kl(v, beta, f[i], u_min, u_max);
     }
     /* over-relaxation 2 u_{k+1} - u_k */
     for (int i = 0; i < n; ++i) ub[i] = 2.0 * un[i] - u[i];
@@ -330,6 +390,39 @@ void orc_energy(int W, int H, const double* tx, const double* ty, const double* 
   }
 }
 
+void orc_energy_l2(int W, int H, const double* tx, const double* ty, const double* G,
+                   const double* f, const double* u, const double* p1, const double* p2,
+                   const double* p3, double lambda, double* primal, double* dual) {
+  int n = W * H;
+  size_t bytes = sizeof(double) * (size_t)n;
+  if (primal) {
+    double* g1 = (double*)malloc(bytes);
+    double* g2 = (double*)malloc(bytes);
+    double* g3 = (double*)malloc(bytes);
+    orc_Lg(W, H, tx, ty, G, u, g1, g2, g3);
+    double reg = 0.0, dat = 0.0;
+    for (int i = 0; i < n; ++i) {
+      reg += sqrt(G[i] * (g1[i] * g1[i] + g2[i] * g2[i] + g3[i] * g3[i]));
+      dat += 0.5 * (u[i] - f[i]) * (u[i] - f[i]) * sqrt(G[i]);
+    }
+    *primal = reg + lambda * dat;
+    free(g1);
+    free(g2);
+    free(g3);
+  }
+  if (dual) {
+    double* dv = (double*)malloc(bytes);
+    orc_divg(W, H, tx, ty, G, p1, p2, p3, dv);
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double w = -dv[i];
+      acc += w * f[i] - w * w / (2.0 * lambda * sqrt(G[i]));
+    }
+    *dual = acc;
+    free(dv);
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Stream: the state carried from packet to packet. */
 struct orc_stream {
@@ -351,6 +444,8 @@ static int prm_valid(const orc_params* p) {
   if (!(p->u_init > 0.0)) return 0;
   if (!(p->tau > 0.0) || !(p->sigma > 0.0) || !(p->time_scale >= 0.0)) return 0;
   if (p->data_mode != 0 && p->data_mode != 1) return 0;
+  if (p->data_term != 0 && p->data_term != 1) return 0;
+  if (p->tvl1_iters < 0 || (p->tvl1_iters > 0 && !(p->tvl1_lambda > 0.0))) return 0;
   return 1;
 }
 
@@ -451,6 +546,12 @@ int orc_solve(orc_stream* s, int K) {
     if (pr->t_max_us > 0 && d > pr->t_max_us) d = pr->t_max_us;
     s->tau[i] = pr->time_scale * (double)d;
   }
+  if (pr->tvl1_iters > 0) { /* denoise the surface first (Sec. 4) */
+    double* t0 = (double*)malloc(sizeof(double) * (size_t)n);
+    memcpy(t0, s->tau, sizeof(double) * (size_t)n);
+    orc_tvl1(s->W, s->H, t0, pr->tvl1_iters, pr->tvl1_lambda, s->tau);
+    free(t0);
+  }
   orc_metric(s->W, s->H, s->tau, s->tx, s->ty, s->G);
   /* data image: Eq. intensity_update applied once per event, starting from the
    * previous reconstruction u^{n-1} (data_mode 0) or the previous f (data_mode 1);
@@ -464,8 +565,8 @@ int orc_solve(orc_stream* s, int K) {
     s->n_pos[i] = 0;
     s->n_neg[i] = 0;
   }
-  orc_pd_iterations(s->W, s->H, s->tx, s->ty, s->G, s->f, s->u, s->p1, s->p2, s->p3, K,
-                    pr->tau, pr->sigma, pr->lambda, pr->u_min, pr->u_max);
+  orc_pd_iterations_dt(s->W, s->H, s->tx, s->ty, s->G, s->f, s->u, s->p1, s->p2, s->p3, K,
+                       pr->tau, pr->sigma, pr->lambda, pr->u_min, pr->u_max, pr->data_term);
   return ORC_OK;
 }
 
@@ -521,7 +622,11 @@ int orc_set(orc_stream* s, int which, const void* in) {
 
 int orc_stream_energy(const orc_stream* s, double* primal, double* dual) {
   if (!s) return ORC_ERR_INVALID_ARG;
-  orc_energy(s->W, s->H, s->tx, s->ty, s->G, s->f, s->u, s->p1, s->p2, s->p3,
-             s->prm.lambda, s->prm.u_min, s->prm.u_max, primal, dual);
+  if (s->prm.data_term)
+    orc_energy_l2(s->W, s->H, s->tx, s->ty, s->G, s->f, s->u, s->p1, s->p2, s->p3,
+                  s->prm.lambda, primal, dual);
+  else
+    orc_energy(s->W, s->H, s->tx, s->ty, s->G, s->f, s->u, s->p1, s->p2, s->p3,
+               s->prm.lambda, s->prm.u_min, s->prm.u_max, primal, dual);
   return ORC_OK;
 }

@@ -47,6 +47,9 @@ typedef struct {
   int t_init_first;   /* 1: never-fired pixels take the first pushed timestamp */
   int data_mode;      /* 0: f = previous u stepped at event pixels; 1: persistent f */
   int manifold;       /* 1: t from the events; 0: t = const (manifold switched off) */
+  int data_term;      /* 0: generalised KL with box (Eq. data_term); 1: L2 / ROF (Eq. 7) */
+  int tvl1_iters;     /* TV-L1 iterations on the time surface before the metric; 0 = off */
+  double tvl1_lambda; /* data weight of that TV-L1 denoising */
 } orc_params;
 
 /* ---- stateless operators (each cites the passage it implements) ---- */
@@ -70,6 +73,17 @@ void orc_divg(int W, int H, const double* tx, const double* ty, const double* G,
 /* Closed-form KL proximal root with clamping (Eq. update_rules, first line). */
 double orc_prox_kl(double v, double beta, double f, double u_min, double u_max);
 
+/* Proximal map of the L2 data term of Eq. 7 (ROF on the manifold): the minimiser of
+ * (u - v)^2/(2 tau) + (lambda/2) sqrt(G) (u - f)^2 is (v + beta f)/(1 + beta),
+ * beta = tau lambda sqrt(G); no box constraint. */
+double orc_prox_l2(double v, double beta, double f);
+
+/* TV-L1 denoising of the time surface (Sec. 4: a few iterations of a TV-L1 method
+ * before the surface is used): min_s sum |L_x s| + |L_y s| + lam sum |s - t0|
+ * (anisotropic TV), K Chambolle-Pock iterations from s = t0, q = 0 with steps
+ * 1/sqrt(8).  out[W*H] receives s. */
+void orc_tvl1(int W, int H, const double* t0, int K, double lam, double* out);
+
 /* Projection onto the metric ball ||p|| <= sqrt(G) (Eq. update_rules, second line). */
 void orc_project(double p1, double p2, double p3, double sqrtG, double* out3);
 
@@ -80,12 +94,25 @@ void orc_pd_iterations(int W, int H, const double* tx, const double* ty, const d
                        int K, double tau, double sigma, double lambda,
                        double u_min, double u_max);
 
+/* As orc_pd_iterations with the data term chosen by data_term (0 KL with box, 1 L2). */
+void orc_pd_iterations_dt(int W, int H, const double* tx, const double* ty, const double* G,
+                          const double* f, double* u, double* p1, double* p2, double* p3,
+                          int K, double tau, double sigma, double lambda, double u_min,
+                          double u_max, int data_term);
+
 /* Primal energy of Eq. 5 and the dual function of the saddle form (Eq.
  * primal_dual_energy) at a feasible p.  Either output pointer may be NULL. */
 void orc_energy(int W, int H, const double* tx, const double* ty, const double* G,
                 const double* f, const double* u, const double* p1, const double* p2,
                 const double* p3, double lambda, double u_min, double u_max,
                 double* primal, double* dual);
+
+/* Energy and dual value for the L2 data term of Eq. 7: primal ||L_g u||_g +
+ * (lambda/2) sum sqrt(G)(u - f)^2; dual sum min_u (lambda/2) sqrt(G)(u - f)^2 + w u =
+ * sum w f - w^2 / (2 lambda sqrt(G)), w = -div_g p. */
+void orc_energy_l2(int W, int H, const double* tx, const double* ty, const double* G,
+                   const double* f, const double* u, const double* p1, const double* p2,
+                   const double* p3, double lambda, double* primal, double* dual);
 
 /* Reverse-mode derivative of orc_pd_iterations (K iterations from (u0, p0) with
  * fixed metric and f) for a loss L with given dL/du_K (gu_K[W*H]).  Outputs:

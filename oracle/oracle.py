@@ -66,6 +66,9 @@ class _Params(ctypes.Structure):
         ("t_init_first", ctypes.c_int),
         ("data_mode", ctypes.c_int),
         ("manifold", ctypes.c_int),
+        ("data_term", ctypes.c_int),
+        ("tvl1_iters", ctypes.c_int),
+        ("tvl1_lambda", ctypes.c_double),
     ]
 
 
@@ -90,6 +93,12 @@ def _lib_handle():
             lib.orc_pd_grad.argtypes = [i, i, _D, _D, _D, _D, _D, _D, i, d, d, d, d, d, _D,
                                         _D, _D, _D, _D]
             lib.orc_energy.argtypes = [i, i, _D, _D, _D, _D, _D, _D, _D, _D, d, d, d, _D, _D]
+            lib.orc_energy_l2.argtypes = [i, i, _D, _D, _D, _D, _D, _D, _D, _D, d, _D, _D]
+            lib.orc_prox_l2.argtypes = [d, d, d]
+            lib.orc_prox_l2.restype = d
+            lib.orc_tvl1.argtypes = [i, i, _D, i, d, _D]
+            lib.orc_pd_iterations_dt.argtypes = [i, i, _D, _D, _D, _D, _D, _D, _D, _D,
+                                                 i, d, d, d, d, d, i]
             lib.orc_create.argtypes = [i, i, ctypes.POINTER(_Params)]
             lib.orc_create.restype = vp
             lib.orc_destroy.argtypes = [vp]
@@ -189,6 +198,42 @@ def pd_grad(tx, ty, G, f, u0, p0, K, tau, sigma, lam, u_min, u_max, gu_K):
     return gu0, gp0, gf, gl.value
 
 
+def prox_l2(v, beta, f) -> float:
+    return _lib_handle().orc_prox_l2(float(v), float(beta), float(f))
+
+
+def tvl1(t0, K, lam):
+    """Anisotropic TV-L1 denoising of a surface, K iterations."""
+    t0 = _f64(t0)
+    H, W = t0.shape
+    out = np.empty_like(t0)
+    _lib_handle().orc_tvl1(W, H, _dp(t0), int(K), float(lam), _dp(out))
+    return out
+
+
+def pd_iterations_dt(tx, ty, G, f, u, p, K, tau, sigma, lam, u_min, u_max, data_term):
+    tx, ty, G, f = (_f64(a) for a in (tx, ty, G, f))
+    u = _f64(u).copy()
+    p = _f64(p).copy()
+    H, W = u.shape
+    _lib_handle().orc_pd_iterations_dt(W, H, _dp(tx), _dp(ty), _dp(G), _dp(f), _dp(u),
+                                       _dp(p[0]), _dp(p[1]), _dp(p[2]), int(K), float(tau),
+                                       float(sigma), float(lam), float(u_min), float(u_max),
+                                       int(data_term))
+    return u, p
+
+
+def energy_l2(tx, ty, G, f, u, p, lam):
+    tx, ty, G, f, u = (_f64(a) for a in (tx, ty, G, f, u))
+    p = _f64(p)
+    H, W = u.shape
+    pr, du = ctypes.c_double(), ctypes.c_double()
+    _lib_handle().orc_energy_l2(W, H, _dp(tx), _dp(ty), _dp(G), _dp(f), _dp(u), _dp(p[0]),
+                                _dp(p[1]), _dp(p[2]), float(lam), ctypes.byref(pr),
+                                ctypes.byref(du))
+    return pr.value, du.value
+
+
 def energy(tx, ty, G, f, u, p, lam, u_min, u_max):
     """(primal energy of Eq. 5, dual value) at (u, p)."""
     tx, ty, G, f, u = (_f64(a) for a in (tx, ty, G, f, u))
@@ -218,13 +263,17 @@ class OracleParams:
     t_init_us: int | None = None  # None: never-fired pixels take the first timestamp
     data_mode: int = 0
     manifold: int = 1
+    data_term: int = 0       # 0 KL with box, 1 L2 (Eq. 7)
+    tvl1_iters: int = 0      # TV-L1 iterations on the time surface (0 = off)
+    tvl1_lambda: float = 1.0
 
     def _c(self) -> _Params:
         return _Params(self.lam, self.delta_pos, self.delta_neg, self.u_min, self.u_max,
                        self.u_init, self.tau, self.sigma, self.time_scale,
                        int(self.t_max_us), int(self.t_init_us or 0),
                        1 if self.t_init_us is None else 0, int(self.data_mode),
-                       int(self.manifold))
+                       int(self.manifold), int(self.data_term), int(self.tvl1_iters),
+                       float(self.tvl1_lambda))
 
 
 class OracleStream:
