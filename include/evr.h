@@ -79,6 +79,13 @@ typedef struct {
                          2 BF16; arithmetic stays FP32 and both are rounded to the format
                          every iteration.  16-bit formats need the multi-launch tiled
                          solver (not the unfused or persistent ones). */
+  int data_term;      /* 0: generalised KL with box [u_min, u_max] (Eq. data_term, default);
+                         1: L2 data term of Eq. 7 (ROF on the manifold, no box) */
+  int tvl1_iters;     /* iterations of anisotropic TV-L1 denoising of the time surface
+                         before the metric (Sec. 4, "a few iterations"); 0 = off (default).
+                         Single streams only (evr_batch_create rejects it). */
+  float tvl1_lambda;  /* data weight of that denoising; default 1 (removes isolated
+                         one-pixel outliers, whose anisotropic TV is 4x their height) */
 } evr_params;
 
 typedef struct evr_stream evr_stream; /* opaque handle */

@@ -91,12 +91,13 @@ namespace {
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? EVR_OK : EVR_ERR_CUDA; }
 
 SolveConsts solve_consts(const evr_stream* s) {
-  return SolveConsts{s->prm.tau, s->prm.sigma, s->prm.lambda, s->prm.u_min, s->prm.u_max};
+  return SolveConsts{s->prm.tau, s->prm.sigma, s->prm.lambda, s->prm.u_min, s->prm.u_max,
+                     s->prm.data_term};
 }
 
 PrologueConsts prologue_consts(const evr_stream* s) {
   return PrologueConsts{s->prm.time_scale, s->prm.delta_pos, s->prm.delta_neg,
-                        (long long)s->prm.t_max_us, s->prm.manifold, s->prm.data_mode};
+                        (long long)s->prm.t_max_us, s->prm.manifold, s->prm.data_mode, nullptr};
 }
 
 int params_valid(const evr_params* p) {
@@ -112,6 +113,9 @@ int params_valid(const evr_params* p) {
   if (p->solver < 0 || p->solver > EVR_SOLVER_TILED) return 0;
   if (p->tile_config < 0 || p->tile_config > kNumSolverCfgs) return 0;
   if (p->storage < 0 || p->storage > 2) return 0;
+  if (p->data_term != 0 && p->data_term != 1) return 0;
+  if (p->tvl1_iters < 0 || p->tvl1_iters > 100000) return 0;
+  if (p->tvl1_iters > 0 && !(p->tvl1_lambda > 0.f)) return 0;
   if (p->storage != 0) {
     if (p->solver == EVR_SOLVER_UNFUSED) return 0;
     if (p->tile_config > 0 && kSolverCfgs[p->tile_config - 1].kind != 1) return 0;
@@ -431,6 +435,10 @@ int evr_default_params(evr_params* out) {
   out->manifold = 1;
   out->solver = EVR_SOLVER_AUTO;
   out->tile_config = 0;
+  out->storage = 0;
+  out->data_term = 0;
+  out->tvl1_iters = 0;
+  out->tvl1_lambda = 1.0f;
   return EVR_OK;
 }
 
@@ -581,7 +589,16 @@ int evr_push_events_device(evr_stream* s, const uint16_t* x, const uint16_t* y,
 int evr_solve(evr_stream* s, int iters) {
   if (!s || iters < 0) return EVR_ERR_INVALID_ARG;
   cudaStream_t st = s->stream;
-  if (launch_prologue(s->P, s->cur, prologue_consts(s), st)) return EVR_ERR_CUDA;
+  PrologueConsts pc = prologue_consts(s);
+  if (s->prm.tvl1_iters > 0 && s->prm.manifold) {
+    // denoise the time surface in the free buffer (1 - cur) and the ubar plane
+    const int o = 1 - s->cur;
+    if (launch_tvl1(s->P, pc, s->prm.tvl1_iters, s->prm.tvl1_lambda, s->P.u[o], s->P.p1[o],
+                    s->P.p2[o], s->P.p3[o], s->P.ubar, st))
+      return EVR_ERR_CUDA;
+    pc.tau_plane = s->P.p1[o];
+  }
+  if (launch_prologue(s->P, s->cur, pc, st)) return EVR_ERR_CUDA;
   if (iters == 0) return EVR_OK;
   if (!s->tuned) {
     autotune(s, iters);

@@ -63,12 +63,13 @@ struct evr_batch {
 namespace {
 
 SolveConsts consts(const evr_batch* b) {
-  return SolveConsts{b->prm.tau, b->prm.sigma, b->prm.lambda, b->prm.u_min, b->prm.u_max};
+  return SolveConsts{b->prm.tau, b->prm.sigma, b->prm.lambda, b->prm.u_min, b->prm.u_max,
+                     b->prm.data_term};
 }
 
 PrologueConsts pconsts(const evr_batch* b) {
   return PrologueConsts{b->prm.time_scale, b->prm.delta_pos, b->prm.delta_neg,
-                        (long long)b->prm.t_max_us, b->prm.manifold, b->prm.data_mode};
+                        (long long)b->prm.t_max_us, b->prm.manifold, b->prm.data_mode, nullptr};
 }
 
 BatchRef bref(const evr_batch* b, bool tiles) {
@@ -220,7 +221,8 @@ int evr_batch_create(int n, const int* W, const int* H, const evr_params* params
   if (!out) return EVR_ERR_INVALID_ARG;
   *out = nullptr;
   if (n <= 0 || !W || !H || !params || !check_params(params)) return EVR_ERR_INVALID_ARG;
-  if (params->solver == EVR_SOLVER_UNFUSED) return EVR_ERR_NOT_SUPPORTED;
+  if (params->solver == EVR_SOLVER_UNFUSED || params->tvl1_iters > 0)
+    return EVR_ERR_NOT_SUPPORTED;
   if (params->tile_config > 0 && kSolverCfgs[params->tile_config - 1].kind != 1)
     return EVR_ERR_NOT_SUPPORTED;
   for (int s = 0; s < n; ++s)

@@ -60,12 +60,14 @@ struct BatchRef {
 
 struct SolveConsts {
   float tau, sigma, lambda, u_min, u_max;
+  int data_term;  // 0 KL with box, 1 L2 (Eq. 7)
 };
 
 struct PrologueConsts {
   float time_scale, delta_pos, delta_neg;
   long long t_max_us;
   int manifold, data_mode;
+  const float* tau_plane;  // denoised time surface (pitched), or null: from t_last
 };
 
 // Tiled solvers.  A tile template is an extended tile of EW x EH pixels (an owned
@@ -99,6 +101,10 @@ int launch_init(const Planes& P, float u_init, long long clock0, long long t_ini
 int launch_push(const Planes& P, const uint16_t* x, const uint16_t* y, const long long* t,
                 const int8_t* pol, int n, void* stream);
 int launch_prologue(const Planes& P, int cur, const PrologueConsts& c, void* stream);
+// Anisotropic TV-L1 denoising of the time surface (Sec. 4) into s (pitched plane),
+// with scratch planes t0, q1, q2, sbar; K iterations from s = t0, q = 0.
+int launch_tvl1(const Planes& P, const PrologueConsts& c, int K, float lam, float* t0, float* s,
+                float* q1, float* q2, float* sbar, void* stream);
 // Batched: one CTA of 32 x 8 threads per work item (stream, block); blocks of a W x H
 // stream are numbered by = b / ceil(W/32), bx = b % ceil(W/32).
 int launch_prologue_batch(const BatchRef& B, int n_work, const PrologueConsts& c, void* stream);

@@ -308,9 +308,16 @@ __device__ __forceinline__ void prologue_px_body(const Planes& P, int cur, const
   long long clock = P.sc->clock;
   long long t_init = P.sc->t_init_set ? P.sc->t_init : clock;
   size_t i = (size_t)y * P.pitch + x;
-  float t0 = time_surface(P.t_last[i], clock, t_init, c);
-  float a = (x < P.W - 1) ? time_surface(P.t_last[i + 1], clock, t_init, c) - t0 : 0.0f;
-  float b = (y < P.H - 1) ? time_surface(P.t_last[i + P.pitch], clock, t_init, c) - t0 : 0.0f;
+  float a, b;
+  if (c.tau_plane) {  // surface denoised beforehand (TV-L1)
+    const float* T = c.tau_plane;
+    a = (x < P.W - 1) ? T[i + 1] - T[i] : 0.0f;
+    b = (y < P.H - 1) ? T[i + P.pitch] - T[i] : 0.0f;
+  } else {
+    float t0 = time_surface(P.t_last[i], clock, t_init, c);
+    a = (x < P.W - 1) ? time_surface(P.t_last[i + 1], clock, t_init, c) - t0 : 0.0f;
+    b = (y < P.H - 1) ? time_surface(P.t_last[i + P.pitch], clock, t_init, c) - t0 : 0.0f;
+  }
   float G = 1.0f + a * a + b * b;
   P.tx[i] = a;
   P.ty[i] = b;
@@ -344,6 +351,70 @@ __global__ void __launch_bounds__(256) k_prologue(Planes P, int cur, PrologueCon
   }
   __syncthreads();
   prologue_px_body(sP, cur, c, blk);
+}
+
+// ---------------------------------------------------------------- TV-L1 of the surface
+// Anisotropic TV-L1 (Sec. 4: the timestamps are denoised with a few TV-L1 iterations
+// before the surface is used): min_s sum |L_x s| + |L_y s| + lam sum |s - t0|,
+// Chambolle-Pock with steps 1/sqrt(8), from s = t0, q = 0.
+__global__ void k_tvl1_init(Planes P, PrologueConsts c, float* t0, float* s, float* q1,
+                            float* q2) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.W || y >= P.H) return;
+  long long clock = P.sc->clock;
+  long long t_init = P.sc->t_init_set ? P.sc->t_init : clock;
+  size_t i = (size_t)y * P.pitch + x;
+  float v = time_surface(P.t_last[i], clock, t_init, c);
+  t0[i] = v;
+  s[i] = v;
+  q1[i] = 0.0f;
+  q2[i] = 0.0f;
+}
+
+// s+ = t0 + shrink(s + st div q - t0, st lam), sbar = 2 s+ - s
+__global__ void k_tvl1_primal(Planes P, float st, float lam, const float* t0, float* s,
+                              const float* q1, const float* q2, float* sbar) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.W || y >= P.H) return;
+  size_t i = (size_t)y * P.pitch + x;
+  float div = 0.0f;
+  if (x < P.W - 1) div += q1[i];
+  if (x > 0) div -= q1[i - 1];
+  if (y < P.H - 1) div += q2[i];
+  if (y > 0) div -= q2[i - P.pitch];
+  float d = s[i] + st * div - t0[i];
+  float a = st * lam;
+  float sh = (d > a) ? d - a : ((d < -a) ? d + a : 0.0f);
+  float sn = t0[i] + sh;
+  sbar[i] = 2.0f * sn - s[i];
+  s[i] = sn;
+}
+
+// q = clip(q + st grad(sbar), -1, 1) per component
+__global__ void k_tvl1_dual(Planes P, float st, const float* sbar, float* q1, float* q2) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.W || y >= P.H) return;
+  size_t i = (size_t)y * P.pitch + x;
+  float gx = (x < P.W - 1) ? sbar[i + 1] - sbar[i] : 0.0f;
+  float gy = (y < P.H - 1) ? sbar[i + P.pitch] - sbar[i] : 0.0f;
+  q1[i] = fminf(1.0f, fmaxf(-1.0f, q1[i] + st * gx));
+  q2[i] = fminf(1.0f, fmaxf(-1.0f, q2[i] + st * gy));
+}
+
+int launch_tvl1(const Planes& P, const PrologueConsts& c, int K, float lam, float* t0, float* s,
+                float* q1, float* q2, float* sbar, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  dim3 blk(32, 8), grd((P.W + 31) / 32, (P.H + 7) / 8);
+  const float step = 1.0f / sqrtf(8.0f);
+  k_tvl1_init<<<grd, blk, 0, st>>>(P, c, t0, s, q1, q2);
+  for (int k = 0; k < K; ++k) {
+    k_tvl1_primal<<<grd, blk, 0, st>>>(P, step, lam, t0, s, q1, q2, sbar);
+    k_tvl1_dual<<<grd, blk, 0, st>>>(P, step, sbar, q1, q2);
+  }
+  return (int)cudaGetLastError();
 }
 
 int launch_prologue(const Planes& P, int cur, const PrologueConsts& c, void* stream) {
@@ -380,7 +451,8 @@ __global__ void k_primal(Planes P, int cur, SolveConsts c) {
   float u = P.u[cur][i];
   float v = u + c.tau * div;
   float beta = c.tau * c.lambda * P.sG[i];
-  float un = prox_kl(v, beta, P.f[i], c.u_min, c.u_max);
+  float un = c.data_term ? (v + beta * P.f[i]) / (1.0f + beta)  // Eq. 7, no box
+                         : prox_kl(v, beta, P.f[i], c.u_min, c.u_max);
   P.u[cur][i] = un;
   P.ubar[i] = 2.0f * un - u;
 }
@@ -450,16 +522,23 @@ __global__ void __launch_bounds__(kGapThreads) k_gap_partial(Planes P, int cur, 
     double g2 = ((1.0 + a * a) * uy - a * b * ux) / G;
     double g3 = (a * ux + b * uy) / G;
     reg += sqrt(G * (g1 * g1 + g2 * g2 + g3 * g3));
-    dat += (u - (f == 0.0 ? 0.0 : f * log(u))) * sG;
+    if (c.data_term)
+      dat += 0.5 * (u - f) * (u - f) * sG;  // Eq. 7
+    else
+      dat += (u - (f == 0.0 ? 0.0 : f * log(u))) * sG;
     double q1, q2, q1m = 0.0, q2m = 0.0, d;
     mt64(P, i, cur, q1, q2);
     if (x > 0) mt64(P, i - 1, cur, q1m, d);
     if (y > 0) mt64(P, i - P.pitch, cur, d, q2m);
     double div = ((x < P.W - 1) ? q1 : 0.0) - q1m + ((y < P.H - 1) ? q2 : 0.0) - q2m;
     double aa = lam * sG, w = -div;
-    double us = (aa + w > 0.0) ? aa * f / (aa + w) : umax;
-    us = fmin(fmax(us, umin), umax);
-    dua += aa * (us - (f == 0.0 ? 0.0 : f * log(us))) + w * us;
+    if (c.data_term) {  // min_u (aa/2)(u - f)^2 + w u = w f - w^2 / (2 aa)
+      dua += w * f - w * w / (2.0 * aa);
+    } else {
+      double us = (aa + w > 0.0) ? aa * f / (aa + w) : umax;
+      us = fmin(fmax(us, umin), umax);
+      dua += aa * (us - (f == 0.0 ? 0.0 : f * log(us))) + w * us;
+    }
   }
   s[0][threadIdx.x] = reg;
   s[1][threadIdx.x] = dat;

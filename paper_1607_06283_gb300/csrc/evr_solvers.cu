@@ -200,8 +200,14 @@ struct Tile {
         tb[k] = P.ty[i];
         iG[k] = P.iG[i];
         sG[k] = P.sG[i];
-        bt[k] = tl * sG[k];
-        fb4[k] = 4.0f * bt[k] * P.f[i];
+        const float beta = tl * sG[k];
+        if (c.data_term) {  // Eq. 7: u+ = (v + beta f) / (1 + beta)
+          bt[k] = 1.0f / (1.0f + beta);
+          fb4[k] = beta * P.f[i];
+        } else {
+          bt[k] = beta;
+          fb4[k] = 4.0f * beta * P.f[i];
+        }
         if (gx0 + lx(k) < P.W - 1) mx |= 1u << k;
         if (gy0 + ly(k) < P.H - 1) my |= 1u << k;
       } else {  // off the sensor: finite filler, masked out of every neighbour term
@@ -261,7 +267,7 @@ struct Tile {
       float q2m = (ky == 0) ? sm.q2last[ty0][lx(k)] : q2r[k - 1];
       float div = (q1r[k] - q1m) + (q2r[k] - q2m);
       float v = fmaf(c.tau, div, u[k]);
-      float un = tile_prox(v, bt[k], fb4[k], c.u_min, c.u_max);
+      float un = c.data_term ? (v + fb4[k]) * bt[k] : tile_prox(v, bt[k], fb4[k], c.u_min, c.u_max);
       float ub = S::rnd(2.0f * un - u[k]);
       u[k] = un;
       q1r[k] = ub;  // from here on: ubar of pixel k
@@ -330,7 +336,7 @@ struct Tile {
 // waits for the previous pass to complete before reading (u, p), and only then lets
 // the next pass launch -- so no pass can run ahead of the prologue.
 template <int KX, int KY, int NTY, typename ST>
-__global__ void __launch_bounds__(32 * NTY) k_tiled(Planes P, int src, int iters, int R,
+__global__ void __launch_bounds__(32 * NTY, 1) k_tiled(Planes P, int src, int iters, int R,
                                                     SolveConsts c, int tiles_x, BatchRef B,
                                                     int pass) {
   __shared__ TileSmem<KX, KY, NTY, ST> sm;

@@ -57,6 +57,9 @@ class evr_params(ctypes.Structure):
         ("solver", ctypes.c_int),
         ("tile_config", ctypes.c_int),
         ("storage", ctypes.c_int),
+        ("data_term", ctypes.c_int),
+        ("tvl1_iters", ctypes.c_int),
+        ("tvl1_lambda", ctypes.c_float),
     ]
 
 

@@ -34,8 +34,8 @@ def test_default_params(evr):
 
 
 def test_struct_layout_matches_header(evr):
-    # 9 floats, pad, 2 int64 (8-byte aligned), 5 ints, tail pad to 8
-    assert ctypes.sizeof(evr.evr_params) == 9 * 4 + 4 + 2 * 8 + 5 * 4 + 4
+    # 9 floats, pad, 2 int64 (8-byte aligned), 6 ints + 1 float, tail pad to 8
+    assert ctypes.sizeof(evr.evr_params) == 9 * 4 + 4 + 2 * 8 + 7 * 4 + 4
 
 
 def test_argument_errors_need_no_gpu(evr):
@@ -59,8 +59,9 @@ def test_argument_errors_need_no_gpu(evr):
 def test_ptxas_reports_no_spills_in_the_iteration_kernels(evr):
     """Register pressure check on the built kernels (from nvcc -Xptxas -v)."""
     import os
-    log = os.path.join(os.path.dirname(build.LIB), "evr_kernels.ptxas.txt")
-    text = open(log).read()
+    text = ""
+    for f in ("evr_kernels.ptxas.txt", "evr_solvers.ptxas.txt"):
+        text += open(os.path.join(os.path.dirname(build.LIB), f)).read()
     blocks = text.split("Compiling entry function")
     for b in blocks[1:]:
         name = b.split("'")[1]

@@ -34,7 +34,8 @@ def oracle_params(p, **kw):
         sigma=float(p.sigma), time_scale=float(np.float32(p.time_scale)),
         t_max_us=int(p.t_max_us),
         t_init_us=None if p.t_init_us == -(2 ** 63) else int(p.t_init_us),
-        data_mode=int(p.data_mode), manifold=int(p.manifold), **kw)
+        data_mode=int(p.data_mode), manifold=int(p.manifold), data_term=int(p.data_term),
+        tvl1_iters=int(p.tvl1_iters), tvl1_lambda=float(np.float32(p.tvl1_lambda)), **kw)
 
 
 N_CFGS = 24  # solver configurations selectable with evr_params.tile_config = 1..N_CFGS
@@ -191,7 +192,10 @@ def test_ragged_sizes(E, W, H, name, solver, tile):
 
 
 @pytest.mark.parametrize("over", [dict(manifold=0), dict(data_mode=1), dict(t_max_us=0),
-                                  dict(t_init_us=0), dict(lambda_=5.0), dict(time_scale=0.02)])
+                                  dict(t_init_us=0), dict(lambda_=5.0), dict(time_scale=0.02),
+                                  dict(data_term=1), dict(data_term=1, lambda_=3.0, solver=1),
+                                  dict(tvl1_iters=10), dict(tvl1_iters=10, tvl1_lambda=0.5),
+                                  dict(tvl1_iters=5, data_term=1, solver=1)])
 def test_parameter_variants(E, over):
     rng = np.random.default_rng(17)
     W, H = 70, 45
@@ -233,10 +237,11 @@ def test_tiled_is_deterministic_and_matches_unfused(E, rects128):
 
 
 # ----------------------------------------------------------------- FP64 gap
-def test_gap_matches_oracle_and_shrinks(E, rects128):
+@pytest.mark.parametrize("data_term", [0, 1])
+def test_gap_matches_oracle_and_shrinks(E, rects128, data_term):
     """data_mode 1 keeps f fixed across solve calls, so the checkpoints see one problem."""
     cfg = CONFIGS["rects128"]
-    g, o = make_pair(E, cfg.W, cfg.H, data_mode=1)
+    g, o = make_pair(E, cfg.W, cfg.H, data_mode=1, data_term=data_term)
     s = rects128.slice(0, 4 * cfg.packet)
     g.push(s.x, s.y, s.t, s.pol)
     o.push(s.x, s.y, s.t, s.pol)
