@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="evr_params.tile_config")
     ap.add_argument("--storage", type=int, default=0, help="evr_params.storage (0 FP32, 1 FP16, "
                     "2 BF16)")
+    ap.add_argument("--tvl1", type=int, default=0, help="evr_params.tvl1_iters")
     ap.add_argument("--check-error", action="store_true",
                     help="also state the max-abs error vs the FP64 oracle on one packet")
     return ap.parse_args()
@@ -208,7 +209,8 @@ def error_vs_oracle(E, cfg, stream, p):
         lam=float(p.lambda_), delta_pos=float(p.delta_pos), delta_neg=float(p.delta_neg),
         u_min=float(p.u_min), u_max=float(p.u_max), u_init=float(p.u_init), tau=float(p.tau),
         sigma=float(p.sigma), time_scale=float(np.float32(p.time_scale)),
-        t_max_us=int(p.t_max_us)))
+        t_max_us=int(p.t_max_us), data_term=int(p.data_term), tvl1_iters=int(p.tvl1_iters),
+        tvl1_lambda=float(np.float32(p.tvl1_lambda))))
     for k in range(2):
         a = k * cfg.packet
         g.push(stream.x[a:a + cfg.packet], stream.y[a:a + cfg.packet],
@@ -302,6 +304,7 @@ def run_ours(args):
     p.solver = args.solver
     p.tile_config = args.tile
     p.storage = args.storage
+    p.tvl1_iters = args.tvl1
     g = E.Stream(cfg.W, cfg.H, p)
     E.evr_set_cuda_stream(g.h, cur.cuda_stream)
 
@@ -408,6 +411,7 @@ def run_ours(args):
             "config": {"workload": describe(cfg), "sensor": f"{cfg.W}x{cfg.H}",
                        "events_per_step": cfg.packet, "iters": cfg.iters,
                        "solver": g.solver_name, "parallelism": f"{world} independent streams",
+                       "tvl1_iters": args.tvl1,
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "inputs": "device-resident event arrays (evr_push_events_device)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -529,12 +533,92 @@ def run_batch_bench(args):
     return 0
 
 
+# ----------------------------------------------------------------------- differentiation
+def run_diff_bench(args):
+    """64 streams of 240x180: per step and stream, f = data_image(u_prev, n+-, C),
+    u = packet_solve(f, lambda) with 30 unrolled iterations (checkpoints every 10), an L2
+    loss against the ground-truth frame, and the backward pass to lambda, C and f."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_1607_06283_gb300 import build
+    build.build()
+    from paper_1607_06283_gb300 import autograd as AG
+    from paper_1607_06283_gb300 import evr as E
+    from evsim.configs import StreamConfig, make_batch
+    n_streams, W, H, packet, K, every = 64, 240, 180, 2000, 30, 10
+    cfgs = [StreamConfig(f"diff{s}", W, H, "rects", 40, 5000 + s, 2 * packet, packet, K,
+                         speed=120.0, noise=0.01, dt_us=250.0) for s in range(n_streams)]
+    streams = make_batch(cfgs)
+    dev = torch.device("cuda")
+    items = []
+    for st in streams:
+        g = E.Stream(W, H)
+        a = st.slice(0, packet)
+        g.push(a.x, a.y, a.t, a.pol)
+        g.solve(K)
+        b = st.slice(packet, 2 * packet)
+        u_prev = g.state(E.EVR_STATE_U)
+        p0 = g.p()
+        g.push(b.x, b.y, b.t, b.pol)
+        npos, nneg = g.state(E.EVR_STATE_NPOS), g.state(E.EVR_STATE_NNEG)
+        g.solve(0)  # metric of this packet
+        tx, ty = g.state(E.EVR_STATE_TX), g.state(E.EVR_STATE_TY)
+        target = np.exp(st.log_frame(float(b.t[-1])) - st.log_frame(float(st.t[0]))).astype(
+            np.float32)
+        g.close()
+        items.append([torch.from_numpy(np.ascontiguousarray(a_)).to(dev) for a_ in
+                      (u_prev, p0, npos, nneg, tx, ty, target)])
+    lam = torch.tensor(90.0, device=dev, requires_grad=True)
+    C = torch.tensor(0.15, device=dev, requires_grad=True)
+
+    def step():
+        for (u_prev, p0, npos, nneg, tx, ty, target) in items:
+            f = AG.data_image(u_prev, npos, nneg, C, C)
+            u, _ = AG.packet_solve(f, lam, u_prev, p0, tx, ty, K, every)
+            loss = ((u - target) ** 2).mean()
+            loss.backward()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    solves = n_streams * args.steps
+    line = {
+        "metric": METRIC, "value": solves / (ms * 1e-3), "unit": "differentiated packet solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "gpix_iter_per_s_fwd_bwd": solves * W * H * K / (ms * 1e-3) / 1e9,
+        "events_per_s": solves * packet / (ms * 1e-3),
+        "config": {"workload": "diff64: 64 streams of 240x180 rectangles scenes, 2000-event "
+                               "packets, 30 unrolled iterations, checkpoints every 10, L2 loss "
+                               "vs ground-truth frames, gradients w.r.t. lambda, C and f",
+                   "timing": "CUDA events around the whole step (64 forward + backward per "
+                             "step, autograd on the host in the loop)"},
+        "wall_s": wall,
+        "grad": {"lambda": float(lam.grad), "C": float(C.grad)},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.config == "batch256":
         return run_batch_bench(args)
+    if args.config == "diff64":
+        return run_diff_bench(args)
     return run_ours(args)
 
 
