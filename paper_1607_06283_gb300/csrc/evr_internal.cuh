@@ -84,7 +84,7 @@ struct SolverCfg {
 };
 constexpr int kNumTileShapes = 6;
 extern const TileShape kTileShapes[kNumTileShapes];
-constexpr int kNumSolverCfgs = 24;
+constexpr int kNumSolverCfgs = 34;
 extern const SolverCfg kSolverCfgs[kNumSolverCfgs];
 
 constexpr int kGapBlocks = 304;   // fixed: the reduction order does not depend on W, H

@@ -39,6 +39,10 @@ const SolverCfg kSolverCfgs[kNumSolverCfgs] = {
     {1, 3, 3}, {1, 4, 4},
     {2, 0, 1}, {2, 0, 2}, {2, 0, 3}, {2, 0, 4}, {2, 1, 1}, {2, 1, 2}, {2, 1, 3}, {2, 2, 2},
     {2, 2, 4}, {2, 3, 2}, {2, 4, 2}, {2, 5, 1}, {2, 5, 2}, {2, 5, 3},
+    // more halo widths for the multi-launch solver: one pass fewer per packet where the
+    // grid still fits one wave
+    {1, 2, 9}, {1, 2, 10}, {1, 4, 8}, {1, 0, 5}, {1, 0, 7}, {1, 0, 8}, {1, 1, 6}, {1, 1, 8},
+    {1, 4, 6}, {1, 3, 5},
 };
 
 // ---------------------------------------------------------------- pointwise maps
