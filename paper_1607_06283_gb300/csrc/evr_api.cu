@@ -218,9 +218,9 @@ int enqueue_iterations(evr_stream* s, int iters, int cur, cudaStream_t st, int* 
     return cur;
   }
   const SolverCfg& cfg = kSolverCfgs[s->cfg];
-  for (int done = 0; done < iters; done += cfg.R) {
+  for (int done = 0, pass = 0; done < iters; done += cfg.R, ++pass) {
     int it = iters - done < cfg.R ? iters - done : cfg.R;
-    if (launch_tiled_pass(s->P, cfg, cur, it, c, st)) return -1;
+    if (launch_tiled_pass(s->P, cfg, cur, it, pass, c, st)) return -1;
     cur = 1 - cur;
     *launches += 1;
   }

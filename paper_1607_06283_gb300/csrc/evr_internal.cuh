@@ -116,8 +116,9 @@ int launch_push_batch(const Planes* descs, int n_streams, const uint16_t* x, con
 // Batched buffer flip after `passes` tiled passes: curs[s] ^= passes & 1 for active s.
 int launch_batch_flip(int* curs, const int* active, int n_streams, int passes, void* stream);
 int launch_unfused_iteration(const Planes& P, int cur, const SolveConsts& c, void* stream);
-// kind 1: `iters` <= R iterations from buffer src into buffer 1 - src.
-int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters,
+// kind 1: `iters` <= R iterations from buffer src into buffer 1 - src; `pass` is the
+// pass's index within the packet (0 right after the prologue).
+int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters, int pass,
                       const SolveConsts& c, void* stream);
 // kind 1 over a batch: one CTA per work item (stream, tile); pass j of a step reads
 // buffer curs[s] ^ (j & 1).  Inactive streams are skipped.

@@ -335,10 +335,11 @@ struct Tile {
 
 // ---------------------------------------------------------------- kind 1
 // Launched with programmatic stream serialisation: a pass may start while the
-// previous one drains.  It first loads the packet constants (written by the
-// prologue, which finished before the previous pass got past its own wait), then
-// waits for the previous pass to complete before reading (u, p), and only then lets
-// the next pass launch -- so no pass can run ahead of the prologue.
+// previous one drains.  Pass j > 0 of a packet first loads the packet constants
+// (written by the prologue, which completed before pass j - 1 got past its own wait),
+// then waits for the previous pass to complete before reading (u, p), and only then
+// lets the next pass launch -- so no pass can run ahead of the prologue.  Pass 0
+// loads everything after its wait.
 template <int KX, int KY, int NTY, typename ST>
 __global__ void __launch_bounds__(32 * NTY, 1) k_tiled(Planes P, int src, int iters, int R,
                                                     SolveConsts c, int tiles_x, BatchRef B,
@@ -360,9 +361,12 @@ __global__ void __launch_bounds__(32 * NTY, 1) k_tiled(Planes P, int src, int it
   Tile<KX, KY, NTY, ST> T;
   T.setup(tile, tiles_x, R);
   Tile<KX, KY, NTY, ST>::zero_pads(sm);
-  T.load_consts(sP, c);
+  // The first pass of a packet follows the prologue, whose writes are only guaranteed
+  // visible after the wait; later passes may read the constants before it.
+  if (pass > 0) T.load_consts(sP, c);
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" :::);
+  if (pass == 0) T.load_consts(sP, c);
   T.load_state(sP, src);
   for (int it = 0; it < iters; ++it) T.iterate(sm, c);
   T.store(sP, 1 - src, false);
@@ -482,14 +486,14 @@ static int launch_k_tiled(int blocks, const Planes& P, int src, int iters, int R
 }
 
 template <int KX, int KY, int NTY>
-static int run_tiled(const Planes& P, int R, int src, int iters, const SolveConsts& c,
-                     cudaStream_t st) {
+static int run_tiled(const Planes& P, int R, int src, int iters, int pass,
+                     const SolveConsts& c, cudaStream_t st) {
   int tx, ty;
   if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters > R || iters < 1)
     return (int)cudaErrorInvalidValue;
   return launch_k_tiled<KX, KY, NTY>(tx * ty, P, src, iters, R, c, tx,
-                                     BatchRef{nullptr, nullptr, nullptr, nullptr}, 0, P.storage,
-                                     st);
+                                     BatchRef{nullptr, nullptr, nullptr, nullptr}, pass,
+                                     P.storage, st);
 }
 
 template <int KX, int KY, int NTY>
@@ -542,10 +546,10 @@ static int run_persist(const Planes& P, int R, int cur, int iters, int base,
     default: break;                                                  \
   }
 
-int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters,
+int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters, int pass,
                       const SolveConsts& c, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  EVR_SHAPE_DISPATCH(run_tiled, P, cfg.R, src, iters, c, st)
+  EVR_SHAPE_DISPATCH(run_tiled, P, cfg.R, src, iters, pass, c, st)
   return (int)cudaErrorInvalidValue;
 }
 
