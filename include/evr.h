@@ -170,8 +170,12 @@ int evr_get_image_device(evr_stream* s, float* out_dev, size_t len);
  * Returns the first pending device-side rejection, if any. */
 int evr_get_state(evr_stream* s, int which, void* out_host, size_t bytes);
 
-/* Overwrite a state plane from host memory (u, p1, p2, p3 only; bytes = W*H*4).
- * Used to restore checkpoints.  Synchronises. */
+/* Overwrite a state plane from host memory, with the layout evr_get_state returns:
+ * u, p1, p2, p3, f (float), t_last (int64; a never-fired pixel may hold t_init), n+, n-
+ * (int32), clock and t_init (int64[1]; writing t_init marks it as set).  With the
+ * values read from another stream after at least one event, this restores a
+ * checkpoint: the restored stream continues bit-identically.  The metric planes are
+ * recomputed by every solve and cannot be written.  Synchronises. */
 int evr_set_state(evr_stream* s, int which, const void* in_host, size_t bytes);
 
 /* Primal energy of Eq. 5 and the dual value of the saddle form (Eq.
@@ -310,6 +314,16 @@ int evr_synchronize(evr_stream* s);
  * launches and the pixel-iterations they performed since timing was enabled. */
 int evr_enable_kernel_timing(evr_stream* s, int enable);
 int evr_kernel_time(evr_stream* s, double* ms, int64_t* launches, int64_t* pixel_iters);
+
+/* Failure-detection self-test of the persistent solver's bounded waits (the paper has
+ * no counterpart).  Launches it once over the current state with one CTA that never
+ * publishes its progress flag: its neighbours' waits run out, set an abort flag that
+ * every other CTA polls, and record EVR_ERR_TIMEOUT; all CTAs return.  The stream's
+ * (u, p) are restored and its flags cleared afterwards, so it stays usable.  Returns
+ * the status the device reported (EVR_ERR_TIMEOUT when detection works),
+ * EVR_ERR_NOT_SUPPORTED when no persistent configuration fits the sensor.  Takes well
+ * under a second.  Synchronises. */
+int evr_selftest_wait_timeout(evr_stream* s);
 
 /* Description of the solver in use, e.g. "tiled 32x32 R4"; static storage. */
 const char* evr_solver_name(evr_stream* s);

@@ -729,17 +729,36 @@ int evr_get_state(evr_stream* s, int which, void* out_host, size_t bytes) {
 
 int evr_set_state(evr_stream* s, int which, const void* in_host, size_t bytes) {
   if (!s || !in_host) return EVR_ERR_INVALID_ARG;
-  if (which < EVR_STATE_U || which > EVR_STATE_P3) return EVR_ERR_INVALID_ARG;
+  cudaError_t e = cudaSuccess;
+  if (which == EVR_STATE_CLOCK || which == EVR_STATE_TINIT) {
+    if (bytes != 8) return EVR_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return EVR_ERR_CUDA;
+    long long v;
+    std::memcpy(&v, in_host, 8);
+    if (which == EVR_STATE_CLOCK) {
+      e = cudaMemcpy(&s->P.sc->clock, &v, 8, cudaMemcpyHostToDevice);
+    } else {
+      const int one = 1;
+      e = cudaMemcpy(&s->P.sc->t_init, &v, 8, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(&s->P.sc->t_init_set, &one, 4, cudaMemcpyHostToDevice);
+    }
+    s->h_clock_valid = false;  // the host mirror refreshes at the next synchronising call
+    return cuda_err(e);
+  }
+  const bool plane = (which >= EVR_STATE_U && which <= EVR_STATE_F) || which == EVR_STATE_TLAST ||
+                     which == EVR_STATE_NPOS || which == EVR_STATE_NNEG;
+  if (!plane) return EVR_ERR_INVALID_ARG;
   size_t elem = 0;
   void* dst = plane_ptr(s, which, &elem);
   if (bytes != elem * s->W * s->H) return EVR_ERR_INVALID_ARG;
-  const bool narrow = s->P.storage != 0 && which != EVR_STATE_U;
-  cudaError_t e = cudaMemcpy2DAsync(narrow ? (void*)s->P.ubar : dst, elem * s->pitch, in_host,
-                                    elem * s->W, elem * s->W, s->H, cudaMemcpyHostToDevice,
-                                    s->stream);
+  const bool narrow = s->P.storage != 0 && which >= EVR_STATE_P1 && which <= EVR_STATE_P3;
+  e = cudaMemcpy2DAsync(narrow ? (void*)s->P.ubar : dst, elem * s->pitch, in_host, elem * s->W,
+                        elem * s->W, s->H, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess && narrow && launch_p_convert(s->P, dst, s->P.ubar, 0, s->stream))
     e = cudaErrorUnknown;
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (which == EVR_STATE_TLAST || which == EVR_STATE_NPOS || which == EVR_STATE_NNEG)
+    s->h_clock_valid = false;
   return cuda_err(e);
 }
 
@@ -776,6 +795,38 @@ int evr_kernel_time(evr_stream* s, double* ms, int64_t* launches, int64_t* pixel
   *launches = s->t_launches;
   *pixel_iters = s->t_pixiters;
   return cuda_err(cudaGetLastError());
+}
+
+int evr_selftest_wait_timeout(evr_stream* s) {
+  if (!s) return EVR_ERR_INVALID_ARG;
+  int ci = -1;
+  for (int k = 0; k < kNumSolverCfgs && ci < 0; ++k)
+    if (kSolverCfgs[k].kind == 2 && solver_cfg_usable(s->P, kSolverCfgs[k]) &&
+        solver_cfg_ctas(s->P, kSolverCfgs[k]) >= 2)
+      ci = k;
+  if (ci < 0) return EVR_ERR_NOT_SUPPORTED;
+  int rc = sync_status(s);  // report nothing stale as the test's result
+  if (rc != EVR_OK && rc != EVR_ERR_TIMEOUT) return rc;
+  const size_t plane = (size_t)s->pitch * s->H * sizeof(float);
+  float* save = nullptr;
+  if (cudaMalloc((void**)&save, 4 * plane) != cudaSuccess) return EVR_ERR_OOM;
+  const int cur0 = s->cur;
+  float* live[4] = {s->P.u[cur0], s->P.p1[cur0], s->P.p2[cur0], s->P.p3[cur0]};
+  for (int k = 0; k < 4; ++k)
+    cudaMemcpyAsync((char*)save + k * plane, live[k], plane, cudaMemcpyDeviceToDevice, s->stream);
+  clear_flags(s);
+  const SolverCfg& cfg = kSolverCfgs[ci];
+  // three passes, so every CTA waits on its neighbours at least twice
+  int e = launch_persistent(s->P, cfg, cur0, 3 * cfg.R, 0, solve_consts(s), s->stream, 0);
+  rc = e ? EVR_ERR_CUDA : sync_status(s);  // clears status, flags and abort on a timeout
+  for (int k = 0; k < 4; ++k)
+    cudaMemcpyAsync(live[k], (char*)save + k * plane, plane, cudaMemcpyDeviceToDevice, s->stream);
+  cudaStreamSynchronize(s->stream);
+  cudaFree(save);
+  clear_flags(s);
+  s->cur = cur0;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return EVR_ERR_CUDA;
+  return rc;
 }
 
 const char* evr_solver_name(evr_stream* s) { return s ? s->name : ""; }

@@ -128,8 +128,10 @@ int launch_tiled_pass_batch(const BatchRef& B, int n_work, const SolverCfg& cfg,
 // cur ^ (ceil(iters / R) & 1).  `base` is the value of every CTA's progress flag at
 // launch (flags cleared by the host start at 0; each launch adds passes - 1).
 // Returns cudaErrorCooperativeLaunchTooLarge when the grid cannot be co-resident.
+// silent_cta >= 0 (wait self-test only): that CTA never publishes its progress flag, so
+// its neighbours' bounded waits run out and the launch ends with EVR_ERR_TIMEOUT.
 int launch_persistent(const Planes& P, const SolverCfg& cfg, int cur, int iters, int base,
-                      const SolveConsts& c, void* stream);
+                      const SolveConsts& c, void* stream, int silent_cta = -1);
 // Whether the configuration can run on this sensor (tile fits, grid co-resident).
 bool solver_cfg_usable(const Planes& P, const SolverCfg& cfg);
 int solver_cfg_ctas(const Planes& P, const SolverCfg& cfg);

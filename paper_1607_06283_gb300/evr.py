@@ -87,6 +87,7 @@ def _load():
         "evr_enable_kernel_timing": ([vp, i], i),
         "evr_kernel_time": ([vp, vp, vp, vp], i),
         "evr_solver_name": ([vp], ctypes.c_char_p),
+        "evr_selftest_wait_timeout": ([vp], i),
         "evr_strerror": ([i], ctypes.c_char_p),
         "evr_gap_static": ([vp] * 7 + [i, i, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        vp, vp], i),
@@ -227,9 +228,17 @@ def evr_get_state(h, which: int, W: int, H: int):
     return (out[0] if out.size == 1 and which in (EVR_STATE_CLOCK, EVR_STATE_TINIT) else out), rc
 
 
-def evr_set_state(h, which: int, arr: np.ndarray) -> None:
-    a = np.ascontiguousarray(arr, dtype=np.float32)
+def evr_set_state(h, which: int, arr) -> None:
+    if which in (EVR_STATE_CLOCK, EVR_STATE_TINIT):
+        a = np.array([int(arr)], dtype=np.int64)
+    else:
+        a = np.ascontiguousarray(arr, dtype=_STATE_DT[which])
     _check(_lib.evr_set_state(h, int(which), a.ctypes.data, a.nbytes), "evr_set_state")
+
+
+CHECKPOINT_PLANES = (EVR_STATE_U, EVR_STATE_P1, EVR_STATE_P2, EVR_STATE_P3, EVR_STATE_F,
+                     EVR_STATE_TLAST, EVR_STATE_NPOS, EVR_STATE_NNEG, EVR_STATE_CLOCK,
+                     EVR_STATE_TINIT)
 
 
 def evr_gap(h):
@@ -322,6 +331,15 @@ class Stream:
 
     def gap(self):
         return evr_gap(self.h)
+
+    def save(self) -> dict:
+        """Checkpoint: every plane needed to resume the stream."""
+        return {w: np.copy(self.state(w)) for w in CHECKPOINT_PLANES}
+
+    def load(self, ckpt: dict) -> None:
+        """Restore a checkpoint taken with save() from a stream of the same size."""
+        for w in CHECKPOINT_PLANES:
+            evr_set_state(self.h, w, ckpt[w])
 
     def synchronize(self) -> int:
         return evr_synchronize(self.h)

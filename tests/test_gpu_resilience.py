@@ -1,0 +1,92 @@
+"""Checkpoint/resume and failure detection through the C ABI.
+
+Checkpoint: a stream's state read with evr_get_state and written into a fresh stream
+with evr_set_state resumes bit-identically.  Failure detection: the persistent
+solver's neighbour waits are bounded; the self-test leaves one CTA's progress flag
+unset, the waits run out, the device reports EVR_ERR_TIMEOUT, and the stream keeps
+working.  No GPU fault is involved: the failure is a flag that nothing sets.
+"""
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_06283_gb300 import build
+    build.build()
+    from paper_1607_06283_gb300 import evr
+    return evr
+
+
+def packets(seed, W, H, n, per):
+    rng = np.random.default_rng(seed)
+    out, t = [], 5000
+    for _ in range(n):
+        x = rng.integers(0, W, per).astype(np.uint16)
+        y = rng.integers(0, H, per).astype(np.uint16)
+        ts = t + np.sort(rng.integers(0, 4000, per)).astype(np.int64)
+        t = int(ts[-1])
+        out.append((x, y, ts, rng.choice(np.array([-1, 1], np.int8), per)))
+    return out
+
+
+@pytest.mark.parametrize("over", [dict(solver=2, tile_config=2), dict(solver=1),
+                                  dict(solver=2, tile_config=8, storage=1),
+                                  dict(solver=2, tile_config=12, data_mode=1)])
+def test_checkpoint_resume_is_bit_identical(E, over):
+    W, H = 90, 70
+    pk = packets(1, W, H, 8, 600)
+    a = E.Stream(W, H, **over)
+    for x, y, t, p in pk[:4]:
+        assert a.push(x, y, t, p) == 0
+        a.solve(20)
+    ckpt = a.save()
+    b = E.Stream(W, H, **over)
+    b.load(ckpt)
+    for g in (a, b):
+        for x, y, t, p in pk[4:]:
+            assert g.push(x, y, t, p) == 0
+            g.solve(20)
+    for w in (E.EVR_STATE_U, E.EVR_STATE_P1, E.EVR_STATE_P3, E.EVR_STATE_TLAST,
+              E.EVR_STATE_F):
+        np.testing.assert_array_equal(b.state(w), a.state(w))
+    assert int(b.state(E.EVR_STATE_CLOCK)) == int(a.state(E.EVR_STATE_CLOCK))
+
+
+def test_checkpoint_rejects_wrong_sizes(E):
+    g = E.Stream(16, 8)
+    with pytest.raises(E.EvrError):
+        E.evr_set_state(g.h, E.EVR_STATE_U, np.zeros((8, 15), np.float32))
+    with pytest.raises(E.EvrError):
+        E.evr_set_state(g.h, E.EVR_STATE_SQRTG, np.zeros((8, 16), np.float32))
+
+
+def test_wait_timeout_is_detected_and_the_stream_recovers(E):
+    W, H = 100, 60
+    pk = packets(2, W, H, 6, 500)
+    a = E.Stream(W, H, solver=2, tile_config=12)   # persistent configuration
+    twin = E.Stream(W, H, solver=2, tile_config=12)
+    for g in (a, twin):
+        for x, y, t, p in pk[:3]:
+            assert g.push(x, y, t, p) == 0
+            g.solve(15)
+    t0 = time.perf_counter()
+    rc = E._lib.evr_selftest_wait_timeout(a.h)
+    dt = time.perf_counter() - t0
+    assert rc == E.EVR_ERR_TIMEOUT, rc
+    assert dt < 10.0
+    assert a.synchronize() == 0  # reported once
+    np.testing.assert_array_equal(a.image(), twin.image())  # state restored
+    for g in (a, twin):
+        for x, y, t, p in pk[3:]:
+            assert g.push(x, y, t, p) == 0
+            g.solve(15)
+    assert a.synchronize() == 0
+    np.testing.assert_array_equal(a.image(), twin.image())  # solver works after the test
