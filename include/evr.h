@@ -262,30 +262,35 @@ const char* evr_batch_solver_name(evr_batch* b);
  * the adjoint of its iteration, Eq. cont_iterates with Eq. update_rules) ----
  * The solve is u_K = S(u_0, p_0, f, lambda) with the metric fixed: K unrolled
  * iterations.  The calls below are stateless and allocate nothing: every plane is
- * caller-owned device memory of H rows of `pitch` floats (pitch >= W, x the column);
- * a dual variable p is 3 such planes back to back (plane stride pitch*H).  tx, ty are
- * L_x t, L_y t of the packet (evr_get_state EVR_STATE_TX / EVR_STATE_TY).  All work is
- * queued on cuda_stream (NULL: legacy default stream).  Errors: EVR_ERR_INVALID_ARG
- * (null pointer, W or H <= 0, pitch < W, K < 1, every < 1), EVR_ERR_CUDA. */
+ * caller-owned device memory of H rows of `pitch` floats (pitch >= W, x the column).
+ * The unrolled calls take n >= 1 independent images of the same W x H at once (one
+ * packet solve each, lambda shared): a scalar field is n such planes back to back
+ * ((n, H, pitch) contiguous), a dual variable p is 3 such fields back to back
+ * ((3, n, H, pitch) contiguous, component stride n*pitch*H).  The images are coupled by
+ * nothing: image b's result is bit-identical to a call with n = 1 on image b alone.
+ * tx, ty are L_x t, L_y t of the packet (evr_get_state EVR_STATE_TX / EVR_STATE_TY).
+ * All work is queued on cuda_stream (NULL: legacy default stream).  Errors:
+ * EVR_ERR_INVALID_ARG (null pointer, W or H <= 0, pitch < W, n < 1, n*H > 524280,
+ * K < 1, every < 1), EVR_ERR_CUDA. */
 
 /* Workspace bytes for evr_unrolled_forward/backward (0 for invalid sizes). */
-size_t evr_unrolled_workspace_bytes(int W, int H, int pitch, int K, int every);
+size_t evr_unrolled_workspace_bytes(int W, int H, int pitch, int n, int K, int every);
 
 /* K iterations from (u0, p0) (FP32, IEEE division and square root), storing (u, p)
  * checkpoints every `every` iterations in `workspace`; result in u_out, p_out. */
 int evr_unrolled_forward(const float* tx, const float* ty, const float* f, const float* u0,
-                         const float* p0, int W, int H, int pitch, float lambda, float tau,
-                         float sigma, float u_min, float u_max, int K, int every,
+                         const float* p0, int W, int H, int pitch, int n, float lambda,
+                         float tau, float sigma, float u_min, float u_max, int K, int every,
                          void* workspace, float* u_out, float* p_out, void* cuda_stream);
 
 /* Reverse mode after evr_unrolled_forward with the same arguments and workspace:
- * from gu_K = dL/du_K and gp_K = dL/dp_K (3 planes; NULL means 0), recompute each
- * checkpoint segment and walk the adjoint back: gu0 = dL/du0 and gp0 = dL/dp0
- * (either may be NULL), gf = dL/df, and glambda_dev[0] = dL/dlambda (device double,
- * FP64 reduction).  Clamped pixels and the projection are differentiated on their
- * active side. */
+ * from gu_K = dL/du_K and gp_K = dL/dp_K (NULL means 0), recompute each checkpoint
+ * segment and walk the adjoint back: gu0 = dL/du0 and gp0 = dL/dp0 (either may be
+ * NULL), gf = dL/df, and glambda_dev[0] = dL/dlambda summed over the n images (device
+ * double, FP64 reduction).  Clamped pixels and the projection are differentiated on
+ * their active side. */
 int evr_unrolled_backward(const float* tx, const float* ty, const float* f, int W, int H,
-                          int pitch, float lambda, float tau, float sigma, float u_min,
+                          int pitch, int n, float lambda, float tau, float sigma, float u_min,
                           float u_max, int K, int every, void* workspace, const float* gu_K,
                           const float* gp_K, float* gu0, float* gp0, float* gf,
                           double* glambda_dev, void* cuda_stream);

@@ -9,7 +9,9 @@ Delta- differentiates a single contrast threshold C.
 
 Argument marshalling only: PyTorch allocates the outputs and the workspace, every
 computation runs in the library's kernels (evr_grad.cu).  Tensors are CUDA float32,
-contiguous, images (H, W) with pitch W, dual variables (3, H, W).
+contiguous, images (H, W) with pitch W and dual variables (3, H, W); or a batch of n
+independent packets of one sensor size, images (n, H, W) and dual variables
+(n, 3, H, W), solved by one call (lambda shared, its gradient summed over the batch).
 """
 from __future__ import annotations
 
@@ -44,53 +46,63 @@ class PacketSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, f, lam, u0, p0, tx, ty, iters: int, every: int, tau: float, sigma: float,
                 u_min: float, u_max: float):
-        H, W = f.shape
+        batched = f.dim() == 3
+        n, H, W = f.shape if batched else (1,) + tuple(f.shape)
+        img = (n, H, W) if batched else (H, W)
         for t in (f, u0, tx, ty):
-            _need(t, (H, W))
-        _need(p0, (3, H, W))
-        nbytes = E._lib.evr_unrolled_workspace_bytes(W, H, W, int(iters), int(every))
+            _need(t, img)
+        _need(p0, (n, 3, H, W) if batched else (3, H, W))
+        # the library's dual layout is component-major: (3, n, H, W)
+        p0c = p0.transpose(0, 1).contiguous() if batched else p0
+        nbytes = E._lib.evr_unrolled_workspace_bytes(W, H, W, n, int(iters), int(every))
         if nbytes == 0:
             raise ValueError("bad sizes for the unrolled solve")
         ws = torch.empty(nbytes, dtype=torch.uint8, device=f.device)
         u_out = torch.empty_like(u0)
-        p_out = torch.empty_like(p0)
+        p_out = torch.empty_like(p0c)
         lam_v = float(lam)
         rc = E._lib.evr_unrolled_forward(
-            _ptr(tx), _ptr(ty), _ptr(f), _ptr(u0), _ptr(p0), W, H, W, _f(lam_v), _f(tau),
+            _ptr(tx), _ptr(ty), _ptr(f), _ptr(u0), _ptr(p0c), W, H, W, n, _f(lam_v), _f(tau),
             _f(sigma), _f(u_min), _f(u_max), int(iters), int(every), _ptr(ws), _ptr(u_out),
             _ptr(p_out), _stream())
         _check(rc, "evr_unrolled_forward")
         ctx.save_for_backward(f, tx, ty, ws)
-        ctx.cfg = (W, H, lam_v, tau, sigma, u_min, u_max, int(iters), int(every))
+        ctx.cfg = (W, H, n, batched, lam_v, tau, sigma, u_min, u_max, int(iters), int(every))
         ctx.lam_shape = lam.shape if torch.is_tensor(lam) else None
-        return u_out, p_out
+        return u_out, (p_out.transpose(0, 1) if batched else p_out)
 
     @staticmethod
     def backward(ctx, gu, gp):
         f, tx, ty, ws = ctx.saved_tensors
-        W, H, lam, tau, sigma, u_min, u_max, iters, every = ctx.cfg
+        W, H, n, batched, lam, tau, sigma, u_min, u_max, iters, every = ctx.cfg
         gu = torch.zeros_like(f) if gu is None else gu.contiguous()
-        gp = None if gp is None else gp.contiguous()
+        if gp is not None:
+            gp = gp.transpose(0, 1).contiguous() if batched else gp.contiguous()
         gf = torch.empty_like(f)
         gu0 = torch.empty_like(f)
-        gp0 = torch.empty((3, H, W), dtype=torch.float32, device=f.device)
+        gp0 = torch.empty((3, n, H, W) if batched else (3, H, W), dtype=torch.float32,
+                          device=f.device)
         gl = torch.empty((1,), dtype=torch.float64, device=f.device)
         rc = E._lib.evr_unrolled_backward(
-            _ptr(tx), _ptr(ty), _ptr(f), W, H, W, _f(lam), _f(tau), _f(sigma), _f(u_min),
+            _ptr(tx), _ptr(ty), _ptr(f), W, H, W, n, _f(lam), _f(tau), _f(sigma), _f(u_min),
             _f(u_max), iters, every, _ptr(ws), _ptr(gu), _ptr(gp), _ptr(gu0), _ptr(gp0),
             _ptr(gf), _ptr(gl), _stream())
         _check(rc, "evr_unrolled_backward")
         glam = gl.to(torch.float32).reshape(ctx.lam_shape) if ctx.lam_shape is not None else None
+        if batched:
+            gp0 = gp0.transpose(0, 1)
         return gf, glam, gu0, gp0, None, None, None, None, None, None, None, None
 
 
 class DataImage(torch.autograd.Function):
     @staticmethod
     def forward(ctx, u_prev, npos, nneg, delta_pos, delta_neg):
-        H, W = u_prev.shape
-        _need(u_prev, (H, W))
-        _need(npos, (H, W), torch.int32)
-        _need(nneg, (H, W), torch.int32)
+        shape = tuple(u_prev.shape)
+        _need(u_prev, shape)
+        _need(npos, shape, torch.int32)
+        _need(nneg, shape, torch.int32)
+        W = shape[-1]
+        H = u_prev.numel() // W  # a batch (n, H, W) is n*H rows of one plane
         f = torch.empty_like(u_prev)
         dp, dn = float(delta_pos), float(delta_neg)
         rc = E._lib.evr_data_image(_ptr(u_prev), _ptr(npos), _ptr(nneg), W, H, W, _f(dp), _f(dn),
@@ -105,7 +117,8 @@ class DataImage(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gf):
         f, u_prev, npos, nneg = ctx.saved_tensors
-        H, W = f.shape
+        W = f.shape[-1]
+        H = f.numel() // W
         dp, dn = ctx.deltas
         gf = gf.contiguous()
         g_uprev = torch.empty_like(u_prev)
@@ -124,7 +137,8 @@ class DataImage(torch.autograd.Function):
 def packet_solve(f, lam, u0, p0, tx, ty, iters: int, every: int = 10, tau: float | None = None,
                  sigma: float | None = None, u_min: float | None = None,
                  u_max: float | None = None):
-    """Differentiable K-iteration solve of one packet; returns (u_K, p_K)."""
+    """Differentiable K-iteration solve of one packet, or of a batch of packets
+    ((n, H, W) images); returns (u_K, p_K)."""
     d = E.evr_default_params()
     return PacketSolve.apply(f, lam, u0, p0, tx, ty, iters, every,
                              d.tau if tau is None else tau, d.sigma if sigma is None else sigma,
@@ -133,5 +147,5 @@ def packet_solve(f, lam, u0, p0, tx, ty, iters: int, every: int = 10, tau: float
 
 
 def data_image(u_prev, npos, nneg, delta_pos, delta_neg):
-    """Differentiable data image of one packet."""
+    """Differentiable data image of one packet or a batch of packets."""
     return DataImage.apply(u_prev, npos, nneg, delta_pos, delta_neg)

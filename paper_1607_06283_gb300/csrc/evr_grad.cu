@@ -15,9 +15,13 @@ namespace {
 constexpr int kRedBlocks = 256;
 constexpr int kRedThreads = 256;
 
+// n images of W x Hm stacked vertically into one W x (n Hm) image (H = n Hm): the
+// forward differences and divergences use the row within the member, so the members
+// stay independent (zero y-difference on each member's last row).
 struct Geo {
   int W, H, pitch;
   size_t plane;  // pitch * H
+  int Hm;        // rows per member
 };
 
 struct Coef {
@@ -60,12 +64,13 @@ __device__ __forceinline__ float div_g(const Geo& g, const float* tx, const floa
     metric(tx, ty, i - 1, a, b, iG, sG);
     MT(a, b, iG, q[i - 1], q[g.plane + i - 1], q[2 * g.plane + i - 1], q1m, d);
   }
-  if (y > 0) {
+  const int yl = y % g.Hm;
+  if (yl > 0) {
     const size_t j = i - g.pitch;
     metric(tx, ty, j, a, b, iG, sG);
     MT(a, b, iG, q[j], q[g.plane + j], q[2 * g.plane + j], d, q2m);
   }
-  return ((x < g.W - 1) ? q1 : 0.0f) - q1m + ((y < g.H - 1) ? q2 : 0.0f) - q2m;
+  return ((x < g.W - 1) ? q1 : 0.0f) - q1m + ((yl < g.Hm - 1) ? q2 : 0.0f) - q2m;
 }
 
 // L_g w at (x, y) for a scalar plane w
@@ -76,7 +81,7 @@ __device__ __forceinline__ void Lg(const Geo& g, const float* tx, const float* t
   float a, b, iG, sG;
   metric(tx, ty, i, a, b, iG, sG);
   float wx = (x < g.W - 1) ? w[i + 1] - w[i] : 0.0f;
-  float wy = (y < g.H - 1) ? w[i + g.pitch] - w[i] : 0.0f;
+  float wy = (y % g.Hm < g.Hm - 1) ? w[i + g.pitch] - w[i] : 0.0f;
   Mg(a, b, iG, wx, wy, g1, g2, g3);
 }
 
@@ -283,31 +288,34 @@ size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspac
 }
 
 // A state in the workspace is u | p1 | p2 | p3 with the 256-byte-aligned plane size.
-int check_args(int W, int H, int pitch, int K, int every) {
-  if (W <= 0 || H <= 0 || pitch < W || K < 1 || every < 1) return EVR_ERR_INVALID_ARG;
+int check_args(int W, int H, int pitch, int K, int every, int n) {
+  if (W <= 0 || H <= 0 || pitch < W || K < 1 || every < 1 || n < 1) return EVR_ERR_INVALID_ARG;
+  if ((long long)H * n > 65535LL * 8) return EVR_ERR_INVALID_ARG;  // grid.y limit
   return EVR_OK;
 }
 
 }  // namespace
 
-extern "C" size_t evr_unrolled_workspace_bytes(int W, int H, int pitch, int K, int every) {
-  if (check_args(W, H, pitch, K, every)) return 0;
-  return ws_layout(W, H, pitch, K, every, nullptr, nullptr);
+extern "C" size_t evr_unrolled_workspace_bytes(int W, int H, int pitch, int n, int K,
+                                               int every) {
+  if (check_args(W, H, pitch, K, every, n)) return 0;
+  return ws_layout(W, H * n, pitch, K, every, nullptr, nullptr);
 }
 
 // Forward with checkpoints.  u0, p0 (3 planes) are read; u_out, p_out written.
 extern "C" int evr_unrolled_forward(const float* tx, const float* ty, const float* f,
-                                    const float* u0, const float* p0, int W, int H, int pitch,
-                                    float lambda, float tau, float sigma, float u_min,
+                                    const float* u0, const float* p0, int W, int Hm, int pitch,
+                                    int n, float lambda, float tau, float sigma, float u_min,
                                     float u_max, int K, int every, void* workspace,
                                     float* u_out, float* p_out, void* cuda_stream) {
-  if (check_args(W, H, pitch, K, every)) return EVR_ERR_INVALID_ARG;
+  if (check_args(W, Hm, pitch, K, every, n)) return EVR_ERR_INVALID_ARG;
+  const int H = Hm * n;
   if (!tx || !ty || !f || !u0 || !p0 || !workspace || !u_out || !p_out)
     return EVR_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   Workspace w;
   ws_layout(W, H, pitch, K, every, (char*)workspace, &w);
-  Geo g{W, H, pitch, (size_t)pitch * H};
+  Geo g{W, H, pitch, (size_t)pitch * H, Hm};
   Coef c{tau, sigma, lambda, u_min, u_max};
   const size_t fpl = ((size_t)pitch * H * 4 + 255) / 256 * 256 / 4;  // floats per plane slot
   dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
@@ -344,17 +352,18 @@ extern "C" int evr_unrolled_forward(const float* tx, const float* ty, const floa
 // Backward from dL/du_K (gu_K) and dL/dp_K (gp_K, NULL = 0).  Outputs dL/du0, dL/dp0
 // (3 planes), dL/df and glambda_dev[0] = dL/dlambda.  gu0, gp0 may be NULL.
 extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const float* f, int W,
-                                     int H, int pitch, float lambda, float tau, float sigma,
-                                     float u_min, float u_max, int K, int every,
+                                     int Hm, int pitch, int n, float lambda, float tau,
+                                     float sigma, float u_min, float u_max, int K, int every,
                                      void* workspace, const float* gu_K, const float* gp_K,
                                      float* gu0, float* gp0, float* gf, double* glambda_dev,
                                      void* cuda_stream) {
-  if (check_args(W, H, pitch, K, every)) return EVR_ERR_INVALID_ARG;
+  if (check_args(W, Hm, pitch, K, every, n)) return EVR_ERR_INVALID_ARG;
+  const int H = Hm * n;
   if (!tx || !ty || !f || !workspace || !gu_K || !gf || !glambda_dev) return EVR_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   Workspace w;
   ws_layout(W, H, pitch, K, every, (char*)workspace, &w);
-  Geo g{W, H, pitch, (size_t)pitch * H};
+  Geo g{W, H, pitch, (size_t)pitch * H, Hm};
   Coef c{tau, sigma, lambda, u_min, u_max};
   const size_t fpl = ((size_t)pitch * H * 4 + 255) / 256 * 256 / 4;
   Geo g4 = g;
@@ -408,7 +417,7 @@ extern "C" int evr_data_image(const float* u_prev, const int32_t* npos, const in
                               float* f_out, void* cuda_stream) {
   if (!u_prev || !npos || !nneg || !f_out || W <= 0 || H <= 0 || pitch < W)
     return EVR_ERR_INVALID_ARG;
-  Geo g{W, H, pitch, (size_t)pitch * H};
+  Geo g{W, H, pitch, (size_t)pitch * H, H};
   dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
   k_data_image<<<grd, blk, 0, (cudaStream_t)cuda_stream>>>(g, u_prev, npos, nneg, delta_pos,
                                                            delta_neg, f_out);
@@ -425,7 +434,7 @@ extern "C" int evr_data_image_backward(const float* f, const float* u_prev, cons
       pitch < W)
     return EVR_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  Geo g{W, H, pitch, (size_t)pitch * H};
+  Geo g{W, H, pitch, (size_t)pitch * H, H};
   dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
   k_data_image_bwd<<<grd, blk, 0, st>>>(g, f, u_prev, npos, nneg, delta_pos, delta_neg, gf,
                                         g_uprev, scratch);

@@ -91,10 +91,10 @@ def _load():
         "evr_strerror": ([i], ctypes.c_char_p),
         "evr_gap_static": ([vp] * 7 + [i, i, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        vp, vp], i),
-        "evr_unrolled_workspace_bytes": ([i, i, i, i, i], sz),
-        "evr_unrolled_forward": ([vp] * 5 + [i, i, i] + [ctypes.c_float] * 5 + [i, i] +
+        "evr_unrolled_workspace_bytes": ([i, i, i, i, i, i], sz),
+        "evr_unrolled_forward": ([vp] * 5 + [i, i, i, i] + [ctypes.c_float] * 5 + [i, i] +
                                  [vp] * 4, i),
-        "evr_unrolled_backward": ([vp] * 3 + [i, i, i] + [ctypes.c_float] * 5 + [i, i] +
+        "evr_unrolled_backward": ([vp] * 3 + [i, i, i, i] + [ctypes.c_float] * 5 + [i, i] +
                                   [vp] * 8, i),
         "evr_data_image": ([vp] * 3 + [i, i, i, ctypes.c_float, ctypes.c_float, vp, vp], i),
         "evr_batch_create": ([i, vp, vp, vp, vp], i),

@@ -157,3 +157,64 @@ def test_fit_lambda_and_threshold_to_target(T):
     c_fit, l_fit = float(C.detach()), float(logl.detach().exp())
     assert abs(c_fit - 0.2) < abs(0.1 - 0.2) * 0.5
     assert abs(math.log(l_fit / 25.0)) < abs(math.log(60.0 / 25.0))
+
+
+def test_batched_solve_equals_single_solves_bit_for_bit(T):
+    """n packets in one call: each image's forward state and every gradient are those of
+    the same packet solved alone; dL/dlambda is the sum over the batch."""
+    torch, AG, E = T
+    n, H, W, K, every, lam = 5, 19, 23, 21, 6, 35.0
+    probs = [problem(700 + b, H, W) for b in range(n)]
+    single = []
+    for tx, ty, f, u0, p0, w in probs:
+        ttx, tty, tf, tu0, tp0, tw = cuda(torch, tx, ty, f, u0, p0, w)
+        for t in (tf, tu0, tp0):
+            t.requires_grad_(True)
+        tlam = torch.tensor(lam, device="cuda", requires_grad=True)
+        u, p = AG.packet_solve(tf, tlam, tu0, tp0, ttx, tty, K, every)
+        ((u * tw).sum() + 0.1 * p.sum()).backward()
+        single.append([a.detach().cpu().numpy() for a in (u, p, tf.grad, tu0.grad, tp0.grad)] +
+                      [float(tlam.grad)])
+    stk = [np.stack([pr[k] for pr in probs]) for k in range(6)]
+    ttx, tty, tf, tu0, tp0, tw = cuda(torch, *stk)
+    for t in (tf, tu0, tp0):
+        t.requires_grad_(True)
+    tlam = torch.tensor(lam, device="cuda", requires_grad=True)
+    u, p = AG.packet_solve(tf, tlam, tu0, tp0, ttx, tty, K, every)
+    assert u.shape == (n, H, W) and p.shape == (n, 3, H, W)
+    ((u * tw).sum() + 0.1 * p.sum()).backward()
+    got = [a.detach().cpu().numpy() for a in (u, p, tf.grad, tu0.grad, tp0.grad)]
+    for b in range(n):
+        for k in range(5):
+            np.testing.assert_array_equal(got[k][b], single[b][k], err_msg=f"image {b} out {k}")
+    assert float(tlam.grad) == pytest.approx(sum(s[5] for s in single), rel=1e-5)
+
+
+def test_batched_gradients_match_oracle_on_a_ragged_member(T):
+    """A batch of 3 images of 1 row each (every row is a member's first and last row):
+    no y-coupling between members, gradients against the FP64 oracle per member."""
+    torch, AG, E = T
+    n, H, W, K, lam = 3, 1, 41, 15, 20.0
+    probs = [problem(800 + b, H, W) for b in range(n)]
+    stk = [np.stack([pr[k] for pr in probs]) for k in range(6)]
+    ttx, tty, tf, tu0, tp0, tw = cuda(torch, *stk)
+    tf.requires_grad_(True)
+    tlam = torch.tensor(lam, device="cuda", requires_grad=True)
+    u, _ = AG.packet_solve(tf, tlam, tu0, tp0, ttx, tty, K, 4)
+    (u * tw).sum().backward()
+    gl_sum = 0.0
+    for b, (tx, ty, f, u0, p0, w) in enumerate(probs):
+        otx, oty, oG = oracle_metric(tx, ty)
+        uo, _ = O.pd_iterations(otx, oty, oG, f, u0, p0, K, TAU, TAU, lam, UMIN, UMAX)
+        assert np.max(np.abs(u[b].detach().cpu().numpy() - uo)) <= 1e-4
+        _, _, gf, gl = O.pd_grad(otx, oty, oG, f, u0, p0, K, TAU, TAU, lam, UMIN, UMAX, w)
+        assert rel_err(tf.grad[b].cpu().numpy(), gf) <= GRAD_RTOL
+        gl_sum += gl
+    assert float(tlam.grad) == pytest.approx(gl_sum, rel=GRAD_RTOL, abs=1e-6)
+
+
+def test_batched_call_rejects_bad_sizes(T):
+    torch, AG, E = T
+    assert E._lib.evr_unrolled_workspace_bytes(16, 8, 16, 0, 10, 5) == 0
+    assert E._lib.evr_unrolled_workspace_bytes(16, 8, 16, 70000, 10, 5) == 0
+    assert E._lib.evr_unrolled_workspace_bytes(16, 8, 16, 4, 10, 5) > 0
