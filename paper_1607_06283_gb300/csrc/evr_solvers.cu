@@ -45,49 +45,6 @@ const SolverCfg kSolverCfgs[kNumSolverCfgs] = {
     {1, 4, 6}, {1, 3, 5},
 };
 
-// ---------------------------------------------------------------- pointwise maps
-// L_g u at one pixel (Eq. 3) as M (ux, uy), M = (1/G)[[1+b^2, -ab], [-ab, 1+a^2], [a, b]],
-// a = L_x t, b = L_y t, iG = 1/G.
-__device__ __forceinline__ void tile_M(float a, float b, float iG, float ux, float uy,
-                                       float& g1, float& g2, float& g3) {
-  float w = b * ux - a * uy;
-  g1 = iG * (ux + b * w);
-  g2 = iG * (uy - a * w);
-  g3 = iG * (a * ux + b * uy);
-}
-
-// M^T p, whose ordinary divergence is div_g p = -L_g^* p.
-__device__ __forceinline__ void tile_MT(float a, float b, float iG, float p1, float p2,
-                                        float p3, float& q1, float& q2) {
-  float z = b * p1 - a * p2;
-  q1 = iG * (p1 + b * z + a * p3);
-  q2 = iG * (p2 - a * z + b * p3);
-}
-
-// KL proximal root with clamping (Eq. update_rules, first line) with the MUFU
-// reciprocal square root and reciprocal (a few ulp); for v < beta the root is
-// evaluated as 2 beta f / (sqrt(.) - (v - beta)), free of cancellation.
-// beta = tau lambda sqrt(G) and fb4 = 4 beta f are per-pixel constants of the packet.
-__device__ __forceinline__ float tile_prox(float v, float beta, float fb4, float umin,
-                                           float umax) {
-  float d = v - beta;
-  float disc = fmaf(d, d, fb4);  // > 0 since beta, f > 0
-  float sq = disc * rsqrtf(disc);
-  float rp = 0.5f * (d + sq);
-  float rn = __fdividef(0.5f * fb4, sq - d);
-  float r = (d >= 0.0f) ? rp : rn;
-  return fminf(fmaxf(r, umin), umax);
-}
-
-// Projection onto the metric ball |p| <= sqrt(G) (Eq. update_rules, second line).
-__device__ __forceinline__ void tile_project(float& p1, float& p2, float& p3, float sG) {
-  float n2 = fmaf(p1, p1, fmaf(p2, p2, p3 * p3));
-  float sc = (n2 > sG * sG) ? sG * rsqrtf(n2) : 1.0f;
-  p1 *= sc;
-  p2 *= sc;
-  p3 *= sc;
-}
-
 // ---------------------------------------------------------------- storage formats
 // p (between launches, in HBM/L2) and ubar (in shared memory) are stored as ST; all
 // arithmetic is FP32.  With a 16-bit ST both are rounded to ST every iteration (p
@@ -138,19 +95,34 @@ struct TileSmem {
   ST ubfirst[NTY + 1][EW];    // row ty: ubar of strip ty's first pixel; row NTY pad
 };
 
+// Paired FP32 arithmetic: one packed instruction (FFMA2 / FADD2 / FMUL2 on sm_100 and
+// later) for two pixels, each half rounded exactly like its scalar counterpart.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+// element h of a pair (h a compile-time constant after unrolling)
+__device__ __forceinline__ float& el(float2& v, int h) { return h ? v.y : v.x; }
+
 // The extended tile held by one CTA.  Thread (tx, ty) holds pixels
 // (tx + 32 kx, KY ty + ky): pixel-local state in registers, vertical neighbours
 // inside the strip in registers, and only q1 (read at x-1), ubar (read at x+1) and
-// the strip ends in shared memory.  The image-border rules (forward differences
-// zero on the last column/row, the matching divergence) are two per-pixel masks:
-// q is stored as zero where its difference does not exist and off the sensor, so
-// the divergence needs no tests.
+// the strip ends in shared memory.  Pixels k = 2j and 2j + 1 (vertical neighbours in
+// one strip, KY even) form pair j of every per-pixel array and are updated by paired
+// instructions.  The image-border rules (forward differences zero on the last
+// column/row, the matching divergence) are per-pixel 0/1 factors: q is zero where its
+// difference does not exist and off the sensor, so the divergence needs no tests.
 template <int KX, int KY, int NTY, typename ST = float>
 struct Tile {
-  static constexpr int EW = 32 * KX, EH = NTY * KY, K = KX * KY;
+  static_assert(KY % 2 == 0, "pairs are vertical neighbours within a strip");
+  static constexpr int EW = 32 * KX, EH = NTY * KY, K = KX * KY, KP = K / 2;
   using S = Stor<ST>;
-  float u[K], p1[K], p2[K], p3[K], ta[K], tb[K], iG[K], sG[K], bt[K], fb4[K];
-  unsigned mx, my;  // bit k: forward difference in x (y) exists at pixel k
+  float2 u[KP], p1[KP], p2[KP], p3[KP];  // iterated state
+  // packet constants: a = L_x t, -a, b = L_y t, 1/G, 1/G times the x (y) difference
+  // mask, the masks, sqrt(G), G; data term: KL (-beta, 4 beta f, 2 beta f) with
+  // beta = tau lambda sqrt(G), or L2 (1 / (1 + beta), beta f, unused)
+  float2 A[KP], NA[KP], B[KP], IG[KP], IGX[KP], IGY[KP], MX[KP], MY[KP], SG[KP], SG2[KP];
+  float2 D1[KP], D2[KP], D3[KP];
   int gx0, gy0, R, OW, OH;
 
   __device__ __forceinline__ int lx(int k) const { return threadIdx.x + 32 * (k / KY); }
@@ -192,33 +164,42 @@ struct Tile {
     return (size_t)(gy0 + ly(k)) * P.pitch + (gx0 + lx(k));
   }
 
-  // Packet constants: metric, beta = tau lambda sqrt(G), 4 beta f, border masks.
+  // Packet constants of pixel k.
   __device__ __forceinline__ void load_consts(const Planes& P, const SolveConsts& c) {
     const float tl = c.tau * c.lambda;
-    mx = my = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      if (on(k, P.W, P.H)) {
+      const int j = k >> 1, h = k & 1;
+      float a = 0.0f, b = 0.0f, ig = 1.0f, sg = 1.0f, f = 1.0f, mx = 0.0f, my = 0.0f;
+      if (on(k, P.W, P.H)) {  // off the sensor: finite filler, masked out of every term
         const size_t i = gidx(P, k);
-        ta[k] = P.tx[i];
-        tb[k] = P.ty[i];
-        iG[k] = P.iG[i];
-        sG[k] = P.sG[i];
-        const float beta = tl * sG[k];
-        if (c.data_term) {  // Eq. 7: u+ = (v + beta f) / (1 + beta)
-          bt[k] = 1.0f / (1.0f + beta);
-          fb4[k] = beta * P.f[i];
-        } else {
-          bt[k] = beta;
-          fb4[k] = 4.0f * beta * P.f[i];
-        }
-        if (gx0 + lx(k) < P.W - 1) mx |= 1u << k;
-        if (gy0 + ly(k) < P.H - 1) my |= 1u << k;
-      } else {  // off the sensor: finite filler, masked out of every neighbour term
-        ta[k] = tb[k] = 0.0f;
-        iG[k] = sG[k] = 1.0f;
-        bt[k] = tl;
-        fb4[k] = 4.0f * tl;
+        a = P.tx[i];
+        b = P.ty[i];
+        ig = P.iG[i];
+        sg = P.sG[i];
+        f = P.f[i];
+        mx = (gx0 + lx(k) < P.W - 1) ? 1.0f : 0.0f;
+        my = (gy0 + ly(k) < P.H - 1) ? 1.0f : 0.0f;
+      }
+      el(A[j], h) = a;
+      el(NA[j], h) = -a;
+      el(B[j], h) = b;
+      el(IG[j], h) = ig;
+      el(IGX[j], h) = ig * mx;
+      el(IGY[j], h) = ig * my;
+      el(MX[j], h) = mx;
+      el(MY[j], h) = my;
+      el(SG[j], h) = sg;
+      el(SG2[j], h) = sg * sg;
+      const float beta = tl * sg;
+      if (c.data_term) {  // Eq. 7: u+ = (v + beta f) / (1 + beta)
+        el(D1[j], h) = 1.0f / (1.0f + beta);
+        el(D2[j], h) = beta * f;
+        el(D3[j], h) = 0.0f;
+      } else {
+        el(D1[j], h) = -beta;
+        el(D2[j], h) = 4.0f * beta * f;
+        el(D3[j], h) = 2.0f * beta * f;
       }
     }
   }
@@ -229,15 +210,16 @@ struct Tile {
     const ST *P1 = (const ST*)P.p1[buf], *P2 = (const ST*)P.p2[buf], *P3 = (const ST*)P.p3[buf];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+      const int j = k >> 1, h = k & 1;
       if (on(k, P.W, P.H)) {
         const size_t i = gidx(P, k);
-        u[k] = U[i];
-        p1[k] = S::ld(P1, i);
-        p2[k] = S::ld(P2, i);
-        p3[k] = S::ld(P3, i);
+        el(u[j], h) = U[i];
+        el(p1[j], h) = S::ld(P1, i);
+        el(p2[j], h) = S::ld(P2, i);
+        el(p3[j], h) = S::ld(P3, i);
       } else {
-        u[k] = 1.0f;
-        p1[k] = p2[k] = p3[k] = 0.0f;
+        el(u[j], h) = 1.0f;
+        el(p1[j], h) = el(p2[j], h) = el(p3[j], h) = 0.0f;
       }
     }
   }
@@ -249,69 +231,108 @@ struct Tile {
 
   // One primal-dual iteration over the extended tile (two CTA barriers).
   __device__ __forceinline__ void iterate(TileSmem<KX, KY, NTY, ST>& sm, const SolveConsts& c) {
-    float q1r[K], q2r[K];
+    float2 q1r[KP], q2r[KP];
     const int ty0 = threadIdx.y;
+    const float2 one_neg = dup2(-1.0f);
     // q = M^T p, zero where the matching forward difference does not exist
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int ky = k % KY;
-      float q1, q2;
-      tile_MT(ta[k], tb[k], iG[k], p1[k], p2[k], p3[k], q1, q2);
-      q1r[k] = (mx >> k & 1u) ? q1 : 0.0f;
-      q2r[k] = (my >> k & 1u) ? q2 : 0.0f;
-      sm.q1[ly(k)][lx(k) + 1] = q1r[k];
-      if (ky == KY - 1) sm.q2last[ty0 + 1][lx(k)] = q2r[k];
+    for (int j = 0; j < KP; ++j) {
+      const int k0 = 2 * j, k1 = k0 + 1;
+      const float2 z = fma2(NA[j], p2[j], mul2(B[j], p1[j]));  // b p1 - a p2
+      q1r[j] = mul2(IGX[j], fma2(A[j], p3[j], fma2(B[j], z, p1[j])));
+      q2r[j] = mul2(IGY[j], fma2(B[j], p3[j], fma2(NA[j], z, p2[j])));
+      sm.q1[ly(k0)][lx(k0) + 1] = q1r[j].x;
+      sm.q1[ly(k1)][lx(k1) + 1] = q1r[j].y;
+      if (k1 % KY == KY - 1) sm.q2last[ty0 + 1][lx(k1)] = q2r[j].y;
     }
     __syncthreads();
     // primal step: v = u + tau div(M^T p), u+ = prox(v), ubar = 2 u+ - u
+    const float2 tau2 = dup2(c.tau);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int ky = k % KY;
-      float q1m = sm.q1[ly(k)][lx(k)];
-      float q2m = (ky == 0) ? sm.q2last[ty0][lx(k)] : q2r[k - 1];
-      float div = (q1r[k] - q1m) + (q2r[k] - q2m);
-      float v = fmaf(c.tau, div, u[k]);
-      float un = c.data_term ? (v + fb4[k]) * bt[k] : tile_prox(v, bt[k], fb4[k], c.u_min, c.u_max);
-      float ub = S::rnd(2.0f * un - u[k]);
-      u[k] = un;
-      q1r[k] = ub;  // from here on: ubar of pixel k
-      sm.ub[ly(k)][lx(k)] = S::enc(ub);
-      if (ky == 0) sm.ubfirst[ty0][lx(k)] = S::enc(ub);
+    for (int j = 0; j < KP; ++j) {
+      const int k0 = 2 * j, k1 = k0 + 1;
+      const float2 q1m = make_float2(sm.q1[ly(k0)][lx(k0)], sm.q1[ly(k1)][lx(k1)]);
+      // y - 1 neighbour: pixel k1's is k0; pixel k0's is the pair above or the strip above
+      const float2 q2m = make_float2((k0 % KY == 0) ? sm.q2last[ty0][lx(k0)] : q2r[j - 1].y,
+                                     q2r[j].x);
+      const float2 div = add2(fma2(one_neg, q1m, q1r[j]), fma2(one_neg, q2m, q2r[j]));
+      const float2 v = fma2(tau2, div, u[j]);
+      float2 un;
+      if (c.data_term) {
+        un = mul2(add2(v, D2[j]), D1[j]);
+      } else {
+        // KL root (Eq. update_rules): MUFU reciprocal square root and reciprocal (a few
+        // ulp); for v < beta the root 2 beta f / (sqrt(.) - (v - beta)) avoids the
+        // cancellation of (v - beta + sqrt(.)) / 2.
+        const float2 d = add2(v, D1[j]);       // v - beta
+        const float2 disc = fma2(d, d, D2[j]);  // + 4 beta f > 0
+        const float2 sq = mul2(disc, make_float2(rsqrtf(disc.x), rsqrtf(disc.y)));
+        const float2 rp = mul2(dup2(0.5f), add2(d, sq));
+        const float2 den = fma2(one_neg, d, sq);
+        const float2 rn = mul2(D3[j], make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y)));
+        un.x = fminf(fmaxf(d.x >= 0.0f ? rp.x : rn.x, c.u_min), c.u_max);
+        un.y = fminf(fmaxf(d.y >= 0.0f ? rp.y : rn.y, c.u_min), c.u_max);
+      }
+      float2 ub = fma2(one_neg, u[j], add2(un, un));
+      ub.x = S::rnd(ub.x);
+      ub.y = S::rnd(ub.y);
+      u[j] = un;
+      q1r[j] = ub;  // from here on: ubar of pair j
+      sm.ub[ly(k0)][lx(k0)] = S::enc(ub.x);
+      sm.ub[ly(k1)][lx(k1)] = S::enc(ub.y);
+      if (k0 % KY == 0) sm.ubfirst[ty0][lx(k0)] = S::enc(ub.x);
     }
     __syncthreads();
     // dual step: p = proj(p + sigma M (D_x ubar, D_y ubar))
+    const float2 sig2 = dup2(c.sigma);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int ky = k % KY;
-      const float ub = q1r[k];
-      float ubx = S::dec(sm.ub[ly(k)][lx(k) + 1]);
-      float uby = (ky == KY - 1) ? S::dec(sm.ubfirst[ty0 + 1][lx(k)]) : q1r[k + 1];
-      float ux = (mx >> k & 1u) ? ubx - ub : 0.0f;
-      float uy = (my >> k & 1u) ? uby - ub : 0.0f;
-      float g1, g2, g3;
-      tile_M(ta[k], tb[k], iG[k], ux, uy, g1, g2, g3);
-      float a1 = fmaf(c.sigma, g1, p1[k]);
-      float a2 = fmaf(c.sigma, g2, p2[k]);
-      float a3 = fmaf(c.sigma, g3, p3[k]);
-      tile_project(a1, a2, a3, sG[k]);
-      p1[k] = S::rnd(a1);
-      p2[k] = S::rnd(a2);
-      p3[k] = S::rnd(a3);
+    for (int j = 0; j < KP; ++j) {
+      const int k0 = 2 * j, k1 = k0 + 1;
+      const float2 ub = q1r[j];
+      const float2 ubx = make_float2(S::dec(sm.ub[ly(k0)][lx(k0) + 1]),
+                                     S::dec(sm.ub[ly(k1)][lx(k1) + 1]));
+      // y + 1 neighbour: pixel k0's is k1; pixel k1's is the next pair or the strip below
+      const float2 uby = make_float2(
+          ub.y, (k1 % KY == KY - 1) ? S::dec(sm.ubfirst[ty0 + 1][lx(k1)]) : q1r[j + 1].x);
+      const float2 ux = mul2(MX[j], fma2(one_neg, ub, ubx));
+      const float2 uy = mul2(MY[j], fma2(one_neg, ub, uby));
+      // M (ux, uy), M = (1/G)[[1+b^2, -ab], [-ab, 1+a^2], [a, b]] (Eq. 3)
+      const float2 w = fma2(NA[j], uy, mul2(B[j], ux));
+      const float2 g1 = mul2(IG[j], fma2(B[j], w, ux));
+      const float2 g2 = mul2(IG[j], fma2(NA[j], w, uy));
+      const float2 g3 = mul2(IG[j], fma2(A[j], ux, mul2(B[j], uy)));
+      const float2 a1 = fma2(sig2, g1, p1[j]);
+      const float2 a2 = fma2(sig2, g2, p2[j]);
+      const float2 a3 = fma2(sig2, g3, p3[j]);
+      // projection onto |p| <= sqrt(G) (Eq. update_rules, second line)
+      const float2 n2 = fma2(a1, a1, fma2(a2, a2, mul2(a3, a3)));
+      const float2 t = mul2(SG[j], make_float2(rsqrtf(n2.x), rsqrtf(n2.y)));
+      const float2 sc = make_float2(n2.x > SG2[j].x ? t.x : 1.0f, n2.y > SG2[j].y ? t.y : 1.0f);
+      p1[j] = mul2(a1, sc);
+      p2[j] = mul2(a2, sc);
+      p3[j] = mul2(a3, sc);
+      p1[j].x = S::rnd(p1[j].x);
+      p1[j].y = S::rnd(p1[j].y);
+      p2[j].x = S::rnd(p2[j].x);
+      p2[j].y = S::rnd(p2[j].y);
+      p3[j].x = S::rnd(p3[j].x);
+      p3[j].y = S::rnd(p3[j].y);
     }
   }
 
   // Write (u, p) of the owned pixels (all of them, or only the border band).
-  __device__ __forceinline__ void store(const Planes& P, int buf, bool band_only) const {
+  __device__ __forceinline__ void store(const Planes& P, int buf, bool band_only) {
     float* U = P.u[buf];
     ST *P1 = (ST*)P.p1[buf], *P2 = (ST*)P.p2[buf], *P3 = (ST*)P.p3[buf];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+      const int j = k >> 1, h = k & 1;
       if ((band_only ? band(k) : owned(k)) && on(k, P.W, P.H)) {
         const size_t i = gidx(P, k);
-        U[i] = u[k];
-        P1[i] = S::enc(p1[k]);
-        P2[i] = S::enc(p2[k]);
-        P3[i] = S::enc(p3[k]);
+        U[i] = el(u[j], h);
+        P1[i] = S::enc(el(p1[j], h));
+        P2[i] = S::enc(el(p2[j], h));
+        P3[i] = S::enc(el(p3[j], h));
       }
     }
   }
@@ -322,12 +343,13 @@ struct Tile {
     const ST *P1 = (const ST*)P.p1[buf], *P2 = (const ST*)P.p2[buf], *P3 = (const ST*)P.p3[buf];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+      const int j = k >> 1, h = k & 1;
       if (!owned(k) && on(k, P.W, P.H)) {
         const size_t i = gidx(P, k);
-        u[k] = __ldcg(U + i);
-        p1[k] = S::ldcg(P1, i);
-        p2[k] = S::ldcg(P2, i);
-        p3[k] = S::ldcg(P3, i);
+        el(u[j], h) = __ldcg(U + i);
+        el(p1[j], h) = S::ldcg(P1, i);
+        el(p2[j], h) = S::ldcg(P2, i);
+        el(p3[j], h) = S::ldcg(P3, i);
       }
     }
   }
