@@ -33,6 +33,13 @@ if ROOT not in sys.path:
 
 METRIC = "events/s and Gpixel-iter/s per GB300 at stated error vs FP64; batched vs plain"
 B_ALG = 40  # algorithmic bytes per pixel-iteration, FP32 state (read u,p1,p2,p3,f,t; write u,p)
+# algorithmic bytes per pixel of the packet's front launches, timed with the iteration
+# kernels: the prologue reads t_last (8), n+, n-, u (4 each) and writes L_x t, L_y t,
+# 1/G, sqrt(G), f (4 each) and the cleared counts (4 each); one TV-L1 iteration of the
+# time surface reads t0, s, q1, q2 and writes s, sbar (primal), reads sbar, q1, q2 and
+# writes q1, q2 (dual)
+B_PROLOGUE = 48
+B_TVL1_ITER = 44
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -153,26 +160,29 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("evr_kernels.cu", "evr_solvers.cu", "evr_internal.cuh"):
+    for f in ("evr_kernels.cu", "evr_solvers.cu", "evr_internal.cuh", "evr_api.cu"):
         with open(os.path.join(ROOT, "paper_1607_06283_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(solver_name):
-    """DRAM bytes per launch of the iteration kernel from the committed ncu summary
-    (profiles/k_tiled_blobs346.md), if it was taken on the current kernel source and
+def profiled_traffic(config, solver_name, launches_per_solve):
+    """DRAM bytes per launch of the packet's solve graph from the committed ncu summary
+    (profiles/k_tiled_<config>.md: the DRAM bytes of one solve's launches, captured in
+    the benchmark's own sequence), if it was taken on the current kernel source with
     the same solver configuration; else None."""
-    p = os.path.join(ROOT, "profiles", "k_tiled_blobs346.md")
+    p = os.path.join(ROOT, "profiles", f"k_tiled_{config}.md")
     if not os.path.exists(p):
         return None
     import re
     with open(p) as fh:
         text = fh.read()
-    m = re.search(r"traffic_bytes_per_launch: (\d+) kernel_source_sha: (\w+) solver: (.+)", text)
-    if not m or m.group(2) != kernel_source_hash() or m.group(3).strip() != solver_name:
-        return None
-    return int(m.group(1))
+    for m in re.finditer(r"solve_traffic_bytes: (\d+) launches_per_solve: (\d+) "
+                         r"kernel_source_sha: (\w+) solver: (.+)", text):
+        if (m.group(3) == kernel_source_hash() and m.group(4).strip() == solver_name and
+                int(m.group(2)) == round(launches_per_solve)):
+            return int(m.group(1)) / int(m.group(2))
+    return None
 
 
 def cpu_baseline(cfg, stream, budget_s, max_packets=None):
@@ -396,10 +406,14 @@ def run_ours(args):
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
+        # the timed region of each solve: the front launches (prologue, TV-L1) and the
+        # iteration kernels, one graph per packet
         avg_launch_ms = k_ms / max(1, k_launches)
-        px_per_launch = k_pixiters / max(1, k_launches)
-        achieved = B_ALG * px_per_launch / (avg_launch_ms * 1e-3) / 1e9
-        launches_per_step = 2 + k_launches / args.steps  # push + prologue + iteration kernels
+        alg_bytes = (B_ALG * k_pixiters +
+                     (B_PROLOGUE + B_TVL1_ITER * args.tvl1) * cfg.W * cfg.H * args.steps)
+        bytes_per_launch = alg_bytes / max(1, k_launches)
+        achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
+        launches_per_step = 1 + k_launches / args.steps  # push + the solve's launches
         line = {
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -415,11 +429,15 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "inputs": "device-resident event arrays (evr_push_events_device)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(g.solver_name),
-                         "kernel": "iteration kernels (" + g.solver_name + ")",
+                         "frac": achieved / peak,
+                         "traffic": profiled_traffic(cfg.name, g.solver_name,
+                                                     k_launches / args.steps),
+                         "kernel": "packet solve graph: prologue + iteration kernels (" +
+                                   g.solver_name + ")",
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "avg_launch_us": avg_launch_ms * 1e3,
-                         "bytes_per_launch": B_ALG * px_per_launch},
+                         "launches_per_solve": k_launches / args.steps,
+                         "bytes_per_launch": bytes_per_launch},
             "e2e": {"value": e2e_val, "unit": "events/s",
                     "h2d_bytes_per_step": cfg.packet * (2 + 2 + 8 + 1),
                     "d2h_bytes_per_step": cfg.W * cfg.H * 4},

@@ -313,10 +313,13 @@ int evr_data_image_backward(const float* f, const float* u_prev, const int32_t* 
  * rejection (then clears it), EVR_ERR_CUDA, or EVR_OK. */
 int evr_synchronize(evr_stream* s);
 
-/* Kernel timing with CUDA events on the handle's stream around each solve's
- * iteration kernels (enable = 1 starts and clears, 0 stops).  evr_kernel_time
- * synchronises and reports the total milliseconds, the number of iteration-kernel
- * launches and the pixel-iterations they performed since timing was enabled. */
+/* Kernel timing with CUDA events on the handle's stream around each solve's device
+ * work (enable = 1 starts and clears, 0 stops): the packet's front launches (TV-L1 of
+ * the time surface when enabled, the prologue) and its iteration kernels, which a
+ * tuned multi-launch solve runs as one graph.  The first solve of a handle runs its
+ * front launches and the autotuner before the timed region.  evr_kernel_time
+ * synchronises and reports the total milliseconds, the number of kernel launches in
+ * the timed regions and the pixel-iterations performed since timing was enabled. */
 int evr_enable_kernel_timing(evr_stream* s, int enable);
 int evr_kernel_time(evr_stream* s, double* ms, int64_t* launches, int64_t* pixel_iters);
 

@@ -38,9 +38,10 @@ struct StageSlot {
 };
 
 struct GraphKey {
-  int iters, cur;
+  int iters, cur, front;  // front: the graph starts with the (TV-L1 +) prologue launches
   bool operator<(const GraphKey& o) const {
-    return iters != o.iters ? iters < o.iters : cur < o.cur;
+    if (iters != o.iters) return iters < o.iters;
+    return cur != o.cur ? cur < o.cur : front < o.front;
   }
 };
 
@@ -586,25 +587,39 @@ int evr_push_events_device(evr_stream* s, const uint16_t* x, const uint16_t* y,
   return EVR_OK;
 }
 
-int evr_solve(evr_stream* s, int iters) {
-  if (!s || iters < 0) return EVR_ERR_INVALID_ARG;
-  cudaStream_t st = s->stream;
+// The packet's front launches on stream q: TV-L1 of the time surface (if enabled) and
+// the prologue (metric, f, cleared counts).
+int enqueue_front(evr_stream* s, cudaStream_t q) {
   PrologueConsts pc = prologue_consts(s);
   if (s->prm.tvl1_iters > 0 && s->prm.manifold) {
     // denoise the time surface in the free buffer (1 - cur) and the ubar plane
     const int o = 1 - s->cur;
     if (launch_tvl1(s->P, pc, s->prm.tvl1_iters, s->prm.tvl1_lambda, s->P.u[o], s->P.p1[o],
-                    s->P.p2[o], s->P.p3[o], s->P.ubar, st))
-      return EVR_ERR_CUDA;
+                    s->P.p2[o], s->P.p3[o], s->P.ubar, q))
+      return -1;
     pc.tau_plane = s->P.p1[o];
   }
-  if (launch_prologue(s->P, s->cur, pc, st)) return EVR_ERR_CUDA;
-  if (iters == 0) return EVR_OK;
-  if (!s->tuned) {
+  return launch_prologue(s->P, s->cur, pc, q) ? -1 : 0;
+}
+
+int evr_solve(evr_stream* s, int iters) {
+  if (!s || iters < 0) return EVR_ERR_INVALID_ARG;
+  cudaStream_t st = s->stream;
+  // Once tuned, a multi-launch solve is one graph: front launches + iteration passes
+  // (pass 0 is a programmatic dependent of the prologue).  The persistent solver takes
+  // the front launches directly on the stream.
+  const int front_launches =
+      1 + ((s->prm.tvl1_iters > 0 && s->prm.manifold) ? 1 + 2 * s->prm.tvl1_iters : 0);
+  if (iters == 0) return enqueue_front(s, st) ? EVR_ERR_CUDA : EVR_OK;
+  bool front_done = false;
+  if (!s->tuned) {  // the first solve: front launches, then the autotuner (untimed)
+    if (enqueue_front(s, st)) return EVR_ERR_CUDA;
     autotune(s, iters);
     s->tuned = true;
     set_name(s);
+    front_done = true;
   }
+  const bool direct_front = !front_done && s->cfg >= 0 && kSolverCfgs[s->cfg].kind == 2;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (s->timing) {
     if ((int)s->ev_used.size() >= kMaxTimingPairs) resolve_timing(s);
@@ -617,20 +632,26 @@ int evr_solve(evr_stream* s, int iters) {
     }
     cudaEventRecord(ev.first, st);
   }
-  int launches = 0;
+  if (direct_front && enqueue_front(s, st)) return EVR_ERR_CUDA;
+  const bool graph_front = !front_done && !direct_front;
+  // launches inside the timed region: the front launches unless the first solve ran
+  // them before the autotuner, then the iteration kernels
+  int launches = front_done ? 0 : front_launches;
   if (s->cfg >= 0 && kSolverCfgs[s->cfg].kind == 2) {
     if (run_cfg_direct(s, s->cfg, iters)) return EVR_ERR_CUDA;
-    launches = 1;
+    launches += 1;
   } else {
-    GraphKey key{iters, s->cur};
+    GraphKey key{iters, s->cur, graph_front ? 1 : 0};
     auto it = s->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     int end_cur = s->cur;
     if (it == s->graphs.end()) {
       cudaGraph_t g = nullptr;
+      int captured = 0;
       if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return EVR_ERR_CUDA;
-      int r = enqueue_iterations(s, iters, s->cur, s->cap_stream, &launches);
+      int r = graph_front ? enqueue_front(s, s->cap_stream) : 0;
+      if (r == 0) r = enqueue_iterations(s, iters, s->cur, s->cap_stream, &captured);
       cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
       if (r < 0 || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -644,10 +665,10 @@ int evr_solve(evr_stream* s, int iters) {
       exec = it->second;
     }
     if (s->cfg < 0) {
-      launches = 2 * iters;
+      launches += 2 * iters;
     } else {
       const int passes = (iters + kSolverCfgs[s->cfg].R - 1) / kSolverCfgs[s->cfg].R;
-      launches = passes;
+      launches += passes;
       end_cur = (passes % 2) ? 1 - s->cur : s->cur;
     }
     if (cudaGraphLaunch(exec, st) != cudaSuccess) return EVR_ERR_CUDA;

@@ -338,6 +338,9 @@ __device__ __forceinline__ void prologue_px_body(const Planes& P, int cur, const
 // blocks numbered over its image) and a batch (one work item per CTA).
 __global__ void __launch_bounds__(256) k_prologue(Planes P, int cur, PrologueConsts c,
                                                   BatchRef B) {
+  // The first iteration pass may launch now; it reads nothing of ours before its
+  // griddepcontrol.wait, which returns once this grid has completed.
+  asm volatile("griddepcontrol.launch_dependents;" :::);
   __shared__ Planes sP;  // this CTA's stream, staged once
   int blk = blockIdx.x;
   if (B.descs) {
