@@ -59,6 +59,9 @@ struct Stor<float> {
   static __device__ __forceinline__ float enc(float v) { return v; }
   static __device__ __forceinline__ float dec(float v) { return v; }
   static __device__ __forceinline__ float rnd(float v) { return v; }
+  using T2 = float2;  // two vertically adjacent pixels
+  static __device__ __forceinline__ float2 enc2(float2 v) { return v; }
+  static __device__ __forceinline__ float2 dec2(float2 v) { return v; }
 };
 template <>
 struct Stor<__half> {
@@ -69,6 +72,9 @@ struct Stor<__half> {
   static __device__ __forceinline__ __half enc(float v) { return __float2half_rn(v); }
   static __device__ __forceinline__ float dec(__half v) { return __half2float(v); }
   static __device__ __forceinline__ float rnd(float v) { return __half2float(__float2half_rn(v)); }
+  using T2 = __half2;
+  static __device__ __forceinline__ __half2 enc2(float2 v) { return __floats2half2_rn(v.x, v.y); }
+  static __device__ __forceinline__ float2 dec2(__half2 v) { return __half22float2(v); }
 };
 template <>
 struct Stor<__nv_bfloat16> {
@@ -83,14 +89,21 @@ struct Stor<__nv_bfloat16> {
   static __device__ __forceinline__ float rnd(float v) {
     return __bfloat162float(__float2bfloat16_rn(v));
   }
+  using T2 = __nv_bfloat162;
+  static __device__ __forceinline__ __nv_bfloat162 enc2(float2 v) {
+    return __floats2bfloat162_rn(v.x, v.y);
+  }
+  static __device__ __forceinline__ float2 dec2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
 };
 
 // ---------------------------------------------------------------- one tile
 template <int KX, int KY, int NTY, typename ST = float>
 struct TileSmem {
   static constexpr int EW = 32 * KX, EH = NTY * KY;
-  float q1[EH][EW + 1];    // column 0: left pad (zero)
-  ST ub[EH][EW + 1];       // column EW: right pad (zero)
+  // q1 and ubar of rows 2r and 2r + 1 interleaved in row r (the two pixels of a pair):
+  // one 64-bit (32-bit for 16-bit ST) access per pair
+  float2 q1[EH / 2][EW + 1];             // column 0: left pad (zero)
+  typename Stor<ST>::T2 ub[EH / 2][EW + 1];  // column EW: right pad (zero)
   float q2last[NTY + 1][EW];  // row ty + 1: q2 of strip ty's last pixel; row 0 pad
   ST ubfirst[NTY + 1][EW];    // row ty: ubar of strip ty's first pixel; row NTY pad
 };
@@ -134,9 +147,9 @@ struct Tile {
   using S = Stor<ST>;
   float2 u[KP], p1[KP], p2[KP], p3[KP];  // iterated state
   // packet constants: a = L_x t, -a, b = L_y t, 1/G, 1/G times the x (y) difference
-  // mask, the masks, sqrt(G), G; data term: KL (-beta, 4 beta f, 2 beta f) with
+  // mask, the masks, sqrt(G); data term: KL (-beta, 4 beta f, 2 beta f) with
   // beta = tau lambda sqrt(G), or L2 (1 / (1 + beta), beta f, unused)
-  float2 A[KP], NA[KP], B[KP], IG[KP], IGX[KP], IGY[KP], MX[KP], MY[KP], SG[KP], SG2[KP];
+  float2 A[KP], NA[KP], B[KP], IG[KP], IGX[KP], IGY[KP], MX[KP], MY[KP], SG[KP];
   float2 D1[KP], D2[KP], D3[KP];
   int gx0, gy0, R, OW, OH;
 
@@ -153,9 +166,9 @@ struct Tile {
 
   __device__ __forceinline__ static void zero_pads(TileSmem<KX, KY, NTY, ST>& sm) {
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int i = tid; i < EH; i += 32 * NTY) {
-      sm.q1[i][0] = 0.0f;
-      sm.ub[i][EW] = S::enc(0.0f);
+    for (int i = tid; i < EH / 2; i += 32 * NTY) {
+      sm.q1[i][0] = dup2(0.0f);
+      sm.ub[i][EW] = S::enc2(dup2(0.0f));
     }
     for (int i = tid; i < EW; i += 32 * NTY) {
       sm.q2last[0][i] = 0.0f;
@@ -205,7 +218,6 @@ struct Tile {
       el(MX[j], h) = mx;
       el(MY[j], h) = my;
       el(SG[j], h) = sg;
-      el(SG2[j], h) = sg * sg;
       const float beta = tl * sg;
       if (c.data_term) {  // Eq. 7: u+ = (v + beta f) / (1 + beta)
         el(D1[j], h) = 1.0f / (1.0f + beta);
@@ -256,8 +268,7 @@ struct Tile {
       const float2 z = fma2(NA[j], p2[j], mul2(B[j], p1[j]));  // b p1 - a p2
       q1r[j] = mul2(IGX[j], fma2(A[j], p3[j], fma2(B[j], z, p1[j])));
       q2r[j] = mul2(IGY[j], fma2(B[j], p3[j], fma2(NA[j], z, p2[j])));
-      sm.q1[ly(k0)][lx(k0) + 1] = q1r[j].x;
-      sm.q1[ly(k1)][lx(k1) + 1] = q1r[j].y;
+      sm.q1[ly(k0) / 2][lx(k0) + 1] = q1r[j];
       if (k1 % KY == KY - 1) sm.q2last[ty0 + 1][lx(k1)] = q2r[j].y;
     }
     __syncthreads();
@@ -266,7 +277,7 @@ struct Tile {
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
       const int k0 = 2 * j, k1 = k0 + 1;
-      const float2 q1m = make_float2(sm.q1[ly(k0)][lx(k0)], sm.q1[ly(k1)][lx(k1)]);
+      const float2 q1m = sm.q1[ly(k0) / 2][lx(k0)];
       // y - 1 neighbour: pixel k1's is k0; pixel k0's is the pair above or the strip above
       const float2 q2m = make_float2((k0 % KY == 0) ? sm.q2last[ty0][lx(k0)] : q2r[j - 1].y,
                                      q2r[j].x);
@@ -293,8 +304,7 @@ struct Tile {
       ub.y = S::rnd(ub.y);
       u[j] = un;
       q1r[j] = ub;  // from here on: ubar of pair j
-      sm.ub[ly(k0)][lx(k0)] = S::enc(ub.x);
-      sm.ub[ly(k1)][lx(k1)] = S::enc(ub.y);
+      sm.ub[ly(k0) / 2][lx(k0)] = S::enc2(ub);
       if (k0 % KY == 0) sm.ubfirst[ty0][lx(k0)] = S::enc(ub.x);
     }
     __syncthreads();
@@ -304,8 +314,7 @@ struct Tile {
     for (int j = 0; j < KP; ++j) {
       const int k0 = 2 * j, k1 = k0 + 1;
       const float2 ub = q1r[j];
-      const float2 ubx = make_float2(S::dec(sm.ub[ly(k0)][lx(k0) + 1]),
-                                     S::dec(sm.ub[ly(k1)][lx(k1) + 1]));
+      const float2 ubx = S::dec2(sm.ub[ly(k0) / 2][lx(k0) + 1]);
       // y + 1 neighbour: pixel k0's is k1; pixel k1's is the next pair or the strip below
       const float2 uby = make_float2(
           ub.y, (k1 % KY == KY - 1) ? S::dec(sm.ubfirst[ty0 + 1][lx(k1)]) : q1r[j + 1].x);
@@ -319,10 +328,11 @@ struct Tile {
       const float2 a1 = fma2(sig2, g1, p1[j]);
       const float2 a2 = fma2(sig2, g2, p2[j]);
       const float2 a3 = fma2(sig2, g3, p3[j]);
-      // projection onto |p| <= sqrt(G) (Eq. update_rules, second line)
+      // projection onto |p| <= sqrt(G) (Eq. update_rules, second line):
+      // p / max(1, |p| / sqrt(G)) = p min(1, sqrt(G) / |p|); |p| = 0 gives min(1, inf)
       const float2 n2 = fma2(a1, a1, fma2(a2, a2, mul2(a3, a3)));
       const float2 t = mul2(SG[j], make_float2(rsqrt_mufu(n2.x), rsqrt_mufu(n2.y)));
-      const float2 sc = make_float2(n2.x > SG2[j].x ? t.x : 1.0f, n2.y > SG2[j].y ? t.y : 1.0f);
+      const float2 sc = make_float2(fminf(t.x, 1.0f), fminf(t.y, 1.0f));
       p1[j] = mul2(a1, sc);
       p2[j] = mul2(a2, sc);
       p3[j] = mul2(a3, sc);
