@@ -115,7 +115,11 @@ void set_name(evr_batch* b) {
 
 // Time each multi-launch tiled configuration over the whole batch: single passes that
 // read each stream's current buffer and write the other one (no live state changes).
-void autotune(evr_batch* b) {
+// Time every multi-launch configuration on the whole batch with the packet's iteration
+// count (its passes, the last one shorter) and keep the fastest (best of two runs).  Every
+// timing launch reads the live buffer and writes the other one, which the step graph
+// overwrites anyway, so the live state is untouched.
+void autotune(evr_batch* b, int iters) {
   SolveConsts c = consts(b);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -126,22 +130,24 @@ void autotune(evr_batch* b) {
     if (kSolverCfgs[ci].kind != 1) continue;
     if (build_tile_work(b, ci)) continue;
     const int R = kSolverCfgs[ci].R;
+    const int passes = (iters + R - 1) / R;
     BatchRef B = bref(b, true);
     launch_tiled_pass_batch(B, b->n_work_tile, kSolverCfgs[ci], 0, R, c, b->prm.storage,
-                            b->stream);
-    cudaEventRecord(e0, b->stream);
-    const int reps = 4;
-    for (int r = 0; r < reps; ++r)
-      launch_tiled_pass_batch(B, b->n_work_tile, kSolverCfgs[ci], 0, R, c, b->prm.storage,
-                              b->stream);
-    cudaEventRecord(e1, b->stream);
-    float ms = 0.f;
-    if (cudaEventSynchronize(e1) == cudaSuccess && cudaGetLastError() == cudaSuccess) {
-      cudaEventElapsedTime(&ms, e0, e1);
-      float per_iter = ms / (reps * R);
-      if (per_iter < best) {
-        best = per_iter;
-        best_cfg = ci;
+                            b->stream);  // warm-up
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, b->stream);
+      for (int j = 0; j < passes; ++j)
+        launch_tiled_pass_batch(B, b->n_work_tile, kSolverCfgs[ci], 0,
+                                j + 1 < passes ? R : iters - j * R, c, b->prm.storage,
+                                b->stream);
+      cudaEventRecord(e1, b->stream);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaGetLastError() == cudaSuccess) {
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_cfg = ci;
+        }
       }
     }
   }
@@ -332,7 +338,7 @@ int evr_batch_step_device(evr_batch* b, const uint16_t* x, const uint16_t* y,
                         (const long long*)offsets, b->d_active, st))
     return EVR_ERR_CUDA;
   if (iters > 0 && !b->tuned) {
-    autotune(b);
+    autotune(b, iters);
     drop_graphs(b);  // the tile work list may have moved
     b->tuned = true;
     set_name(b);

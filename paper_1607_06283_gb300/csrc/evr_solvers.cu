@@ -146,10 +146,14 @@ struct Tile {
   static constexpr int EW = 32 * KX, EH = NTY * KY, K = KX * KY, KP = K / 2;
   using S = Stor<ST>;
   float2 u[KP], p1[KP], p2[KP], p3[KP];  // iterated state
-  // packet constants: a = L_x t, -a, b = L_y t, 1/G, 1/G times the x (y) difference
-  // mask, the masks, sqrt(G); data term: KL (-beta, 4 beta f, 2 beta f) with
-  // beta = tau lambda sqrt(G), or L2 (1 / (1 + beta), beta f, unused)
-  float2 A[KP], NA[KP], B[KP], IG[KP], IGX[KP], IGY[KP], MX[KP], MY[KP], SG[KP];
+  // packet constants.  With M = (1/G)[[1+b^2, -ab], [-ab, 1+a^2], [a, b]] (Eq. 3;
+  // a = L_x t, b = L_y t) and the border masks m_x, m_y (1 where the forward difference
+  // in x (y) exists, else 0): E1..E3 = m_x (M11, M12, M31), E4..E6 = m_y (M12, M22, M32).
+  // Then q = (m_x (M^T p)_1, m_y (M^T p)_2) = (E1 p1 + E2 p2 + E3 p3, E4 p1 + E5 p2 + E6 p3)
+  // and M (m_x dx, m_y dy) = (E1 dx + E4 dy, E2 dx + E5 dy, E3 dx + E6 dy): the same six
+  // coefficients serve both operators.  sqrt(G); data term: KL (-beta, 4 beta f,
+  // 2 beta f) with beta = tau lambda sqrt(G), or L2 (1 / (1 + beta), beta f, unused).
+  float2 E1[KP], E2[KP], E3[KP], E4[KP], E5[KP], E6[KP], SG[KP];
   float2 D1[KP], D2[KP], D3[KP];
   int gx0, gy0, R, OW, OH;
 
@@ -209,14 +213,13 @@ struct Tile {
         mx = (gx0 + lx(k) < P.W - 1) ? 1.0f : 0.0f;
         my = (gy0 + ly(k) < P.H - 1) ? 1.0f : 0.0f;
       }
-      el(A[j], h) = a;
-      el(NA[j], h) = -a;
-      el(B[j], h) = b;
-      el(IG[j], h) = ig;
-      el(IGX[j], h) = ig * mx;
-      el(IGY[j], h) = ig * my;
-      el(MX[j], h) = mx;
-      el(MY[j], h) = my;
+      const float m12 = -(ig * (a * b));
+      el(E1[j], h) = mx * (ig * fmaf(b, b, 1.0f));
+      el(E2[j], h) = mx * m12;
+      el(E3[j], h) = mx * (ig * a);
+      el(E4[j], h) = my * m12;
+      el(E5[j], h) = my * (ig * fmaf(a, a, 1.0f));
+      el(E6[j], h) = my * (ig * b);
       el(SG[j], h) = sg;
       const float beta = tl * sg;
       if (c.data_term) {  // Eq. 7: u+ = (v + beta f) / (1 + beta)
@@ -265,9 +268,8 @@ struct Tile {
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
       const int k0 = 2 * j, k1 = k0 + 1;
-      const float2 z = fma2(NA[j], p2[j], mul2(B[j], p1[j]));  // b p1 - a p2
-      q1r[j] = mul2(IGX[j], fma2(A[j], p3[j], fma2(B[j], z, p1[j])));
-      q2r[j] = mul2(IGY[j], fma2(B[j], p3[j], fma2(NA[j], z, p2[j])));
+      q1r[j] = fma2(E3[j], p3[j], fma2(E2[j], p2[j], mul2(E1[j], p1[j])));
+      q2r[j] = fma2(E6[j], p3[j], fma2(E5[j], p2[j], mul2(E4[j], p1[j])));
       sm.q1[ly(k0) / 2][lx(k0) + 1] = q1r[j];
       if (k1 % KY == KY - 1) sm.q2last[ty0 + 1][lx(k1)] = q2r[j].y;
     }
@@ -318,13 +320,12 @@ struct Tile {
       // y + 1 neighbour: pixel k0's is k1; pixel k1's is the next pair or the strip below
       const float2 uby = make_float2(
           ub.y, (k1 % KY == KY - 1) ? S::dec(sm.ubfirst[ty0 + 1][lx(k1)]) : q1r[j + 1].x);
-      const float2 ux = mul2(MX[j], fma2(one_neg, ub, ubx));
-      const float2 uy = mul2(MY[j], fma2(one_neg, ub, uby));
-      // M (ux, uy), M = (1/G)[[1+b^2, -ab], [-ab, 1+a^2], [a, b]] (Eq. 3)
-      const float2 w = fma2(NA[j], uy, mul2(B[j], ux));
-      const float2 g1 = mul2(IG[j], fma2(B[j], w, ux));
-      const float2 g2 = mul2(IG[j], fma2(NA[j], w, uy));
-      const float2 g3 = mul2(IG[j], fma2(A[j], ux, mul2(B[j], uy)));
+      const float2 dx = fma2(one_neg, ub, ubx);
+      const float2 dy = fma2(one_neg, ub, uby);
+      // M (m_x dx, m_y dy) (Eq. 3)
+      const float2 g1 = fma2(E4[j], dy, mul2(E1[j], dx));
+      const float2 g2 = fma2(E5[j], dy, mul2(E2[j], dx));
+      const float2 g3 = fma2(E6[j], dy, mul2(E3[j], dx));
       const float2 a1 = fma2(sig2, g1, p1[j]);
       const float2 a2 = fma2(sig2, g2, p2[j]);
       const float2 a3 = fma2(sig2, g3, p3[j]);
