@@ -33,6 +33,11 @@ if ROOT not in sys.path:
 
 METRIC = "events/s and Gpixel-iter/s per GB300 at stated error vs FP64; batched vs plain"
 B_ALG = 40  # algorithmic bytes per pixel-iteration, FP32 state (read u,p1,p2,p3,f,t; write u,p)
+B_ALG_16 = 28  # the same with p stored in FP16/BF16 (2 B per component)
+
+
+def b_alg(storage):
+    return B_ALG if storage == 0 else B_ALG_16
 # algorithmic bytes per pixel of the packet's front launches, timed with the iteration
 # kernels: the prologue reads t_last (8), n+, n-, u (4 each) and writes L_x t, L_y t,
 # 1/G, sqrt(G), f (4 each) and the cleared counts (4 each); one TV-L1 iteration of the
@@ -409,7 +414,7 @@ def run_ours(args):
         # the timed region of each solve: the front launches (prologue, TV-L1) and the
         # iteration kernels, one graph per packet
         avg_launch_ms = k_ms / max(1, k_launches)
-        alg_bytes = (B_ALG * k_pixiters +
+        alg_bytes = (b_alg(args.storage) * k_pixiters +
                      (B_PROLOGUE + B_TVL1_ITER * args.tvl1) * cfg.W * cfg.H * args.steps)
         bytes_per_launch = alg_bytes / max(1, k_launches)
         achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
@@ -526,7 +531,8 @@ def run_batch_bench(args):
         b2.images(img)
     e2e_s = time.perf_counter() - t0
     peak, peak_kind = measured_peaks()
-    achieved = B_ALG * pxit / (k_ms * 1e-3) / 1e9
+    # the step graph: prologue (B_PROLOGUE per pixel of an active stream) + passes
+    achieved = (b_alg(args.storage) * pxit + B_PROLOGUE * pxit / iters) / (k_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
