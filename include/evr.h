@@ -151,6 +151,22 @@ int evr_get_image(evr_stream* s, float* out_host, size_t len);
  * asynchronous, on the handle's stream. */
 int evr_get_image_device(evr_stream* s, float* out_dev, size_t len);
 
+/* Asynchronous readback of the current image (real-time pipelines: the caller can queue
+ * the next packet while this one is solved and copied).  Queues the copy of u (W*H
+ * floats, row-major, as evr_get_image) into out_host on the handle's CUDA stream and
+ * returns at once with a ticket (> 0) in *ticket.  out_host must stay valid and unread
+ * until evr_wait_image(ticket) has returned; page-locked memory (cudaHostAlloc, pinned
+ * tensors) keeps the copy asynchronous, pageable memory makes the CUDA runtime wait for
+ * it here.  At most 16 readbacks are in flight: the 17th waits for the oldest.  Errors:
+ * EVR_ERR_INVALID_ARG (null pointer, len < W*H), EVR_ERR_OOM, EVR_ERR_CUDA. */
+int evr_get_image_async(evr_stream* s, float* out_host, size_t len, uint64_t* ticket);
+
+/* Wait until the readback `ticket` (and all work queued before it) has completed.
+ * Returns EVR_OK, or, when a device-side rejection was pending at that point, that
+ * code after clearing it as evr_synchronize does (a rejected packet left the state
+ * unchanged; the image is valid).  EVR_ERR_INVALID_ARG for a ticket not issued. */
+int evr_wait_image(evr_stream* s, uint64_t ticket);
+
 /* State planes for tests and checkpoints (dense row-major, W*H elements). */
 #define EVR_STATE_U 0       /* float */
 #define EVR_STATE_P1 1      /* float, dual variable p, component 1 */

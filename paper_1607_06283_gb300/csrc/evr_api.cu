@@ -27,15 +27,22 @@ namespace {
 constexpr int kStageSlots = 2;
 constexpr int kMaxTimingPairs = 8192;
 
+// A packet of n events is staged packed, x | y | t | pol (t at an 8-byte boundary), so
+// one host-to-device copy moves it; the device buffer uses the same layout.
+struct Packed {
+  size_t off_y, off_t, off_p, bytes;
+  explicit Packed(size_t n)
+      : off_y(2 * n), off_t((4 * n + 7) / 8 * 8), off_p(off_t + 8 * n), bytes(off_p + n) {}
+};
+
 struct StageSlot {
-  size_t cap = 0;
-  uint16_t* hx = nullptr;
-  uint16_t* hy = nullptr;
-  long long* ht = nullptr;
-  int8_t* hp = nullptr;
+  size_t cap = 0;            // events
+  char* h = nullptr;         // pinned, 13 * cap bytes
   cudaEvent_t done = nullptr;  // recorded after the slot's host-to-device copy
   bool pending = false;
 };
+
+constexpr int kImgRing = 16;  // asynchronous image readbacks in flight per handle
 
 struct GraphKey {
   int iters, cur, front;  // front: the graph starts with the (TV-L1 +) prologue launches
@@ -62,11 +69,12 @@ struct evr_stream {
   // host-to-device event staging
   StageSlot slot[kStageSlots];
   int next_slot = 0;
-  size_t dcap = 0;
-  uint16_t* dx = nullptr;
-  uint16_t* dy = nullptr;
-  long long* dt = nullptr;
-  int8_t* dp = nullptr;
+  size_t dcap = 0;           // events
+  char* dstage = nullptr;    // device, 13 * dcap bytes
+  // asynchronous image readbacks: completion event and status copy per ticket
+  cudaEvent_t img_ev[kImgRing] = {};
+  int* h_img_status = nullptr;  // pinned, kImgRing ints
+  unsigned long long img_ticket = 0;
   // host mirror of the stream clock for immediate checks
   long long h_clock = 0;
   bool h_have_clock = false;
@@ -139,54 +147,47 @@ void set_name(evr_stream* s) {
 void free_stage(evr_stream* s) {
   for (auto& sl : s->slot) {
     if (sl.done) cudaEventDestroy(sl.done);
-    if (sl.hx) cudaFreeHost(sl.hx);
+    if (sl.h) cudaFreeHost(sl.h);
     sl = StageSlot{};
   }
-  if (s->dx) cudaFree(s->dx);
-  s->dx = nullptr;
-  s->dy = nullptr;
-  s->dt = nullptr;
-  s->dp = nullptr;
+  if (s->dstage) cudaFree(s->dstage);
+  s->dstage = nullptr;
   s->dcap = 0;
+  for (auto& e : s->img_ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  if (s->h_img_status) cudaFreeHost(s->h_img_status);
+  s->h_img_status = nullptr;
 }
 
 // Grow the pinned slot and the device staging buffer to hold n events.
 int ensure_stage(evr_stream* s, StageSlot& sl, size_t n) {
   if (sl.cap < n) {
     if (sl.done) cudaEventSynchronize(sl.done);
-    if (sl.hx) cudaFreeHost(sl.hx);
+    if (sl.h) cudaFreeHost(sl.h);
+    // cap > n, so 13 cap bytes hold Packed(n).bytes <= 13 n + 7
     size_t cap = ((n < 4096 ? 4096 : n + n / 2) + 63) / 64 * 64;
-    char* h = nullptr;
-    if (cudaMallocHost((void**)&h, cap * (2 + 2 + 8 + 1)) != cudaSuccess) {
-      sl.hx = nullptr;
+    if (cudaMallocHost((void**)&sl.h, cap * 13) != cudaSuccess) {
+      sl.h = nullptr;
       sl.cap = 0;
       return EVR_ERR_OOM;
     }
-    // one allocation: x | y | t | pol (hx is the base pointer)
-    sl.hx = (uint16_t*)h;
-    sl.hy = (uint16_t*)(h + cap * 2);
-    sl.ht = (long long*)(h + cap * 4);
-    sl.hp = (int8_t*)(h + cap * 12);
     sl.cap = cap;
     if (!sl.done && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
       return EVR_ERR_CUDA;
   }
   if (s->dcap < n) {
-    if (s->dx) {
+    if (s->dstage) {
       cudaStreamSynchronize(s->stream);
-      cudaFree(s->dx);
+      cudaFree(s->dstage);
     }
     size_t cap = ((n < 4096 ? 4096 : n + n / 2) + 63) / 64 * 64;
-    char* d = nullptr;
-    if (cudaMalloc((void**)&d, cap * (2 + 2 + 8 + 1)) != cudaSuccess) {
-      s->dx = nullptr;
+    if (cudaMalloc((void**)&s->dstage, cap * 13) != cudaSuccess) {
+      s->dstage = nullptr;
       s->dcap = 0;
       return EVR_ERR_OOM;
     }
-    s->dx = (uint16_t*)d;
-    s->dy = (uint16_t*)(d + cap * 2);
-    s->dt = (long long*)(d + cap * 4);
-    s->dp = (int8_t*)(d + cap * 12);
     s->dcap = cap;
   }
   return EVR_OK;
@@ -556,19 +557,20 @@ int evr_push_events(evr_stream* s, const uint16_t* x, const uint16_t* y, const i
   }
   int rc = ensure_stage(s, sl, n);
   if (rc) return rc;
-  std::memcpy(sl.hx, x, n * 2);
-  std::memcpy(sl.hy, y, n * 2);
-  std::memcpy(sl.ht, t_us, n * 8);
-  std::memcpy(sl.hp, pol, n);
+  const Packed L(n);
+  std::memcpy(sl.h, x, n * 2);
+  std::memcpy(sl.h + L.off_y, y, n * 2);
+  std::memcpy(sl.h + L.off_t, t_us, n * 8);
+  std::memcpy(sl.h + L.off_p, pol, n);
   cudaStream_t st = s->stream;
-  cudaError_t e = cudaMemcpyAsync(s->dx, sl.hx, n * 2, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(s->dy, sl.hy, n * 2, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(s->dt, sl.ht, n * 8, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(s->dp, sl.hp, n, cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(s->dstage, sl.h, L.bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(sl.done, st);
   if (e != cudaSuccess) return EVR_ERR_CUDA;
   sl.pending = true;
-  if (launch_push(s->P, s->dx, s->dy, s->dt, s->dp, (int)n, st)) return EVR_ERR_CUDA;
+  char* d = s->dstage;
+  if (launch_push(s->P, (const uint16_t*)d, (const uint16_t*)(d + L.off_y),
+                  (const long long*)(d + L.off_t), (const int8_t*)(d + L.off_p), (int)n, st))
+    return EVR_ERR_CUDA;
   if (s->h_clock_valid) {
     s->h_clock = clock;
     s->h_have_clock = true;
@@ -690,6 +692,42 @@ int evr_get_image(evr_stream* s, float* out_host, size_t len) {
                                     cudaMemcpyDeviceToHost, s->stream);
   if (e != cudaSuccess) return EVR_ERR_CUDA;
   return sync_status(s);
+}
+
+int evr_get_image_async(evr_stream* s, float* out_host, size_t len, uint64_t* ticket) {
+  if (!s || !out_host || !ticket || len < (size_t)s->W * s->H) return EVR_ERR_INVALID_ARG;
+  if (!s->h_img_status) {
+    if (cudaMallocHost((void**)&s->h_img_status, sizeof(int) * kImgRing) != cudaSuccess) {
+      s->h_img_status = nullptr;
+      return EVR_ERR_OOM;
+    }
+    for (auto& e : s->img_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return EVR_ERR_CUDA;
+  }
+  const unsigned long long t = s->img_ticket + 1;
+  const int slot = (int)(t % kImgRing);
+  // a slot is reused only after the readback that held it has completed
+  if (cudaEventSynchronize(s->img_ev[slot]) != cudaSuccess) return EVR_ERR_CUDA;
+  cudaError_t e = cudaMemcpy2DAsync(out_host, (size_t)s->W * 4, s->P.u[s->cur],
+                                    (size_t)s->pitch * 4, (size_t)s->W * 4, s->H,
+                                    cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&s->h_img_status[slot], &s->P.sc->status, sizeof(int),
+                        cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(s->img_ev[slot], s->stream);
+  if (e != cudaSuccess) return EVR_ERR_CUDA;
+  s->img_ticket = t;
+  *ticket = t;
+  return EVR_OK;
+}
+
+int evr_wait_image(evr_stream* s, uint64_t ticket) {
+  if (!s || ticket == 0 || ticket > s->img_ticket) return EVR_ERR_INVALID_ARG;
+  const int slot = (int)(ticket % kImgRing);
+  // a slot recorded again since belongs to a later readback, which completes later
+  if (cudaEventSynchronize(s->img_ev[slot]) != cudaSuccess) return EVR_ERR_CUDA;
+  if (s->img_ticket - ticket < kImgRing && s->h_img_status[slot] != 0) return sync_status(s);
+  return EVR_OK;
 }
 
 int evr_get_image_device(evr_stream* s, float* out_dev, size_t len) {

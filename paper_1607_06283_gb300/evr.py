@@ -80,6 +80,8 @@ def _load():
         "evr_solve": ([vp, i], i),
         "evr_get_image": ([vp, vp, sz], i),
         "evr_get_image_device": ([vp, vp, sz], i),
+        "evr_get_image_async": ([vp, vp, sz, ctypes.POINTER(ctypes.c_uint64)], i),
+        "evr_wait_image": ([vp, ctypes.c_uint64], i),
         "evr_get_state": ([vp, i, vp, sz], i),
         "evr_set_state": ([vp, i, vp, sz], i),
         "evr_gap": ([vp, vp, vp], i),
@@ -204,6 +206,25 @@ def evr_get_image(h, out: np.ndarray) -> int:
     rc = _lib.evr_get_image(h, out.ctypes.data, out.size)
     if rc in (EVR_ERR_INVALID_ARG, EVR_ERR_CUDA):
         _check(rc, "evr_get_image")
+    return rc
+
+
+def evr_get_image_async(h, out: np.ndarray) -> int:
+    """Queues the copy of the image into a float32 host array of W*H elements (pinned
+    memory keeps it asynchronous); returns the ticket for evr_wait_image.  The array
+    must stay alive and unread until then."""
+    assert out.dtype == np.float32 and out.flags["C_CONTIGUOUS"]
+    t = ctypes.c_uint64(0)
+    _check(_lib.evr_get_image_async(h, out.ctypes.data, out.size, ctypes.byref(t)),
+           "evr_get_image_async")
+    return int(t.value)
+
+
+def evr_wait_image(h, ticket: int) -> int:
+    """Waits for a readback; returns the pending device status (0 = none)."""
+    rc = _lib.evr_wait_image(h, ctypes.c_uint64(ticket))
+    if rc in (EVR_ERR_INVALID_ARG, EVR_ERR_CUDA):
+        _check(rc, "evr_wait_image")
     return rc
 
 
