@@ -252,15 +252,25 @@ int evr_batch_step_device(evr_batch* b, const uint16_t* x, const uint16_t* y,
                           int iters);
 
 /* As evr_batch_step_device with host arrays (offsets on the host); the events are
- * copied before the call returns. */
+ * copied into library-owned pinned memory before the call returns (one of two slots;
+ * a slot is reused once its host-to-device copy has completed), then moved to the
+ * device with one copy. */
 int evr_batch_step(evr_batch* b, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
                    const int8_t* pol, const int64_t* offsets, int iters);
 
 /* Image / state plane of stream s (as evr_get_image / evr_get_state); synchronise. */
 int evr_batch_get_image(evr_batch* b, int s, float* out_host, size_t len);
 /* All images, stream after stream, each W[s]*H[s] floats row-major; synchronises.
- * len is the capacity of out_host in floats. */
+ * len is the capacity of out_host in floats.  A device kernel gathers the images into
+ * one buffer (allocated at the first readback), then one copy moves them. */
 int evr_batch_get_images(evr_batch* b, float* out_host, size_t len);
+/* Asynchronous form, as evr_get_image_async: queues the gather and the copy into
+ * out_host (page-locked for an asynchronous copy) and returns a ticket (> 0); at most
+ * 16 in flight.  evr_batch_wait_images(ticket) waits for that copy (EVR_OK,
+ * EVR_ERR_CUDA, EVR_ERR_INVALID_ARG for a ticket not issued); rejected packets are
+ * reported by evr_batch_synchronize. */
+int evr_batch_get_images_async(evr_batch* b, float* out_host, size_t len, uint64_t* ticket);
+int evr_batch_wait_images(evr_batch* b, uint64_t ticket);
 int evr_batch_get_state(evr_batch* b, int s, int which, void* out_host, size_t bytes);
 
 /* Wait; return the first pending rejection (lowest stream index, written to

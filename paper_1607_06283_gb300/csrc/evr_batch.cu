@@ -43,9 +43,18 @@ struct evr_batch {
   bool tuned = false;
   cudaStream_t stream = nullptr, own_stream = nullptr, cap_stream = nullptr;
   std::map<int, cudaGraphExec_t> graphs;  // by iteration count
-  // host-pointer steps: device staging
+  // host-pointer steps: packed pinned staging (two slots) and device staging
   size_t stage_cap = 0;
   char* d_stage = nullptr;
+  char* h_stage[2] = {nullptr, nullptr};
+  size_t h_stage_cap[2] = {0, 0};
+  cudaEvent_t h_stage_done[2] = {nullptr, nullptr};
+  int next_stage = 0;
+  // image readback: every stream's image gathered into one buffer, then one copy
+  long long* d_img_off = nullptr;  // per stream, offset in floats
+  float* d_img = nullptr;          // px_total floats
+  cudaEvent_t img_ev[16] = {};
+  unsigned long long img_ticket = 0;
   long long* d_offsets = nullptr;
   DevScalars* h_sc = nullptr;  // pinned, one per stream
   int* h_curs = nullptr;       // pinned
@@ -59,6 +68,23 @@ struct evr_batch {
   long long px_total = 0;
   char name[96] = {0};
 };
+
+// Every stream's current image into one buffer: stream s at out + off[s], W*H floats,
+// row-major without padding.  One CTA per stream, a warp per row.
+__global__ void __launch_bounds__(256) k_batch_gather(const Planes* __restrict__ descs,
+                                                     const int* __restrict__ curs,
+                                                     const long long* __restrict__ off,
+                                                     float* __restrict__ out) {
+  __shared__ Planes P;
+  const int s = blockIdx.x;
+  if (threadIdx.x == 0) P = descs[s];
+  __syncthreads();
+  const float* u = P.u[curs[s]];
+  float* o = out + off[s];
+  for (int y = threadIdx.x / 32; y < P.H; y += blockDim.x / 32)
+    for (int x = threadIdx.x % 32; x < P.W; x += 32)
+      o[(size_t)y * P.W + x] = u[(size_t)y * P.pitch + x];
+}
 
 namespace {
 
@@ -310,6 +336,14 @@ void evr_batch_destroy(evr_batch* b) {
   if (b->d_work_pro) cudaFree(b->d_work_pro);
   if (b->d_work_tile) cudaFree(b->d_work_tile);
   if (b->d_stage) cudaFree(b->d_stage);
+  for (int k = 0; k < 2; ++k) {
+    if (b->h_stage[k]) cudaFreeHost(b->h_stage[k]);
+    if (b->h_stage_done[k]) cudaEventDestroy(b->h_stage_done[k]);
+  }
+  if (b->d_img_off) cudaFree(b->d_img_off);
+  if (b->d_img) cudaFree(b->d_img);
+  for (auto& e : b->img_ev)
+    if (e) cudaEventDestroy(e);
   if (b->h_sc) cudaFreeHost(b->h_sc);
   if (b->h_curs) cudaFreeHost(b->h_curs);
   if (b->own_stream) cudaStreamDestroy(b->own_stream);
@@ -379,39 +413,53 @@ int evr_batch_step(evr_batch* b, const uint16_t* x, const uint16_t* y, const int
   for (int s = 0; s < b->n; ++s)
     if (offsets[s + 1] < offsets[s] || offsets[0] != 0) return EVR_ERR_INVALID_ARG;
   if (n_ev > 0 && (!x || !y || !t_us || !pol)) return EVR_ERR_INVALID_ARG;
-  const size_t need = (size_t)n_ev * 13 + sizeof(long long) * (b->n + 1) + 1024;
-  if (b->stage_cap < need) {
+  // packed layout, the same in the pinned slot and on the device:
+  // offsets | t | x | y | pol, each part at a 256-byte boundary
+  const size_t o_t = (sizeof(long long) * (b->n + 1) + 255) / 256 * 256;
+  const size_t o_x = o_t + ((size_t)n_ev * 8 + 255) / 256 * 256;
+  const size_t o_y = o_x + ((size_t)n_ev * 2 + 255) / 256 * 256;
+  const size_t o_p = o_y + ((size_t)n_ev * 2 + 255) / 256 * 256;
+  const size_t bytes = o_p + (size_t)n_ev;
+  if (b->stage_cap < bytes) {
     if (b->d_stage) {
       cudaStreamSynchronize(b->stream);
       cudaFree(b->d_stage);
     }
     b->d_stage = nullptr;
     b->stage_cap = 0;
-    if (cudaMalloc((void**)&b->d_stage, need * 2) != cudaSuccess) return EVR_ERR_OOM;
-    b->stage_cap = need * 2;
+    if (cudaMalloc((void**)&b->d_stage, bytes * 2) != cudaSuccess) return EVR_ERR_OOM;
+    b->stage_cap = bytes * 2;
   }
-  char* q = b->d_stage;
-  long long* doff = (long long*)q;
-  q += (sizeof(long long) * (b->n + 1) + 255) / 256 * 256;
-  long long* dt = (long long*)q;
-  q += ((size_t)n_ev * 8 + 255) / 256 * 256;
-  uint16_t* dx = (uint16_t*)q;
-  q += ((size_t)n_ev * 2 + 255) / 256 * 256;
-  uint16_t* dy = (uint16_t*)q;
-  q += ((size_t)n_ev * 2 + 255) / 256 * 256;
-  int8_t* dp = (int8_t*)q;
-  cudaStream_t st = b->stream;
-  cudaError_t e = cudaMemcpyAsync(doff, offsets, sizeof(long long) * (b->n + 1),
-                                  cudaMemcpyHostToDevice, st);
+  const int k = b->next_stage;
+  b->next_stage ^= 1;
+  if (b->h_stage_done[k] && cudaEventSynchronize(b->h_stage_done[k]) != cudaSuccess)
+    return EVR_ERR_CUDA;  // the slot's previous copy has completed
+  if (b->h_stage_cap[k] < bytes) {
+    if (b->h_stage[k]) cudaFreeHost(b->h_stage[k]);
+    b->h_stage[k] = nullptr;
+    b->h_stage_cap[k] = 0;
+    if (cudaMallocHost((void**)&b->h_stage[k], bytes * 2) != cudaSuccess) return EVR_ERR_OOM;
+    b->h_stage_cap[k] = bytes * 2;
+  }
+  if (!b->h_stage_done[k] &&
+      cudaEventCreateWithFlags(&b->h_stage_done[k], cudaEventDisableTiming) != cudaSuccess)
+    return EVR_ERR_CUDA;
+  char* h = b->h_stage[k];
+  std::memcpy(h, offsets, sizeof(long long) * (b->n + 1));
   if (n_ev > 0) {
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, t_us, n_ev * 8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, n_ev * 2, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, n_ev * 2, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, pol, n_ev, cudaMemcpyHostToDevice, st);
+    std::memcpy(h + o_t, t_us, (size_t)n_ev * 8);
+    std::memcpy(h + o_x, x, (size_t)n_ev * 2);
+    std::memcpy(h + o_y, y, (size_t)n_ev * 2);
+    std::memcpy(h + o_p, pol, (size_t)n_ev);
   }
+  cudaStream_t st = b->stream;
+  char* q = b->d_stage;
+  cudaError_t e = cudaMemcpyAsync(q, h, bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->h_stage_done[k], st);
   if (e != cudaSuccess) return EVR_ERR_CUDA;
-  // pageable sources: the copies above complete before returning to the caller
-  return evr_batch_step_device(b, dx, dy, (const int64_t*)dt, dp, (const int64_t*)doff, iters);
+  return evr_batch_step_device(b, (const uint16_t*)(q + o_x), (const uint16_t*)(q + o_y),
+                               (const int64_t*)(q + o_t), (const int8_t*)(q + o_p),
+                               (const int64_t*)q, iters);
 }
 
 int evr_batch_get_image(evr_batch* b, int s, float* out_host, size_t len) {
@@ -426,22 +474,63 @@ int evr_batch_get_image(evr_batch* b, int s, float* out_host, size_t len) {
   return e == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
 }
 
+// Queue the gather of all images and their copy to out_host on the batch's stream.
+static int queue_images(evr_batch* b, float* out_host, size_t len) {
+  if ((long long)len < b->px_total) return EVR_ERR_INVALID_ARG;
+  if (!b->d_img) {
+    std::vector<long long> off(b->n);
+    long long acc = 0;
+    for (int s = 0; s < b->n; ++s) {
+      off[s] = acc;
+      acc += (long long)b->planes[s].W * b->planes[s].H;
+    }
+    if (cudaMalloc((void**)&b->d_img_off, sizeof(long long) * b->n) != cudaSuccess)
+      return EVR_ERR_OOM;
+    if (cudaMalloc((void**)&b->d_img, sizeof(float) * (size_t)b->px_total) != cudaSuccess) {
+      cudaFree(b->d_img_off);
+      b->d_img_off = nullptr;
+      b->d_img = nullptr;
+      return EVR_ERR_OOM;
+    }
+    if (cudaMemcpy(b->d_img_off, off.data(), sizeof(long long) * b->n,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return EVR_ERR_CUDA;
+  }
+  k_batch_gather<<<b->n, 256, 0, b->stream>>>(b->d_descs, b->d_curs, b->d_img_off, b->d_img);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_host, b->d_img, sizeof(float) * (size_t)b->px_total,
+                        cudaMemcpyDeviceToHost, b->stream);
+  return e == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}
+
 int evr_batch_get_images(evr_batch* b, float* out_host, size_t len) {
   if (!b || !out_host) return EVR_ERR_INVALID_ARG;
-  size_t need = 0;
-  for (int s = 0; s < b->n; ++s) need += (size_t)b->planes[s].W * b->planes[s].H;
-  if (len < need) return EVR_ERR_INVALID_ARG;
-  if (read_back(b)) return EVR_ERR_CUDA;
-  cudaError_t e = cudaSuccess;
-  float* q = out_host;
-  for (int s = 0; s < b->n && e == cudaSuccess; ++s) {
-    const Planes& P = b->planes[s];
-    e = cudaMemcpy2DAsync(q, (size_t)P.W * 4, P.u[b->h_curs[s]], (size_t)P.pitch * 4,
-                          (size_t)P.W * 4, P.H, cudaMemcpyDeviceToHost, b->stream);
-    q += (size_t)P.W * P.H;
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  return e == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+  int rc = queue_images(b, out_host, len);
+  if (rc) return rc;
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}
+
+int evr_batch_get_images_async(evr_batch* b, float* out_host, size_t len, uint64_t* ticket) {
+  if (!b || !out_host || !ticket) return EVR_ERR_INVALID_ARG;
+  if (!b->img_ev[0])
+    for (auto& e : b->img_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return EVR_ERR_CUDA;
+  const unsigned long long t = b->img_ticket + 1;
+  cudaEvent_t ev = b->img_ev[t % 16];
+  if (cudaEventSynchronize(ev) != cudaSuccess) return EVR_ERR_CUDA;  // slot reuse
+  int rc = queue_images(b, out_host, len);
+  if (rc) return rc;
+  if (cudaEventRecord(ev, b->stream) != cudaSuccess) return EVR_ERR_CUDA;
+  b->img_ticket = t;
+  *ticket = t;
+  return EVR_OK;
+}
+
+int evr_batch_wait_images(evr_batch* b, uint64_t ticket) {
+  if (!b || ticket == 0 || ticket > b->img_ticket) return EVR_ERR_INVALID_ARG;
+  // a slot recorded again since belongs to a later readback, which completes later
+  return cudaEventSynchronize(b->img_ev[ticket % 16]) == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
 }
 
 int evr_batch_get_state(evr_batch* b, int s, int which, void* out_host, size_t bytes) {

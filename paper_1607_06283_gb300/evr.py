@@ -100,6 +100,8 @@ def _load():
                                   [vp] * 8, i),
         "evr_data_image": ([vp] * 3 + [i, i, i, ctypes.c_float, ctypes.c_float, vp, vp], i),
         "evr_batch_create": ([i, vp, vp, vp, vp], i),
+        "evr_batch_get_images_async": ([vp, vp, sz, ctypes.POINTER(ctypes.c_uint64)], i),
+        "evr_batch_wait_images": ([vp, ctypes.c_uint64], i),
         "evr_batch_destroy": ([vp], None),
         "evr_batch_set_cuda_stream": ([vp, vp], i),
         "evr_batch_step_device": ([vp] * 6 + [i], i),
@@ -434,6 +436,19 @@ class Batch:
         _check(_lib.evr_batch_get_images(self.h, out.ctypes.data, out.size),
                "evr_batch_get_images")
         return out
+
+    def images_async(self, out: np.ndarray) -> int:
+        """Queues the readback of all images into `out` (pinned for an asynchronous
+        copy); returns the ticket for wait_images."""
+        assert out.dtype == np.float32 and out.flags["C_CONTIGUOUS"]
+        t = ctypes.c_uint64(0)
+        _check(_lib.evr_batch_get_images_async(self.h, out.ctypes.data, out.size,
+                                               ctypes.byref(t)), "evr_batch_get_images_async")
+        return int(t.value)
+
+    def wait_images(self, ticket: int) -> None:
+        _check(_lib.evr_batch_wait_images(self.h, ctypes.c_uint64(ticket)),
+               "evr_batch_wait_images")
 
     def state(self, s: int, which: int):
         W, H = self.sizes[s]

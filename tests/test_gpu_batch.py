@@ -129,3 +129,39 @@ def test_rejection_is_per_stream_and_idle_streams_are_untouched(E, streams):
     np.testing.assert_array_equal(b.state(1, E.EVR_STATE_U), before[1])
     assert b.synchronize() == (0, -1)
     b.close()
+
+
+def test_gathered_and_async_readback_match_per_stream_images(E, streams):
+    """evr_batch_get_images (device gather + one copy) and its asynchronous form, driven
+    with two steps in flight, give every stream's own image."""
+    import torch
+    b = E.Batch(SIZES, tile_config=1)
+    n_img = sum(w * h for w, h in SIZES)
+    bufs = [torch.empty(n_img, dtype=torch.float32).pin_memory().numpy() for _ in range(2)]
+    seen, prev = [], None
+    for k in range(4):
+        x, y, t, p, off = batch_step_arrays(streams, 300, k)
+        b.step(x, y, t, p, off, 30)
+        tk = b.images_async(bufs[k % 2])
+        if prev is not None:
+            b.wait_images(prev[0])
+            seen.append(prev[1].copy())
+        prev = (tk, bufs[k % 2])
+    b.wait_images(prev[0])
+    seen.append(prev[1].copy())
+    full = b.images()
+    np.testing.assert_array_equal(seen[-1], full)
+    a = 0
+    for s, (W, H) in enumerate(SIZES):
+        np.testing.assert_array_equal(full[a:a + W * H].reshape(H, W), b.image(s))
+        a += W * H
+    # the earlier asynchronous readbacks hold the earlier steps: replay them
+    r = E.Batch(SIZES, tile_config=1)
+    for k in range(4):
+        x, y, t, p, off = batch_step_arrays(streams, 300, k)
+        r.step(x, y, t, p, off, 30)
+        np.testing.assert_array_equal(r.images(), seen[k], err_msg=f"step {k}")
+    with pytest.raises(E.EvrError):
+        b.wait_images(99)
+    b.close()
+    r.close()
