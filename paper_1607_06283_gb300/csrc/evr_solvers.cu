@@ -260,6 +260,9 @@ struct Tile {
   }
 
   // One primal-dual iteration over the extended tile (two CTA barriers).
+  // L2: the data term of Eq. 7 instead of KL (a template argument, so that the loop body
+  // carries no branch on it).
+  template <bool L2>
   __device__ __forceinline__ void iterate(TileSmem<KX, KY, NTY, ST>& sm, const SolveConsts& c) {
     float2 q1r[KP], q2r[KP];
     const int ty0 = threadIdx.y;
@@ -286,7 +289,7 @@ struct Tile {
       const float2 div = add2(fma2(one_neg, q1m, q1r[j]), fma2(one_neg, q2m, q2r[j]));
       const float2 v = fma2(tau2, div, u[j]);
       float2 un;
-      if (c.data_term) {
+      if constexpr (L2) {
         un = mul2(add2(v, D2[j]), D1[j]);
       } else {
         // KL root (Eq. update_rules): MUFU reciprocal square root and reciprocal (a few
@@ -416,7 +419,10 @@ __global__ void __launch_bounds__(32 * NTY, 1) k_tiled(Planes P, int src, int it
   asm volatile("griddepcontrol.launch_dependents;" :::);
   if (pass == 0) T.load_consts(sP, c);
   T.load_state(sP, src);
-  for (int it = 0; it < iters; ++it) T.iterate(sm, c);
+  if (c.data_term)
+    for (int it = 0; it < iters; ++it) T.template iterate<true>(sm, c);
+  else
+    for (int it = 0; it < iters; ++it) T.template iterate<false>(sm, c);
   T.store(sP, 1 - src, false);
 }
 
@@ -452,7 +458,10 @@ __global__ void __launch_bounds__(32 * NTY) k_persist(Planes P, int cur, int ite
   const int bx = cta % tiles_x, by = cta / tiles_x;
   for (int j = 0; j < passes; ++j) {
     const int r = min(R, iters - j * R);
-    for (int it = 0; it < r; ++it) T.iterate(sm, c);
+    if (c.data_term)
+      for (int it = 0; it < r; ++it) T.template iterate<true>(sm, c);
+    else
+      for (int it = 0; it < r; ++it) T.template iterate<false>(sm, c);
     const int buf = cur ^ ((j + 1) & 1);
     if (j == passes - 1) {
       T.store(P, buf, false);
