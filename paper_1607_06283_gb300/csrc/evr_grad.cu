@@ -28,16 +28,22 @@ struct Coef {
   float tau, sigma, lambda, u_min, u_max;
 };
 
-// metric at pixel i from L_x t, L_y t: M = (1/G)[[1+b^2,-ab],[-ab,1+a^2],[a,b]] (Eq. 3)
-__device__ __forceinline__ void metric(const float* tx, const float* ty, size_t i, float& a,
-                                       float& b, float& iG, float& sG) {
-  a = tx[i];
-  b = ty[i];
-  float G = 1.0f + a * a + b * b;
-  iG = 1.0f / G;
-  sG = sqrtf(G);
+// Per-pixel metric of the packet (Eq. 3): L_x t, L_y t and, computed once per call by
+// k_metric with IEEE division and square root, 1/G and sqrt(G), G = 1 + a^2 + b^2.
+struct Met {
+  const float* tx;
+  const float* ty;
+  const float* iG;
+  const float* sG;
+};
+
+__device__ __forceinline__ void metric(const Met& m, size_t i, float& a, float& b, float& iG) {
+  a = m.tx[i];
+  b = m.ty[i];
+  iG = m.iG[i];
 }
 
+// M^T p with M = (1/G)[[1+b^2,-ab],[-ab,1+a^2],[a,b]] (Eq. 3)
 __device__ __forceinline__ void MT(float a, float b, float iG, float p1, float p2, float p3,
                                    float& q1, float& q2) {
   float z = b * p1 - a * p2;
@@ -53,35 +59,31 @@ __device__ __forceinline__ void Mg(float a, float b, float iG, float ux, float u
   g3 = iG * (a * ux + b * uy);
 }
 
-// div(M^T q) at (x, y) for a 3-plane field q (div_g q = -L_g^T q)
-__device__ __forceinline__ float div_g(const Geo& g, const float* tx, const float* ty,
-                                       const float* q, int x, int y) {
-  const size_t i = (size_t)y * g.pitch + x;
-  float a, b, iG, sG, q1, q2, q1m = 0.0f, q2m = 0.0f, d;
-  metric(tx, ty, i, a, b, iG, sG);
+// div(M^T q) at (x, y) for a 3-plane field q (div_g q = -L_g^T q); yl = row in the member
+__device__ __forceinline__ float div_g(const Geo& g, const Met& m, const float* q, int x, int yl,
+                                       size_t i) {
+  float a, b, iG, q1, q2, q1m = 0.0f, q2m = 0.0f, d;
+  metric(m, i, a, b, iG);
   MT(a, b, iG, q[i], q[g.plane + i], q[2 * g.plane + i], q1, q2);
   if (x > 0) {
-    metric(tx, ty, i - 1, a, b, iG, sG);
+    metric(m, i - 1, a, b, iG);
     MT(a, b, iG, q[i - 1], q[g.plane + i - 1], q[2 * g.plane + i - 1], q1m, d);
   }
-  const int yl = y % g.Hm;
   if (yl > 0) {
     const size_t j = i - g.pitch;
-    metric(tx, ty, j, a, b, iG, sG);
+    metric(m, j, a, b, iG);
     MT(a, b, iG, q[j], q[g.plane + j], q[2 * g.plane + j], d, q2m);
   }
   return ((x < g.W - 1) ? q1 : 0.0f) - q1m + ((yl < g.Hm - 1) ? q2 : 0.0f) - q2m;
 }
 
 // L_g w at (x, y) for a scalar plane w
-__device__ __forceinline__ void Lg(const Geo& g, const float* tx, const float* ty,
-                                   const float* w, int x, int y, float& g1, float& g2,
-                                   float& g3) {
-  const size_t i = (size_t)y * g.pitch + x;
-  float a, b, iG, sG;
-  metric(tx, ty, i, a, b, iG, sG);
+__device__ __forceinline__ void Lg(const Geo& g, const Met& m, const float* w, int x, int yl,
+                                   size_t i, float& g1, float& g2, float& g3) {
+  float a, b, iG;
+  metric(m, i, a, b, iG);
   float wx = (x < g.W - 1) ? w[i + 1] - w[i] : 0.0f;
-  float wy = (y % g.Hm < g.Hm - 1) ? w[i + g.pitch] - w[i] : 0.0f;
+  float wy = (yl < g.Hm - 1) ? w[i + g.pitch] - w[i] : 0.0f;
   Mg(a, b, iG, wx, wy, g1, g2, g3);
 }
 
@@ -89,46 +91,55 @@ __device__ __forceinline__ void Lg(const Geo& g, const float* tx, const float* t
   const int x = blockIdx.x * blockDim.x + threadIdx.x;     \
   const int y = blockIdx.y * blockDim.y + threadIdx.y;     \
   if (x >= g.W || y >= g.H) return;                        \
-  const size_t i = (size_t)y * g.pitch + x;
+  const size_t i = (size_t)y * g.pitch + x;                \
+  const int yl = y % g.Hm;
+
+__global__ void k_metric(Geo g, const float* tx, const float* ty, float* iG, float* sG) {
+  PIXEL
+  (void)yl;
+  const float a = tx[i], b = ty[i];
+  const float G = 1.0f + a * a + b * b;
+  iG[i] = 1.0f / G;
+  sG[i] = sqrtf(G);
+}
 
 // ---- forward iteration (reads state k, writes state k+1 and ubar) ----
-__global__ void k_f_primal(Geo g, Coef c, const float* tx, const float* ty, const float* f,
-                           const float* u, const float* p, float* u_out, float* ub) {
+// u_out may be NULL (only ubar wanted); v_out, when not NULL, receives the primal
+// argument v = u + tau div_g p, which the backward step reuses.
+__global__ void k_f_primal(Geo g, Coef c, Met m, const float* f, const float* u,
+                           const float* p, float* u_out, float* ub, float* v_out) {
   PIXEL
-  float a, b, iG, sG;
-  metric(tx, ty, i, a, b, iG, sG);
-  float v = u[i] + c.tau * div_g(g, tx, ty, p, x, y);
-  float beta = c.tau * c.lambda * sG;
+  float v = u[i] + c.tau * div_g(g, m, p, x, yl, i);
+  float beta = c.tau * c.lambda * m.sG[i];
   float d = v - beta;
   float r = 0.5f * (d + sqrtf(d * d + 4.0f * beta * f[i]));
   float un = fminf(fmaxf(r, c.u_min), c.u_max);
-  u_out[i] = un;
+  if (u_out) u_out[i] = un;
   ub[i] = 2.0f * un - u[i];
+  if (v_out) v_out[i] = v;
 }
 
-__global__ void k_f_dual(Geo g, Coef c, const float* tx, const float* ty, const float* ub,
-                         const float* p, float* p_out) {
+__global__ void k_f_dual(Geo g, Coef c, Met m, const float* ub, const float* p, float* p_out) {
   PIXEL
-  float a, b, iG, sG, g1, g2, g3;
-  metric(tx, ty, i, a, b, iG, sG);
-  Lg(g, tx, ty, ub, x, y, g1, g2, g3);
+  float g1, g2, g3;
+  Lg(g, m, ub, x, yl, i, g1, g2, g3);
   float p1 = p[i] + c.sigma * g1, p2 = p[g.plane + i] + c.sigma * g2,
         p3 = p[2 * g.plane + i] + c.sigma * g3;
-  float den = fmaxf(1.0f, sqrtf(p1 * p1 + p2 * p2 + p3 * p3) / sG);
+  float den = fmaxf(1.0f, sqrtf(p1 * p1 + p2 * p2 + p3 * p3) / m.sG[i]);
   p_out[i] = p1 / den;
   p_out[g.plane + i] = p2 / den;
   p_out[2 * g.plane + i] = p3 / den;
 }
 
 // ---- backward of one iteration from state (u, p) ----
-// step 1: ubar (recomputed) and the adjoint through the projection:
-//   apt = J_proj ap_next, written scaled by sigma (it is what L_g^T acts on)
-__global__ void k_b_dual(Geo g, Coef c, const float* tx, const float* ty, const float* ub,
-                         const float* p, const float* ap_next, float* sapt) {
+// step 1: the adjoint through the projection, apt = J_proj ap_next, written scaled by
+// sigma (it is what L_g^T acts on); ubar is the recomputed one of this iteration
+__global__ void k_b_dual(Geo g, Coef c, Met m, const float* ub, const float* p,
+                         const float* ap_next, float* sapt) {
   PIXEL
-  float a, b, iG, sG, g1, g2, g3;
-  metric(tx, ty, i, a, b, iG, sG);
-  Lg(g, tx, ty, ub, x, y, g1, g2, g3);
+  float g1, g2, g3;
+  Lg(g, m, ub, x, yl, i, g1, g2, g3);
+  const float sG = m.sG[i];
   float t1 = p[i] + c.sigma * g1, t2 = p[g.plane + i] + c.sigma * g2,
         t3 = p[2 * g.plane + i] + c.sigma * g3;
   float a1 = ap_next[i], a2 = ap_next[g.plane + i], a3 = ap_next[2 * g.plane + i];
@@ -145,36 +156,54 @@ __global__ void k_b_dual(Geo g, Coef c, const float* tx, const float* ty, const 
   sapt[2 * g.plane + i] = c.sigma * a3;
 }
 
-// step 2: a_ub = -div_g(sigma apt); primal step backwards.  Writes the new au (in
-// place), tau * a_v, and accumulates df and the lambda gradient per pixel.
-__global__ void k_b_primal(Geo g, Coef c, const float* tx, const float* ty, const float* f,
-                           const float* u, const float* p, const float* sapt, float* au,
-                           float* tav, float* gf, double* glam_px) {
-  PIXEL
-  float a, b, iG, sG;
-  metric(tx, ty, i, a, b, iG, sG);
-  float aub = -div_g(g, tx, ty, sapt, x, y);
-  float v = u[i] + c.tau * div_g(g, tx, ty, p, x, y);
-  float beta = c.tau * c.lambda * sG;
-  float d = v - beta;
-  float s = sqrtf(d * d + 4.0f * beta * f[i]);
-  float r = 0.5f * (d + s);
-  float aun = au[i] + 2.0f * aub;
-  float ar = (r < c.u_min || r > c.u_max) ? 0.0f : aun;
-  float av = ar * 0.5f * (1.0f + d / s);
-  gf[i] += ar * (beta / s);
-  glam_px[i] += (double)(ar * 0.5f * (-1.0f + (2.0f * f[i] - v + beta) / s)) *
-                ((double)c.tau * (double)sG);
-  au[i] = -aub + av;
-  tav[i] = c.tau * av;
+// step 2: a_ub = -div_g(sigma apt); the primal step backwards from the recomputed
+// argument v.  Writes the new au (in place), tau * a_v, accumulates df, and writes this
+// block's FP64 sum of the lambda-gradient terms to glam_part[blk] (one slot per block and
+// iteration: the final sum has a fixed order).
+__global__ void __launch_bounds__(256) k_b_primal(Geo g, Coef c, Met m, const float* f,
+                                                  const float* v_in, const float* sapt,
+                                                  float* au, float* tav, float* gf,
+                                                  double* glam_part) {
+  __shared__ double s_l[256];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  double lam_term = 0.0;
+  if (x < g.W && y < g.H) {
+    const size_t i = (size_t)y * g.pitch + x;
+    const int yl = y % g.Hm;
+    const float sG = m.sG[i];
+    const float aub = -div_g(g, m, sapt, x, yl, i);
+    const float v = v_in[i];
+    const float beta = c.tau * c.lambda * sG;
+    const float d = v - beta;
+    const float fi = f[i];
+    const float s = sqrtf(d * d + 4.0f * beta * fi);
+    const float r = 0.5f * (d + s);
+    const float aun = au[i] + 2.0f * aub;
+    const float ar = (r < c.u_min || r > c.u_max) ? 0.0f : aun;
+    const float av = ar * 0.5f * (1.0f + d / s);
+    gf[i] += ar * (beta / s);
+    lam_term = (double)(ar * 0.5f * (-1.0f + (2.0f * fi - v + beta) / s)) *
+               ((double)c.tau * (double)sG);
+    au[i] = -aub + av;
+    tav[i] = c.tau * av;
+  }
+  s_l[t] = lam_term;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (t < h) s_l[t] += s_l[t + h];
+    __syncthreads();
+  }
+  if (t == 0) glam_part[blockIdx.y * gridDim.x + blockIdx.x] = s_l[0];
 }
 
 // step 3: ap = apt - L_g(tau a_v)   (apt = sapt / sigma)
-__global__ void k_b_pupdate(Geo g, Coef c, const float* tx, const float* ty, const float* sapt,
-                            const float* tav, float* ap) {
+__global__ void k_b_pupdate(Geo g, Coef c, Met m, const float* sapt, const float* tav,
+                            float* ap) {
   PIXEL
   float g1, g2, g3;
-  Lg(g, tx, ty, tav, x, y, g1, g2, g3);
+  Lg(g, m, tav, x, yl, i, g1, g2, g3);
   ap[i] = sapt[i] / c.sigma - g1;
   ap[g.plane + i] = sapt[g.plane + i] / c.sigma - g2;
   ap[2 * g.plane + i] = sapt[2 * g.plane + i] / c.sigma - g3;
@@ -182,16 +211,13 @@ __global__ void k_b_pupdate(Geo g, Coef c, const float* tx, const float* ty, con
 
 __global__ void k_zero(Geo g, float* a, int planes) {
   PIXEL
+  (void)yl;
   for (int k = 0; k < planes; ++k) a[k * g.plane + i] = 0.0f;
-}
-
-__global__ void k_zero_d(Geo g, double* a) {
-  PIXEL
-  a[i] = 0.0;
 }
 
 __global__ void k_copy(Geo g, const float* src, float* dst, int planes) {
   PIXEL
+  (void)yl;
   for (int k = 0; k < planes; ++k) dst[k * g.plane + i] = src[k * g.plane + i];
 }
 
@@ -234,6 +260,7 @@ __global__ void __launch_bounds__(kRedBlocks) k_red_final(const double* partials
 __global__ void k_data_image(Geo g, const float* u_prev, const int* npos, const int* nneg,
                              float dpos, float dneg, float* f) {
   PIXEL
+  (void)yl;
   f[i] = u_prev[i] * expf(dpos * (float)npos[i] - dneg * (float)nneg[i]);
 }
 
@@ -243,6 +270,7 @@ __global__ void k_data_image_bwd(Geo g, const float* f, const float* u_prev, con
                                  const int* nneg, float dpos, float dneg, const float* gf,
                                  float* g_uprev, double* terms) {
   PIXEL
+  (void)yl;
   float e = expf(dpos * (float)npos[i] - dneg * (float)nneg[i]);
   if (g_uprev) g_uprev[i] = gf[i] * e;
   terms[i] = (double)gf[i] * (double)f[i] * (double)npos[i];
@@ -253,37 +281,47 @@ struct Workspace {
   float* ck;       // n_ck checkpoints x 4 planes
   float* tape;     // max(every, 2) states x 4 planes
   float* ub;       // 1 plane
+  float* v;        // 1 plane: the primal argument of the iteration being reversed
   float* sapt;     // 3 planes
   float* au;       // 1 plane
   float* ap;       // 3 planes
   float* tav;      // 1 plane
-  double* glam;    // 1 double plane
+  float* iG;       // 1 plane: 1/G
+  float* sG;       // 1 plane: sqrt(G)
+  double* glam;    // K x (blocks of the pixel grid): per-block lambda-gradient sums
   double* partials;  // 4 * kRedBlocks doubles
 };
+
+constexpr int kBlkX = 32, kBlkY = 8;  // pixel-kernel block
+
+size_t pixel_blocks(int W, int H) {
+  return (size_t)((W + kBlkX - 1) / kBlkX) * ((H + kBlkY - 1) / kBlkY);
+}
 
 size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspace* w) {
   const size_t plane = (size_t)pitch * H;
   const size_t fpl = (plane * 4 + 255) / 256 * 256;
-  const size_t dpl = (plane * 8 + 255) / 256 * 256;
   const int n_ck = (K + every - 1) / every;
   size_t off = 0;
   auto take = [&](size_t b) {
     size_t o = off;
-    off += b;
+    off += (b + 255) / 256 * 256;
     return base ? base + o : nullptr;
   };
   Workspace t;
   t.ck = (float*)take(fpl * 4 * (size_t)(n_ck > 0 ? n_ck : 1));
   t.tape = (float*)take(fpl * 4 * (size_t)(every > 2 ? every : 2));  // >= 2: forward ping-pong
   t.ub = (float*)take(fpl);
+  t.v = (float*)take(fpl);
   t.sapt = (float*)take(fpl * 3);
   t.au = (float*)take(fpl);
   t.ap = (float*)take(fpl * 3);
   t.tav = (float*)take(fpl);
-  t.glam = (double*)take(dpl);
+  t.iG = (float*)take(fpl);
+  t.sG = (float*)take(fpl);
+  t.glam = (double*)take(sizeof(double) * (size_t)K * pixel_blocks(W, H));
   t.partials = (double*)take(sizeof(double) * 4 * kRedBlocks);
   if (w) *w = t;
-  (void)W;
   return off;
 }
 
@@ -291,6 +329,8 @@ size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspac
 int check_args(int W, int H, int pitch, int K, int every, int n) {
   if (W <= 0 || H <= 0 || pitch < W || K < 1 || every < 1 || n < 1) return EVR_ERR_INVALID_ARG;
   if ((long long)H * n > 65535LL * 8) return EVR_ERR_INVALID_ARG;  // grid.y limit
+  if ((long long)K * (long long)pixel_blocks(W, H * n) > 0x7fffffffLL)
+    return EVR_ERR_INVALID_ARG;  // per-block lambda sums are indexed with int
   return EVR_OK;
 }
 
@@ -318,17 +358,16 @@ extern "C" int evr_unrolled_forward(const float* tx, const float* ty, const floa
   Geo g{W, H, pitch, (size_t)pitch * H, Hm};
   Coef c{tau, sigma, lambda, u_min, u_max};
   const size_t fpl = ((size_t)pitch * H * 4 + 255) / 256 * 256 / 4;  // floats per plane slot
-  dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
+  dim3 blk(kBlkX, kBlkY), grd((W + kBlkX - 1) / kBlkX, (H + kBlkY - 1) / kBlkY);
+  k_metric<<<grd, blk, 0, st>>>(g, tx, ty, w.iG, w.sG);
+  const Met m{tx, ty, w.iG, w.sG};
   // state buffers: two ping-pong states in the tape area (u | p1 p2 p3)
   float* su[2] = {w.tape, w.tape + 4 * fpl};
   Geo g4 = g;
   g4.plane = fpl;  // states use the aligned plane stride
   // copy (u0, p0) into state 0
-  {
-    Geo gi = g;  // caller planes: stride pitch * H
-    k_copy<<<grd, blk, 0, st>>>(gi, u0, su[0], 1);
-    for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(gi, p0 + k * gi.plane, su[0] + (1 + k) * fpl, 1);
-  }
+  k_copy<<<grd, blk, 0, st>>>(g, u0, su[0], 1);
+  for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, p0 + k * g.plane, su[0] + (1 + k) * fpl, 1);
   int cur = 0;
   for (int k = 0; k < K; ++k) {
     if (k % every == 0) {
@@ -337,15 +376,12 @@ extern "C" int evr_unrolled_forward(const float* tx, const float* ty, const floa
     }
     float* s0 = su[cur];
     float* s1 = su[1 - cur];
-    k_f_primal<<<grd, blk, 0, st>>>(g4, c, tx, ty, f, s0, s0 + fpl, s1, w.ub);
-    k_f_dual<<<grd, blk, 0, st>>>(g4, c, tx, ty, w.ub, s0 + fpl, s1 + fpl);
+    k_f_primal<<<grd, blk, 0, st>>>(g4, c, m, f, s0, s0 + fpl, s1, w.ub, nullptr);
+    k_f_dual<<<grd, blk, 0, st>>>(g4, c, m, w.ub, s0 + fpl, s1 + fpl);
     cur = 1 - cur;
   }
-  {
-    Geo go = g;
-    k_copy<<<grd, blk, 0, st>>>(go, su[cur], u_out, 1);
-    for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(go, su[cur] + (1 + k) * fpl, p_out + k * go.plane, 1);
-  }
+  k_copy<<<grd, blk, 0, st>>>(g, su[cur], u_out, 1);
+  for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, su[cur] + (1 + k) * fpl, p_out + k * g.plane, 1);
   return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
 }
 
@@ -368,8 +404,11 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
   const size_t fpl = ((size_t)pitch * H * 4 + 255) / 256 * 256 / 4;
   Geo g4 = g;
   g4.plane = fpl;
-  dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
-  // adjoint of the final state: au = gu_K, ap = 0; gf = 0; glam = 0
+  dim3 blk(kBlkX, kBlkY), grd((W + kBlkX - 1) / kBlkX, (H + kBlkY - 1) / kBlkY);
+  const size_t nblk = pixel_blocks(W, H);
+  k_metric<<<grd, blk, 0, st>>>(g, tx, ty, w.iG, w.sG);
+  const Met m{tx, ty, w.iG, w.sG};
+  // adjoint of the final state: au = gu_K, ap = gp_K or 0; gf = 0
   k_copy<<<grd, blk, 0, st>>>(g, gu_K, w.au, 1);
   if (gp_K) {
     for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, gp_K + k * g.plane, w.ap + k * fpl, 1);
@@ -377,7 +416,6 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
     k_zero<<<grd, blk, 0, st>>>(g4, w.ap, 3);
   }
   k_zero<<<grd, blk, 0, st>>>(g, gf, 1);
-  k_zero_d<<<grd, blk, 0, st>>>(g, w.glam);
   const int n_ck = (K + every - 1) / every;
   for (int cseg = n_ck - 1; cseg >= 0; --cseg) {
     const int k0 = cseg * every, k1 = (k0 + every < K) ? k0 + every : K;
@@ -386,27 +424,25 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
     for (int k = k0; k + 1 < k1; ++k) {
       float* s0 = w.tape + (size_t)(k - k0) * 4 * fpl;
       float* s1 = s0 + 4 * fpl;
-      k_f_primal<<<grd, blk, 0, st>>>(g4, c, tx, ty, f, s0, s0 + fpl, s1, w.ub);
-      k_f_dual<<<grd, blk, 0, st>>>(g4, c, tx, ty, w.ub, s0 + fpl, s1 + fpl);
+      k_f_primal<<<grd, blk, 0, st>>>(g4, c, m, f, s0, s0 + fpl, s1, w.ub, nullptr);
+      k_f_dual<<<grd, blk, 0, st>>>(g4, c, m, w.ub, s0 + fpl, s1 + fpl);
     }
     for (int k = k1 - 1; k >= k0; --k) {
       float* s0 = w.tape + (size_t)(k - k0) * 4 * fpl;
-      float* tmp_u = w.tav;  // u' of this iteration is not needed: recompute ubar only
-      k_f_primal<<<grd, blk, 0, st>>>(g4, c, tx, ty, f, s0, s0 + fpl, tmp_u, w.ub);
-      k_b_dual<<<grd, blk, 0, st>>>(g4, c, tx, ty, w.ub, s0 + fpl, w.ap, w.sapt);
-      k_b_primal<<<grd, blk, 0, st>>>(g4, c, tx, ty, f, s0, s0 + fpl, w.sapt, w.au, w.tav, gf,
-                                      w.glam);
-      k_b_pupdate<<<grd, blk, 0, st>>>(g4, c, tx, ty, w.sapt, w.tav, w.ap);
+      // ubar and the primal argument v of iteration k (u_{k+1} itself is not needed)
+      k_f_primal<<<grd, blk, 0, st>>>(g4, c, m, f, s0, s0 + fpl, nullptr, w.ub, w.v);
+      k_b_dual<<<grd, blk, 0, st>>>(g4, c, m, w.ub, s0 + fpl, w.ap, w.sapt);
+      k_b_primal<<<grd, blk, 0, st>>>(g4, c, m, f, w.v, w.sapt, w.au, w.tav, gf,
+                                      w.glam + (size_t)k * nblk);
+      k_b_pupdate<<<grd, blk, 0, st>>>(g4, c, m, w.sapt, w.tav, w.ap);
     }
   }
   if (gu0) k_copy<<<grd, blk, 0, st>>>(g, w.au, gu0, 1);
   if (gp0)
-    for (int k = 0; k < 3; ++k) {
-      Geo go = g;
-      k_copy<<<grd, blk, 0, st>>>(go, w.ap + k * fpl, gp0 + k * go.plane, 1);
-    }
-  Geo gd = g;
-  gd.plane = 0;
+    for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, w.ap + k * fpl, gp0 + k * g.plane, 1);
+  // dL/dlambda: the K x nblk per-block sums, in index order
+  const long long nl = (long long)K * (long long)nblk;
+  Geo gd{(int)nl, 1, (int)nl, 0, 1};
   k_red_partial<<<kRedBlocks, kRedThreads, 0, st>>>(gd, w.glam, 1, w.partials);
   k_red_final<<<1, kRedBlocks, 0, st>>>(w.partials, 1, glambda_dev);
   return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
