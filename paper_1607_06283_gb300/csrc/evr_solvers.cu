@@ -281,7 +281,7 @@ struct Tile {
     const float2 tau2 = dup2(c.tau);
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
-      const int k0 = 2 * j, k1 = k0 + 1;
+      const int k0 = 2 * j;
       const float2 q1m = sm.q1[ly(k0) / 2][lx(k0)];
       // y - 1 neighbour: pixel k1's is k0; pixel k0's is the pair above or the strip above
       const float2 q2m = make_float2((k0 % KY == 0) ? sm.q2last[ty0][lx(k0)] : q2r[j - 1].y,
@@ -391,8 +391,14 @@ struct Tile {
 // then waits for the previous pass to complete before reading (u, p), and only then
 // lets the next pass launch -- so no pass can run ahead of the prologue.  Pass 0
 // loads everything after its wait.
+// Resident CTAs per SM the register budget is sized for: three for the 256-thread FP32
+// tile with two pixel pairs per thread (so that the next pass's CTAs can become resident
+// while the current pass runs; 80 registers, no spills), one otherwise.
 template <int KX, int KY, int NTY, typename ST>
-__global__ void __launch_bounds__(32 * NTY, 1) k_tiled(Planes P, int src, int iters, int R,
+constexpr int kTiledMinBlocks = (NTY == 8 && KX * KY == 4 && sizeof(ST) == 4) ? 3 : 1;
+
+template <int KX, int KY, int NTY, typename ST>
+__global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>)) k_tiled(Planes P, int src, int iters, int R,
                                                     SolveConsts c, int tiles_x, BatchRef B,
                                                     int pass) {
   __shared__ TileSmem<KX, KY, NTY, ST> sm;
