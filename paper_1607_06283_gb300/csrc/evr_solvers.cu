@@ -31,6 +31,7 @@ const TileShape kTileShapes[kNumTileShapes] = {
     {64, 32, 8},   // 3: 256 threads, 8 px each
     {64, 32, 16},  // 4: 512 threads, 4 px each
     {32, 16, 8},   // 5: 256 threads, 2 px each
+    {32, 48, 12},  // 6: 384 threads, 4 px each
 };
 
 // {kind, shape, R}
@@ -43,6 +44,8 @@ const SolverCfg kSolverCfgs[kNumSolverCfgs] = {
     // grid still fits one wave
     {1, 2, 9}, {1, 2, 10}, {1, 4, 8}, {1, 0, 5}, {1, 0, 7}, {1, 0, 8}, {1, 1, 6}, {1, 1, 8},
     {1, 4, 6}, {1, 3, 5},
+    // the 384-thread tile, two resident CTAs per SM
+    {1, 6, 3}, {1, 6, 4}, {1, 6, 5}, {1, 6, 6}, {1, 6, 8},
 };
 
 // ---------------------------------------------------------------- storage formats
@@ -391,11 +394,14 @@ struct Tile {
 // then waits for the previous pass to complete before reading (u, p), and only then
 // lets the next pass launch -- so no pass can run ahead of the prologue.  Pass 0
 // loads everything after its wait.
-// Resident CTAs per SM the register budget is sized for: three for the 256-thread FP32
-// tile with two pixel pairs per thread (so that the next pass's CTAs can become resident
-// while the current pass runs; 80 registers, no spills), one otherwise.
+// Resident CTAs per SM the register budget is sized for: FP32 tiles with two pixel pairs
+// per thread get as many CTAs as fit at 80 registers (no spills; three of 256 threads,
+// two of 384), so that more warps hide latency and the next pass's CTAs can become
+// resident while the current pass runs; one otherwise.
 template <int KX, int KY, int NTY, typename ST>
-constexpr int kTiledMinBlocks = (NTY == 8 && KX * KY == 4 && sizeof(ST) == 4) ? 3 : 1;
+constexpr int kTiledMinBlocks =
+    (KX * KY == 4 && sizeof(ST) == 4 && 65536 / (32 * NTY * 80) > 1) ? 65536 / (32 * NTY * 80)
+                                                                      : 1;
 
 template <int KX, int KY, int NTY, typename ST>
 __global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>)) k_tiled(Planes P, int src, int iters, int R,
@@ -607,6 +613,7 @@ static int run_persist(const Planes& P, int R, int cur, int iters, int base, int
     case 3: return FN<2, 4, 8>(__VA_ARGS__);                         \
     case 4: return FN<2, 2, 16>(__VA_ARGS__);                        \
     case 5: return FN<1, 2, 8>(__VA_ARGS__);                         \
+    case 6: return FN<1, 4, 12>(__VA_ARGS__);                        \
     default: break;                                                  \
   }
 
