@@ -84,7 +84,7 @@ struct SolverCfg {
 };
 constexpr int kNumTileShapes = 7;
 extern const TileShape kTileShapes[kNumTileShapes];
-constexpr int kNumSolverCfgs = 39;
+constexpr int kNumSolverCfgs = 42;
 extern const SolverCfg kSolverCfgs[kNumSolverCfgs];
 
 constexpr int kGapBlocks = 304;   // fixed: the reduction order does not depend on W, H

@@ -45,7 +45,7 @@ const SolverCfg kSolverCfgs[kNumSolverCfgs] = {
     {1, 2, 9}, {1, 2, 10}, {1, 4, 8}, {1, 0, 5}, {1, 0, 7}, {1, 0, 8}, {1, 1, 6}, {1, 1, 8},
     {1, 4, 6}, {1, 3, 5},
     // the 384-thread tile, two resident CTAs per SM
-    {1, 6, 3}, {1, 6, 4}, {1, 6, 5}, {1, 6, 6}, {1, 6, 8},
+    {1, 6, 3}, {1, 6, 4}, {1, 6, 5}, {1, 6, 6}, {1, 6, 7}, {1, 6, 8}, {1, 6, 9}, {1, 6, 10},
 };
 
 // ---------------------------------------------------------------- storage formats
