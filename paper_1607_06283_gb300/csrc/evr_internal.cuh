@@ -82,9 +82,9 @@ struct TileShape {
 struct SolverCfg {
   int kind, shape, R;
 };
-constexpr int kNumTileShapes = 7;
+constexpr int kNumTileShapes = 8;
 extern const TileShape kTileShapes[kNumTileShapes];
-constexpr int kNumSolverCfgs = 42;
+constexpr int kNumSolverCfgs = 46;
 extern const SolverCfg kSolverCfgs[kNumSolverCfgs];
 
 constexpr int kGapBlocks = 304;   // fixed: the reduction order does not depend on W, H

@@ -32,6 +32,7 @@ const TileShape kTileShapes[kNumTileShapes] = {
     {64, 32, 16},  // 4: 512 threads, 4 px each
     {32, 16, 8},   // 5: 256 threads, 2 px each
     {32, 48, 12},  // 6: 384 threads, 4 px each
+    {32, 64, 32},  // 7: 1024 threads, 2 px each
 };
 
 // {kind, shape, R}
@@ -46,6 +47,8 @@ const SolverCfg kSolverCfgs[kNumSolverCfgs] = {
     {1, 4, 6}, {1, 3, 5},
     // the 384-thread tile, two resident CTAs per SM
     {1, 6, 3}, {1, 6, 4}, {1, 6, 5}, {1, 6, 6}, {1, 6, 7}, {1, 6, 8}, {1, 6, 9}, {1, 6, 10},
+    // the 1024-thread tile (32 warps on one SM)
+    {1, 7, 6}, {1, 7, 8}, {1, 7, 9}, {1, 7, 10},
 };
 
 // ---------------------------------------------------------------- storage formats
@@ -614,6 +617,7 @@ static int run_persist(const Planes& P, int R, int cur, int iters, int base, int
     case 4: return FN<2, 2, 16>(__VA_ARGS__);                        \
     case 5: return FN<1, 2, 8>(__VA_ARGS__);                         \
     case 6: return FN<1, 4, 12>(__VA_ARGS__);                        \
+    case 7: return FN<1, 2, 32>(__VA_ARGS__);                        \
     default: break;                                                  \
   }
 

@@ -38,7 +38,7 @@ def oracle_params(p, **kw):
         tvl1_iters=int(p.tvl1_iters), tvl1_lambda=float(np.float32(p.tvl1_lambda)), **kw)
 
 
-N_CFGS = 42  # solver configurations selectable with evr_params.tile_config = 1..N_CFGS
+N_CFGS = 46  # solver configurations selectable with evr_params.tile_config = 1..N_CFGS
 SOLVERS = [("unfused", 1, 0)] + [(f"cfg{k}", 2, k) for k in range(1, N_CFGS + 1)]
 
 
