@@ -103,19 +103,27 @@ int launch_init(const Planes& P, float u_init, long long clock0, long long t_ini
 }
 
 // ---------------------------------------------------------------- event scatter
-// Code of event i when all events before it are valid (then the running clock is
-// t[i-1], or the stream clock for i = 0): range, then polarity, then time.
-__device__ __forceinline__ int event_code(const uint16_t* x, const uint16_t* y,
-                                          const long long* t, const int8_t* pol, int i, int W,
-                                          int H, long long clock, int have_clock) {
-  if ((int)x[i] >= W || (int)y[i] >= H) return kErrOutOfRange;
-  if (pol[i] == 0) return kErrBadPolarity;
-  if (i > 0) {
-    if (t[i] < t[i - 1]) return kErrNonmonotonic;
-  } else if (have_clock && t[0] < clock) {
+// Code of an event (x, y, t, polarity; tprev = t of the event before it) when all events
+// before it are valid (then the running clock is tprev, or the stream clock for the
+// first event): range, then polarity, then time.
+__device__ __forceinline__ int event_code_of(int xi, int yi, long long ti, long long tprev,
+                                             int pi, bool first, int W, int H, long long clock,
+                                             int have_clock) {
+  if (xi >= W || yi >= H) return kErrOutOfRange;
+  if (pi == 0) return kErrBadPolarity;
+  if (!first) {
+    if (ti < tprev) return kErrNonmonotonic;
+  } else if (have_clock && ti < clock) {
     return kErrNonmonotonic;
   }
   return 0;
+}
+
+__device__ __forceinline__ int event_code(const uint16_t* x, const uint16_t* y,
+                                          const long long* t, const int8_t* pol, int i, int W,
+                                          int H, long long clock, int have_clock) {
+  return event_code_of((int)x[i], (int)y[i], t[i], i > 0 ? t[i - 1] : 0, (int)pol[i], i == 0,
+                       W, H, clock, have_clock);
 }
 
 // Warp-aggregated commit of events [base, n) with stride `stride`: lanes holding
@@ -154,13 +162,27 @@ __device__ __forceinline__ void push_cta(const Planes& P, const uint16_t* __rest
   __shared__ int s_bad;
   __shared__ long long s_clock;
   __shared__ int s_have;
+  // each thread's first event is loaded while thread 0 fetches the stream's clock
+  const int i0 = threadIdx.x;
+  int x0 = 0, y0 = 0, p0 = 1;
+  long long t0 = 0, tp0 = 0;
+  if (i0 < n) {
+    x0 = x[i0];
+    y0 = y[i0];
+    t0 = t[i0];
+    p0 = pol[i0];
+    if (i0 > 0) tp0 = t[i0 - 1];
+  }
   if (threadIdx.x == 0) {
     s_bad = n;
     s_clock = P.sc->clock;
     s_have = P.sc->t_init_set;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
+  if (i0 < n &&
+      event_code_of(x0, y0, t0, tp0, p0, i0 == 0, P.W, P.H, s_clock, s_have) != 0)
+    atomicMin(&s_bad, i0);
+  for (int i = i0 + blockDim.x; i < n; i += blockDim.x)
     if (event_code(x, y, t, pol, i, P.W, P.H, s_clock, s_have) != 0) atomicMin(&s_bad, i);
   __syncthreads();
   int bad = s_bad;
