@@ -133,16 +133,30 @@ __global__ void k_f_dual(Geo g, Coef c, Met m, const float* ub, const float* p, 
 
 // ---- backward of one iteration from state (u, p) ----
 // step 1: the adjoint through the projection, apt = J_proj ap_next, written scaled by
-// sigma (it is what L_g^T acts on); ubar is the recomputed one of this iteration
+// sigma (it is what L_g^T acts on); ubar is the recomputed one of this iteration.
+// ap_next, the adjoint of the next iteration's p, is read from `ap` for the last
+// iteration, else formed here from that iteration's sigma apt (in `sapt`, updated in
+// place: each pixel reads and writes only its own entries) and tau a_v (`tav`):
+// ap_next = apt - L_g(tau a_v).
 __global__ void k_b_dual(Geo g, Coef c, Met m, const float* ub, const float* p,
-                         const float* ap_next, float* sapt) {
+                         const float* ap, const float* tav, float* sapt) {
   PIXEL
   float g1, g2, g3;
+  float a1, a2, a3;
+  if (tav) {
+    Lg(g, m, tav, x, yl, i, g1, g2, g3);
+    a1 = sapt[i] / c.sigma - g1;
+    a2 = sapt[g.plane + i] / c.sigma - g2;
+    a3 = sapt[2 * g.plane + i] / c.sigma - g3;
+  } else {
+    a1 = ap[i];
+    a2 = ap[g.plane + i];
+    a3 = ap[2 * g.plane + i];
+  }
   Lg(g, m, ub, x, yl, i, g1, g2, g3);
   const float sG = m.sG[i];
   float t1 = p[i] + c.sigma * g1, t2 = p[g.plane + i] + c.sigma * g2,
         t3 = p[2 * g.plane + i] + c.sigma * g3;
-  float a1 = ap_next[i], a2 = ap_next[g.plane + i], a3 = ap_next[2 * g.plane + i];
   float nrm = sqrtf(t1 * t1 + t2 * t2 + t3 * t3);
   if (nrm > sG) {
     float dot = (t1 * a1 + t2 * a2 + t3 * a3) / (nrm * nrm);
@@ -431,15 +445,19 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
       float* s0 = w.tape + (size_t)(k - k0) * 4 * fpl;
       // ubar and the primal argument v of iteration k (u_{k+1} itself is not needed)
       k_f_primal<<<grd, blk, 0, st>>>(g4, c, m, f, s0, s0 + fpl, nullptr, w.ub, w.v);
-      k_b_dual<<<grd, blk, 0, st>>>(g4, c, m, w.ub, s0 + fpl, w.ap, w.sapt);
+      // the adjoint of p_{k+1}: the given one for the last iteration, else from the
+      // reversed iteration k + 1 (fused here)
+      k_b_dual<<<grd, blk, 0, st>>>(g4, c, m, w.ub, s0 + fpl, w.ap,
+                                    k == K - 1 ? nullptr : w.tav, w.sapt);
       k_b_primal<<<grd, blk, 0, st>>>(g4, c, m, f, w.v, w.sapt, w.au, w.tav, gf,
                                       w.glam + (size_t)k * nblk);
-      k_b_pupdate<<<grd, blk, 0, st>>>(g4, c, m, w.sapt, w.tav, w.ap);
     }
   }
   if (gu0) k_copy<<<grd, blk, 0, st>>>(g, w.au, gu0, 1);
-  if (gp0)
+  if (gp0) {  // the adjoint of p_0 from the reversed iteration 0
+    k_b_pupdate<<<grd, blk, 0, st>>>(g4, c, m, w.sapt, w.tav, w.ap);
     for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, w.ap + k * fpl, gp0 + k * g.plane, 1);
+  }
   // dL/dlambda: the K x nblk per-block sums, in index order
   const long long nl = (long long)K * (long long)nblk;
   Geo gd{(int)nl, 1, (int)nl, 0, 1};
