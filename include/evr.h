@@ -363,6 +363,12 @@ int evr_kernel_time(evr_stream* s, double* ms, int64_t* launches, int64_t* pixel
  * under a second.  Synchronises. */
 int evr_selftest_wait_timeout(evr_stream* s);
 
+/* Fault injection for tests (the paper has no counterpart): the n-th library
+ * allocation of device or page-locked host memory after this call fails as if memory
+ * were exhausted (the calls that make it then return EVR_ERR_OOM or EVR_ERR_CUDA and
+ * release what they had allocated); n <= 0 disables.  Returns EVR_OK. */
+int evr_test_fail_alloc_after(int n);
+
 /* Description of the solver in use, e.g. "tiled 32x32 R4"; static storage. */
 const char* evr_solver_name(evr_stream* s);
 

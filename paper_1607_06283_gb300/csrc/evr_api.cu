@@ -18,10 +18,50 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
+#include <atomic>
+
 #include "../../include/evr.h"
 #include "evr_internal.cuh"
 
 using namespace evr;
+
+// ---------------------------------------------------------------- allocation hook
+namespace {
+std::atomic<int> g_fail_countdown{0};  // > 0: the allocation that takes it to 0 fails
+
+bool alloc_fails() {
+  int c = g_fail_countdown.load();
+  while (c > 0)
+    if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+  return false;
+}
+
+// NVTX range for the duration of a C ABI call (visible to profilers and tracers; a no-op
+// when none is attached)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+}  // namespace
+
+namespace evr {
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  if (alloc_fails()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+cudaError_t host_alloc(void** p, size_t bytes) {
+  if (alloc_fails()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, bytes);
+}
+}  // namespace evr
 
 namespace {
 
@@ -180,7 +220,7 @@ int ensure_stage(evr_stream* s, StageSlot& sl, size_t n) {
     if (sl.h) cudaFreeHost(sl.h);
     // cap > n, so 13 cap bytes hold Packed(n).bytes <= 13 n + 7
     size_t cap = ((n < 4096 ? 4096 : n + n / 2) + 63) / 64 * 64;
-    if (cudaMallocHost((void**)&sl.h, cap * 13) != cudaSuccess) {
+    if (host_alloc((void**)&sl.h, cap * 13) != cudaSuccess) {
       sl.h = nullptr;
       sl.cap = 0;
       return EVR_ERR_OOM;
@@ -195,7 +235,7 @@ int ensure_stage(evr_stream* s, StageSlot& sl, size_t n) {
       cudaFree(s->dstage);
     }
     size_t cap = ((n < 4096 ? 4096 : n + n / 2) + 63) / 64 * 64;
-    if (cudaMalloc((void**)&s->dstage, cap * 13) != cudaSuccess) {
+    if (dev_alloc((void**)&s->dstage, cap * 13) != cudaSuccess) {
       s->dstage = nullptr;
       s->dcap = 0;
       return EVR_ERR_OOM;
@@ -265,7 +305,7 @@ int run_cfg_direct(evr_stream* s, int ci, int iters) {
 void autotune(evr_stream* s, int iters) {
   const size_t plane = (size_t)s->pitch * s->H * sizeof(float);
   float* save = nullptr;
-  if (cudaMalloc((void**)&save, 4 * plane) != cudaSuccess) {
+  if (dev_alloc((void**)&save, 4 * plane) != cudaSuccess) {
     s->cfg = 0;
     return;
   }
@@ -488,7 +528,7 @@ int evr_create(int W, int H, const evr_params* params, evr_stream** out) {
   s->pitch = (W + 31) / 32 * 32;
   const size_t total = evr::state_bytes(W, H, true);
   char* base = nullptr;
-  if (cudaMalloc((void**)&base, total) != cudaSuccess) {
+  if (dev_alloc((void**)&base, total) != cudaSuccess) {
     delete s;
     return EVR_ERR_OOM;
   }
@@ -500,8 +540,8 @@ int evr_create(int W, int H, const evr_params* params, evr_stream** out) {
   int rc = EVR_OK;
   if (cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMallocHost((void**)&s->h_gap, sizeof(double) * 2) != cudaSuccess ||
-      cudaMallocHost((void**)&s->h_sc, sizeof(DevScalars)) != cudaSuccess)
+      host_alloc((void**)&s->h_gap, sizeof(double) * 2) != cudaSuccess ||
+      host_alloc((void**)&s->h_sc, sizeof(DevScalars)) != cudaSuccess)
     rc = EVR_ERR_CUDA;
   s->stream = s->own_stream;
   const bool first = params->t_init_us == EVR_T_INIT_FIRST;
@@ -564,6 +604,7 @@ int evr_set_cuda_stream(evr_stream* s, void* cuda_stream) {
 
 int evr_push_events(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
                     const int8_t* pol, size_t n) {
+  Range range("evr_push_events");
   if (!s) return EVR_ERR_INVALID_ARG;
   if (n == 0) return EVR_OK;
   if (!x || !y || !t_us || !pol || n > (size_t)INT_MAX) return EVR_ERR_INVALID_ARG;
@@ -608,6 +649,7 @@ int evr_push_events(evr_stream* s, const uint16_t* x, const uint16_t* y, const i
 
 int evr_push_events_device(evr_stream* s, const uint16_t* x, const uint16_t* y,
                            const int64_t* t_us, const int8_t* pol, size_t n) {
+  Range range("evr_push_events_device");
   if (!s) return EVR_ERR_INVALID_ARG;
   if (n == 0) return EVR_OK;
   if (!x || !y || !t_us || !pol || n > (size_t)INT_MAX) return EVR_ERR_INVALID_ARG;
@@ -633,6 +675,7 @@ int enqueue_front(evr_stream* s, cudaStream_t q) {
 }
 
 int evr_solve(evr_stream* s, int iters) {
+  Range range("evr_solve");
   if (!s || iters < 0) return EVR_ERR_INVALID_ARG;
   cudaStream_t st = s->stream;
   // Once tuned, a multi-launch solve is one graph: front launches + iteration passes
@@ -746,6 +789,7 @@ int evr_solve(evr_stream* s, int iters) {
 }
 
 int evr_get_image(evr_stream* s, float* out_host, size_t len) {
+  Range range("evr_get_image");
   if (!s || !out_host || len < (size_t)s->W * s->H) return EVR_ERR_INVALID_ARG;
   cudaError_t e = cudaMemcpy2DAsync(out_host, (size_t)s->W * 4, s->P.u[s->cur],
                                     (size_t)s->pitch * 4, (size_t)s->W * 4, s->H,
@@ -755,9 +799,10 @@ int evr_get_image(evr_stream* s, float* out_host, size_t len) {
 }
 
 int evr_get_image_async(evr_stream* s, float* out_host, size_t len, uint64_t* ticket) {
+  Range range("evr_get_image_async");
   if (!s || !out_host || !ticket || len < (size_t)s->W * s->H) return EVR_ERR_INVALID_ARG;
   if (!s->h_img_status) {
-    if (cudaMallocHost((void**)&s->h_img_status, sizeof(int) * kImgRing) != cudaSuccess) {
+    if (host_alloc((void**)&s->h_img_status, sizeof(int) * kImgRing) != cudaSuccess) {
       s->h_img_status = nullptr;
       return EVR_ERR_OOM;
     }
@@ -782,6 +827,7 @@ int evr_get_image_async(evr_stream* s, float* out_host, size_t len, uint64_t* ti
 }
 
 int evr_wait_image(evr_stream* s, uint64_t ticket) {
+  Range range("evr_wait_image");
   if (!s || ticket == 0 || ticket > s->img_ticket) return EVR_ERR_INVALID_ARG;
   const int slot = (int)(ticket % kImgRing);
   // a slot recorded again since belongs to a later readback, which completes later
@@ -882,6 +928,7 @@ int evr_set_state(evr_stream* s, int which, const void* in_host, size_t bytes) {
 }
 
 int evr_gap(evr_stream* s, double* primal, double* dual) {
+  Range range("evr_gap");
   if (!s || !primal || !dual) return EVR_ERR_INVALID_ARG;
   if (launch_gap(s->P, s->cur, solve_consts(s), s->d_gap, s->stream)) return EVR_ERR_CUDA;
   if (cudaMemcpyAsync(s->h_gap, s->d_gap, 16, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
@@ -893,6 +940,7 @@ int evr_gap(evr_stream* s, double* primal, double* dual) {
 }
 
 int evr_synchronize(evr_stream* s) {
+  Range range("evr_synchronize");
   if (!s) return EVR_ERR_INVALID_ARG;
   return sync_status(s);
 }
@@ -928,7 +976,7 @@ int evr_selftest_wait_timeout(evr_stream* s) {
   if (rc != EVR_OK && rc != EVR_ERR_TIMEOUT) return rc;
   const size_t plane = (size_t)s->pitch * s->H * sizeof(float);
   float* save = nullptr;
-  if (cudaMalloc((void**)&save, 4 * plane) != cudaSuccess) return EVR_ERR_OOM;
+  if (dev_alloc((void**)&save, 4 * plane) != cudaSuccess) return EVR_ERR_OOM;
   const int cur0 = s->cur;
   float* live[4] = {s->P.u[cur0], s->P.p1[cur0], s->P.p2[cur0], s->P.p3[cur0]};
   for (int k = 0; k < 4; ++k)
@@ -949,6 +997,11 @@ int evr_selftest_wait_timeout(evr_stream* s) {
 }
 
 const char* evr_solver_name(evr_stream* s) { return s ? s->name : ""; }
+
+int evr_test_fail_alloc_after(int n) {
+  g_fail_countdown.store(n > 0 ? n : 0);
+  return EVR_OK;
+}
 
 const char* evr_strerror(int code) {
   switch (code) {

@@ -18,6 +18,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/evr.h"
 #include "evr_internal.cuh"
 
@@ -88,6 +90,12 @@ __global__ void __launch_bounds__(256) k_batch_gather(const Planes* __restrict__
 
 namespace {
 
+// NVTX range for the duration of a C ABI call (a no-op when no tool is attached)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+
 SolveConsts consts(const evr_batch* b) {
   return SolveConsts{b->prm.tau, b->prm.sigma, b->prm.lambda, b->prm.u_min, b->prm.u_max,
                      b->prm.data_term};
@@ -114,7 +122,7 @@ int build_tile_work(evr_batch* b, int ci) {
   }
   if (b->d_work_tile) cudaFree(b->d_work_tile);
   b->d_work_tile = nullptr;
-  if (cudaMalloc((void**)&b->d_work_tile, sizeof(int2) * w.size()) != cudaSuccess)
+  if (dev_alloc((void**)&b->d_work_tile, sizeof(int2) * w.size()) != cudaSuccess)
     return EVR_ERR_OOM;
   if (cudaMemcpy(b->d_work_tile, w.data(), sizeof(int2) * w.size(), cudaMemcpyHostToDevice) !=
       cudaSuccess)
@@ -273,7 +281,7 @@ int evr_batch_create(int n, const int* W, const int* H, const evr_params* params
   }
   const size_t tail = total;
   total += sizeof(Planes) * n + 256 + 2 * sizeof(int) * n + 256;
-  if (cudaMalloc((void**)&b->dev, total) != cudaSuccess) {
+  if (dev_alloc((void**)&b->dev, total) != cudaSuccess) {
     delete b;
     return EVR_ERR_OOM;
   }
@@ -292,14 +300,14 @@ int evr_batch_create(int n, const int* W, const int* H, const evr_params* params
   cudaError_t e = cudaMemcpy(b->d_descs, b->planes.data(), sizeof(Planes) * n,
                              cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->d_curs, 0, 2 * sizeof(int) * n);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_work_pro, sizeof(int2) * pro.size());
+  if (e == cudaSuccess) e = dev_alloc((void**)&b->d_work_pro, sizeof(int2) * pro.size());
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_work_pro, pro.data(), sizeof(int2) * pro.size(), cudaMemcpyHostToDevice);
   b->n_work_pro = (int)pro.size();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_sc, sizeof(DevScalars) * n);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_curs, sizeof(int) * n);
+  if (e == cudaSuccess) e = host_alloc((void**)&b->h_sc, sizeof(DevScalars) * n);
+  if (e == cudaSuccess) e = host_alloc((void**)&b->h_curs, sizeof(int) * n);
   b->stream = b->own_stream;
   const bool first = params->t_init_us == EVR_T_INIT_FIRST;
   const long long t0 = first ? 0 : (long long)params->t_init_us;
@@ -365,6 +373,7 @@ int evr_batch_set_cuda_stream(evr_batch* b, void* cuda_stream) {
 int evr_batch_step_device(evr_batch* b, const uint16_t* x, const uint16_t* y,
                           const int64_t* t_us, const int8_t* pol, const int64_t* offsets,
                           int iters) {
+  Range range("evr_batch_step_device");
   if (!b || !offsets || iters < 0) return EVR_ERR_INVALID_ARG;
   if (!x || !y || !t_us || !pol) return EVR_ERR_INVALID_ARG;
   cudaStream_t st = b->stream;
@@ -408,6 +417,7 @@ int evr_batch_step_device(evr_batch* b, const uint16_t* x, const uint16_t* y,
 
 int evr_batch_step(evr_batch* b, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
                    const int8_t* pol, const int64_t* offsets, int iters) {
+  Range range("evr_batch_step");
   if (!b || !offsets || iters < 0) return EVR_ERR_INVALID_ARG;
   const long long n_ev = offsets[b->n];
   for (int s = 0; s < b->n; ++s)
@@ -427,7 +437,7 @@ int evr_batch_step(evr_batch* b, const uint16_t* x, const uint16_t* y, const int
     }
     b->d_stage = nullptr;
     b->stage_cap = 0;
-    if (cudaMalloc((void**)&b->d_stage, bytes * 2) != cudaSuccess) return EVR_ERR_OOM;
+    if (dev_alloc((void**)&b->d_stage, bytes * 2) != cudaSuccess) return EVR_ERR_OOM;
     b->stage_cap = bytes * 2;
   }
   const int k = b->next_stage;
@@ -438,7 +448,7 @@ int evr_batch_step(evr_batch* b, const uint16_t* x, const uint16_t* y, const int
     if (b->h_stage[k]) cudaFreeHost(b->h_stage[k]);
     b->h_stage[k] = nullptr;
     b->h_stage_cap[k] = 0;
-    if (cudaMallocHost((void**)&b->h_stage[k], bytes * 2) != cudaSuccess) return EVR_ERR_OOM;
+    if (host_alloc((void**)&b->h_stage[k], bytes * 2) != cudaSuccess) return EVR_ERR_OOM;
     b->h_stage_cap[k] = bytes * 2;
   }
   if (!b->h_stage_done[k] &&
@@ -484,9 +494,9 @@ static int queue_images(evr_batch* b, float* out_host, size_t len) {
       off[s] = acc;
       acc += (long long)b->planes[s].W * b->planes[s].H;
     }
-    if (cudaMalloc((void**)&b->d_img_off, sizeof(long long) * b->n) != cudaSuccess)
+    if (dev_alloc((void**)&b->d_img_off, sizeof(long long) * b->n) != cudaSuccess)
       return EVR_ERR_OOM;
-    if (cudaMalloc((void**)&b->d_img, sizeof(float) * (size_t)b->px_total) != cudaSuccess) {
+    if (dev_alloc((void**)&b->d_img, sizeof(float) * (size_t)b->px_total) != cudaSuccess) {
       cudaFree(b->d_img_off);
       b->d_img_off = nullptr;
       b->d_img = nullptr;
@@ -505,6 +515,7 @@ static int queue_images(evr_batch* b, float* out_host, size_t len) {
 }
 
 int evr_batch_get_images(evr_batch* b, float* out_host, size_t len) {
+  Range range("evr_batch_get_images");
   if (!b || !out_host) return EVR_ERR_INVALID_ARG;
   int rc = queue_images(b, out_host, len);
   if (rc) return rc;
@@ -512,6 +523,7 @@ int evr_batch_get_images(evr_batch* b, float* out_host, size_t len) {
 }
 
 int evr_batch_get_images_async(evr_batch* b, float* out_host, size_t len, uint64_t* ticket) {
+  Range range("evr_batch_get_images_async");
   if (!b || !out_host || !ticket) return EVR_ERR_INVALID_ARG;
   if (!b->img_ev[0])
     for (auto& e : b->img_ev)

@@ -98,6 +98,11 @@ int check_device();
 // kernel launchers (evr_kernels.cu); all return cudaError_t as int
 int launch_init(const Planes& P, float u_init, long long clock0, long long t_init, int t_init_set,
                 void* stream);
+// Library allocations (device and page-locked host memory) go through these, so that a
+// test can make the n-th next one fail (evr_test_fail_alloc_after).
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t host_alloc(void** p, size_t bytes);
+
 int launch_push(const Planes& P, const uint16_t* x, const uint16_t* y, const long long* t,
                 const int8_t* pol, int n, void* stream);
 int launch_prologue(const Planes& P, int cur, const PrologueConsts& c, void* stream);

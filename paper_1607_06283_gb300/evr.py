@@ -91,6 +91,7 @@ def _load():
         "evr_solver_name": ([vp], ctypes.c_char_p),
         "evr_selftest_wait_timeout": ([vp], i),
         "evr_strerror": ([i], ctypes.c_char_p),
+        "evr_test_fail_alloc_after": ([i], i),
         "evr_gap_static": ([vp] * 7 + [i, i, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        vp, vp], i),
         "evr_unrolled_workspace_bytes": ([i, i, i, i, i, i], sz),

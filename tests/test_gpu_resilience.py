@@ -90,3 +90,72 @@ def test_wait_timeout_is_detected_and_the_stream_recovers(E):
             g.solve(15)
     assert a.synchronize() == 0
     np.testing.assert_array_equal(a.image(), twin.image())  # solver works after the test
+
+
+def _free_bytes():
+    import torch
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+def test_allocation_failures_are_reported_and_release_everything(E):
+    """Fault injection on the host side: every allocation of evr_create / evr_batch_create
+    in turn is made to fail; each attempt reports OOM (or CUDA) and leaves no device
+    memory behind, and the library works afterwards."""
+    E.Stream(64, 48).close()  # context and module loaded
+    free0 = _free_bytes()
+    failed = 0
+    for n in range(1, 12):
+        E._lib.evr_test_fail_alloc_after(n)
+        try:
+            g = E.Stream(64, 48)
+        except E.EvrError as e:
+            assert e.code in (E.EVR_ERR_OOM, E.EVR_ERR_CUDA), e.code
+            failed += 1
+            continue
+        g.close()  # n was past the last allocation of evr_create
+        break
+    for n in range(1, 12):
+        E._lib.evr_test_fail_alloc_after(n)
+        try:
+            b = E.Batch([(40, 30), (17, 9)])
+        except E.EvrError as e:
+            assert e.code in (E.EVR_ERR_OOM, E.EVR_ERR_CUDA), e.code
+            failed += 1
+            continue
+        b.close()
+        break
+    E._lib.evr_test_fail_alloc_after(0)
+    assert failed >= 4  # every allocation site of both creates was exercised
+    assert abs(_free_bytes() - free0) < (8 << 20)
+    pk = packets(4, 64, 48, 2, 300)
+    g = E.Stream(64, 48)
+    for x, y, t, p in pk:
+        assert g.push(x, y, t, p) == 0
+        g.solve(10)
+    assert g.synchronize() == 0
+
+
+def test_push_staging_allocation_failure_leaves_the_stream_unchanged(E):
+    W, H = 80, 40
+    small = packets(5, W, H, 1, 200)[0]
+    big = packets(6, W, H, 1, 6000)[0]  # grows the pinned slot and the device buffer
+    big = (big[0], big[1], big[2] + small[2][-1], big[3])
+    a, twin = E.Stream(W, H), E.Stream(W, H)
+    for g in (a, twin):
+        assert g.push(*small) == 0
+        g.solve(10)
+    E._lib.evr_test_fail_alloc_after(1)
+    with pytest.raises(E.EvrError) as ei:
+        E._check(E._lib.evr_push_events(a.h, big[0].ctypes.data, big[1].ctypes.data,
+                                        big[2].ctypes.data, big[3].ctypes.data, len(big[0])),
+                 "evr_push_events")
+    E._lib.evr_test_fail_alloc_after(0)
+    assert ei.value.code == E.EVR_ERR_OOM
+    for g in (a, twin):
+        g.solve(10)
+    np.testing.assert_array_equal(a.image(), twin.image())
+    for g in (a, twin):  # and the stream takes the packet afterwards
+        assert g.push(*big) == 0
+        g.solve(10)
+    np.testing.assert_array_equal(a.image(), twin.image())
