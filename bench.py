@@ -45,6 +45,9 @@ def b_alg(storage):
 # writes q1, q2 (dual)
 B_PROLOGUE = 48
 B_TVL1_ITER = 44
+# the push, per event: reads x, y, t, pol (13 B) and updates t_last (8 B read + write) and
+# one count (4 B read + write) of its pixel
+B_PUSH_EVENT = 37
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -172,9 +175,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(config, solver_name, launches_per_solve):
-    """DRAM bytes per launch of the packet's solve graph from the committed ncu summary
-    (profiles/k_tiled_<config>.md: the DRAM bytes of one solve's launches, captured in
+def profiled_traffic(config, solver_name, launches_per_step):
+    """DRAM bytes per launch of the packet's step graph from the committed ncu summary
+    (profiles/k_tiled_<config>.md: the DRAM bytes of one step's launches, captured in
     the benchmark's own sequence), if it was taken on the current kernel source with
     the same solver configuration; else None."""
     p = os.path.join(ROOT, "profiles", f"k_tiled_{config}.md")
@@ -183,10 +186,10 @@ def profiled_traffic(config, solver_name, launches_per_solve):
     import re
     with open(p) as fh:
         text = fh.read()
-    for m in re.finditer(r"solve_traffic_bytes: (\d+) launches_per_solve: (\d+) "
+    for m in re.finditer(r"step_traffic_bytes: (\d+) launches_per_step: (\d+) "
                          r"kernel_source_sha: (\w+) solver: (.+)", text):
         if (m.group(3) == kernel_source_hash() and m.group(4).strip() == solver_name and
-                int(m.group(2)) == round(launches_per_solve)):
+                int(m.group(2)) == round(launches_per_step)):
             return int(m.group(1)) / int(m.group(2))
     return None
 
@@ -336,12 +339,11 @@ def run_ours(args):
     offs = np.concatenate([[0], np.cumsum([b - a for a, b, _ in steps])])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def step(k):
+    def step(k):  # push (device arrays) and solve: one graph per packet once settled
         s, e = int(offs[k]), int(offs[k + 1])
-        rc = g.push_device(dx[s:e], dy[s:e], dt_[s:e], dp[s:e])
+        rc = E.evr_step_device(g.h, dx[s:e], dy[s:e], dt_[s:e], dp[s:e], cfg.iters)
         if rc:
-            raise RuntimeError(f"push failed: {rc}")
-        g.solve(cfg.iters)
+            raise RuntimeError(f"step failed: {rc}")
 
     for k in range(args.warmup):
         step(k)
@@ -425,14 +427,15 @@ def run_ours(args):
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
-        # the timed region of each solve: the front launches (prologue, TV-L1) and the
-        # iteration kernels, one graph per packet
+        # the timed region of each step: one graph per packet with the push, the front
+        # launches (prologue, TV-L1) and the iteration kernels
         avg_launch_ms = k_ms / max(1, k_launches)
         alg_bytes = (b_alg(args.storage) * k_pixiters +
-                     (B_PROLOGUE + B_TVL1_ITER * args.tvl1) * cfg.W * cfg.H * args.steps)
+                     (B_PROLOGUE + B_TVL1_ITER * args.tvl1) * cfg.W * cfg.H * args.steps +
+                     B_PUSH_EVENT * ev_timed)
         bytes_per_launch = alg_bytes / max(1, k_launches)
         achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
-        launches_per_step = 1 + k_launches / args.steps  # push + the solve's launches
+        launches_per_step = k_launches / args.steps
         line = {
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -446,16 +449,17 @@ def run_ours(args):
                        "solver": g.solver_name, "parallelism": f"{world} independent streams",
                        "tvl1_iters": args.tvl1,
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
-                       "inputs": "device-resident event arrays (evr_push_events_device)"},
+                       "inputs": "device-resident event arrays (evr_step_device: push "
+                                 "and solve)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": profiled_traffic(cfg.name, g.solver_name,
                                                      k_launches / args.steps),
-                         "kernel": "packet solve graph: prologue + iteration kernels (" +
-                                   g.solver_name + ")",
+                         "kernel": "packet step graph: push + prologue + iteration "
+                                   "kernels (" + g.solver_name + ")",
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "avg_launch_us": avg_launch_ms * 1e3,
-                         "launches_per_solve": k_launches / args.steps,
+                         "launches_per_step": k_launches / args.steps,
                          "bytes_per_launch": bytes_per_launch},
             "e2e": {"value": e2e_val, "unit": "events/s",
                     "h2d_bytes_per_step": cfg.packet * (2 + 2 + 8 + 1),

@@ -146,6 +146,15 @@ int evr_push_events_device(evr_stream* s, const uint16_t* x, const uint16_t* y,
  * Errors: EVR_ERR_INVALID_ARG (iters < 0), EVR_ERR_CUDA. */
 int evr_solve(evr_stream* s, int iters);
 
+/* Push and solve in one call: the same as evr_push_events_device(s, x, y, t_us, pol, n)
+ * followed by evr_solve(s, iters), with the same results.  Once the solver is settled
+ * (after the autotuner and its refinement, multi-launch solvers, packets of at most 32768
+ * events) the push, the packet's front launches and its iteration kernels run as one
+ * CUDA graph, the prologue starting as a programmatic dependent of the push; otherwise
+ * the two calls are made.  Asynchronous; errors as the two calls. */
+int evr_step_device(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
+                    const int8_t* pol, size_t n, int iters);
+
 /* Copy the current image u (W*H floats, row-major) to host memory; synchronises.
  * len is the capacity of out_host in floats and must be >= W*H.  Returns the first
  * pending device-side rejection, if any, else EVR_OK. */

@@ -137,6 +137,13 @@ struct evr_stream {
   DevScalars* h_sc = nullptr;  // pinned
   // graphs of the per-packet iteration launches
   std::map<GraphKey, cudaGraphExec_t> graphs;
+  // push-and-solve graphs (evr_step_device): the executable, its graph and push node
+  struct Fused {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphNode_t push = nullptr;
+  };
+  std::map<GraphKey, Fused> fused;
   // kernel timing
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free, ev_used;
@@ -248,6 +255,11 @@ int ensure_stage(evr_stream* s, StageSlot& sl, size_t n) {
 void drop_graphs(evr_stream* s) {
   for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
   s->graphs.clear();
+  for (auto& kv : s->fused) {
+    cudaGraphExecDestroy(kv.second.exec);
+    cudaGraphDestroy(kv.second.graph);
+  }
+  s->fused.clear();
 }
 
 // Clear the persistent solver's progress flags (required whenever the set of CTAs
@@ -785,6 +797,84 @@ int evr_solve(evr_stream* s, int iters) {
       set_name(s);
     }
   }
+  return EVR_OK;
+}
+
+int evr_step_device(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
+                    const int8_t* pol, size_t n, int iters) {
+  Range range("evr_step_device");
+  if (!s || iters < 0) return EVR_ERR_INVALID_ARG;
+  if (n > 0 && (!x || !y || !t_us || !pol)) return EVR_ERR_INVALID_ARG;
+  if (n > (size_t)INT_MAX) return EVR_ERR_INVALID_ARG;
+  const bool refining = s->n_cand > 1 && s->refine_done < s->n_cand * kRefineReps;
+  // one graph (push, front launches, passes) once the multi-launch solver is settled
+  // and the packet fits the one-CTA push; otherwise the two calls
+  if (n == 0 || n > 32768 || iters == 0 || !s->tuned || refining ||
+      (s->cfg >= 0 && kSolverCfgs[s->cfg].kind == 2)) {
+    int rc = n ? evr_push_events_device(s, x, y, t_us, pol, n) : EVR_OK;
+    return rc ? rc : evr_solve(s, iters);
+  }
+  cudaStream_t st = s->stream;
+  const int in = (int)n;
+  GraphKey key{iters, s->cur, 2, s->cfg};
+  auto it = s->fused.find(key);
+  evr_stream::Fused* fg = nullptr;
+  if (it == s->fused.end()) {
+    evr_stream::Fused nf;
+    int captured = 0;
+    if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return EVR_ERR_CUDA;
+    int r = launch_push(s->P, x, y, (const long long*)t_us, pol, in, s->cap_stream) ? -1 : 0;
+    if (r == 0) r = enqueue_front(s, s->cap_stream);
+    // enqueue_iterations returns the buffer holding the result, or -1
+    if (r == 0 && enqueue_iterations(s, iters, s->cur, s->cap_stream, &captured) < 0) r = -1;
+    cudaError_t e = cudaStreamEndCapture(s->cap_stream, &nf.graph);
+    size_t roots = 1;
+    if (r == 0 && e == cudaSuccess) e = cudaGraphGetRootNodes(nf.graph, &nf.push, &roots);
+    if (r == 0 && e == cudaSuccess && roots == 1)
+      e = cudaGraphInstantiate(&nf.exec, nf.graph, 0);
+    if (r < 0 || e != cudaSuccess || roots != 1 || !nf.exec) {
+      if (nf.exec) cudaGraphExecDestroy(nf.exec);
+      if (nf.graph) cudaGraphDestroy(nf.graph);
+      return EVR_ERR_CUDA;
+    }
+    fg = &(s->fused[key] = nf);
+  } else {
+    fg = &it->second;
+    // this call's packet: the push node's arguments (Planes, x, y, t, pol, n)
+    cudaKernelNodeParams kp;
+    if (cudaGraphKernelNodeGetParams(fg->push, &kp) != cudaSuccess) return EVR_ERR_CUDA;
+    const long long* tt = (const long long*)t_us;
+    void* args[6] = {(void*)&s->P, (void*)&x, (void*)&y, (void*)&tt, (void*)&pol, (void*)&in};
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    if (cudaGraphExecKernelNodeSetParams(fg->exec, fg->push, &kp) != cudaSuccess)
+      return EVR_ERR_CUDA;
+  }
+  const int passes = (s->cfg < 0) ? 0 : (iters + kSolverCfgs[s->cfg].R - 1) / kSolverCfgs[s->cfg].R;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (s->timing) {
+    if ((int)s->ev_used.size() >= kMaxTimingPairs) resolve_timing(s);
+    if (s->ev_free.empty()) {
+      cudaEventCreate(&ev.first);
+      cudaEventCreate(&ev.second);
+    } else {
+      ev = s->ev_free.back();
+      s->ev_free.pop_back();
+    }
+    cudaEventRecord(ev.first, st);
+  }
+  if (cudaGraphLaunch(fg->exec, st) != cudaSuccess) return EVR_ERR_CUDA;
+  if (s->timing) {
+    cudaEventRecord(ev.second, st);
+    s->ev_used.push_back(ev);
+    const int front =
+        1 + ((s->prm.tvl1_iters > 0 && s->prm.manifold) ? 1 + 2 * s->prm.tvl1_iters : 0);
+    s->ev_launches.push_back(1 + front + (s->cfg < 0 ? 2 * iters : passes));
+    s->ev_pixiters.push_back((long long)s->W * s->H * iters);
+  }
+  if (s->cfg < 0 ? false : (passes % 2)) s->cur = 1 - s->cur;
+  s->h_clock_valid = false;
   return EVR_OK;
 }
 

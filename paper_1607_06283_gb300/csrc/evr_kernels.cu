@@ -206,6 +206,9 @@ __global__ void __launch_bounds__(1024) k_push_one_cta(Planes P, const uint16_t*
                                                        const uint16_t* __restrict__ y,
                                                        const long long* __restrict__ t,
                                                        const int8_t* __restrict__ pol, int n) {
+  // a programmatically dependent prologue may launch now: it waits for this grid's
+  // completion (griddepcontrol.wait) before reading anything this kernel writes
+  asm volatile("griddepcontrol.launch_dependents;" :::);
   push_cta(P, x, y, t, pol, n);
 }
 
@@ -360,8 +363,12 @@ __device__ __forceinline__ void prologue_px_body(const Planes& P, int cur, const
 // blocks numbered over its image) and a batch (one work item per CTA).
 __global__ void __launch_bounds__(256) k_prologue(Planes P, int cur, PrologueConsts c,
                                                   BatchRef B) {
-  // The first iteration pass may launch now; it reads nothing of ours before its
-  // griddepcontrol.wait, which returns once this grid has completed.
+  // Launched as a programmatic dependent of the push (in the fused push-and-solve
+  // graph): wait for its completion before reading the pixel state (a no-op when
+  // launched without that relation).  The first iteration pass may launch now; it
+  // reads nothing of ours before its own griddepcontrol.wait, which returns once this
+  // grid has completed.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" :::);
   __shared__ Planes sP;  // this CTA's stream, staged once
   int blk = blockIdx.x;
@@ -444,10 +451,19 @@ int launch_tvl1(const Planes& P, const PrologueConsts& c, int K, float lam, floa
 
 int launch_prologue(const Planes& P, int cur, const PrologueConsts& c, void* stream) {
   const int nb = ((P.W + 31) / 32) * ((P.H + 7) / 8);
-  k_prologue<<<nb, dim3(32, 8), 0, (cudaStream_t)stream>>>(P, cur, c,
-                                                            BatchRef{nullptr, nullptr, nullptr,
-                                                                     nullptr});
-  return (int)cudaGetLastError();
+  // programmatic stream serialisation: the prologue may start while its predecessor
+  // (the push) drains; it waits for it before reading (griddepcontrol.wait)
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(nb);
+  lc.blockDim = dim3(32, 8);
+  lc.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&lc, k_prologue, P, cur, c,
+                                 BatchRef{nullptr, nullptr, nullptr, nullptr});
 }
 
 int launch_prologue_batch(const BatchRef& B, int n_work, const PrologueConsts& c, void* stream) {

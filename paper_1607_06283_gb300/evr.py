@@ -78,6 +78,7 @@ def _load():
         "evr_push_events": ([vp, vp, vp, vp, vp, sz], i),
         "evr_push_events_device": ([vp, vp, vp, vp, vp, sz], i),
         "evr_solve": ([vp, i], i),
+        "evr_step_device": ([vp, vp, vp, vp, vp, sz, i], i),
         "evr_get_image": ([vp, vp, sz], i),
         "evr_get_image_device": ([vp, vp, sz], i),
         "evr_get_image_async": ([vp, vp, sz, ctypes.POINTER(ctypes.c_uint64)], i),
@@ -197,6 +198,15 @@ def evr_push_events_device(h, x, y, t_us, pol) -> int:
             raise ValueError("device events must be contiguous CUDA tensors of equal length")
     return _lib.evr_push_events_device(h, x.data_ptr(), y.data_ptr(), t_us.data_ptr(),
                                        pol.data_ptr(), n)
+
+
+def evr_step_device(h, x, y, t_us, pol, iters: int) -> int:
+    """Push (device tensors) and solve in one call; returns 0 or the immediate error."""
+    rc = _lib.evr_step_device(h, x.data_ptr(), y.data_ptr(), t_us.data_ptr(), pol.data_ptr(),
+                              int(x.numel()), int(iters))
+    if rc in (EVR_ERR_INVALID_ARG, EVR_ERR_CUDA, EVR_ERR_OOM):
+        _check(rc, "evr_step_device")
+    return rc
 
 
 def evr_solve(h, iters: int) -> None:
