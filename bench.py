@@ -397,10 +397,9 @@ def run_ours(args):
 
     def step_host(k, slot):
         s, e = int(offs[k]), int(offs[k + 1])
-        rc = E.evr_push_events(g2.h, hx[s:e], hy[s:e], t_all[s:e], hp[s:e])
+        rc = E.evr_step(g2.h, hx[s:e], hy[s:e], t_all[s:e], hp[s:e], cfg.iters)
         if rc:
-            raise RuntimeError(f"push failed: {rc}")
-        E.evr_solve(g2.h, cfg.iters)
+            raise RuntimeError(f"step failed: {rc}")
         return E.evr_get_image_async(g2.h, imgs[slot])
 
     def wait(ticket):
@@ -464,7 +463,7 @@ def run_ours(args):
             "e2e": {"value": e2e_val, "unit": "events/s",
                     "h2d_bytes_per_step": cfg.packet * (2 + 2 + 8 + 1),
                     "d2h_bytes_per_step": cfg.W * cfg.H * 4 + 4,  # image + status word
-                    "calls": "evr_push_events (host arrays) + evr_solve + "
+                    "calls": "evr_step (host arrays: push and solve) + "
                              "evr_get_image_async into pinned memory, two steps in flight"},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clocks,

@@ -155,6 +155,12 @@ int evr_solve(evr_stream* s, int iters);
 int evr_step_device(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
                     const int8_t* pol, size_t n, int iters);
 
+/* The same with host arrays: evr_push_events followed by evr_solve, with the same checks
+ * and results; when fused, the staging copy, the push, the front launches and the
+ * iteration kernels form one graph.  The arrays may be reused when the call returns. */
+int evr_step(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
+             const int8_t* pol, size_t n, int iters);
+
 /* Copy the current image u (W*H floats, row-major) to host memory; synchronises.
  * len is the capacity of out_host in floats and must be >= W*H.  Returns the first
  * pending device-side rejection, if any, else EVR_OK. */

@@ -142,6 +142,7 @@ struct evr_stream {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphNode_t push = nullptr;
+    cudaGraphNode_t copy = nullptr;  // host-array steps: the staging copy before the push
   };
   std::map<GraphKey, Fused> fused;
   // kernel timing
@@ -614,13 +615,14 @@ int evr_set_cuda_stream(evr_stream* s, void* cuda_stream) {
   return EVR_OK;
 }
 
-int evr_push_events(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
-                    const int8_t* pol, size_t n) {
-  Range range("evr_push_events");
-  if (!s) return EVR_ERR_INVALID_ARG;
-  if (n == 0) return EVR_OK;
-  if (!x || !y || !t_us || !pol || n > (size_t)INT_MAX) return EVR_ERR_INVALID_ARG;
-  // immediate checks on the host, in the order the device applies them
+}  // extern "C"
+
+namespace {
+// Immediate host checks of a host-array packet (in the order the device applies them)
+// and its packed copy into the next pinned slot.  On success *slot is the slot and
+// *clock the packet's last timestamp.
+int stage_host(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
+               const int8_t* pol, size_t n, StageSlot** slot, long long* clock_out) {
   long long clock = s->h_clock;
   bool have = s->h_have_clock && s->h_clock_valid;
   for (size_t i = 0; i < n; ++i) {
@@ -643,19 +645,42 @@ int evr_push_events(evr_stream* s, const uint16_t* x, const uint16_t* y, const i
   std::memcpy(sl.h + L.off_y, y, n * 2);
   std::memcpy(sl.h + L.off_t, t_us, n * 8);
   std::memcpy(sl.h + L.off_p, pol, n);
-  cudaStream_t st = s->stream;
-  cudaError_t e = cudaMemcpyAsync(s->dstage, sl.h, L.bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaEventRecord(sl.done, st);
-  if (e != cudaSuccess) return EVR_ERR_CUDA;
-  sl.pending = true;
-  char* d = s->dstage;
-  if (launch_push(s->P, (const uint16_t*)d, (const uint16_t*)(d + L.off_y),
-                  (const long long*)(d + L.off_t), (const int8_t*)(d + L.off_p), (int)n, st))
-    return EVR_ERR_CUDA;
+  *slot = &sl;
+  *clock_out = clock;
+  return EVR_OK;
+}
+
+void note_clock(evr_stream* s, long long clock) {
   if (s->h_clock_valid) {
     s->h_clock = clock;
     s->h_have_clock = true;
   }
+}
+}  // namespace
+
+extern "C" {
+
+int evr_push_events(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
+                    const int8_t* pol, size_t n) {
+  Range range("evr_push_events");
+  if (!s) return EVR_ERR_INVALID_ARG;
+  if (n == 0) return EVR_OK;
+  if (!x || !y || !t_us || !pol || n > (size_t)INT_MAX) return EVR_ERR_INVALID_ARG;
+  StageSlot* sl = nullptr;
+  long long clock = 0;
+  int rc = stage_host(s, x, y, t_us, pol, n, &sl, &clock);
+  if (rc) return rc;
+  const Packed L(n);
+  cudaStream_t st = s->stream;
+  cudaError_t e = cudaMemcpyAsync(s->dstage, sl->h, L.bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(sl->done, st);
+  if (e != cudaSuccess) return EVR_ERR_CUDA;
+  sl->pending = true;
+  char* d = s->dstage;
+  if (launch_push(s->P, (const uint16_t*)d, (const uint16_t*)(d + L.off_y),
+                  (const long long*)(d + L.off_t), (const int8_t*)(d + L.off_p), (int)n, st))
+    return EVR_ERR_CUDA;
+  note_clock(s, clock);
   return EVR_OK;
 }
 
@@ -800,23 +825,25 @@ int evr_solve(evr_stream* s, int iters) {
   return EVR_OK;
 }
 
-int evr_step_device(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
-                    const int8_t* pol, size_t n, int iters) {
-  Range range("evr_step_device");
-  if (!s || iters < 0) return EVR_ERR_INVALID_ARG;
-  if (n > 0 && (!x || !y || !t_us || !pol)) return EVR_ERR_INVALID_ARG;
-  if (n > (size_t)INT_MAX) return EVR_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+// Whether a step runs as one fused graph: the solver is settled (tuned, refinement over),
+// multi-launch, and the packet fits the one-CTA push.
+bool fused_ok(const evr_stream* s, size_t n, int iters) {
   const bool refining = s->n_cand > 1 && s->refine_done < s->n_cand * kRefineReps;
-  // one graph (push, front launches, passes) once the multi-launch solver is settled
-  // and the packet fits the one-CTA push; otherwise the two calls
-  if (n == 0 || n > 32768 || iters == 0 || !s->tuned || refining ||
-      (s->cfg >= 0 && kSolverCfgs[s->cfg].kind == 2)) {
-    int rc = n ? evr_push_events_device(s, x, y, t_us, pol, n) : EVR_OK;
-    return rc ? rc : evr_solve(s, iters);
-  }
+  return n > 0 && n <= 32768 && iters > 0 && s->tuned && !refining &&
+         !(s->cfg >= 0 && kSolverCfgs[s->cfg].kind == 2);
+}
+
+// One packet as one graph: [staging copy (host arrays: copy_src, copy_bytes)], push of the
+// events at x, y, t, pol (device), the front launches and the iteration kernels.  The
+// graph is cached per (iters, buffer, kind, configuration); later calls update the copy
+// and push nodes.
+int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t copy_bytes,
+               const uint16_t* x, const uint16_t* y, const long long* t, const int8_t* pol) {
   cudaStream_t st = s->stream;
-  const int in = (int)n;
-  GraphKey key{iters, s->cur, 2, s->cfg};
+  GraphKey key{iters, s->cur, copy_src ? 3 : 2, s->cfg};
   auto it = s->fused.find(key);
   evr_stream::Fused* fg = nullptr;
   if (it == s->fused.end()) {
@@ -824,16 +851,29 @@ int evr_step_device(evr_stream* s, const uint16_t* x, const uint16_t* y, const i
     int captured = 0;
     if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return EVR_ERR_CUDA;
-    int r = launch_push(s->P, x, y, (const long long*)t_us, pol, in, s->cap_stream) ? -1 : 0;
+    int r = 0;
+    if (copy_src && cudaMemcpyAsync(s->dstage, copy_src, copy_bytes, cudaMemcpyHostToDevice,
+                                    s->cap_stream) != cudaSuccess)
+      r = -1;
+    if (r == 0 && launch_push(s->P, x, y, t, pol, n, s->cap_stream)) r = -1;
     if (r == 0) r = enqueue_front(s, s->cap_stream);
     // enqueue_iterations returns the buffer holding the result, or -1
     if (r == 0 && enqueue_iterations(s, iters, s->cur, s->cap_stream, &captured) < 0) r = -1;
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &nf.graph);
-    size_t roots = 1;
-    if (r == 0 && e == cudaSuccess) e = cudaGraphGetRootNodes(nf.graph, &nf.push, &roots);
-    if (r == 0 && e == cudaSuccess && roots == 1)
+    size_t roots = 1, deps = 1;
+    cudaGraphNode_t root = nullptr;
+    if (r == 0 && e == cudaSuccess) e = cudaGraphGetRootNodes(nf.graph, &root, &roots);
+    if (r == 0 && e == cudaSuccess && roots == 1) {
+      if (copy_src) {
+        nf.copy = root;
+        e = cudaGraphNodeGetDependentNodes(root, &nf.push, nullptr, &deps);
+      } else {
+        nf.push = root;
+      }
+    }
+    if (r == 0 && e == cudaSuccess && roots == 1 && deps == 1)
       e = cudaGraphInstantiate(&nf.exec, nf.graph, 0);
-    if (r < 0 || e != cudaSuccess || roots != 1 || !nf.exec) {
+    if (r < 0 || e != cudaSuccess || roots != 1 || deps != 1 || !nf.exec) {
       if (nf.exec) cudaGraphExecDestroy(nf.exec);
       if (nf.graph) cudaGraphDestroy(nf.graph);
       return EVR_ERR_CUDA;
@@ -841,17 +881,21 @@ int evr_step_device(evr_stream* s, const uint16_t* x, const uint16_t* y, const i
     fg = &(s->fused[key] = nf);
   } else {
     fg = &it->second;
+    if (copy_src && cudaGraphExecMemcpyNodeSetParams1D(fg->exec, fg->copy, s->dstage, copy_src,
+                                                       copy_bytes, cudaMemcpyHostToDevice) !=
+                        cudaSuccess)
+      return EVR_ERR_CUDA;
     // this call's packet: the push node's arguments (Planes, x, y, t, pol, n)
     cudaKernelNodeParams kp;
     if (cudaGraphKernelNodeGetParams(fg->push, &kp) != cudaSuccess) return EVR_ERR_CUDA;
-    const long long* tt = (const long long*)t_us;
-    void* args[6] = {(void*)&s->P, (void*)&x, (void*)&y, (void*)&tt, (void*)&pol, (void*)&in};
+    void* args[6] = {(void*)&s->P, (void*)&x, (void*)&y, (void*)&t, (void*)&pol, (void*)&n};
     kp.kernelParams = args;
     kp.extra = nullptr;
     if (cudaGraphExecKernelNodeSetParams(fg->exec, fg->push, &kp) != cudaSuccess)
       return EVR_ERR_CUDA;
   }
-  const int passes = (s->cfg < 0) ? 0 : (iters + kSolverCfgs[s->cfg].R - 1) / kSolverCfgs[s->cfg].R;
+  const int passes =
+      (s->cfg < 0) ? 0 : (iters + kSolverCfgs[s->cfg].R - 1) / kSolverCfgs[s->cfg].R;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (s->timing) {
     if ((int)s->ev_used.size() >= kMaxTimingPairs) resolve_timing(s);
@@ -873,8 +917,52 @@ int evr_step_device(evr_stream* s, const uint16_t* x, const uint16_t* y, const i
     s->ev_launches.push_back(1 + front + (s->cfg < 0 ? 2 * iters : passes));
     s->ev_pixiters.push_back((long long)s->W * s->H * iters);
   }
-  if (s->cfg < 0 ? false : (passes % 2)) s->cur = 1 - s->cur;
-  s->h_clock_valid = false;
+  if (s->cfg >= 0 && passes % 2) s->cur = 1 - s->cur;
+  return EVR_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int evr_step_device(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
+                    const int8_t* pol, size_t n, int iters) {
+  Range range("evr_step_device");
+  if (!s || iters < 0) return EVR_ERR_INVALID_ARG;
+  if (n > 0 && (!x || !y || !t_us || !pol)) return EVR_ERR_INVALID_ARG;
+  if (n > (size_t)INT_MAX) return EVR_ERR_INVALID_ARG;
+  if (!fused_ok(s, n, iters)) {
+    int rc = n ? evr_push_events_device(s, x, y, t_us, pol, n) : EVR_OK;
+    return rc ? rc : evr_solve(s, iters);
+  }
+  int rc = fused_step(s, iters, (int)n, nullptr, 0, x, y, (const long long*)t_us, pol);
+  if (rc == EVR_OK) s->h_clock_valid = false;
+  return rc;
+}
+
+int evr_step(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
+             const int8_t* pol, size_t n, int iters) {
+  Range range("evr_step");
+  if (!s || iters < 0) return EVR_ERR_INVALID_ARG;
+  if (n > 0 && (!x || !y || !t_us || !pol)) return EVR_ERR_INVALID_ARG;
+  if (n > (size_t)INT_MAX) return EVR_ERR_INVALID_ARG;
+  if (!fused_ok(s, n, iters)) {
+    int rc = n ? evr_push_events(s, x, y, t_us, pol, n) : EVR_OK;
+    return rc ? rc : evr_solve(s, iters);
+  }
+  StageSlot* sl = nullptr;
+  long long clock = 0;
+  int rc = stage_host(s, x, y, t_us, pol, n, &sl, &clock);
+  if (rc) return rc;
+  const Packed L(n);
+  char* d = s->dstage;
+  rc = fused_step(s, iters, (int)n, sl->h, L.bytes, (const uint16_t*)d,
+                  (const uint16_t*)(d + L.off_y), (const long long*)(d + L.off_t),
+                  (const int8_t*)(d + L.off_p));
+  if (rc) return rc;
+  // the slot is free again once this packet's graph has run
+  if (cudaEventRecord(sl->done, s->stream) != cudaSuccess) return EVR_ERR_CUDA;
+  sl->pending = true;
+  note_clock(s, clock);
   return EVR_OK;
 }
 

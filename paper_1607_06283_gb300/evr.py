@@ -79,6 +79,7 @@ def _load():
         "evr_push_events_device": ([vp, vp, vp, vp, vp, sz], i),
         "evr_solve": ([vp, i], i),
         "evr_step_device": ([vp, vp, vp, vp, vp, sz, i], i),
+        "evr_step": ([vp, vp, vp, vp, vp, sz, i], i),
         "evr_get_image": ([vp, vp, sz], i),
         "evr_get_image_device": ([vp, vp, sz], i),
         "evr_get_image_async": ([vp, vp, sz, ctypes.POINTER(ctypes.c_uint64)], i),
@@ -206,6 +207,21 @@ def evr_step_device(h, x, y, t_us, pol, iters: int) -> int:
                               int(x.numel()), int(iters))
     if rc in (EVR_ERR_INVALID_ARG, EVR_ERR_CUDA, EVR_ERR_OOM):
         _check(rc, "evr_step_device")
+    return rc
+
+
+def evr_step(h, x, y, t_us, pol, iters: int) -> int:
+    """Push (host arrays) and solve in one call; returns 0 or the immediate error code of
+    the host-side checks (as evr_push_events)."""
+    x, px = _host(x, np.uint16)
+    y, py = _host(y, np.uint16)
+    t, pt = _host(t_us, np.int64)
+    p, pp = _host(pol, np.int8)
+    if not (len(y) == len(t) == len(p) == len(x)):
+        raise ValueError("event arrays differ in length")
+    rc = _lib.evr_step(h, px, py, pt, pp, len(x), int(iters))
+    if rc in (EVR_ERR_INVALID_ARG, EVR_ERR_CUDA, EVR_ERR_OOM):
+        _check(rc, "evr_step")
     return rc
 
 

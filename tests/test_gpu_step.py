@@ -77,3 +77,24 @@ def test_step_with_empty_and_large_packets_and_a_rejection(T):
         assert ra == rb
         np.testing.assert_array_equal(a.image(), b.image())
     assert int(a.state(E.EVR_STATE_CLOCK)) == int(b.state(E.EVR_STATE_CLOCK))
+
+
+@pytest.mark.parametrize("over", [{}, dict(tile_config=45)])
+def test_host_step_equals_push_then_solve(T, over):
+    """evr_step (host arrays, staging copy inside the graph) against evr_push_events +
+    evr_solve; the host-side checks reject a bad packet before anything is queued."""
+    torch, E = T
+    W, H = 120, 77
+    pk = packets(4, W, H, 12, 900)
+    a, b = E.Stream(W, H, **over), E.Stream(W, H, **over)
+    for k, (x, y, t, p) in enumerate(pk):
+        assert E.evr_step(a.h, x, y, t, p, 25) == 0
+        assert b.push(x, y, t, p) == 0
+        b.solve(25)
+        if k in (0, 6, 11):
+            np.testing.assert_array_equal(a.image(), b.image(), err_msg=f"packet {k}")
+    x, y, t, p = packets(5, W, H, 1, 50)[0]
+    x = x.copy()
+    x[3] = W
+    assert E.evr_step(a.h, x, y, t + pk[-1][2][-1], p, 25) == E.EVR_ERR_OUT_OF_RANGE
+    np.testing.assert_array_equal(a.image(), b.image())
