@@ -274,7 +274,8 @@ int clear_flags(evr_stream* s) {
 
 // The multi-launch iteration launches of one packet (unfused or kind 1):
 // `iters` iterations from buffer `cur`.  Returns the buffer holding the result.
-int enqueue_iterations(evr_stream* s, int iters, int cur, cudaStream_t st, int* launches) {
+int enqueue_iterations(evr_stream* s, int iters, int cur, cudaStream_t st, int* launches,
+                       const PrologueConsts* front = nullptr) {
   SolveConsts c = solve_consts(s);
   *launches = 0;
   if (s->cfg < 0) {
@@ -287,7 +288,7 @@ int enqueue_iterations(evr_stream* s, int iters, int cur, cudaStream_t st, int* 
   const SolverCfg& cfg = kSolverCfgs[s->cfg];
   for (int done = 0, pass = 0; done < iters; done += cfg.R, ++pass) {
     int it = iters - done < cfg.R ? iters - done : cfg.R;
-    if (launch_tiled_pass(s->P, cfg, cur, it, pass, c, st)) return -1;
+    if (launch_tiled_pass(s->P, cfg, cur, it, pass, c, st, front)) return -1;
     cur = 1 - cur;
     *launches += 1;
   }
@@ -711,6 +712,23 @@ int enqueue_front(evr_stream* s, cudaStream_t q) {
   return launch_prologue(s->P, s->cur, pc, q) ? -1 : 0;
 }
 
+}  // extern "C"
+
+namespace {
+// Whether the packet's front launch (the prologue) can be fused into the first iteration
+// pass: a kind-1 configuration without a register cap, f from the current u
+// (data_mode 0), no TV-L1 plane, at least two passes.
+bool front_fused(const evr_stream* s, int iters) {
+  if (s->cfg < 0) return false;
+  const SolverCfg& cfg = kSolverCfgs[s->cfg];
+  if (cfg.kind != 1 || !tiled_front_fusable(cfg, s->P.storage)) return false;
+  if (s->prm.data_mode != 0 || (s->prm.tvl1_iters > 0 && s->prm.manifold)) return false;
+  return (iters + cfg.R - 1) / cfg.R >= 2;
+}
+}  // namespace
+
+extern "C" {
+
 int evr_solve(evr_stream* s, int iters) {
   Range range("evr_solve");
   if (!s || iters < 0) return EVR_ERR_INVALID_ARG;
@@ -753,9 +771,12 @@ int evr_solve(evr_stream* s, int iters) {
   }
   if (direct_front && enqueue_front(s, st)) return EVR_ERR_CUDA;
   const bool graph_front = !front_done && !direct_front;
+  const bool fuse = graph_front && front_fused(s, iters);
+  const PrologueConsts pc = prologue_consts(s);
   // launches inside the timed region: the front launches unless the first solve ran
-  // them before the autotuner, then the iteration kernels
-  int launches = front_done ? 0 : front_launches;
+  // them before the autotuner or they are fused into the first pass, then the
+  // iteration kernels
+  int launches = (front_done || fuse) ? 0 : front_launches;
   if (s->cfg >= 0 && kSolverCfgs[s->cfg].kind == 2) {
     if (run_cfg_direct(s, s->cfg, iters)) return EVR_ERR_CUDA;
     launches += 1;
@@ -769,8 +790,9 @@ int evr_solve(evr_stream* s, int iters) {
       int captured = 0;
       if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return EVR_ERR_CUDA;
-      int r = graph_front ? enqueue_front(s, s->cap_stream) : 0;
-      if (r == 0) r = enqueue_iterations(s, iters, s->cur, s->cap_stream, &captured);
+      int r = (graph_front && !fuse) ? enqueue_front(s, s->cap_stream) : 0;
+      if (r == 0)
+        r = enqueue_iterations(s, iters, s->cur, s->cap_stream, &captured, fuse ? &pc : nullptr);
       cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
       if (r < 0 || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -843,6 +865,8 @@ bool fused_ok(const evr_stream* s, size_t n, int iters) {
 int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t copy_bytes,
                const uint16_t* x, const uint16_t* y, const long long* t, const int8_t* pol) {
   cudaStream_t st = s->stream;
+  const bool fuse = front_fused(s, iters);  // the prologue inside the first pass
+  const PrologueConsts pc = prologue_consts(s);
   GraphKey key{iters, s->cur, copy_src ? 3 : 2, s->cfg};
   auto it = s->fused.find(key);
   evr_stream::Fused* fg = nullptr;
@@ -856,9 +880,11 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
                                     s->cap_stream) != cudaSuccess)
       r = -1;
     if (r == 0 && launch_push(s->P, x, y, t, pol, n, s->cap_stream)) r = -1;
-    if (r == 0) r = enqueue_front(s, s->cap_stream);
+    if (r == 0 && !fuse) r = enqueue_front(s, s->cap_stream);
     // enqueue_iterations returns the buffer holding the result, or -1
-    if (r == 0 && enqueue_iterations(s, iters, s->cur, s->cap_stream, &captured) < 0) r = -1;
+    if (r == 0 && enqueue_iterations(s, iters, s->cur, s->cap_stream, &captured,
+                                     fuse ? &pc : nullptr) < 0)
+      r = -1;
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &nf.graph);
     size_t roots = 1, deps = 1;
     cudaGraphNode_t root = nullptr;
@@ -913,7 +939,7 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
     cudaEventRecord(ev.second, st);
     s->ev_used.push_back(ev);
     const int front =
-        1 + ((s->prm.tvl1_iters > 0 && s->prm.manifold) ? 1 + 2 * s->prm.tvl1_iters : 0);
+        fuse ? 0 : 1 + ((s->prm.tvl1_iters > 0 && s->prm.manifold) ? 1 + 2 * s->prm.tvl1_iters : 0);
     s->ev_launches.push_back(1 + front + (s->cfg < 0 ? 2 * iters : passes));
     s->ev_pixiters.push_back((long long)s->W * s->H * iters);
   }

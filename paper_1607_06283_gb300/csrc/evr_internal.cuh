@@ -70,6 +70,32 @@ struct PrologueConsts {
   const float* tau_plane;  // denoised time surface (pitched), or null: from t_last
 };
 
+// Per-pixel arithmetic of the packet prologue, shared by the prologue kernel and by a
+// first iteration pass that computes the packet's constants itself, so that both give
+// the same bits (the operation order is fixed by explicit fmaf).
+#ifdef __CUDACC__
+// Time surface (time since the pixel's last event, Sec. 3.1), scaled and clamped.
+__device__ __forceinline__ float time_surface(long long tl, long long clock, long long t_init,
+                                              const PrologueConsts& c) {
+  if (!c.manifold) return 0.0f;
+  long long last = (tl == kNeverFired) ? t_init : tl;
+  long long d = clock - last;
+  if (c.t_max_us > 0 && d > c.t_max_us) d = c.t_max_us;
+  return __fmul_rn((float)d, c.time_scale);
+}
+// forward difference of the time surface (a subtraction that is never contracted)
+__device__ __forceinline__ float surface_diff(float t1, float t0) { return __fsub_rn(t1, t0); }
+// G = 1 + t_x^2 + t_y^2 (text after Eq. 3)
+__device__ __forceinline__ float metric_G(float a, float b) {
+  return fmaf(b, b, fmaf(a, a, 1.0f));
+}
+// f = base exp(Delta+ n+ - Delta- n-) (Eq. intensity_update, compounded)
+__device__ __forceinline__ float data_image(float base, int np, int nn,
+                                           const PrologueConsts& c) {
+  return __fmul_rn(base, expf(fmaf(c.delta_pos, (float)np, -(c.delta_neg * (float)nn))));
+}
+#endif
+
 // Tiled solvers.  A tile template is an extended tile of EW x EH pixels (an owned
 // tile plus an R-pixel halo on every side) processed by 32 x NTY threads.  A solver
 // configuration is a template, a halo width R and a kind:
@@ -123,8 +149,14 @@ int launch_batch_flip(int* curs, const int* active, int n_streams, int passes, v
 int launch_unfused_iteration(const Planes& P, int cur, const SolveConsts& c, void* stream);
 // kind 1: `iters` <= R iterations from buffer src into buffer 1 - src; `pass` is the
 // pass's index within the packet (0 right after the prologue).
+// With front != NULL the packet's front launches are fused into the passes: pass 0
+// computes the prologue's constants itself (data_mode 0, no TV-L1 plane) and pass 1
+// clears the event counts; the caller runs at least two passes.
 int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters, int pass,
-                      const SolveConsts& c, void* stream);
+                      const SolveConsts& c, void* stream, const PrologueConsts* front = nullptr);
+// Whether launch_tiled_pass supports a fused front for this configuration and storage
+// (tiles without a register cap).
+int tiled_front_fusable(const SolverCfg& cfg, int storage);
 // kind 1 over a batch: one CTA per work item (stream, tile); pass j of a step reads
 // buffer curs[s] ^ (j & 1).  Inactive streams are skipped.
 int launch_tiled_pass_batch(const BatchRef& B, int n_work, const SolverCfg& cfg, int pass,

@@ -313,15 +313,6 @@ int launch_push(const Planes& P, const uint16_t* x, const uint16_t* y, const lon
 }
 
 // ---------------------------------------------------------------- packet prologue
-// Time surface (time since the pixel's last event, Sec. 3.1), scaled and clamped.
-__device__ __forceinline__ float time_surface(long long tl, long long clock, long long t_init,
-                                              const PrologueConsts& c) {
-  if (!c.manifold) return 0.0f;
-  long long last = (tl == kNeverFired) ? t_init : tl;
-  long long d = clock - last;
-  if (c.t_max_us > 0 && d > c.t_max_us) d = c.t_max_us;
-  return (float)d * c.time_scale;
-}
 
 // One pixel of the prologue (block `blk` of the stream's 32 x 8 blocks).
 __device__ __forceinline__ void prologue_px_body(const Planes& P, int cur, const PrologueConsts& c,
@@ -340,18 +331,17 @@ __device__ __forceinline__ void prologue_px_body(const Planes& P, int cur, const
     b = (y < P.H - 1) ? T[i + P.pitch] - T[i] : 0.0f;
   } else {
     float t0 = time_surface(P.t_last[i], clock, t_init, c);
-    a = (x < P.W - 1) ? time_surface(P.t_last[i + 1], clock, t_init, c) - t0 : 0.0f;
-    b = (y < P.H - 1) ? time_surface(P.t_last[i + P.pitch], clock, t_init, c) - t0 : 0.0f;
+    a = (x < P.W - 1) ? surface_diff(time_surface(P.t_last[i + 1], clock, t_init, c), t0) : 0.0f;
+    b = (y < P.H - 1) ? surface_diff(time_surface(P.t_last[i + P.pitch], clock, t_init, c), t0)
+                      : 0.0f;
   }
-  float G = 1.0f + a * a + b * b;
+  float G = metric_G(a, b);
   P.tx[i] = a;
   P.ty[i] = b;
   P.iG[i] = 1.0f / G;
   P.sG[i] = sqrtf(G);
-  int np = P.npos[i], nn = P.nneg[i];
   float base = (c.data_mode == 0) ? P.u[cur][i] : P.f[i];
-  float e = c.delta_pos * (float)np - c.delta_neg * (float)nn;
-  P.f[i] = base * expf(e);
+  P.f[i] = data_image(base, P.npos[i], P.nneg[i], c);
   P.npos[i] = 0;
   P.nneg[i] = 0;
 }

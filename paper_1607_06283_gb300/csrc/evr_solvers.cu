@@ -202,12 +202,37 @@ struct Tile {
     return (size_t)(gy0 + ly(k)) * P.pitch + (gx0 + lx(k));
   }
 
-  // Packet constants of pixel k.
+  // Packet constants of pixel k from its metric (a = L_x t, b = L_y t, 1/G, sqrt(G)), f
+  // and its border masks.
+  __device__ __forceinline__ void set_consts(int k, float a, float b, float ig, float sg,
+                                             float f, float mx, float my, float tl,
+                                             const SolveConsts& c) {
+    const int j = k >> 1, h = k & 1;
+    const float m12 = -(ig * (a * b));
+    el(E1[j], h) = mx * (ig * fmaf(b, b, 1.0f));
+    el(E2[j], h) = mx * m12;
+    el(E3[j], h) = mx * (ig * a);
+    el(E4[j], h) = my * m12;
+    el(E5[j], h) = my * (ig * fmaf(a, a, 1.0f));
+    el(E6[j], h) = my * (ig * b);
+    el(SG[j], h) = sg;
+    const float beta = tl * sg;
+    if (c.data_term) {  // Eq. 7: u+ = (v + beta f) / (1 + beta)
+      el(D1[j], h) = 1.0f / (1.0f + beta);
+      el(D2[j], h) = beta * f;
+      el(D3[j], h) = 0.0f;
+    } else {
+      el(D1[j], h) = -beta;
+      el(D2[j], h) = 4.0f * beta * f;
+      el(D3[j], h) = 2.0f * beta * f;
+    }
+  }
+
+  // Packet constants from the planes the prologue wrote.
   __device__ __forceinline__ void load_consts(const Planes& P, const SolveConsts& c) {
     const float tl = c.tau * c.lambda;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int j = k >> 1, h = k & 1;
       float a = 0.0f, b = 0.0f, ig = 1.0f, sg = 1.0f, f = 1.0f, mx = 0.0f, my = 0.0f;
       if (on(k, P.W, P.H)) {  // off the sensor: finite filler, masked out of every term
         const size_t i = gidx(P, k);
@@ -219,25 +244,58 @@ struct Tile {
         mx = (gx0 + lx(k) < P.W - 1) ? 1.0f : 0.0f;
         my = (gy0 + ly(k) < P.H - 1) ? 1.0f : 0.0f;
       }
-      const float m12 = -(ig * (a * b));
-      el(E1[j], h) = mx * (ig * fmaf(b, b, 1.0f));
-      el(E2[j], h) = mx * m12;
-      el(E3[j], h) = mx * (ig * a);
-      el(E4[j], h) = my * m12;
-      el(E5[j], h) = my * (ig * fmaf(a, a, 1.0f));
-      el(E6[j], h) = my * (ig * b);
-      el(SG[j], h) = sg;
-      const float beta = tl * sg;
-      if (c.data_term) {  // Eq. 7: u+ = (v + beta f) / (1 + beta)
-        el(D1[j], h) = 1.0f / (1.0f + beta);
-        el(D2[j], h) = beta * f;
-        el(D3[j], h) = 0.0f;
-      } else {
-        el(D1[j], h) = -beta;
-        el(D2[j], h) = 4.0f * beta * f;
-        el(D3[j], h) = 2.0f * beta * f;
-      }
+      set_consts(k, a, b, ig, sg, f, mx, my, tl, c);
     }
+  }
+
+  // Packet constants computed here, as the prologue computes them (the first pass of a
+  // packet whose front launch is fused into it): time surface, metric and f = u exp(...)
+  // from the integrated events, the current u (load_state first) and the stream clock.
+  // The owned pixels' values are written to the planes for the later passes.
+  __device__ __forceinline__ void front_consts(const Planes& P, const SolveConsts& c,
+                                               const PrologueConsts& pc) {
+    const float tl = c.tau * c.lambda;
+    const long long clock = P.sc->clock;
+    const long long t_init = P.sc->t_init_set ? P.sc->t_init : clock;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float a = 0.0f, b = 0.0f, ig = 1.0f, sg = 1.0f, f = 1.0f, mx = 0.0f, my = 0.0f;
+      if (on(k, P.W, P.H)) {
+        const size_t i = gidx(P, k);
+        const int gx = gx0 + lx(k), gy = gy0 + ly(k);
+        const float t0 = time_surface(P.t_last[i], clock, t_init, pc);
+        a = (gx < P.W - 1) ? surface_diff(time_surface(P.t_last[i + 1], clock, t_init, pc), t0)
+                           : 0.0f;
+        b = (gy < P.H - 1)
+                ? surface_diff(time_surface(P.t_last[i + P.pitch], clock, t_init, pc), t0)
+                : 0.0f;
+        const float G = metric_G(a, b);
+        ig = 1.0f / G;
+        sg = sqrtf(G);
+        f = data_image(el(u[k >> 1], k & 1), P.npos[i], P.nneg[i], pc);
+        mx = (gx < P.W - 1) ? 1.0f : 0.0f;
+        my = (gy < P.H - 1) ? 1.0f : 0.0f;
+        if (owned(k)) {
+          P.tx[i] = a;
+          P.ty[i] = b;
+          P.iG[i] = ig;
+          P.sG[i] = sg;
+          P.f[i] = f;
+        }
+      }
+      set_consts(k, a, b, ig, sg, f, mx, my, tl, c);
+    }
+  }
+
+  // The owned pixels' event counts, consumed by the previous pass's front_consts.
+  __device__ __forceinline__ void clear_counts(const Planes& P) const {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (owned(k) && on(k, P.W, P.H)) {
+        const size_t i = gidx(P, k);
+        P.npos[i] = 0;
+        P.nneg[i] = 0;
+      }
   }
 
   // Iterated state (u, p) from buffer buf.
@@ -406,10 +464,12 @@ constexpr int kTiledMinBlocks =
     (KX * KY == 4 && sizeof(ST) == 4 && 65536 / (32 * NTY * 80) > 1) ? 65536 / (32 * NTY * 80)
                                                                       : 1;
 
-template <int KX, int KY, int NTY, typename ST>
-__global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>)) k_tiled(Planes P, int src, int iters, int R,
-                                                    SolveConsts c, int tiles_x, BatchRef B,
-                                                    int pass) {
+// FRONT: the packet's front launch is fused into the passes (instantiated only for tiles
+// without a register cap, kTiledMinBlocks == 1).
+template <int KX, int KY, int NTY, typename ST, bool FRONT>
+__global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>))
+    k_tiled(Planes P, int src, int iters, int R, SolveConsts c, int tiles_x, BatchRef B,
+            int pass, PrologueConsts pc) {
   __shared__ TileSmem<KX, KY, NTY, ST> sm;
   __shared__ Planes sP;  // this CTA's stream, staged once (no per-thread local copy)
   int tile = blockIdx.x;
@@ -428,12 +488,26 @@ __global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>)) 
   T.setup(tile, tiles_x, R);
   Tile<KX, KY, NTY, ST>::zero_pads(sm);
   // The first pass of a packet follows the prologue, whose writes are only guaranteed
-  // visible after the wait; later passes may read the constants before it.
-  if (pass > 0) T.load_consts(sP, c);
+  // visible after the wait; later passes may read the constants before it.  With the
+  // front fused (FRONT, single streams only) pass 0 computes the constants itself
+  // after its wait (the push has then completed) and writes the owned ones; pass 1 reads
+  // them after its own wait and clears the owned event counts.
+  const bool early = pass > (FRONT ? 1 : 0);
+  if (early) T.load_consts(sP, c);
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" :::);
-  if (pass == 0) T.load_consts(sP, c);
-  T.load_state(sP, src);
+  if constexpr (FRONT) {
+    T.load_state(sP, src);  // front_consts takes f from the current u
+    if (pass == 0) {
+      T.front_consts(sP, c, pc);
+    } else if (!early) {
+      T.load_consts(sP, c);
+      T.clear_counts(sP);
+    }
+  } else {
+    if (!early) T.load_consts(sP, c);
+    T.load_state(sP, src);
+  }
   if (c.data_term)
     for (int it = 0; it < iters; ++it) T.template iterate<true>(sm, c);
   else
@@ -530,10 +604,25 @@ static int tiles_of(const Planes& P, int R, int* tx, int* ty) {
   return 1;
 }
 
+template <int KX, int KY, int NTY, typename ST>
+static cudaError_t launch_k_tiled_st(cudaLaunchConfig_t* lc, const Planes& P, int src,
+                                     int iters, int R, const SolveConsts& c, int tx,
+                                     const BatchRef& B, int pass, const PrologueConsts* front) {
+  if (front) {
+    if constexpr (kTiledMinBlocks<KX, KY, NTY, ST> == 1)
+      return cudaLaunchKernelEx(lc, k_tiled<KX, KY, NTY, ST, true>, P, src, iters, R, c, tx, B,
+                                pass, *front);
+    else
+      return cudaErrorInvalidValue;
+  }
+  return cudaLaunchKernelEx(lc, k_tiled<KX, KY, NTY, ST, false>, P, src, iters, R, c, tx, B,
+                            pass, PrologueConsts{});
+}
+
 template <int KX, int KY, int NTY>
 static int launch_k_tiled(int blocks, const Planes& P, int src, int iters, int R,
                           const SolveConsts& c, int tx, const BatchRef& B, int pass,
-                          int storage, cudaStream_t st) {
+                          int storage, cudaStream_t st, const PrologueConsts* front) {
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(blocks);
   lc.blockDim = dim3(32, NTY);
@@ -545,28 +634,38 @@ static int launch_k_tiled(int blocks, const Planes& P, int src, int iters, int R
   lc.numAttrs = 1;
   switch (storage) {
     case 0:
-      return (int)cudaLaunchKernelEx(&lc, k_tiled<KX, KY, NTY, float>, P, src, iters, R, c, tx,
-                                     B, pass);
+      return (int)launch_k_tiled_st<KX, KY, NTY, float>(&lc, P, src, iters, R, c, tx, B, pass,
+                                                        front);
     case 1:
-      return (int)cudaLaunchKernelEx(&lc, k_tiled<KX, KY, NTY, __half>, P, src, iters, R, c, tx,
-                                     B, pass);
+      return (int)launch_k_tiled_st<KX, KY, NTY, __half>(&lc, P, src, iters, R, c, tx, B, pass,
+                                                         front);
     case 2:
-      return (int)cudaLaunchKernelEx(&lc, k_tiled<KX, KY, NTY, __nv_bfloat16>, P, src, iters, R,
-                                     c, tx, B, pass);
+      return (int)launch_k_tiled_st<KX, KY, NTY, __nv_bfloat16>(&lc, P, src, iters, R, c, tx, B,
+                                                                pass, front);
     default:
       return (int)cudaErrorInvalidValue;
   }
 }
 
 template <int KX, int KY, int NTY>
+static bool front_fusable(int storage) {
+  switch (storage) {
+    case 0: return kTiledMinBlocks<KX, KY, NTY, float> == 1;
+    case 1: return kTiledMinBlocks<KX, KY, NTY, __half> == 1;
+    case 2: return kTiledMinBlocks<KX, KY, NTY, __nv_bfloat16> == 1;
+    default: return false;
+  }
+}
+
+template <int KX, int KY, int NTY>
 static int run_tiled(const Planes& P, int R, int src, int iters, int pass,
-                     const SolveConsts& c, cudaStream_t st) {
+                     const SolveConsts& c, cudaStream_t st, const PrologueConsts* front) {
   int tx, ty;
   if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters > R || iters < 1)
     return (int)cudaErrorInvalidValue;
   return launch_k_tiled<KX, KY, NTY>(tx * ty, P, src, iters, R, c, tx,
                                      BatchRef{nullptr, nullptr, nullptr, nullptr}, pass,
-                                     P.storage, st);
+                                     P.storage, st, front);
 }
 
 template <int KX, int KY, int NTY>
@@ -576,7 +675,8 @@ static int run_tiled_batch(const BatchRef& B, int n_work, int R, int pass, int i
   if (R < 1 || OW < R || OH < R || iters > R || iters < 1) return (int)cudaErrorInvalidValue;
   if (n_work <= 0) return 0;
   Planes dummy{};
-  return launch_k_tiled<KX, KY, NTY>(n_work, dummy, 0, iters, R, c, 0, B, pass, storage, st);
+  return launch_k_tiled<KX, KY, NTY>(n_work, dummy, 0, iters, R, c, 0, B, pass, storage, st,
+                                     nullptr);
 }
 
 template <int KX, int KY, int NTY>
@@ -622,9 +722,9 @@ static int run_persist(const Planes& P, int R, int cur, int iters, int base, int
   }
 
 int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters, int pass,
-                      const SolveConsts& c, void* stream) {
+                      const SolveConsts& c, void* stream, const PrologueConsts* front) {
   cudaStream_t st = (cudaStream_t)stream;
-  EVR_SHAPE_DISPATCH(run_tiled, P, cfg.R, src, iters, pass, c, st)
+  EVR_SHAPE_DISPATCH(run_tiled, P, cfg.R, src, iters, pass, c, st, front)
   return (int)cudaErrorInvalidValue;
 }
 
@@ -634,6 +734,21 @@ int launch_tiled_pass_batch(const BatchRef& B, int n_work, const SolverCfg& cfg,
   if (cfg.kind != 1) return (int)cudaErrorInvalidValue;
   EVR_SHAPE_DISPATCH(run_tiled_batch, B, n_work, cfg.R, pass, iters, c, storage, st)
   return (int)cudaErrorInvalidValue;
+}
+
+int tiled_front_fusable(const SolverCfg& cfg, int storage) {
+  if (cfg.kind != 1) return 0;
+  switch (cfg.shape) {
+    case 0: return front_fusable<1, 4, 8>(storage);
+    case 1: return front_fusable<1, 2, 16>(storage);
+    case 2: return front_fusable<1, 4, 16>(storage);
+    case 3: return front_fusable<2, 4, 8>(storage);
+    case 4: return front_fusable<2, 2, 16>(storage);
+    case 5: return front_fusable<1, 2, 8>(storage);
+    case 6: return front_fusable<1, 4, 12>(storage);
+    case 7: return front_fusable<1, 2, 32>(storage);
+    default: return 0;
+  }
 }
 
 int launch_persistent(const Planes& P, const SolverCfg& cfg, int cur, int iters, int base,
