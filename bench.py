@@ -385,12 +385,14 @@ def run_ours(args):
     # ---- end to end through the C ABI with host buffers (same number of steps): every
     # step pushes its packet from host arrays (the library stages it in pinned memory and
     # copies it to the device), solves, and reads the image back into pinned host memory.
-    # Readbacks are asynchronous with two in flight: step k is queued before the image of
-    # step k - 1 is waited for, as a real-time consumer would drive the stream.
+    # Readbacks are asynchronous with three steps in flight: step k is queued before the
+    # image of step k - 2 is waited for, as a real-time consumer with a short queue would
+    # drive the stream.
     g2 = E.Stream(cfg.W, cfg.H, p)
     E.evr_set_cuda_stream(g2.h, cur.cuda_stream)
+    depth = 3  # steps in flight: the image of step j - depth + 1 is waited for after step j
     imgs = [torch.empty((cfg.H, cfg.W), dtype=torch.float32).pin_memory().numpy()
-            for _ in range(2)]
+            for _ in range(depth)]
     hx = stream.x[idx]
     hy = stream.y[idx]
     hp = stream.pol[idx]
@@ -408,18 +410,18 @@ def run_ours(args):
             raise RuntimeError(f"wait_image: {rc}")
 
     for k in range(args.warmup):
-        wait(step_host(k, k % 2))
+        wait(step_host(k, k % depth))
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
     e0 = time.perf_counter()
-    prev = None
+    pending = []
     for j in range(args.steps):
-        t = step_host(args.warmup + j, j % 2)
-        if prev is not None:
-            wait(prev)
-        prev = t
-    wait(prev)
+        pending.append(step_host(args.warmup + j, j % depth))
+        if len(pending) == depth:
+            wait(pending.pop(0))
+    for t in pending:
+        wait(t)
     e2e_s = time.perf_counter() - e0
     e2e_s, _ = reduce_timing(e2e_s, 0.0, pg, "cuda")
     e2e_val = ev_total / e2e_s
@@ -464,7 +466,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": cfg.packet * (2 + 2 + 8 + 1),
                     "d2h_bytes_per_step": cfg.W * cfg.H * 4 + 4,  # image + status word
                     "calls": "evr_step (host arrays: push and solve) + "
-                             "evr_get_image_async into pinned memory, two steps in flight"},
+                             "evr_get_image_async into pinned memory, three steps in flight"},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clocks,
             "wall_s_timed": wall,

@@ -52,7 +52,7 @@ extern "C" {
 #define EVR_SOLVER_AUTO 0      /* pick the tiled solver, tile shape from the autotuner: at
                                   the first solve every configuration is timed on the
                                   sensor (state saved and restored); the up to three
-                                  closest then take turns on the next six solves, timed
+                                  closest then take turns on the next nine solves, timed
                                   with CUDA events, and the fastest is kept */
 #define EVR_SOLVER_UNFUSED 1   /* two kernels per iteration (primal step, dual step) */
 #define EVR_SOLVER_TILED 2     /* temporally blocked tiles, several iterations per launch */
@@ -172,8 +172,11 @@ int evr_get_image_device(evr_stream* s, float* out_dev, size_t len);
 
 /* Asynchronous readback of the current image (real-time pipelines: the caller can queue
  * the next packet while this one is solved and copied).  Queues the copy of u (W*H
- * floats, row-major, as evr_get_image) into out_host on the handle's CUDA stream and
- * returns at once with a ticket (> 0) in *ticket.  out_host must stay valid and unread
+ * floats, row-major, as evr_get_image) into out_host and returns at once with a ticket
+ * (> 0) in *ticket: on the handle's CUDA stream, in order with the solves, u is copied
+ * into one of three library-owned device staging images; the copy to the host then
+ * runs on a library-owned stream, overlapping the next packets' kernels, and completes
+ * at evr_wait_image(ticket) (not at a synchronisation of the handle's stream).  out_host must stay valid and unread
  * until evr_wait_image(ticket) has returned; page-locked memory (cudaHostAlloc, pinned
  * tensors) keeps the copy asynchronous, pageable memory makes the CUDA runtime wait for
  * it here.  At most 16 readbacks are in flight: the 17th waits for the oldest.  Errors:

@@ -65,7 +65,7 @@ cudaError_t host_alloc(void** p, size_t bytes) {
 
 namespace {
 
-constexpr int kStageSlots = 2;
+constexpr int kStageSlots = 4;  // pinned staging slots: packets whose copy may be in flight
 constexpr int kMaxTimingPairs = 8192;
 
 // A packet of n events is staged packed, x | y | t | pol (t at an 8-byte boundary), so
@@ -84,6 +84,7 @@ struct StageSlot {
 };
 
 constexpr int kImgRing = 16;  // asynchronous image readbacks in flight per handle
+constexpr int kImgStage = 3;  // device staging images of the asynchronous readbacks
 
 struct GraphKey {
   int iters, cur, front;  // front: the graph starts with the (TV-L1 +) prologue launches
@@ -96,7 +97,7 @@ struct GraphKey {
 };
 
 constexpr int kRefineCands = 3;  // configurations refined on real solves
-constexpr int kRefineReps = 2;   // real solves per candidate
+constexpr int kRefineReps = 3;   // real solves per candidate
 
 }  // namespace
 
@@ -124,9 +125,14 @@ struct evr_stream {
   size_t dcap = 0;           // events
   char* dstage = nullptr;    // device, 13 * dcap bytes
   // asynchronous image readbacks: completion event and status copy per ticket
-  cudaEvent_t img_ev[kImgRing] = {};
+  cudaEvent_t img_ev[kImgRing] = {};  // recorded on copy_stream after each readback
   int* h_img_status = nullptr;  // pinned, kImgRing ints
   unsigned long long img_ticket = 0;
+  // the device-to-host part of an asynchronous readback runs on copy_stream from one of
+  // kImgStage staging images (W*H floats each), overlapping the next packets' kernels
+  cudaStream_t copy_stream = nullptr;
+  float* d_img_stage = nullptr;
+  cudaEvent_t stage_ready[kImgStage] = {};
   // host mirror of the stream clock for immediate checks
   long long h_clock = 0;
   bool h_have_clock = false;
@@ -213,10 +219,21 @@ void free_stage(evr_stream* s) {
   if (s->dstage) cudaFree(s->dstage);
   s->dstage = nullptr;
   s->dcap = 0;
+  if (s->copy_stream) {
+    cudaStreamSynchronize(s->copy_stream);
+    cudaStreamDestroy(s->copy_stream);
+    s->copy_stream = nullptr;
+  }
   for (auto& e : s->img_ev) {
     if (e) cudaEventDestroy(e);
     e = nullptr;
   }
+  for (auto& e : s->stage_ready) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  if (s->d_img_stage) cudaFree(s->d_img_stage);
+  s->d_img_stage = nullptr;
   if (s->h_img_status) cudaFreeHost(s->h_img_status);
   s->h_img_status = nullptr;
 }
@@ -1005,25 +1022,48 @@ int evr_get_image(evr_stream* s, float* out_host, size_t len) {
 int evr_get_image_async(evr_stream* s, float* out_host, size_t len, uint64_t* ticket) {
   Range range("evr_get_image_async");
   if (!s || !out_host || !ticket || len < (size_t)s->W * s->H) return EVR_ERR_INVALID_ARG;
+  const size_t img = (size_t)s->W * s->H;
   if (!s->h_img_status) {
     if (host_alloc((void**)&s->h_img_status, sizeof(int) * kImgRing) != cudaSuccess) {
       s->h_img_status = nullptr;
       return EVR_ERR_OOM;
     }
+    if (dev_alloc((void**)&s->d_img_stage, sizeof(float) * img * kImgStage) != cudaSuccess) {
+      cudaFreeHost(s->h_img_status);
+      s->h_img_status = nullptr;
+      s->d_img_stage = nullptr;
+      return EVR_ERR_OOM;
+    }
+    if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return EVR_ERR_CUDA;
     for (auto& e : s->img_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return EVR_ERR_CUDA;
+    for (auto& e : s->stage_ready)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return EVR_ERR_CUDA;
   }
   const unsigned long long t = s->img_ticket + 1;
-  const int slot = (int)(t % kImgRing);
-  // a slot is reused only after the readback that held it has completed
+  const int slot = (int)(t % kImgRing), stage = (int)(t % kImgStage);
+  float* dst = s->d_img_stage + (size_t)stage * img;
+  // a ring slot is reused only after the readback that held it has completed
   if (cudaEventSynchronize(s->img_ev[slot]) != cudaSuccess) return EVR_ERR_CUDA;
-  cudaError_t e = cudaMemcpy2DAsync(out_host, (size_t)s->W * 4, s->P.u[s->cur],
-                                    (size_t)s->pitch * 4, (size_t)s->W * 4, s->H,
-                                    cudaMemcpyDeviceToHost, s->stream);
+  cudaError_t e = cudaSuccess;
+  // the staging image is reused once its previous host copy (ticket t - kImgStage) is done
+  if (t > kImgStage)
+    e = cudaStreamWaitEvent(s->stream, s->img_ev[(t - kImgStage) % kImgRing], 0);
+  // on the handle's stream, in order with the solves: the image into staging, the status
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(dst, (size_t)s->W * 4, s->P.u[s->cur], (size_t)s->pitch * 4,
+                          (size_t)s->W * 4, s->H, cudaMemcpyDeviceToDevice, s->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&s->h_img_status[slot], &s->P.sc->status, sizeof(int),
                         cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(s->img_ev[slot], s->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(s->stage_ready[stage], s->stream);
+  // on the copy stream: staging to the host, then the ticket's event
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy_stream, s->stage_ready[stage], 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_host, dst, sizeof(float) * img, cudaMemcpyDeviceToHost,
+                        s->copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(s->img_ev[slot], s->copy_stream);
   if (e != cudaSuccess) return EVR_ERR_CUDA;
   s->img_ticket = t;
   *ticket = t;
