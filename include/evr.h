@@ -286,9 +286,10 @@ int evr_batch_get_image(evr_batch* b, int s, float* out_host, size_t len);
  * len is the capacity of out_host in floats.  A device kernel gathers the images into
  * one buffer (allocated at the first readback), then one copy moves them. */
 int evr_batch_get_images(evr_batch* b, float* out_host, size_t len);
-/* Asynchronous form, as evr_get_image_async: queues the gather and the copy into
- * out_host (page-locked for an asynchronous copy) and returns a ticket (> 0); at most
- * 16 in flight.  evr_batch_wait_images(ticket) waits for that copy (EVR_OK,
+/* Asynchronous form, as evr_get_image_async: queues the gather (into one of two
+ * library-owned staging buffers, on the batch's stream) and the copy into out_host (on
+ * a library-owned stream; page-locked memory for an asynchronous copy) and returns a
+ * ticket (> 0); at most 16 in flight.  evr_batch_wait_images(ticket) waits for that copy (EVR_OK,
  * EVR_ERR_CUDA, EVR_ERR_INVALID_ARG for a ticket not issued); rejected packets are
  * reported by evr_batch_synchronize. */
 int evr_batch_get_images_async(evr_batch* b, float* out_host, size_t len, uint64_t* ticket);

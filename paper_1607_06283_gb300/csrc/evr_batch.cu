@@ -54,8 +54,11 @@ struct evr_batch {
   int next_stage = 0;
   // image readback: every stream's image gathered into one buffer, then one copy
   long long* d_img_off = nullptr;  // per stream, offset in floats
-  float* d_img = nullptr;          // px_total floats
-  cudaEvent_t img_ev[16] = {};
+  float* d_img = nullptr;          // px_total floats (synchronous readback, staging 0)
+  float* d_img2 = nullptr;         // staging 1 of the asynchronous readbacks
+  cudaEvent_t img_ev[16] = {};     // recorded on copy_stream after each readback
+  cudaEvent_t stage_ready[2] = {};
+  cudaStream_t copy_stream = nullptr;  // the host copies of asynchronous readbacks
   unsigned long long img_ticket = 0;
   long long* d_offsets = nullptr;
   DevScalars* h_sc = nullptr;  // pinned, one per stream
@@ -348,9 +351,16 @@ void evr_batch_destroy(evr_batch* b) {
     if (b->h_stage[k]) cudaFreeHost(b->h_stage[k]);
     if (b->h_stage_done[k]) cudaEventDestroy(b->h_stage_done[k]);
   }
+  if (b->copy_stream) {
+    cudaStreamSynchronize(b->copy_stream);
+    cudaStreamDestroy(b->copy_stream);
+  }
   if (b->d_img_off) cudaFree(b->d_img_off);
   if (b->d_img) cudaFree(b->d_img);
+  if (b->d_img2) cudaFree(b->d_img2);
   for (auto& e : b->img_ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : b->stage_ready)
     if (e) cudaEventDestroy(e);
   if (b->h_sc) cudaFreeHost(b->h_sc);
   if (b->h_curs) cudaFreeHost(b->h_curs);
@@ -485,55 +495,82 @@ int evr_batch_get_image(evr_batch* b, int s, float* out_host, size_t len) {
 }
 
 // Queue the gather of all images and their copy to out_host on the batch's stream.
-static int queue_images(evr_batch* b, float* out_host, size_t len) {
-  if ((long long)len < b->px_total) return EVR_ERR_INVALID_ARG;
-  if (!b->d_img) {
-    std::vector<long long> off(b->n);
-    long long acc = 0;
-    for (int s = 0; s < b->n; ++s) {
-      off[s] = acc;
-      acc += (long long)b->planes[s].W * b->planes[s].H;
-    }
-    if (dev_alloc((void**)&b->d_img_off, sizeof(long long) * b->n) != cudaSuccess)
-      return EVR_ERR_OOM;
-    if (dev_alloc((void**)&b->d_img, sizeof(float) * (size_t)b->px_total) != cudaSuccess) {
-      cudaFree(b->d_img_off);
-      b->d_img_off = nullptr;
-      b->d_img = nullptr;
-      return EVR_ERR_OOM;
-    }
-    if (cudaMemcpy(b->d_img_off, off.data(), sizeof(long long) * b->n,
-                   cudaMemcpyHostToDevice) != cudaSuccess)
-      return EVR_ERR_CUDA;
+// The gather buffer and per-stream offsets (allocated at the first readback).
+static int ensure_gather(evr_batch* b) {
+  if (b->d_img) return EVR_OK;
+  std::vector<long long> off(b->n);
+  long long acc = 0;
+  for (int s = 0; s < b->n; ++s) {
+    off[s] = acc;
+    acc += (long long)b->planes[s].W * b->planes[s].H;
   }
-  k_batch_gather<<<b->n, 256, 0, b->stream>>>(b->d_descs, b->d_curs, b->d_img_off, b->d_img);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(out_host, b->d_img, sizeof(float) * (size_t)b->px_total,
-                        cudaMemcpyDeviceToHost, b->stream);
-  return e == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+  if (dev_alloc((void**)&b->d_img_off, sizeof(long long) * b->n) != cudaSuccess)
+    return EVR_ERR_OOM;
+  if (dev_alloc((void**)&b->d_img, sizeof(float) * (size_t)b->px_total) != cudaSuccess) {
+    cudaFree(b->d_img_off);
+    b->d_img_off = nullptr;
+    b->d_img = nullptr;
+    return EVR_ERR_OOM;
+  }
+  if (cudaMemcpy(b->d_img_off, off.data(), sizeof(long long) * b->n, cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return EVR_ERR_CUDA;
+  return EVR_OK;
 }
 
 int evr_batch_get_images(evr_batch* b, float* out_host, size_t len) {
   Range range("evr_batch_get_images");
   if (!b || !out_host) return EVR_ERR_INVALID_ARG;
-  int rc = queue_images(b, out_host, len);
+  if ((long long)len < b->px_total) return EVR_ERR_INVALID_ARG;
+  int rc = ensure_gather(b);
   if (rc) return rc;
-  return cudaStreamSynchronize(b->stream) == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+  k_batch_gather<<<b->n, 256, 0, b->stream>>>(b->d_descs, b->d_curs, b->d_img_off, b->d_img);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_host, b->d_img, sizeof(float) * (size_t)b->px_total,
+                        cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
 }
 
+// Asynchronous: the gather into one of two staging buffers runs on the batch's stream in
+// order with the steps; the host copy runs on copy_stream and overlaps the next steps.
 int evr_batch_get_images_async(evr_batch* b, float* out_host, size_t len, uint64_t* ticket) {
   Range range("evr_batch_get_images_async");
   if (!b || !out_host || !ticket) return EVR_ERR_INVALID_ARG;
-  if (!b->img_ev[0])
+  if ((long long)len < b->px_total) return EVR_ERR_INVALID_ARG;
+  int rc = ensure_gather(b);
+  if (rc) return rc;
+  if (!b->copy_stream) {
+    if (dev_alloc((void**)&b->d_img2, sizeof(float) * (size_t)b->px_total) != cudaSuccess) {
+      b->d_img2 = nullptr;
+      return EVR_ERR_OOM;
+    }
+    if (cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return EVR_ERR_CUDA;
     for (auto& e : b->img_ev)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return EVR_ERR_CUDA;
+    for (auto& e : b->stage_ready)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return EVR_ERR_CUDA;
+  }
   const unsigned long long t = b->img_ticket + 1;
-  cudaEvent_t ev = b->img_ev[t % 16];
-  if (cudaEventSynchronize(ev) != cudaSuccess) return EVR_ERR_CUDA;  // slot reuse
-  int rc = queue_images(b, out_host, len);
-  if (rc) return rc;
-  if (cudaEventRecord(ev, b->stream) != cudaSuccess) return EVR_ERR_CUDA;
+  const int slot = (int)(t % 16), stage = (int)(t % 2);
+  float* dst = stage ? b->d_img2 : b->d_img;
+  if (cudaEventSynchronize(b->img_ev[slot]) != cudaSuccess) return EVR_ERR_CUDA;  // ring reuse
+  cudaError_t e = cudaSuccess;
+  // the staging buffer is reused once its previous host copy (ticket t - 2) is done
+  if (t > 2) e = cudaStreamWaitEvent(b->stream, b->img_ev[(t - 2) % 16], 0);
+  if (e == cudaSuccess) {
+    k_batch_gather<<<b->n, 256, 0, b->stream>>>(b->d_descs, b->d_curs, b->d_img_off, dst);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b->stage_ready[stage], b->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->copy_stream, b->stage_ready[stage], 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_host, dst, sizeof(float) * (size_t)b->px_total,
+                        cudaMemcpyDeviceToHost, b->copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b->img_ev[slot], b->copy_stream);
+  if (e != cudaSuccess) return EVR_ERR_CUDA;
   b->img_ticket = t;
   *ticket = t;
   return EVR_OK;
