@@ -325,8 +325,11 @@ const char* evr_batch_solver_name(evr_batch* b);
 /* Workspace bytes for evr_unrolled_forward/backward (0 for invalid sizes). */
 size_t evr_unrolled_workspace_bytes(int W, int H, int pitch, int n, int K, int every);
 
-/* K iterations from (u0, p0) (FP32, IEEE division and square root), storing (u, p)
- * checkpoints every `every` iterations in `workspace`; result in u_out, p_out. */
+/* K iterations from (u0, p0), storing (u, p) checkpoints every `every` iterations in
+ * `workspace`; result in u_out, p_out.  The iterations are the solver's tiled FP32 passes
+ * (MUFU reciprocal square root and reciprocal, a few ulp); evr_unrolled_backward
+ * recomputes each segment with the same passes, so it sees the same states bit for bit
+ * for any checkpoint spacing. */
 int evr_unrolled_forward(const float* tx, const float* ty, const float* f, const float* u0,
                          const float* p0, int W, int H, int pitch, int n, float lambda,
                          float tau, float sigma, float u_min, float u_max, int K, int every,

@@ -463,6 +463,7 @@ char* carve_state(char* base, int W, int H, bool solo, Planes* out) {
   Planes P{};
   P.W = W;
   P.H = H;
+  P.Hm = H;
   P.pitch = (W + 31) / 32 * 32;
   const size_t plane = (size_t)P.pitch * H;
   const size_t fb = al256(plane * 4), lb = al256(plane * 8);

@@ -1,7 +1,9 @@
 // evr_grad.cu -- differentiation of one packet's solve (K unrolled iterations of
 // Eq. cont_iterates with Eq. update_rules) by a hand-written adjoint, with (u, p)
-// checkpoints every `every` iterations.  FP32 kernels with IEEE division and square
-// root; the lambda gradient and the contrast-threshold sums are reduced in FP64.
+// checkpoints every `every` iterations.  The iterations themselves (forward, and the
+// recomputation of each checkpoint segment) are the solver's tiled FP32 passes; the
+// adjoint kernels use IEEE division and square root; the lambda gradient and the
+// contrast-threshold sums are reduced in FP64.
 //
 // All memory (inputs, outputs and the workspace) belongs to the caller; nothing here
 // allocates.  Planes are H rows of `pitch` floats; a dual variable is 3 such planes
@@ -9,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/evr.h"
+#include "evr_internal.cuh"
 
 namespace {
 
@@ -119,17 +122,6 @@ __global__ void k_f_primal(Geo g, Coef c, Met m, const float* f, const float* u,
   if (v_out) v_out[i] = v;
 }
 
-__global__ void k_f_dual(Geo g, Coef c, Met m, const float* ub, const float* p, float* p_out) {
-  PIXEL
-  float g1, g2, g3;
-  Lg(g, m, ub, x, yl, i, g1, g2, g3);
-  float p1 = p[i] + c.sigma * g1, p2 = p[g.plane + i] + c.sigma * g2,
-        p3 = p[2 * g.plane + i] + c.sigma * g3;
-  float den = fmaxf(1.0f, sqrtf(p1 * p1 + p2 * p2 + p3 * p3) / m.sG[i]);
-  p_out[i] = p1 / den;
-  p_out[g.plane + i] = p2 / den;
-  p_out[2 * g.plane + i] = p3 / den;
-}
 
 // ---- backward of one iteration from state (u, p) ----
 // step 1: the adjoint through the projection, apt = J_proj ap_next, written scaled by
@@ -300,6 +292,7 @@ struct Workspace {
   float* au;       // 1 plane
   float* ap;       // 3 planes
   float* tav;      // 1 plane
+  float* xs;       // 2 states x 4 planes: ping-pong buffers of the recomputing passes
   float* iG;       // 1 plane: 1/G
   float* sG;       // 1 plane: sqrt(G)
   double* glam;    // K x (blocks of the pixel grid): per-block lambda-gradient sums
@@ -331,12 +324,45 @@ size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspac
   t.au = (float*)take(fpl);
   t.ap = (float*)take(fpl * 3);
   t.tav = (float*)take(fpl);
+  t.xs = (float*)take(fpl * 8);
   t.iG = (float*)take(fpl);
   t.sG = (float*)take(fpl);
   t.glam = (double*)take(sizeof(double) * (size_t)K * pixel_blocks(W, H));
   t.partials = (double*)take(sizeof(double) * 4 * kRedBlocks);
   if (w) *w = t;
   return off;
+}
+
+// The iterations of the forward pass and of the reverse pass's recomputation run as the
+// solver's tiled passes (FP32, one pixel pair per thread, a kUnrolledR-pixel halo) over
+// the stacked images; their per-pixel arithmetic does not depend on how the iterations
+// are split into launches, so the recomputed states equal the forward's bit for bit.
+constexpr int kUnrolledR = 5;
+
+// The two ping-pong states a0, a1 (u | p1 | p2 | p3, plane stride fpl floats) and the
+// packet's planes as the tiled passes' descriptor.
+evr::Planes unrolled_planes(int W, int H, int Hm, int pitch, const float* tx, const float* ty,
+                            const float* f, float* iG, float* sG, float* a0, float* a1,
+                            size_t fpl) {
+  evr::Planes P{};
+  P.W = W;
+  P.H = H;
+  P.Hm = Hm;
+  P.pitch = pitch;
+  float* st[2] = {a0, a1};
+  for (int b = 0; b < 2; ++b) {
+    P.u[b] = st[b];
+    P.p1[b] = st[b] + fpl;
+    P.p2[b] = st[b] + 2 * fpl;
+    P.p3[b] = st[b] + 3 * fpl;
+  }
+  P.tx = const_cast<float*>(tx);
+  P.ty = const_cast<float*>(ty);
+  P.f = const_cast<float*>(f);
+  P.iG = iG;
+  P.sG = sG;
+  P.storage = 0;
+  return P;
 }
 
 // A state in the workspace is u | p1 | p2 | p3 with the 256-byte-aligned plane size.
@@ -370,11 +396,9 @@ extern "C" int evr_unrolled_forward(const float* tx, const float* ty, const floa
   Workspace w;
   ws_layout(W, H, pitch, K, every, (char*)workspace, &w);
   Geo g{W, H, pitch, (size_t)pitch * H, Hm};
-  Coef c{tau, sigma, lambda, u_min, u_max};
   const size_t fpl = ((size_t)pitch * H * 4 + 255) / 256 * 256 / 4;  // floats per plane slot
   dim3 blk(kBlkX, kBlkY), grd((W + kBlkX - 1) / kBlkX, (H + kBlkY - 1) / kBlkY);
   k_metric<<<grd, blk, 0, st>>>(g, tx, ty, w.iG, w.sG);
-  const Met m{tx, ty, w.iG, w.sG};
   // state buffers: two ping-pong states in the tape area (u | p1 p2 p3)
   float* su[2] = {w.tape, w.tape + 4 * fpl};
   Geo g4 = g;
@@ -382,17 +406,19 @@ extern "C" int evr_unrolled_forward(const float* tx, const float* ty, const floa
   // copy (u0, p0) into state 0
   k_copy<<<grd, blk, 0, st>>>(g, u0, su[0], 1);
   for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, p0 + k * g.plane, su[0] + (1 + k) * fpl, 1);
+  const evr::Planes P = unrolled_planes(W, H, Hm, pitch, tx, ty, f, w.iG, w.sG, su[0], su[1],
+                                        fpl);
+  const evr::SolveConsts sc{tau, sigma, lambda, u_min, u_max, 0};
   int cur = 0;
-  for (int k = 0; k < K; ++k) {
-    if (k % every == 0) {
-      float* dst = w.ck + (size_t)(k / every) * 4 * fpl;
-      k_copy<<<grd, blk, 0, st>>>(g4, su[cur], dst, 4);
+  for (int k0 = 0; k0 < K; k0 += every) {  // a checkpoint, then the segment's passes
+    k_copy<<<grd, blk, 0, st>>>(g4, su[cur], w.ck + (size_t)(k0 / every) * 4 * fpl, 4);
+    for (int left = (K - k0 < every) ? K - k0 : every, pass = 0; left > 0; ++pass) {
+      const int r = left < kUnrolledR ? left : kUnrolledR;
+      if (evr::launch_tiled_tape(P, kUnrolledR, cur, r, pass, sc, nullptr, 0, 0, st))
+        return EVR_ERR_CUDA;
+      cur ^= 1;
+      left -= r;
     }
-    float* s0 = su[cur];
-    float* s1 = su[1 - cur];
-    k_f_primal<<<grd, blk, 0, st>>>(g4, c, m, f, s0, s0 + fpl, s1, w.ub, nullptr);
-    k_f_dual<<<grd, blk, 0, st>>>(g4, c, m, w.ub, s0 + fpl, s1 + fpl);
-    cur = 1 - cur;
   }
   k_copy<<<grd, blk, 0, st>>>(g, su[cur], u_out, 1);
   for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, su[cur] + (1 + k) * fpl, p_out + k * g.plane, 1);
@@ -430,16 +456,28 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
     k_zero<<<grd, blk, 0, st>>>(g4, w.ap, 3);
   }
   k_zero<<<grd, blk, 0, st>>>(g, gf, 1);
+  const evr::Planes PR =
+      unrolled_planes(W, H, Hm, pitch, tx, ty, f, w.iG, w.sG, w.xs, w.xs + 4 * fpl, fpl);
+  const evr::SolveConsts sc{tau, sigma, lambda, u_min, u_max, 0};
   const int n_ck = (K + every - 1) / every;
   for (int cseg = n_ck - 1; cseg >= 0; --cseg) {
     const int k0 = cseg * every, k1 = (k0 + every < K) ? k0 + every : K;
-    // recompute states k0 .. k1-1 into the tape (slot j = state k0 + j)
+    // recompute states k0 .. k1-1 into the tape (slot j = state k0 + j): the checkpoint
+    // into slot 0 and into the passes' first ping-pong state, then tiled passes that
+    // write every state they produce into the tape
     k_copy<<<grd, blk, 0, st>>>(g4, w.ck + (size_t)cseg * 4 * fpl, w.tape, 4);
-    for (int k = k0; k + 1 < k1; ++k) {
-      float* s0 = w.tape + (size_t)(k - k0) * 4 * fpl;
-      float* s1 = s0 + 4 * fpl;
-      k_f_primal<<<grd, blk, 0, st>>>(g4, c, m, f, s0, s0 + fpl, s1, w.ub, nullptr);
-      k_f_dual<<<grd, blk, 0, st>>>(g4, c, m, w.ub, s0 + fpl, s1 + fpl);
+    if (k1 - k0 > 1) {
+      k_copy<<<grd, blk, 0, st>>>(g4, w.ck + (size_t)cseg * 4 * fpl, w.xs, 4);
+      int src = 0;
+      for (int done = 0, pass = 0; done < k1 - k0 - 1; ++pass) {
+        const int left = k1 - k0 - 1 - done;
+        const int r = left < kUnrolledR ? left : kUnrolledR;
+        if (evr::launch_tiled_tape(PR, kUnrolledR, src, r, pass, sc, w.tape, (long long)fpl,
+                                   done, st))
+          return EVR_ERR_CUDA;
+        src ^= 1;
+        done += r;
+      }
     }
     for (int k = k1 - 1; k >= k0; --k) {
       float* s0 = w.tape + (size_t)(k - k0) * 4 * fpl;

@@ -30,6 +30,8 @@ constexpr int kMaxCtas = 1024;
 
 struct Planes {
   int W, H, pitch;
+  int Hm;  // rows per image: H for a stream; n images of Hm rows stacked into H = n Hm
+           // rows are independent (no forward difference across an image's last row)
   float* u[2];
   float* p1[2];
   float* p2[2];
@@ -157,6 +159,14 @@ int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters,
 // Whether launch_tiled_pass supports a fused front for this configuration and storage
 // (tiles without a register cap).
 int tiled_front_fusable(const SolverCfg& cfg, int storage);
+// The unrolled solve's passes (FP32, the 32 x 32 tile with one pixel pair per thread and
+// an R-pixel halo): `iters` <= R iterations from buffer src into 1 - src; with a tape,
+// the state after each iteration it is also written to tape slot tape_first + it + 1
+// (4 planes of tape_plane floats per slot).
+constexpr int kTapeKX = 1, kTapeKY = 2, kTapeNTY = 16;
+int launch_tiled_tape(const Planes& P, int R, int src, int iters, int pass,
+                      const SolveConsts& c, float* tape, long long tape_plane, int tape_first,
+                      void* stream);
 // kind 1 over a batch: one CTA per work item (stream, tile); pass j of a step reads
 // buffer curs[s] ^ (j & 1).  Inactive streams are skipped.
 int launch_tiled_pass_batch(const BatchRef& B, int n_work, const SolverCfg& cfg, int pass,

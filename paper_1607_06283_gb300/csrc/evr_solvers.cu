@@ -242,7 +242,8 @@ struct Tile {
         sg = P.sG[i];
         f = P.f[i];
         mx = (gx0 + lx(k) < P.W - 1) ? 1.0f : 0.0f;
-        my = (gy0 + ly(k) < P.H - 1) ? 1.0f : 0.0f;
+        const int gy = gy0 + ly(k);
+        my = ((P.Hm == P.H ? gy : gy % P.Hm) < P.Hm - 1) ? 1.0f : 0.0f;
       }
       set_consts(k, a, b, ig, sg, f, mx, my, tl, c);
     }
@@ -274,7 +275,7 @@ struct Tile {
         sg = sqrtf(G);
         f = data_image(el(u[k >> 1], k & 1), P.npos[i], P.nneg[i], pc);
         mx = (gx < P.W - 1) ? 1.0f : 0.0f;
-        my = (gy < P.H - 1) ? 1.0f : 0.0f;
+        my = (gy % P.Hm < P.Hm - 1) ? 1.0f : 0.0f;
         if (owned(k)) {
           P.tx[i] = a;
           P.ty[i] = b;
@@ -296,6 +297,22 @@ struct Tile {
         P.npos[i] = 0;
         P.nneg[i] = 0;
       }
+  }
+
+  // The owned pixels' state (u, p) into one slot of a tape: 4 FP32 planes of
+  // `plane` floats each (pitched like the stream's planes).
+  __device__ __forceinline__ void store_tape(float* slot, long long plane, const Planes& P) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int j = k >> 1, h = k & 1;
+      if (owned(k) && on(k, P.W, P.H)) {
+        const size_t i = gidx(P, k);
+        slot[i] = el(u[j], h);
+        slot[plane + i] = el(p1[j], h);
+        slot[2 * plane + i] = el(p2[j], h);
+        slot[3 * plane + i] = el(p3[j], h);
+      }
+    }
   }
 
   // Iterated state (u, p) from buffer buf.
@@ -464,12 +481,16 @@ constexpr int kTiledMinBlocks =
     (KX * KY == 4 && sizeof(ST) == 4 && 65536 / (32 * NTY * 80) > 1) ? 65536 / (32 * NTY * 80)
                                                                       : 1;
 
-// FRONT: the packet's front launch is fused into the passes (instantiated only for tiles
-// without a register cap, kTiledMinBlocks == 1).
-template <int KX, int KY, int NTY, typename ST, bool FRONT>
+// MODE 0: plain passes.  MODE 1 (FRONT): the packet's front launch is fused into the
+// passes (instantiated only for tiles without a register cap, kTiledMinBlocks == 1).
+// MODE 2 (tape, FP32 only): after iteration it of this launch the owned state is also
+// written to tape slot tape_first + it + 1 (slot stride 4 tape_plane floats), for the
+// reverse pass of the unrolled solve.
+template <int KX, int KY, int NTY, typename ST, int MODE>
 __global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>))
     k_tiled(Planes P, int src, int iters, int R, SolveConsts c, int tiles_x, BatchRef B,
-            int pass, PrologueConsts pc) {
+            int pass, PrologueConsts pc, float* tape, long long tape_plane, int tape_first) {
+  constexpr bool FRONT = MODE == 1;
   __shared__ TileSmem<KX, KY, NTY, ST> sm;
   __shared__ Planes sP;  // this CTA's stream, staged once (no per-thread local copy)
   int tile = blockIdx.x;
@@ -508,10 +529,20 @@ __global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>))
     if (!early) T.load_consts(sP, c);
     T.load_state(sP, src);
   }
-  if (c.data_term)
-    for (int it = 0; it < iters; ++it) T.template iterate<true>(sm, c);
-  else
-    for (int it = 0; it < iters; ++it) T.template iterate<false>(sm, c);
+  if constexpr (MODE == 2) {
+    for (int it = 0; it < iters; ++it) {
+      if (c.data_term)
+        T.template iterate<true>(sm, c);
+      else
+        T.template iterate<false>(sm, c);
+      T.store_tape(tape + (long long)(tape_first + it + 1) * 4 * tape_plane, tape_plane, sP);
+    }
+  } else {
+    if (c.data_term)
+      for (int it = 0; it < iters; ++it) T.template iterate<true>(sm, c);
+    else
+      for (int it = 0; it < iters; ++it) T.template iterate<false>(sm, c);
+  }
   T.store(sP, 1 - src, false);
 }
 
@@ -610,13 +641,13 @@ static cudaError_t launch_k_tiled_st(cudaLaunchConfig_t* lc, const Planes& P, in
                                      const BatchRef& B, int pass, const PrologueConsts* front) {
   if (front) {
     if constexpr (kTiledMinBlocks<KX, KY, NTY, ST> == 1)
-      return cudaLaunchKernelEx(lc, k_tiled<KX, KY, NTY, ST, true>, P, src, iters, R, c, tx, B,
-                                pass, *front);
+      return cudaLaunchKernelEx(lc, k_tiled<KX, KY, NTY, ST, 1>, P, src, iters, R, c, tx, B,
+                                pass, *front, (float*)nullptr, 0LL, 0);
     else
       return cudaErrorInvalidValue;
   }
-  return cudaLaunchKernelEx(lc, k_tiled<KX, KY, NTY, ST, false>, P, src, iters, R, c, tx, B,
-                            pass, PrologueConsts{});
+  return cudaLaunchKernelEx(lc, k_tiled<KX, KY, NTY, ST, 0>, P, src, iters, R, c, tx, B, pass,
+                            PrologueConsts{}, (float*)nullptr, 0LL, 0);
 }
 
 template <int KX, int KY, int NTY>
@@ -734,6 +765,30 @@ int launch_tiled_pass_batch(const BatchRef& B, int n_work, const SolverCfg& cfg,
   if (cfg.kind != 1) return (int)cudaErrorInvalidValue;
   EVR_SHAPE_DISPATCH(run_tiled_batch, B, n_work, cfg.R, pass, iters, c, storage, st)
   return (int)cudaErrorInvalidValue;
+}
+
+int launch_tiled_tape(const Planes& P, int R, int src, int iters, int pass,
+                      const SolveConsts& c, float* tape, long long tape_plane, int tape_first,
+                      void* stream) {
+  int tx, ty;
+  if (!tiles_of<kTapeKX, kTapeKY, kTapeNTY>(P, R, &tx, &ty) || iters > R || iters < 1)
+    return (int)cudaErrorInvalidValue;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(tx * ty);
+  lc.blockDim = dim3(32, kTapeNTY);
+  lc.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  if (tape)
+    return (int)cudaLaunchKernelEx(&lc, k_tiled<kTapeKX, kTapeKY, kTapeNTY, float, 2>, P, src,
+                                   iters, R, c, tx, BatchRef{nullptr, nullptr, nullptr, nullptr},
+                                   pass, PrologueConsts{}, tape, tape_plane, tape_first);
+  return (int)cudaLaunchKernelEx(&lc, k_tiled<kTapeKX, kTapeKY, kTapeNTY, float, 0>, P, src,
+                                 iters, R, c, tx, BatchRef{nullptr, nullptr, nullptr, nullptr},
+                                 pass, PrologueConsts{}, (float*)nullptr, 0LL, 0);
 }
 
 int tiled_front_fusable(const SolverCfg& cfg, int storage) {
