@@ -337,7 +337,8 @@ int evr_unrolled_forward(const float* tx, const float* ty, const float* f, const
 
 /* Reverse mode after evr_unrolled_forward with the same arguments and workspace:
  * from gu_K = dL/du_K and gp_K = dL/dp_K (NULL means 0), recompute each checkpoint
- * segment and walk the adjoint back: gu0 = dL/du0 and gp0 = dL/dp0 (either may be
+ * segment (states, primal arguments v and ubar of every iteration, kept in the
+ * workspace) and walk the adjoint back: gu0 = dL/du0 and gp0 = dL/dp0 (either may be
  * NULL), gf = dL/df, and glambda_dev[0] = dL/dlambda summed over the n images (device
  * double, FP64 reduction).  Clamped pixels and the projection are differentiated on
  * their active side. */

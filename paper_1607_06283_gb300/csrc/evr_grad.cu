@@ -106,26 +106,9 @@ __global__ void k_metric(Geo g, const float* tx, const float* ty, float* iG, flo
   sG[i] = sqrtf(G);
 }
 
-// ---- forward iteration (reads state k, writes state k+1 and ubar) ----
-// u_out may be NULL (only ubar wanted); v_out, when not NULL, receives the primal
-// argument v = u + tau div_g p, which the backward step reuses.
-__global__ void k_f_primal(Geo g, Coef c, Met m, const float* f, const float* u,
-                           const float* p, float* u_out, float* ub, float* v_out) {
-  PIXEL
-  float v = u[i] + c.tau * div_g(g, m, p, x, yl, i);
-  float beta = c.tau * c.lambda * m.sG[i];
-  float d = v - beta;
-  float r = 0.5f * (d + sqrtf(d * d + 4.0f * beta * f[i]));
-  float un = fminf(fmaxf(r, c.u_min), c.u_max);
-  if (u_out) u_out[i] = un;
-  ub[i] = 2.0f * un - u[i];
-  if (v_out) v_out[i] = v;
-}
-
-
 // ---- backward of one iteration from state (u, p) ----
 // step 1: the adjoint through the projection, apt = J_proj ap_next, written scaled by
-// sigma (it is what L_g^T acts on); ubar is the recomputed one of this iteration.
+// sigma (it is what L_g^T acts on); ubar is this iteration's, from the tape.
 // ap_next, the adjoint of the next iteration's p, is read from `ap` for the last
 // iteration, else formed here from that iteration's sigma apt (in `sapt`, updated in
 // place: each pixel reads and writes only its own entries) and tau a_v (`tav`):
@@ -162,8 +145,8 @@ __global__ void k_b_dual(Geo g, Coef c, Met m, const float* ub, const float* p,
   sapt[2 * g.plane + i] = c.sigma * a3;
 }
 
-// step 2: a_ub = -div_g(sigma apt); the primal step backwards from the recomputed
-// argument v.  Writes the new au (in place), tau * a_v, accumulates df, and writes this
+// step 2: a_ub = -div_g(sigma apt); the primal step backwards from this iteration's
+// argument v (from the tape).  Writes the new au (in place), tau * a_v, accumulates df, and writes this
 // block's FP64 sum of the lambda-gradient terms to glam_part[blk] (one slot per block and
 // iteration: the final sum has a fixed order).
 __global__ void __launch_bounds__(256) k_b_primal(Geo g, Coef c, Met m, const float* f,
@@ -285,9 +268,8 @@ __global__ void k_data_image_bwd(Geo g, const float* f, const float* u_prev, con
 
 struct Workspace {
   float* ck;       // n_ck checkpoints x 4 planes
-  float* tape;     // max(every, 2) states x 4 planes
-  float* ub;       // 1 plane
-  float* v;        // 1 plane: the primal argument of the iteration being reversed
+  float* tape;     // max(every, 2) + 1 slots x 6 planes: u p1 p2 p3 of a state, then the
+                   // v and ubar of the iteration that starts from it
   float* sapt;     // 3 planes
   float* au;       // 1 plane
   float* ap;       // 3 planes
@@ -317,9 +299,7 @@ size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspac
   };
   Workspace t;
   t.ck = (float*)take(fpl * 4 * (size_t)(n_ck > 0 ? n_ck : 1));
-  t.tape = (float*)take(fpl * 4 * (size_t)(every > 2 ? every : 2));  // >= 2: forward ping-pong
-  t.ub = (float*)take(fpl);
-  t.v = (float*)take(fpl);
+  t.tape = (float*)take(fpl * 6 * (size_t)((every > 2 ? every : 2) + 1));
   t.sapt = (float*)take(fpl * 3);
   t.au = (float*)take(fpl);
   t.ap = (float*)take(fpl * 3);
@@ -462,32 +442,27 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
   const int n_ck = (K + every - 1) / every;
   for (int cseg = n_ck - 1; cseg >= 0; --cseg) {
     const int k0 = cseg * every, k1 = (k0 + every < K) ? k0 + every : K;
-    // recompute states k0 .. k1-1 into the tape (slot j = state k0 + j): the checkpoint
-    // into slot 0 and into the passes' first ping-pong state, then tiled passes that
-    // write every state they produce into the tape
+    // recompute iterations k0 .. k1-1 into the tape (slot j: state k0 + j, then the v
+    // and ubar of iteration k0 + j): the checkpoint into slot 0 and into the passes'
+    // first ping-pong state, then tiled passes that write what every iteration computes
     k_copy<<<grd, blk, 0, st>>>(g4, w.ck + (size_t)cseg * 4 * fpl, w.tape, 4);
-    if (k1 - k0 > 1) {
-      k_copy<<<grd, blk, 0, st>>>(g4, w.ck + (size_t)cseg * 4 * fpl, w.xs, 4);
-      int src = 0;
-      for (int done = 0, pass = 0; done < k1 - k0 - 1; ++pass) {
-        const int left = k1 - k0 - 1 - done;
-        const int r = left < kUnrolledR ? left : kUnrolledR;
-        if (evr::launch_tiled_tape(PR, kUnrolledR, src, r, pass, sc, w.tape, (long long)fpl,
-                                   done, st))
-          return EVR_ERR_CUDA;
-        src ^= 1;
-        done += r;
-      }
+    k_copy<<<grd, blk, 0, st>>>(g4, w.ck + (size_t)cseg * 4 * fpl, w.xs, 4);
+    for (int done = 0, pass = 0, src = 0; done < k1 - k0; ++pass) {
+      const int left = k1 - k0 - done;
+      const int r = left < kUnrolledR ? left : kUnrolledR;
+      if (evr::launch_tiled_tape(PR, kUnrolledR, src, r, pass, sc, w.tape, (long long)fpl,
+                                 done, st))
+        return EVR_ERR_CUDA;
+      src ^= 1;
+      done += r;
     }
     for (int k = k1 - 1; k >= k0; --k) {
-      float* s0 = w.tape + (size_t)(k - k0) * 4 * fpl;
-      // ubar and the primal argument v of iteration k (u_{k+1} itself is not needed)
-      k_f_primal<<<grd, blk, 0, st>>>(g4, c, m, f, s0, s0 + fpl, nullptr, w.ub, w.v);
+      const float* s0 = w.tape + (size_t)(k - k0) * 6 * fpl;
       // the adjoint of p_{k+1}: the given one for the last iteration, else from the
       // reversed iteration k + 1 (fused here)
-      k_b_dual<<<grd, blk, 0, st>>>(g4, c, m, w.ub, s0 + fpl, w.ap,
+      k_b_dual<<<grd, blk, 0, st>>>(g4, c, m, s0 + 5 * fpl, s0 + fpl, w.ap,
                                     k == K - 1 ? nullptr : w.tav, w.sapt);
-      k_b_primal<<<grd, blk, 0, st>>>(g4, c, m, f, w.v, w.sapt, w.au, w.tav, gf,
+      k_b_primal<<<grd, blk, 0, st>>>(g4, c, m, f, s0 + 4 * fpl, w.sapt, w.au, w.tav, gf,
                                       w.glam + (size_t)k * nblk);
     }
   }

@@ -161,6 +161,7 @@ struct Tile {
   // 2 beta f) with beta = tau lambda sqrt(G), or L2 (1 / (1 + beta), beta f, unused).
   float2 E1[KP], E2[KP], E3[KP], E4[KP], E5[KP], E6[KP], SG[KP];
   float2 D1[KP], D2[KP], D3[KP];
+  float2 vs[KP], ubs[KP];  // tape mode: the last iteration's primal argument and ubar
   int gx0, gy0, R, OW, OH;
 
   __device__ __forceinline__ int lx(int k) const { return threadIdx.x + 32 * (k / KY); }
@@ -299,18 +300,23 @@ struct Tile {
       }
   }
 
-  // The owned pixels' state (u, p) into one slot of a tape: 4 FP32 planes of
-  // `plane` floats each (pitched like the stream's planes).
-  __device__ __forceinline__ void store_tape(float* slot, long long plane, const Planes& P) {
+  // Tape mode, after an iteration: its primal argument v and ubar into planes 4 and 5
+  // of the slot of the state it started from, and the new state (u, p) into planes 0-3
+  // of the next slot (6 FP32 planes of `plane` floats per slot, pitched like the
+  // stream's planes; owned pixels).
+  __device__ __forceinline__ void store_tape(float* from, float* next, long long plane,
+                                             const Planes& P) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int j = k >> 1, h = k & 1;
       if (owned(k) && on(k, P.W, P.H)) {
         const size_t i = gidx(P, k);
-        slot[i] = el(u[j], h);
-        slot[plane + i] = el(p1[j], h);
-        slot[2 * plane + i] = el(p2[j], h);
-        slot[3 * plane + i] = el(p3[j], h);
+        from[4 * plane + i] = el(vs[j], h);
+        from[5 * plane + i] = el(ubs[j], h);
+        next[i] = el(u[j], h);
+        next[plane + i] = el(p1[j], h);
+        next[2 * plane + i] = el(p2[j], h);
+        next[3 * plane + i] = el(p3[j], h);
       }
     }
   }
@@ -343,7 +349,8 @@ struct Tile {
   // One primal-dual iteration over the extended tile (two CTA barriers).
   // L2: the data term of Eq. 7 instead of KL (a template argument, so that the loop body
   // carries no branch on it).
-  template <bool L2>
+  // SAVE: keep this iteration's primal argument v and ubar in vs, ubs (tape mode).
+  template <bool L2, bool SAVE = false>
   __device__ __forceinline__ void iterate(TileSmem<KX, KY, NTY, ST>& sm, const SolveConsts& c) {
     float2 q1r[KP], q2r[KP];
     const int ty0 = threadIdx.y;
@@ -369,6 +376,7 @@ struct Tile {
                                      q2r[j].x);
       const float2 div = add2(fma2(one_neg, q1m, q1r[j]), fma2(one_neg, q2m, q2r[j]));
       const float2 v = fma2(tau2, div, u[j]);
+      if constexpr (SAVE) vs[j] = v;
       float2 un;
       if constexpr (L2) {
         un = mul2(add2(v, D2[j]), D1[j]);
@@ -390,6 +398,7 @@ struct Tile {
       ub.y = S::rnd(ub.y);
       u[j] = un;
       q1r[j] = ub;  // from here on: ubar of pair j
+      if constexpr (SAVE) ubs[j] = ub;
       sm.ub[ly(k0) / 2][lx(k0)] = S::enc2(ub);
       if (k0 % KY == 0) sm.ubfirst[ty0][lx(k0)] = S::enc(ub.x);
     }
@@ -483,9 +492,9 @@ constexpr int kTiledMinBlocks =
 
 // MODE 0: plain passes.  MODE 1 (FRONT): the packet's front launch is fused into the
 // passes (instantiated only for tiles without a register cap, kTiledMinBlocks == 1).
-// MODE 2 (tape, FP32 only): after iteration it of this launch the owned state is also
-// written to tape slot tape_first + it + 1 (slot stride 4 tape_plane floats), for the
-// reverse pass of the unrolled solve.
+// MODE 2 (tape, FP32 only): iteration it of this launch also writes its v and ubar into
+// tape slot tape_first + it and the state it produces into slot tape_first + it + 1
+// (slot stride 6 tape_plane floats), for the reverse pass of the unrolled solve.
 template <int KX, int KY, int NTY, typename ST, int MODE>
 __global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>))
     k_tiled(Planes P, int src, int iters, int R, SolveConsts c, int tiles_x, BatchRef B,
@@ -532,10 +541,11 @@ __global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>))
   if constexpr (MODE == 2) {
     for (int it = 0; it < iters; ++it) {
       if (c.data_term)
-        T.template iterate<true>(sm, c);
+        T.template iterate<true, true>(sm, c);
       else
-        T.template iterate<false>(sm, c);
-      T.store_tape(tape + (long long)(tape_first + it + 1) * 4 * tape_plane, tape_plane, sP);
+        T.template iterate<false, true>(sm, c);
+      float* from = tape + (long long)(tape_first + it) * 6 * tape_plane;
+      T.store_tape(from, from + 6 * tape_plane, tape_plane, sP);
     }
   } else {
     if (c.data_term)
