@@ -320,7 +320,7 @@ const char* evr_batch_solver_name(evr_batch* b);
  * tx, ty are L_x t, L_y t of the packet (evr_get_state EVR_STATE_TX / EVR_STATE_TY).
  * All work is queued on cuda_stream (NULL: legacy default stream).  Errors:
  * EVR_ERR_INVALID_ARG (null pointer, W or H <= 0, pitch < W, n < 1, n*H > 524280,
- * K < 1, every < 1), EVR_ERR_CUDA. */
+ * n*H*pitch >= 2^31, K < 1, every < 1), EVR_ERR_CUDA. */
 
 /* Workspace bytes for evr_unrolled_forward/backward (0 for invalid sizes). */
 size_t evr_unrolled_workspace_bytes(int W, int H, int pitch, int n, int K, int every);
@@ -338,10 +338,12 @@ int evr_unrolled_forward(const float* tx, const float* ty, const float* f, const
 /* Reverse mode after evr_unrolled_forward with the same arguments and workspace:
  * from gu_K = dL/du_K and gp_K = dL/dp_K (NULL means 0), recompute each checkpoint
  * segment (states, primal arguments v and ubar of every iteration, kept in the
- * workspace) and walk the adjoint back: gu0 = dL/du0 and gp0 = dL/dp0 (either may be
- * NULL), gf = dL/df, and glambda_dev[0] = dL/dlambda summed over the n images (device
- * double, FP64 reduction).  Clamped pixels and the projection are differentiated on
- * their active side. */
+ * workspace) and walk the adjoint back on tiled passes of a few iterations each: gu0 =
+ * dL/du0 and gp0 = dL/dp0 (either may be NULL), gf = dL/df, and glambda_dev[0] =
+ * dL/dlambda summed over the n images (device double: FP32 sums over 64 pixels per
+ * iteration, reduced in FP64 in a fixed order).  Clamped pixels and the projection are
+ * differentiated on their active side; 1/|p| and 1/s of the KL root are MUFU reciprocal
+ * square roots (a few ulp). */
 int evr_unrolled_backward(const float* tx, const float* ty, const float* f, int W, int H,
                           int pitch, int n, float lambda, float tau, float sigma, float u_min,
                           float u_max, int K, int every, void* workspace, const float* gu_K,

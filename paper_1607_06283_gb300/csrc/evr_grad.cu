@@ -1,9 +1,9 @@
 // evr_grad.cu -- differentiation of one packet's solve (K unrolled iterations of
 // Eq. cont_iterates with Eq. update_rules) by a hand-written adjoint, with (u, p)
 // checkpoints every `every` iterations.  The iterations themselves (forward, and the
-// recomputation of each checkpoint segment) are the solver's tiled FP32 passes; the
-// adjoint kernels use IEEE division and square root; the lambda gradient and the
-// contrast-threshold sums are reduced in FP64.
+// recomputation of each checkpoint segment) are the solver's tiled FP32 passes, and so
+// is the reverse pass (k_rev_tiled); the lambda gradient is summed in FP32 per warp and
+// iteration and in FP64 from there, the contrast-threshold sums in FP64.
 //
 // All memory (inputs, outputs and the workspace) belongs to the caller; nothing here
 // allocates.  Planes are H rows of `pitch` floats; a dual variable is 3 such planes
@@ -46,38 +46,13 @@ __device__ __forceinline__ void metric(const Met& m, size_t i, float& a, float& 
   iG = m.iG[i];
 }
 
-// M^T p with M = (1/G)[[1+b^2,-ab],[-ab,1+a^2],[a,b]] (Eq. 3)
-__device__ __forceinline__ void MT(float a, float b, float iG, float p1, float p2, float p3,
-                                   float& q1, float& q2) {
-  float z = b * p1 - a * p2;
-  q1 = iG * (p1 + b * z + a * p3);
-  q2 = iG * (p2 - a * z + b * p3);
-}
-
+// M (ux, uy) with M = (1/G)[[1+b^2,-ab],[-ab,1+a^2],[a,b]] (Eq. 3)
 __device__ __forceinline__ void Mg(float a, float b, float iG, float ux, float uy, float& g1,
                                    float& g2, float& g3) {
   float w = b * ux - a * uy;
   g1 = iG * (ux + b * w);
   g2 = iG * (uy - a * w);
   g3 = iG * (a * ux + b * uy);
-}
-
-// div(M^T q) at (x, y) for a 3-plane field q (div_g q = -L_g^T q); yl = row in the member
-__device__ __forceinline__ float div_g(const Geo& g, const Met& m, const float* q, int x, int yl,
-                                       size_t i) {
-  float a, b, iG, q1, q2, q1m = 0.0f, q2m = 0.0f, d;
-  metric(m, i, a, b, iG);
-  MT(a, b, iG, q[i], q[g.plane + i], q[2 * g.plane + i], q1, q2);
-  if (x > 0) {
-    metric(m, i - 1, a, b, iG);
-    MT(a, b, iG, q[i - 1], q[g.plane + i - 1], q[2 * g.plane + i - 1], q1m, d);
-  }
-  if (yl > 0) {
-    const size_t j = i - g.pitch;
-    metric(m, j, a, b, iG);
-    MT(a, b, iG, q[j], q[g.plane + j], q[2 * g.plane + j], d, q2m);
-  }
-  return ((x < g.W - 1) ? q1 : 0.0f) - q1m + ((yl < g.Hm - 1) ? q2 : 0.0f) - q2m;
 }
 
 // L_g w at (x, y) for a scalar plane w
@@ -106,96 +81,202 @@ __global__ void k_metric(Geo g, const float* tx, const float* ty, float* iG, flo
   sG[i] = sqrtf(G);
 }
 
-// ---- backward of one iteration from state (u, p) ----
-// step 1: the adjoint through the projection, apt = J_proj ap_next, written scaled by
-// sigma (it is what L_g^T acts on); ubar is this iteration's, from the tape.
-// ap_next, the adjoint of the next iteration's p, is read from `ap` for the last
-// iteration, else formed here from that iteration's sigma apt (in `sapt`, updated in
-// place: each pixel reads and writes only its own entries) and tau a_v (`tav`):
-// ap_next = apt - L_g(tau a_v).
-__global__ void k_b_dual(Geo g, Coef c, Met m, const float* ub, const float* p,
-                         const float* ap, const float* tav, float* sapt) {
-  PIXEL
-  float g1, g2, g3;
-  float a1, a2, a3;
-  if (tav) {
-    Lg(g, m, tav, x, yl, i, g1, g2, g3);
-    a1 = sapt[i] / c.sigma - g1;
-    a2 = sapt[g.plane + i] / c.sigma - g2;
-    a3 = sapt[2 * g.plane + i] / c.sigma - g3;
-  } else {
-    a1 = ap[i];
-    a2 = ap[g.plane + i];
-    a3 = ap[2 * g.plane + i];
-  }
-  Lg(g, m, ub, x, yl, i, g1, g2, g3);
-  const float sG = m.sG[i];
-  float t1 = p[i] + c.sigma * g1, t2 = p[g.plane + i] + c.sigma * g2,
-        t3 = p[2 * g.plane + i] + c.sigma * g3;
-  float nrm = sqrtf(t1 * t1 + t2 * t2 + t3 * t3);
-  if (nrm > sG) {
-    float dot = (t1 * a1 + t2 * a2 + t3 * a3) / (nrm * nrm);
-    float s = sG / nrm;
-    a1 = s * (a1 - t1 * dot);
-    a2 = s * (a2 - t2 * dot);
-    a3 = s * (a3 - t3 * dot);
-  }
-  sapt[i] = c.sigma * a1;
-  sapt[g.plane + i] = c.sigma * a2;
-  sapt[2 * g.plane + i] = c.sigma * a3;
-}
+// ---- the reverse pass, tiled ----
+// One launch reverses up to kRevR consecutive iterations k_hi, k_hi - 1, ... of one
+// checkpoint segment on overlapped tiles: a 32 x 2 kRevNTY tile (one lane per column,
+// a vertical pair of pixels per thread) owns its interior and carries a kRevR-pixel
+// halo.  Reversing an iteration reads tau a_v of the later iteration at x+1 and y+1 (in
+// L_g) and the new a_pt at x-1 and y-1 (in div_g), so, as in the forward, the values
+// stay exact on the tile shrunk by one pixel per side and iteration.  The adjoint state
+// (a_u, a_pt, tau a_v and the accumulated dL/df) stays in registers across the launch's
+// iterations; per iteration only the tape's p, v and ubar are read.
+//
+// Reversing iteration k (state k = tape slot, adjoints of u_{k+1}, p_{k+1} given):
+//   a_p(k+1) = a_pt(k+1) - L_g(tau a_v(k+1))   (the given one if k = K-1)
+//   projection adjoint: pt = p_k + sigma L_g ubar_k; outside the ball
+//     a_pt = (sqrt(G)/|pt|) (a_p - pt (pt . a_p) / |pt|^2), else a_pt = a_p
+//   a_ubar = -div_g(sigma a_pt)
+//   KL root r(v, beta, f) with d = v - beta, s = sqrt(d^2 + 4 beta f):
+//     a_r = (a_u + 2 a_ubar) where r lies inside [u_min, u_max], else 0
+//     a_v = a_r (1 + d / s) / 2;  dL/df += a_r beta / s;
+//     dL/dlambda += a_r (-1 + (2 f - v + beta) / s) / 2 * tau sqrt(G)
+//   a_u(k) = -a_ubar + a_v
+// 1/|pt| and 1/s are MUFU reciprocal square roots (no divisions).  The lambda terms are
+// summed in FP32 over each warp's 64 pixels in a fixed order and in FP64 from there on
+// (GB300 issues FP64 arithmetic at a small fraction of the FP32 rate).
+constexpr int kRevR = 4;
+constexpr int kRevNTY = 16;
 
-// step 2: a_ub = -div_g(sigma apt); the primal step backwards from this iteration's
-// argument v (from the tape).  Writes the new au (in place), tau * a_v, accumulates df, and writes this
-// block's FP64 sum of the lambda-gradient terms to glam_part[blk] (one slot per block and
-// iteration: the final sum has a fixed order).
-__global__ void __launch_bounds__(256) k_b_primal(Geo g, Coef c, Met m, const float* f,
-                                                  const float* v_in, const float* sapt,
-                                                  float* au, float* tav, float* gf,
-                                                  double* glam_part) {
-  __shared__ double s_l[256];
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int t = threadIdx.y * blockDim.x + threadIdx.x;
-  double lam_term = 0.0;
-  if (x < g.W && y < g.H) {
-    const size_t i = (size_t)y * g.pitch + x;
-    const int yl = y % g.Hm;
-    const float sG = m.sG[i];
-    const float aub = -div_g(g, m, sapt, x, yl, i);
-    const float v = v_in[i];
-    const float beta = c.tau * c.lambda * sG;
-    const float d = v - beta;
-    const float fi = f[i];
-    const float s = sqrtf(d * d + 4.0f * beta * fi);
-    const float r = 0.5f * (d + s);
-    const float aun = au[i] + 2.0f * aub;
-    const float ar = (r < c.u_min || r > c.u_max) ? 0.0f : aun;
-    const float av = ar * 0.5f * (1.0f + d / s);
-    gf[i] += ar * (beta / s);
-    lam_term = (double)(ar * 0.5f * (-1.0f + (2.0f * fi - v + beta) / s)) *
-               ((double)c.tau * (double)sG);
-    au[i] = -aub + av;
-    tav[i] = c.tau * av;
+struct RevArgs {
+  Geo g;
+  Coef c;
+  Met m;
+  const float* f;
+  const float* tape;  // slots of 6 planes (u p1 p2 p3 v ubar), plane stride g.plane
+  int slot_hi;        // tape slot of iteration k_hi
+  int k_hi, iters;
+  int first;          // iteration k_hi is the last one: its a_p(k+1) is given in a_in
+  const float* a_in;  // a_u, then a_pt (3 planes), then tau a_v: 5 planes
+  float* a_out;
+  float* gf;
+  double* glam;       // per (iteration, tile, warp) lambda sums
+  int tiles_x, tiles_total;
+};
+
+__global__ void __launch_bounds__(32 * kRevNTY, 2) k_rev_tiled(RevArgs A) {
+  constexpr int NT = kRevNTY, EW = 32, EH = 2 * NT, R = kRevR;
+  constexpr int OW = EW - 2 * R, OH = EH - 2 * R;
+  __shared__ float tv[EH + 1][EW + 1];  // tau a_v; column EW and row EH: zero pads
+  __shared__ float q1s[EH][EW + 1];     // (M^T sigma a_pt)_1 masked; column 0: zero pad
+  __shared__ float q2s[EH + 1][EW];     // (M^T sigma a_pt)_2 masked; row 0: zero pad
+  const Geo& g = A.g;
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int tile = blockIdx.x;
+  const int gx0 = (tile % A.tiles_x) * OW - R, gy0 = (tile / A.tiles_x) * OH - R;
+  const int x = gx0 + lane;
+  const float tau = A.c.tau, sigma = A.c.sigma;
+  float E1[2], E2[2], E3[2], E4[2], E5[2], E6[2], sg[2], fi[2];
+  float au[2], a1[2], a2[2], a3[2], tav[2], gfa[2];
+  bool in[2], own[2];
+  unsigned idx[2];     // pixel index (planes hold fewer than 2^31 floats)
+  unsigned ydiff = 0;  // bit h: pixel h has a y + 1 neighbour in its member
+  for (int h = 0; h < 2; ++h) {
+    const int ly = 2 * ty + h, y = gy0 + ly;
+    in[h] = x >= 0 && x < g.W && y >= 0 && y < g.H;
+    own[h] = in[h] && lane >= R && lane < R + OW && ly >= R && ly < R + OH;
+    E1[h] = E2[h] = E3[h] = E4[h] = E5[h] = E6[h] = sg[h] = fi[h] = 0.0f;
+    au[h] = a1[h] = a2[h] = a3[h] = tav[h] = gfa[h] = 0.0f;
+    idx[h] = 0;
+    if (in[h]) {
+      const unsigned i = (unsigned)y * (unsigned)g.pitch + (unsigned)x;
+      const int yl = y % g.Hm;
+      const float mx = x < g.W - 1 ? 1.0f : 0.0f, my = yl < g.Hm - 1 ? 1.0f : 0.0f;
+      idx[h] = i;
+      if (yl < g.Hm - 1) ydiff |= 1u << h;
+      const float a = A.m.tx[i], b = A.m.ty[i], ig = A.m.iG[i];
+      const float m12 = -(ig * (a * b));
+      E1[h] = mx * (ig * fmaf(b, b, 1.0f));
+      E2[h] = mx * m12;
+      E3[h] = mx * (ig * a);
+      E4[h] = my * m12;
+      E5[h] = my * (ig * fmaf(a, a, 1.0f));
+      E6[h] = my * (ig * b);
+      sg[h] = A.m.sG[i];
+      fi[h] = A.f[i];
+      au[h] = A.a_in[i];
+      a1[h] = A.a_in[g.plane + i];
+      a2[h] = A.a_in[2 * g.plane + i];
+      a3[h] = A.a_in[3 * g.plane + i];
+      tav[h] = A.a_in[4 * g.plane + i];
+      if (own[h]) gfa[h] = A.gf[i];
+    }
+    tv[ly][lane] = tav[h];
   }
-  s_l[t] = lam_term;
+  const int tid = ty * 32 + lane;
+  for (int i = tid; i < EH + 1; i += 32 * NT) tv[i][EW] = 0.0f;
+  for (int i = tid; i < EW; i += 32 * NT) {
+    tv[EH][i] = 0.0f;
+    q2s[0][i] = 0.0f;
+  }
+  for (int i = tid; i < EH; i += 32 * NT) q1s[i][0] = 0.0f;
   __syncthreads();
-  for (int h = 128; h > 0; h >>= 1) {
-    if (t < h) s_l[t] += s_l[t + h];
+  const float tl = tau * A.c.lambda;
+  for (int it = 0; it < A.iters; ++it) {
+    const float* slot = A.tape + (size_t)(A.slot_hi - it) * 6 * g.plane;
+    // projection adjoint
+    for (int h = 0; h < 2; ++h) {
+      const int ly = 2 * ty + h;
+      float b1 = a1[h], b2 = a2[h], b3 = a3[h];
+      if (!(A.first && it == 0)) {
+        const float dx = tv[ly][lane + 1] - tav[h], dy = tv[ly + 1][lane] - tav[h];
+        b1 -= fmaf(E4[h], dy, E1[h] * dx);
+        b2 -= fmaf(E5[h], dy, E2[h] * dx);
+        b3 -= fmaf(E6[h], dy, E3[h] * dx);
+      }
+      float p1 = 0.0f, p2 = 0.0f, p3 = 0.0f, ux = 0.0f, uy = 0.0f;
+      if (in[h]) {
+        const unsigned i = idx[h];
+        p1 = slot[g.plane + i];
+        p2 = slot[2 * g.plane + i];
+        p3 = slot[3 * g.plane + i];
+        const float* ubp = slot + 5 * g.plane;
+        const float ub = ubp[i];
+        // the x + 1 and y + 1 neighbours where the differences exist, else the pixel
+        // itself (those differences are masked out)
+        ux = ubp[x < g.W - 1 ? i + 1 : i] - ub;
+        uy = ubp[(ydiff >> h) & 1u ? i + (unsigned)g.pitch : i] - ub;
+      }
+      const float t1 = fmaf(sigma, fmaf(E4[h], uy, E1[h] * ux), p1);
+      const float t2 = fmaf(sigma, fmaf(E5[h], uy, E2[h] * ux), p2);
+      const float t3 = fmaf(sigma, fmaf(E6[h], uy, E3[h] * ux), p3);
+      const float n2 = fmaf(t1, t1, fmaf(t2, t2, t3 * t3));
+      const float inv = rsqrtf(n2);  // n2 = 0: inf, and n2 * inv is NaN: inside the ball
+      if (n2 * inv > sg[h]) {
+        const float dot = fmaf(t1, b1, fmaf(t2, b2, t3 * b3)) * (inv * inv);
+        const float sc = sg[h] * inv;
+        b1 = sc * fmaf(-t1, dot, b1);
+        b2 = sc * fmaf(-t2, dot, b2);
+        b3 = sc * fmaf(-t3, dot, b3);
+      }
+      a1[h] = b1;
+      a2[h] = b2;
+      a3[h] = b3;
+      q1s[ly][lane + 1] = sigma * fmaf(E3[h], b3, fmaf(E2[h], b2, E1[h] * b1));
+      q2s[ly + 1][lane] = sigma * fmaf(E6[h], b3, fmaf(E5[h], b2, E4[h] * b1));
+    }
+    __syncthreads();
+    // primal adjoint
+    float lam = 0.0f;
+    for (int h = 0; h < 2; ++h) {
+      const int ly = 2 * ty + h;
+      const float div = (q1s[ly][lane + 1] - q1s[ly][lane]) + (q2s[ly + 1][lane] - q2s[ly][lane]);
+      const float aub = -div;
+      float av = 0.0f;  // outside the image: no data term (and no 0/0)
+      if (in[h]) {
+        const float v = slot[4 * g.plane + idx[h]];
+        const float beta = tl * sg[h];
+        const float d = v - beta;
+        const float disc = fmaf(d, d, 4.0f * beta * fi[h]);
+        const float rs = rsqrtf(disc);  // 1 / s
+        const float r = 0.5f * fmaf(disc, rs, d);
+        const float aun = fmaf(2.0f, aub, au[h]);
+        const float ar = (r < A.c.u_min || r > A.c.u_max) ? 0.0f : aun;
+        av = ar * 0.5f * fmaf(d, rs, 1.0f);
+        if (own[h]) {
+          gfa[h] = fmaf(ar, beta * rs, gfa[h]);
+          lam = fmaf(ar * 0.5f * fmaf(2.0f * fi[h] - v + beta, rs, -1.0f), tau * sg[h], lam);
+        }
+      }
+      au[h] = av - aub;
+      tav[h] = tau * av;
+      tv[ly][lane] = tav[h];
+    }
+    // this warp's lambda sum of the iteration, in a fixed order
+    for (int o = 16; o > 0; o >>= 1) lam += __shfl_down_sync(0xffffffffu, lam, o);
+    if (lane == 0)
+      A.glam[((size_t)(A.k_hi - it) * A.tiles_total + tile) * NT + ty] = (double)lam;
     __syncthreads();
   }
-  if (t == 0) glam_part[blockIdx.y * gridDim.x + blockIdx.x] = s_l[0];
+  for (int h = 0; h < 2; ++h) {
+    if (!own[h]) continue;
+    const unsigned i = idx[h];
+    A.a_out[i] = au[h];
+    A.a_out[g.plane + i] = a1[h];
+    A.a_out[2 * g.plane + i] = a2[h];
+    A.a_out[3 * g.plane + i] = a3[h];
+    A.a_out[4 * g.plane + i] = tav[h];
+    A.gf[i] = gfa[h];
+  }
 }
 
-// step 3: ap = apt - L_g(tau a_v)   (apt = sapt / sigma)
-__global__ void k_b_pupdate(Geo g, Coef c, Met m, const float* sapt, const float* tav,
-                            float* ap) {
+// The adjoint of p_0: a_p = a_pt - L_g(tau a_v) of the reversed iteration 0.
+__global__ void k_b_pupdate(Geo g, Met m, const float* apt, const float* tav, float* ap) {
   PIXEL
   float g1, g2, g3;
   Lg(g, m, tav, x, yl, i, g1, g2, g3);
-  ap[i] = sapt[i] / c.sigma - g1;
-  ap[g.plane + i] = sapt[g.plane + i] / c.sigma - g2;
-  ap[2 * g.plane + i] = sapt[2 * g.plane + i] / c.sigma - g3;
+  ap[i] = apt[i] - g1;
+  ap[g.plane + i] = apt[g.plane + i] - g2;
+  ap[2 * g.plane + i] = apt[2 * g.plane + i] - g3;
 }
 
 __global__ void k_zero(Geo g, float* a, int planes) {
@@ -270,21 +351,28 @@ struct Workspace {
   float* ck;       // n_ck checkpoints x 4 planes
   float* tape;     // max(every, 2) + 1 slots x 6 planes: u p1 p2 p3 of a state, then the
                    // v and ubar of the iteration that starts from it
-  float* sapt;     // 3 planes
-  float* au;       // 1 plane
-  float* ap;       // 3 planes
-  float* tav;      // 1 plane
+  float* adj;      // 2 x 5 planes: ping-pong adjoint states (a_u, a_pt, tau a_v)
+  float* ap;       // 3 planes: dL/dp0 before the copy out
   float* xs;       // 2 states x 4 planes: ping-pong buffers of the recomputing passes
   float* iG;       // 1 plane: 1/G
   float* sG;       // 1 plane: sqrt(G)
-  double* glam;    // K x (blocks of the pixel grid): per-block lambda-gradient sums
+  double* glam;    // K x (reverse tiles x warps): per-warp lambda-gradient sums
   double* partials;  // 4 * kRedBlocks doubles
 };
 
 constexpr int kBlkX = 32, kBlkY = 8;  // pixel-kernel block
 
-size_t pixel_blocks(int W, int H) {
-  return (size_t)((W + kBlkX - 1) / kBlkX) * ((H + kBlkY - 1) / kBlkY);
+// Tiles of the reverse pass over a W x H image (kRevR-pixel halos).
+void rev_tiles(int W, int H, int* tx, int* total) {
+  const int OW = 32 - 2 * kRevR, OH = 2 * kRevNTY - 2 * kRevR;
+  *tx = (W + OW - 1) / OW;
+  *total = *tx * ((H + OH - 1) / OH);
+}
+
+size_t lam_slots(int W, int H) {
+  int tx, total;
+  rev_tiles(W, H, &tx, &total);
+  return (size_t)total * kRevNTY;
 }
 
 size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspace* w) {
@@ -300,14 +388,12 @@ size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspac
   Workspace t;
   t.ck = (float*)take(fpl * 4 * (size_t)(n_ck > 0 ? n_ck : 1));
   t.tape = (float*)take(fpl * 6 * (size_t)((every > 2 ? every : 2) + 1));
-  t.sapt = (float*)take(fpl * 3);
-  t.au = (float*)take(fpl);
+  t.adj = (float*)take(fpl * 10);
   t.ap = (float*)take(fpl * 3);
-  t.tav = (float*)take(fpl);
   t.xs = (float*)take(fpl * 8);
   t.iG = (float*)take(fpl);
   t.sG = (float*)take(fpl);
-  t.glam = (double*)take(sizeof(double) * (size_t)K * pixel_blocks(W, H));
+  t.glam = (double*)take(sizeof(double) * (size_t)K * lam_slots(W, H));
   t.partials = (double*)take(sizeof(double) * 4 * kRedBlocks);
   if (w) *w = t;
   return off;
@@ -349,8 +435,9 @@ evr::Planes unrolled_planes(int W, int H, int Hm, int pitch, const float* tx, co
 int check_args(int W, int H, int pitch, int K, int every, int n) {
   if (W <= 0 || H <= 0 || pitch < W || K < 1 || every < 1 || n < 1) return EVR_ERR_INVALID_ARG;
   if ((long long)H * n > 65535LL * 8) return EVR_ERR_INVALID_ARG;  // grid.y limit
-  if ((long long)K * (long long)pixel_blocks(W, H * n) > 0x7fffffffLL)
-    return EVR_ERR_INVALID_ARG;  // per-block lambda sums are indexed with int
+  if ((long long)pitch * H * n >= 0x7fffffffLL) return EVR_ERR_INVALID_ARG;  // 32-bit indices
+  if ((long long)K * (long long)lam_slots(W, H * n) > 0x7fffffffLL)
+    return EVR_ERR_INVALID_ARG;  // the lambda sums are reduced with int indices
   return EVR_OK;
 }
 
@@ -425,17 +512,31 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
   Geo g4 = g;
   g4.plane = fpl;
   dim3 blk(kBlkX, kBlkY), grd((W + kBlkX - 1) / kBlkX, (H + kBlkY - 1) / kBlkY);
-  const size_t nblk = pixel_blocks(W, H);
   k_metric<<<grd, blk, 0, st>>>(g, tx, ty, w.iG, w.sG);
   const Met m{tx, ty, w.iG, w.sG};
-  // adjoint of the final state: au = gu_K, ap = gp_K or 0; gf = 0
-  k_copy<<<grd, blk, 0, st>>>(g, gu_K, w.au, 1);
+  // adjoint of the final state into the first adjoint buffer: a_u = gu_K and, in the
+  // a_pt planes, a_p = gp_K or 0 (the first reversed iteration reads it as given);
+  // gf = 0
+  float* adj[2] = {w.adj, w.adj + 5 * fpl};
+  k_copy<<<grd, blk, 0, st>>>(g, gu_K, adj[0], 1);
   if (gp_K) {
-    for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, gp_K + k * g.plane, w.ap + k * fpl, 1);
+    for (int k = 0; k < 3; ++k)
+      k_copy<<<grd, blk, 0, st>>>(g, gp_K + k * g.plane, adj[0] + (1 + k) * fpl, 1);
   } else {
-    k_zero<<<grd, blk, 0, st>>>(g4, w.ap, 3);
+    k_zero<<<grd, blk, 0, st>>>(g4, adj[0] + fpl, 3);
   }
+  k_zero<<<grd, blk, 0, st>>>(g4, adj[0] + 4 * fpl, 1);
   k_zero<<<grd, blk, 0, st>>>(g, gf, 1);
+  RevArgs ra{};
+  ra.g = g4;
+  ra.c = c;
+  ra.m = m;
+  ra.f = f;
+  ra.tape = w.tape;
+  ra.gf = gf;
+  ra.glam = w.glam;
+  rev_tiles(W, H, &ra.tiles_x, &ra.tiles_total);
+  int cur = 0;
   const evr::Planes PR =
       unrolled_planes(W, H, Hm, pitch, tx, ty, f, w.iG, w.sG, w.xs, w.xs + 4 * fpl, fpl);
   const evr::SolveConsts sc{tau, sigma, lambda, u_min, u_max, 0};
@@ -456,23 +557,27 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
       src ^= 1;
       done += r;
     }
-    for (int k = k1 - 1; k >= k0; --k) {
-      const float* s0 = w.tape + (size_t)(k - k0) * 6 * fpl;
-      // the adjoint of p_{k+1}: the given one for the last iteration, else from the
-      // reversed iteration k + 1 (fused here)
-      k_b_dual<<<grd, blk, 0, st>>>(g4, c, m, s0 + 5 * fpl, s0 + fpl, w.ap,
-                                    k == K - 1 ? nullptr : w.tav, w.sapt);
-      k_b_primal<<<grd, blk, 0, st>>>(g4, c, m, f, s0 + 4 * fpl, w.sapt, w.au, w.tav, gf,
-                                      w.glam + (size_t)k * nblk);
+    // reverse the segment's iterations, kRevR per launch, ping-ponging the adjoint state
+    for (int k = k1 - 1; k >= k0;) {
+      const int r = (k - k0 + 1) < kRevR ? (k - k0 + 1) : kRevR;
+      ra.slot_hi = k - k0;
+      ra.k_hi = k;
+      ra.iters = r;
+      ra.first = (k == K - 1);
+      ra.a_in = adj[cur];
+      ra.a_out = adj[cur ^ 1];
+      k_rev_tiled<<<ra.tiles_total, dim3(32, kRevNTY), 0, st>>>(ra);
+      cur ^= 1;
+      k -= r;
     }
   }
-  if (gu0) k_copy<<<grd, blk, 0, st>>>(g, w.au, gu0, 1);
+  if (gu0) k_copy<<<grd, blk, 0, st>>>(g, adj[cur], gu0, 1);
   if (gp0) {  // the adjoint of p_0 from the reversed iteration 0
-    k_b_pupdate<<<grd, blk, 0, st>>>(g4, c, m, w.sapt, w.tav, w.ap);
+    k_b_pupdate<<<grd, blk, 0, st>>>(g4, m, adj[cur] + fpl, adj[cur] + 4 * fpl, w.ap);
     for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, w.ap + k * fpl, gp0 + k * g.plane, 1);
   }
-  // dL/dlambda: the K x nblk per-block sums, in index order
-  const long long nl = (long long)K * (long long)nblk;
+  // dL/dlambda: the K x (tiles x warps) sums, in index order
+  const long long nl = (long long)K * (long long)lam_slots(W, H);
   Geo gd{(int)nl, 1, (int)nl, 0, 1};
   k_red_partial<<<kRedBlocks, kRedThreads, 0, st>>>(gd, w.glam, 1, w.partials);
   k_red_final<<<1, kRedBlocks, 0, st>>>(w.partials, 1, glambda_dev);
