@@ -16,7 +16,7 @@
 namespace {
 
 constexpr int kRedBlocks = 256;
-constexpr int kRedThreads = 256;
+constexpr int kRedThreads = 1024;
 
 // n images of W x Hm stacked vertically into one W x (n Hm) image (H = n Hm): the
 // forward differences and divergences use the row within the member, so the members
@@ -102,7 +102,7 @@ __global__ void k_metric(Geo g, const float* tx, const float* ty, float* iG, flo
 //     dL/dlambda += a_r (-1 + (2 f - v + beta) / s) / 2 * tau sqrt(G)
 //   a_u(k) = -a_ubar + a_v
 // 1/|pt| and 1/s are MUFU reciprocal square roots (no divisions).  The lambda terms are
-// summed in FP32 over each warp's 64 pixels in a fixed order and in FP64 from there on
+// summed in FP32 over each tile's owned pixels in a fixed order and in FP64 from there on
 // (GB300 issues FP64 arithmetic at a small fraction of the FP32 rate).
 constexpr int kRevR = 4;
 constexpr int kRevNTY = 16;
@@ -112,14 +112,15 @@ struct RevArgs {
   Coef c;
   Met m;
   const float* f;
-  const float* tape;  // slots of 6 planes (u p1 p2 p3 v ubar), plane stride g.plane
+  const float* tape;  // slots of 5 planes (p1 p2 p3 v ubar), plane stride g.plane
   int slot_hi;        // tape slot of iteration k_hi
   int k_hi, iters;
-  int first;          // iteration k_hi is the last one: its a_p(k+1) is given in a_in
-  const float* a_in;  // a_u, then a_pt (3 planes), then tau a_v: 5 planes
-  float* a_out;
+  int first;          // iteration k_hi is the last one: its a_p(k+1) is given in a_in[1..3]
+  // a_u, a_pt (3 planes), tau a_v at the start (a null plane reads as 0) and at the end
+  const float* a_in[5];
+  float* a_out[5];
   float* gf;
-  double* glam;       // per (iteration, tile, warp) lambda sums
+  double* glam;       // per (iteration, tile) lambda sums
   int tiles_x, tiles_total;
 };
 
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2) k_rev_tiled(RevArgs A) {
   __shared__ float tv[EH + 1][EW + 1];  // tau a_v; column EW and row EH: zero pads
   __shared__ float q1s[EH][EW + 1];     // (M^T sigma a_pt)_1 masked; column 0: zero pad
   __shared__ float q2s[EH + 1][EW];     // (M^T sigma a_pt)_2 masked; row 0: zero pad
+  __shared__ float lsum[NT];            // the warps' lambda sums of an iteration
   const Geo& g = A.g;
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int tile = blockIdx.x;
@@ -163,11 +165,11 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2) k_rev_tiled(RevArgs A) {
       E6[h] = my * (ig * b);
       sg[h] = A.m.sG[i];
       fi[h] = A.f[i];
-      au[h] = A.a_in[i];
-      a1[h] = A.a_in[g.plane + i];
-      a2[h] = A.a_in[2 * g.plane + i];
-      a3[h] = A.a_in[3 * g.plane + i];
-      tav[h] = A.a_in[4 * g.plane + i];
+      au[h] = A.a_in[0] ? A.a_in[0][i] : 0.0f;
+      a1[h] = A.a_in[1] ? A.a_in[1][i] : 0.0f;
+      a2[h] = A.a_in[2] ? A.a_in[2][i] : 0.0f;
+      a3[h] = A.a_in[3] ? A.a_in[3][i] : 0.0f;
+      tav[h] = A.a_in[4] ? A.a_in[4][i] : 0.0f;
       if (own[h]) gfa[h] = A.gf[i];
     }
     tv[ly][lane] = tav[h];
@@ -181,34 +183,47 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2) k_rev_tiled(RevArgs A) {
   for (int i = tid; i < EH; i += 32 * NT) q1s[i][0] = 0.0f;
   __syncthreads();
   const float tl = tau * A.c.lambda;
+  const unsigned PL = (unsigned)g.plane;  // plane stride (< 2^31 floats, checked)
+  // x + 1 neighbour offset where the x-difference exists (else the pixel itself: that
+  // difference is masked out); y + 1: pixel 1 of the pair for pixel 0, the next thread
+  // row for pixel 1, where the y-difference exists
+  const unsigned ox = x < g.W - 1 ? 1u : 0u;
+  const unsigned oy1 = (ydiff & 2u) ? (unsigned)g.pitch : 0u;
   for (int it = 0; it < A.iters; ++it) {
-    const float* slot = A.tape + (size_t)(A.slot_hi - it) * 6 * g.plane;
+    const float* slot = A.tape + (size_t)(A.slot_hi - it) * 5 * g.plane;  // uniform
+    // the iteration's tape values of both pixels, all loads issued together
+    float p1[2], p2[2], p3[2], ub[2], ubx[2], vk[2];
+    float uby1 = 0.0f;
+    for (int h = 0; h < 2; ++h) {
+      p1[h] = p2[h] = p3[h] = ub[h] = ubx[h] = vk[h] = 0.0f;
+      if (in[h]) {
+        const unsigned i = idx[h];
+        p1[h] = slot[i];
+        p2[h] = slot[PL + i];
+        p3[h] = slot[2 * PL + i];
+        vk[h] = slot[3 * PL + i];
+        ub[h] = slot[4 * PL + i];
+        ubx[h] = slot[4 * PL + i + ox];
+        if (h == 1) uby1 = slot[4 * PL + i + oy1];
+      }
+    }
+    float q1o[2], q2o[2];  // this thread's own (M^T sigma a_pt) entries
     // projection adjoint
     for (int h = 0; h < 2; ++h) {
       const int ly = 2 * ty + h;
       float b1 = a1[h], b2 = a2[h], b3 = a3[h];
       if (!(A.first && it == 0)) {
-        const float dx = tv[ly][lane + 1] - tav[h], dy = tv[ly + 1][lane] - tav[h];
+        const float tyn = h == 0 ? tav[1] : tv[ly + 1][lane];
+        const float dx = tv[ly][lane + 1] - tav[h], dy = tyn - tav[h];
         b1 -= fmaf(E4[h], dy, E1[h] * dx);
         b2 -= fmaf(E5[h], dy, E2[h] * dx);
         b3 -= fmaf(E6[h], dy, E3[h] * dx);
       }
-      float p1 = 0.0f, p2 = 0.0f, p3 = 0.0f, ux = 0.0f, uy = 0.0f;
-      if (in[h]) {
-        const unsigned i = idx[h];
-        p1 = slot[g.plane + i];
-        p2 = slot[2 * g.plane + i];
-        p3 = slot[3 * g.plane + i];
-        const float* ubp = slot + 5 * g.plane;
-        const float ub = ubp[i];
-        // the x + 1 and y + 1 neighbours where the differences exist, else the pixel
-        // itself (those differences are masked out)
-        ux = ubp[x < g.W - 1 ? i + 1 : i] - ub;
-        uy = ubp[(ydiff >> h) & 1u ? i + (unsigned)g.pitch : i] - ub;
-      }
-      const float t1 = fmaf(sigma, fmaf(E4[h], uy, E1[h] * ux), p1);
-      const float t2 = fmaf(sigma, fmaf(E5[h], uy, E2[h] * ux), p2);
-      const float t3 = fmaf(sigma, fmaf(E6[h], uy, E3[h] * ux), p3);
+      const float uyn = h == 0 ? ((ydiff & 1u) ? ub[1] : ub[0]) : uby1;
+      const float ux = ubx[h] - ub[h], uy = in[h] ? uyn - ub[h] : 0.0f;
+      const float t1 = fmaf(sigma, fmaf(E4[h], uy, E1[h] * ux), p1[h]);
+      const float t2 = fmaf(sigma, fmaf(E5[h], uy, E2[h] * ux), p2[h]);
+      const float t3 = fmaf(sigma, fmaf(E6[h], uy, E3[h] * ux), p3[h]);
       const float n2 = fmaf(t1, t1, fmaf(t2, t2, t3 * t3));
       const float inv = rsqrtf(n2);  // n2 = 0: inf, and n2 * inv is NaN: inside the ball
       if (n2 * inv > sg[h]) {
@@ -221,19 +236,25 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2) k_rev_tiled(RevArgs A) {
       a1[h] = b1;
       a2[h] = b2;
       a3[h] = b3;
-      q1s[ly][lane + 1] = sigma * fmaf(E3[h], b3, fmaf(E2[h], b2, E1[h] * b1));
-      q2s[ly + 1][lane] = sigma * fmaf(E6[h], b3, fmaf(E5[h], b2, E4[h] * b1));
+      // rounded products (no contraction into the later differences): a neighbour's
+      // value read from shared memory and the thread's own from a register are the same
+      // number, so a pixel's result does not depend on its place in the tile
+      q1o[h] = __fmul_rn(sigma, fmaf(E3[h], b3, fmaf(E2[h], b2, E1[h] * b1)));
+      q2o[h] = __fmul_rn(sigma, fmaf(E6[h], b3, fmaf(E5[h], b2, E4[h] * b1)));
+      q1s[ly][lane + 1] = q1o[h];
+      if (h == 1) q2s[ly + 1][lane] = q2o[h];  // read by the thread row below
     }
     __syncthreads();
     // primal adjoint
     float lam = 0.0f;
     for (int h = 0; h < 2; ++h) {
       const int ly = 2 * ty + h;
-      const float div = (q1s[ly][lane + 1] - q1s[ly][lane]) + (q2s[ly + 1][lane] - q2s[ly][lane]);
+      const float q2m = h == 0 ? q2s[ly][lane] : q2o[0];
+      const float div = (q1o[h] - q1s[ly][lane]) + (q2o[h] - q2m);
       const float aub = -div;
       float av = 0.0f;  // outside the image: no data term (and no 0/0)
       if (in[h]) {
-        const float v = slot[4 * g.plane + idx[h]];
+        const float v = vk[h];
         const float beta = tl * sg[h];
         const float d = v - beta;
         const float disc = fmaf(d, d, 4.0f * beta * fi[h]);
@@ -248,35 +269,42 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2) k_rev_tiled(RevArgs A) {
         }
       }
       au[h] = av - aub;
-      tav[h] = tau * av;
+      tav[h] = __fmul_rn(tau, av);
       tv[ly][lane] = tav[h];
     }
-    // this warp's lambda sum of the iteration, in a fixed order
+    // the tile's lambda sum of the iteration, in FP32 in a fixed order (within each warp,
+    // then over the warps by warp 0)
     for (int o = 16; o > 0; o >>= 1) lam += __shfl_down_sync(0xffffffffu, lam, o);
-    if (lane == 0)
-      A.glam[((size_t)(A.k_hi - it) * A.tiles_total + tile) * NT + ty] = (double)lam;
+    if (lane == 0) lsum[ty] = lam;
     __syncthreads();
+    if (ty == 0) {
+      float t = lane < NT ? lsum[lane] : 0.0f;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) A.glam[(size_t)(A.k_hi - it) * A.tiles_total + tile] = (double)t;
+    }
   }
   for (int h = 0; h < 2; ++h) {
     if (!own[h]) continue;
     const unsigned i = idx[h];
-    A.a_out[i] = au[h];
-    A.a_out[g.plane + i] = a1[h];
-    A.a_out[2 * g.plane + i] = a2[h];
-    A.a_out[3 * g.plane + i] = a3[h];
-    A.a_out[4 * g.plane + i] = tav[h];
+    A.a_out[0][i] = au[h];
+    A.a_out[1][i] = a1[h];
+    A.a_out[2][i] = a2[h];
+    A.a_out[3][i] = a3[h];
+    A.a_out[4][i] = tav[h];
     A.gf[i] = gfa[h];
   }
 }
 
-// The adjoint of p_0: a_p = a_pt - L_g(tau a_v) of the reversed iteration 0.
-__global__ void k_b_pupdate(Geo g, Met m, const float* apt, const float* tav, float* ap) {
+// The adjoint of p_0: a_p = a_pt - L_g(tau a_v) of the reversed iteration 0 (a_pt with
+// plane stride g.plane, the output with plane stride out_plane).
+__global__ void k_b_pupdate(Geo g, Met m, const float* apt, const float* tav, float* ap,
+                            size_t out_plane) {
   PIXEL
   float g1, g2, g3;
   Lg(g, m, tav, x, yl, i, g1, g2, g3);
   ap[i] = apt[i] - g1;
-  ap[g.plane + i] = apt[g.plane + i] - g2;
-  ap[2 * g.plane + i] = apt[2 * g.plane + i] - g3;
+  ap[out_plane + i] = apt[g.plane + i] - g2;
+  ap[2 * out_plane + i] = apt[2 * g.plane + i] - g3;
 }
 
 __global__ void k_zero(Geo g, float* a, int planes) {
@@ -343,20 +371,20 @@ __global__ void k_data_image_bwd(Geo g, const float* f, const float* u_prev, con
   (void)yl;
   float e = expf(dpos * (float)npos[i] - dneg * (float)nneg[i]);
   if (g_uprev) g_uprev[i] = gf[i] * e;
-  terms[i] = (double)gf[i] * (double)f[i] * (double)npos[i];
-  terms[g.plane + i] = -(double)gf[i] * (double)f[i] * (double)nneg[i];
+  const float gff = gf[i] * f[i];  // FP32 products (GB300's FP64 rate is low), FP64 sums
+  terms[i] = (double)(gff * (float)npos[i]);
+  terms[g.plane + i] = -(double)(gff * (float)nneg[i]);
 }
 
 struct Workspace {
   float* ck;       // n_ck checkpoints x 4 planes
-  float* tape;     // max(every, 2) + 1 slots x 6 planes: u p1 p2 p3 of a state, then the
-                   // v and ubar of the iteration that starts from it
+  float* tape;     // `every` slots x 5 planes: p1 p2 p3 of the state an iteration starts
+                   // from, then its v and ubar
   float* adj;      // 2 x 5 planes: ping-pong adjoint states (a_u, a_pt, tau a_v)
-  float* ap;       // 3 planes: dL/dp0 before the copy out
-  float* xs;       // 2 states x 4 planes: ping-pong buffers of the recomputing passes
+  float* xs;       // 2 states x 4 planes: ping-pong buffers of the passes
   float* iG;       // 1 plane: 1/G
   float* sG;       // 1 plane: sqrt(G)
-  double* glam;    // K x (reverse tiles x warps): per-warp lambda-gradient sums
+  double* glam;    // K x (reverse tiles): per-tile lambda-gradient sums
   double* partials;  // 4 * kRedBlocks doubles
 };
 
@@ -372,7 +400,7 @@ void rev_tiles(int W, int H, int* tx, int* total) {
 size_t lam_slots(int W, int H) {
   int tx, total;
   rev_tiles(W, H, &tx, &total);
-  return (size_t)total * kRevNTY;
+  return (size_t)total;
 }
 
 size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspace* w) {
@@ -387,9 +415,8 @@ size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspac
   };
   Workspace t;
   t.ck = (float*)take(fpl * 4 * (size_t)(n_ck > 0 ? n_ck : 1));
-  t.tape = (float*)take(fpl * 6 * (size_t)((every > 2 ? every : 2) + 1));
+  t.tape = (float*)take(fpl * 5 * (size_t)every);
   t.adj = (float*)take(fpl * 10);
-  t.ap = (float*)take(fpl * 3);
   t.xs = (float*)take(fpl * 8);
   t.iG = (float*)take(fpl);
   t.sG = (float*)take(fpl);
@@ -405,23 +432,14 @@ size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspac
 // are split into launches, so the recomputed states equal the forward's bit for bit.
 constexpr int kUnrolledR = 5;
 
-// The two ping-pong states a0, a1 (u | p1 | p2 | p3, plane stride fpl floats) and the
-// packet's planes as the tiled passes' descriptor.
+// The packet's planes as the tiled passes' descriptor (the state buffers are set per pass).
 evr::Planes unrolled_planes(int W, int H, int Hm, int pitch, const float* tx, const float* ty,
-                            const float* f, float* iG, float* sG, float* a0, float* a1,
-                            size_t fpl) {
+                            const float* f, float* iG, float* sG) {
   evr::Planes P{};
   P.W = W;
   P.H = H;
   P.Hm = Hm;
   P.pitch = pitch;
-  float* st[2] = {a0, a1};
-  for (int b = 0; b < 2; ++b) {
-    P.u[b] = st[b];
-    P.p1[b] = st[b] + fpl;
-    P.p2[b] = st[b] + 2 * fpl;
-    P.p3[b] = st[b] + 3 * fpl;
-  }
   P.tx = const_cast<float*>(tx);
   P.ty = const_cast<float*>(ty);
   P.f = const_cast<float*>(f);
@@ -429,6 +447,51 @@ evr::Planes unrolled_planes(int W, int H, int Hm, int pitch, const float* tx, co
   P.sG = sG;
   P.storage = 0;
   return P;
+}
+
+// A state (u, p1, p2, p3): four planes anywhere (the workspace's, or the caller's).
+struct State {
+  float* u;
+  float* p[3];
+};
+
+State ws_state(float* base, size_t fpl) {
+  return State{base, {base + fpl, base + 2 * fpl, base + 3 * fpl}};
+}
+
+// One tiled pass of `iters` iterations from state a into state b (a is only read).
+int tiled_pass(evr::Planes P, const State& a, const State& b, int iters, int pass,
+               const evr::SolveConsts& sc, float* tape, size_t fpl, int tape_first,
+               cudaStream_t st) {
+  P.u[0] = a.u;
+  P.p1[0] = a.p[0];
+  P.p2[0] = a.p[1];
+  P.p3[0] = a.p[2];
+  P.u[1] = b.u;
+  P.p1[1] = b.p[0];
+  P.p2[1] = b.p[1];
+  P.p3[1] = b.p[2];
+  return evr::launch_tiled_tape(P, kUnrolledR, 0, iters, pass, sc, tape, (long long)fpl,
+                                tape_first, st);
+}
+
+// The passes of one checkpoint segment of len iterations from state `from`: through the
+// two ping-pong states xs, the last pass writing into `to` (not one of xs), or, with
+// to = NULL, into whichever of xs is free (with a tape, every iteration's p, v and ubar
+// go to tape slots 0 .. len-1).
+int segment_passes(const evr::Planes& P, const State& from, const State* to, int len,
+                   const evr::SolveConsts& sc, float* xs, float* tape, size_t fpl,
+                   cudaStream_t st) {
+  const State x[2] = {ws_state(xs, fpl), ws_state(xs + 4 * fpl, fpl)};
+  State a = from;
+  for (int done = 0, pass = 0; done < len; ++pass) {
+    const int r = (len - done) < kUnrolledR ? (len - done) : kUnrolledR;
+    const State b = (done + r == len && to) ? *to : x[pass & 1];
+    if (tiled_pass(P, a, b, r, pass, sc, tape, fpl, done, st)) return 1;
+    a = b;
+    done += r;
+  }
+  return 0;
 }
 
 // A state in the workspace is u | p1 | p2 | p3 with the 256-byte-aligned plane size.
@@ -466,29 +529,19 @@ extern "C" int evr_unrolled_forward(const float* tx, const float* ty, const floa
   const size_t fpl = ((size_t)pitch * H * 4 + 255) / 256 * 256 / 4;  // floats per plane slot
   dim3 blk(kBlkX, kBlkY), grd((W + kBlkX - 1) / kBlkX, (H + kBlkY - 1) / kBlkY);
   k_metric<<<grd, blk, 0, st>>>(g, tx, ty, w.iG, w.sG);
-  // state buffers: two ping-pong states in the tape area (u | p1 p2 p3)
-  float* su[2] = {w.tape, w.tape + 4 * fpl};
-  Geo g4 = g;
-  g4.plane = fpl;  // states use the aligned plane stride
-  // copy (u0, p0) into state 0
-  k_copy<<<grd, blk, 0, st>>>(g, u0, su[0], 1);
-  for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, p0 + k * g.plane, su[0] + (1 + k) * fpl, 1);
-  const evr::Planes P = unrolled_planes(W, H, Hm, pitch, tx, ty, f, w.iG, w.sG, su[0], su[1],
-                                        fpl);
+  // checkpoint 0 = (u0, p0); checkpoint j + 1 and the result are written by the last pass
+  // of segment j
+  k_copy<<<grd, blk, 0, st>>>(g, u0, w.ck, 1);
+  for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, p0 + k * g.plane, w.ck + (1 + k) * fpl, 1);
+  const evr::Planes P = unrolled_planes(W, H, Hm, pitch, tx, ty, f, w.iG, w.sG);
   const evr::SolveConsts sc{tau, sigma, lambda, u_min, u_max, 0};
-  int cur = 0;
-  for (int k0 = 0; k0 < K; k0 += every) {  // a checkpoint, then the segment's passes
-    k_copy<<<grd, blk, 0, st>>>(g4, su[cur], w.ck + (size_t)(k0 / every) * 4 * fpl, 4);
-    for (int left = (K - k0 < every) ? K - k0 : every, pass = 0; left > 0; ++pass) {
-      const int r = left < kUnrolledR ? left : kUnrolledR;
-      if (evr::launch_tiled_tape(P, kUnrolledR, cur, r, pass, sc, nullptr, 0, 0, st))
-        return EVR_ERR_CUDA;
-      cur ^= 1;
-      left -= r;
-    }
+  const State out{u_out, {p_out, p_out + g.plane, p_out + 2 * g.plane}};
+  for (int k0 = 0, seg = 0; k0 < K; k0 += every, ++seg) {
+    const int len = (K - k0 < every) ? K - k0 : every;
+    const State from = ws_state(w.ck + (size_t)seg * 4 * fpl, fpl);
+    const State to = (k0 + len < K) ? ws_state(w.ck + (size_t)(seg + 1) * 4 * fpl, fpl) : out;
+    if (segment_passes(P, from, &to, len, sc, w.xs, nullptr, fpl, st)) return EVR_ERR_CUDA;
   }
-  k_copy<<<grd, blk, 0, st>>>(g, su[cur], u_out, 1);
-  for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, su[cur] + (1 + k) * fpl, p_out + k * g.plane, 1);
   return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
 }
 
@@ -514,19 +567,12 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
   dim3 blk(kBlkX, kBlkY), grd((W + kBlkX - 1) / kBlkX, (H + kBlkY - 1) / kBlkY);
   k_metric<<<grd, blk, 0, st>>>(g, tx, ty, w.iG, w.sG);
   const Met m{tx, ty, w.iG, w.sG};
-  // adjoint of the final state into the first adjoint buffer: a_u = gu_K and, in the
-  // a_pt planes, a_p = gp_K or 0 (the first reversed iteration reads it as given);
-  // gf = 0
-  float* adj[2] = {w.adj, w.adj + 5 * fpl};
-  k_copy<<<grd, blk, 0, st>>>(g, gu_K, adj[0], 1);
-  if (gp_K) {
-    for (int k = 0; k < 3; ++k)
-      k_copy<<<grd, blk, 0, st>>>(g, gp_K + k * g.plane, adj[0] + (1 + k) * fpl, 1);
-  } else {
-    k_zero<<<grd, blk, 0, st>>>(g4, adj[0] + fpl, 3);
-  }
-  k_zero<<<grd, blk, 0, st>>>(g4, adj[0] + 4 * fpl, 1);
   k_zero<<<grd, blk, 0, st>>>(g, gf, 1);
+  const evr::Planes PR = unrolled_planes(W, H, Hm, pitch, tx, ty, f, w.iG, w.sG);
+  const evr::SolveConsts sc{tau, sigma, lambda, u_min, u_max, 0};
+  // the reverse passes: the first reads the given adjoints (gu_K, and gp_K as a_p of the
+  // last iteration; NULL reads as 0), then two ping-pong adjoint states in the workspace;
+  // the last writes a_u straight into gu0
   RevArgs ra{};
   ra.g = g4;
   ra.c = c;
@@ -536,47 +582,40 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
   ra.gf = gf;
   ra.glam = w.glam;
   rev_tiles(W, H, &ra.tiles_x, &ra.tiles_total);
-  int cur = 0;
-  const evr::Planes PR =
-      unrolled_planes(W, H, Hm, pitch, tx, ty, f, w.iG, w.sG, w.xs, w.xs + 4 * fpl, fpl);
-  const evr::SolveConsts sc{tau, sigma, lambda, u_min, u_max, 0};
+  float* adj[2] = {w.adj, w.adj + 5 * fpl};
+  const float* given[5] = {gu_K, gp_K, gp_K ? gp_K + g.plane : nullptr,
+                           gp_K ? gp_K + 2 * g.plane : nullptr, nullptr};
+  int cur = -1;  // the adjoint state's buffer; -1: the given adjoints
   const int n_ck = (K + every - 1) / every;
   for (int cseg = n_ck - 1; cseg >= 0; --cseg) {
     const int k0 = cseg * every, k1 = (k0 + every < K) ? k0 + every : K;
-    // recompute iterations k0 .. k1-1 into the tape (slot j: state k0 + j, then the v
-    // and ubar of iteration k0 + j): the checkpoint into slot 0 and into the passes'
-    // first ping-pong state, then tiled passes that write what every iteration computes
-    k_copy<<<grd, blk, 0, st>>>(g4, w.ck + (size_t)cseg * 4 * fpl, w.tape, 4);
-    k_copy<<<grd, blk, 0, st>>>(g4, w.ck + (size_t)cseg * 4 * fpl, w.xs, 4);
-    for (int done = 0, pass = 0, src = 0; done < k1 - k0; ++pass) {
-      const int left = k1 - k0 - done;
-      const int r = left < kUnrolledR ? left : kUnrolledR;
-      if (evr::launch_tiled_tape(PR, kUnrolledR, src, r, pass, sc, w.tape, (long long)fpl,
-                                 done, st))
-        return EVR_ERR_CUDA;
-      src ^= 1;
-      done += r;
-    }
-    // reverse the segment's iterations, kRevR per launch, ping-ponging the adjoint state
+    // replay iterations k0 .. k1-1 from the checkpoint, every iteration writing the p it
+    // starts from, its v and its ubar to tape slot k - k0 (the states themselves go to
+    // the ping-pong buffers only)
+    const State from = ws_state(w.ck + (size_t)cseg * 4 * fpl, fpl);
+    if (segment_passes(PR, from, nullptr, k1 - k0, sc, w.xs, w.tape, fpl, st))
+      return EVR_ERR_CUDA;
+    // reverse the segment's iterations, kRevR per launch
     for (int k = k1 - 1; k >= k0;) {
       const int r = (k - k0 + 1) < kRevR ? (k - k0 + 1) : kRevR;
+      const int nxt = cur == 0 ? 1 : 0;
       ra.slot_hi = k - k0;
       ra.k_hi = k;
       ra.iters = r;
       ra.first = (k == K - 1);
-      ra.a_in = adj[cur];
-      ra.a_out = adj[cur ^ 1];
+      for (int q = 0; q < 5; ++q) {
+        ra.a_in[q] = cur < 0 ? given[q] : adj[cur] + q * fpl;
+        ra.a_out[q] = adj[nxt] + q * fpl;
+      }
+      if (k - r < 0 && gu0) ra.a_out[0] = gu0;  // the last launch: dL/du0 itself
       k_rev_tiled<<<ra.tiles_total, dim3(32, kRevNTY), 0, st>>>(ra);
-      cur ^= 1;
+      cur = nxt;
       k -= r;
     }
   }
-  if (gu0) k_copy<<<grd, blk, 0, st>>>(g, adj[cur], gu0, 1);
-  if (gp0) {  // the adjoint of p_0 from the reversed iteration 0
-    k_b_pupdate<<<grd, blk, 0, st>>>(g4, m, adj[cur] + fpl, adj[cur] + 4 * fpl, w.ap);
-    for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, w.ap + k * fpl, gp0 + k * g.plane, 1);
-  }
-  // dL/dlambda: the K x (tiles x warps) sums, in index order
+  if (gp0)  // the adjoint of p_0 from the reversed iteration 0
+    k_b_pupdate<<<grd, blk, 0, st>>>(g4, m, adj[cur] + fpl, adj[cur] + 4 * fpl, gp0, g.plane);
+  // dL/dlambda: the K x tiles sums, in index order
   const long long nl = (long long)K * (long long)lam_slots(W, H);
   Geo gd{(int)nl, 1, (int)nl, 0, 1};
   k_red_partial<<<kRedBlocks, kRedThreads, 0, st>>>(gd, w.glam, 1, w.partials);

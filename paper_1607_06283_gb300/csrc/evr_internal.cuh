@@ -161,9 +161,8 @@ int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters,
 int tiled_front_fusable(const SolverCfg& cfg, int storage);
 // The unrolled solve's passes (FP32, the 32 x 32 tile with one pixel pair per thread and
 // an R-pixel halo): `iters` <= R iterations from buffer src into 1 - src; with a tape,
-// iteration it also writes its primal argument v and ubar into planes 4, 5 of tape slot
-// tape_first + it and the state it produces into planes 0-3 of slot tape_first + it + 1
-// (6 planes of tape_plane floats per slot).
+// iteration it also writes the p it starts from, its primal argument v and its ubar
+// into tape slot tape_first + it (planes p1 p2 p3 v ubar of tape_plane floats).
 constexpr int kTapeKX = 1, kTapeKY = 2, kTapeNTY = 16;
 int launch_tiled_tape(const Planes& P, int R, int src, int iters, int pass,
                       const SolveConsts& c, float* tape, long long tape_plane, int tape_first,

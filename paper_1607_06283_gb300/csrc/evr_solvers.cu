@@ -300,23 +300,30 @@ struct Tile {
       }
   }
 
-  // Tape mode, after an iteration: its primal argument v and ubar into planes 4 and 5
-  // of the slot of the state it started from, and the new state (u, p) into planes 0-3
-  // of the next slot (6 FP32 planes of `plane` floats per slot, pitched like the
-  // stream's planes; owned pixels).
-  __device__ __forceinline__ void store_tape(float* from, float* next, long long plane,
-                                             const Planes& P) {
+  // Tape mode: the dual state p_k the iteration starts from (before it), then its primal
+  // argument v and ubar (after it), into one slot of 5 FP32 planes p1 p2 p3 v ubar of
+  // `plane` floats each (pitched like the stream's planes; owned pixels).
+  __device__ __forceinline__ void store_tape_p(float* slot, long long plane, const Planes& P) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int j = k >> 1, h = k & 1;
       if (owned(k) && on(k, P.W, P.H)) {
         const size_t i = gidx(P, k);
-        from[4 * plane + i] = el(vs[j], h);
-        from[5 * plane + i] = el(ubs[j], h);
-        next[i] = el(u[j], h);
-        next[plane + i] = el(p1[j], h);
-        next[2 * plane + i] = el(p2[j], h);
-        next[3 * plane + i] = el(p3[j], h);
+        slot[i] = el(p1[j], h);
+        slot[plane + i] = el(p2[j], h);
+        slot[2 * plane + i] = el(p3[j], h);
+      }
+    }
+  }
+  __device__ __forceinline__ void store_tape_vub(float* slot, long long plane,
+                                                 const Planes& P) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int j = k >> 1, h = k & 1;
+      if (owned(k) && on(k, P.W, P.H)) {
+        const size_t i = gidx(P, k);
+        slot[3 * plane + i] = el(vs[j], h);
+        slot[4 * plane + i] = el(ubs[j], h);
       }
     }
   }
@@ -492,9 +499,9 @@ constexpr int kTiledMinBlocks =
 
 // MODE 0: plain passes.  MODE 1 (FRONT): the packet's front launch is fused into the
 // passes (instantiated only for tiles without a register cap, kTiledMinBlocks == 1).
-// MODE 2 (tape, FP32 only): iteration it of this launch also writes its v and ubar into
-// tape slot tape_first + it and the state it produces into slot tape_first + it + 1
-// (slot stride 6 tape_plane floats), for the reverse pass of the unrolled solve.
+// MODE 2 (tape, FP32 only): iteration it of this launch also writes the p it starts
+// from, its v and its ubar into tape slot tape_first + it (5 planes, slot stride
+// 5 tape_plane floats), for the reverse pass of the unrolled solve.
 template <int KX, int KY, int NTY, typename ST, int MODE>
 __global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>))
     k_tiled(Planes P, int src, int iters, int R, SolveConsts c, int tiles_x, BatchRef B,
@@ -540,12 +547,13 @@ __global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>))
   }
   if constexpr (MODE == 2) {
     for (int it = 0; it < iters; ++it) {
+      float* slot = tape + (long long)(tape_first + it) * 5 * tape_plane;
+      T.store_tape_p(slot, tape_plane, sP);
       if (c.data_term)
         T.template iterate<true, true>(sm, c);
       else
         T.template iterate<false, true>(sm, c);
-      float* from = tape + (long long)(tape_first + it) * 6 * tape_plane;
-      T.store_tape(from, from + 6 * tape_plane, tape_plane, sP);
+      T.store_tape_vub(slot, tape_plane, sP);
     }
   } else {
     if (c.data_term)
