@@ -48,6 +48,12 @@ B_TVL1_ITER = 44
 # the push, per event: reads x, y, t, pol (13 B) and updates t_last (8 B read + write) and
 # one count (4 B read + write) of its pixel
 B_PUSH_EVENT = 37
+# the differentiation's reverse pass (the adjoint state stays on chip within a launch):
+# per reversed pixel-iteration the tape's p (12 B), v and ubar (4 B each); per pixel and
+# launch the adjoint state in and out (5 planes each), dL/df read and written, the metric
+# (L_x t, L_y t, 1/G, sqrt(G)) and f: 17 planes of 4 B
+B_REV_ITER = 20
+B_REV_LAUNCH = 68
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -192,6 +198,31 @@ def profiled_traffic(config, solver_name, launches_per_step):
                 int(m.group(2)) == round(launches_per_step)):
             return int(m.group(1)) / int(m.group(2))
     return None
+
+
+def rev_kernel_hash():
+    """Hash of the reverse-pass kernel's source (the DRAM counters of its summary)."""
+    with open(os.path.join(ROOT, "paper_1607_06283_gb300", "csrc", "evr_grad.cu")) as fh:
+        t = fh.read()
+    a, b = t.index("// ---- the reverse pass, tiled ----"), t.index("// The adjoint of p_0:")
+    return hashlib.sha256(t[a:b].encode()).hexdigest()[:16]
+
+
+def profiled_rev_traffic(bytes_per_launch):
+    """DRAM bytes of an average reverse-pass launch: the committed ncu capture of one
+    launch (profiles/k_rev_tiled_diff64.md), scaled by the algorithmic bytes of the
+    average launch (traffic grows with the pixel-iterations), if it was taken on the
+    current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "k_rev_tiled_diff64.md")
+    if not os.path.exists(p):
+        return None
+    import re
+    with open(p) as fh:
+        m = re.search(r"rev_launch_traffic_bytes: (\d+) rev_launch_alg_bytes: (\d+) "
+                      r"rev_kernel_sha: (\w+)", fh.read())
+    if not m or m.group(3) != rev_kernel_hash():
+        return None
+    return int(m.group(1)) * bytes_per_launch / int(m.group(2))
 
 
 def cpu_baseline(cfg, stream, budget_s, max_packets=None):
@@ -648,6 +679,9 @@ def run_diff_bench(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    E.evr_unrolled_timing_start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     e0.record()
@@ -656,8 +690,21 @@ def run_diff_bench(args):
     e1.record()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    rev_ms, rev_n, rev_pi, rev_pl, launches = E.evr_unrolled_timing_stop()
     ms = e0.elapsed_time(e1)
     solves = n_streams * args.steps
+    peak, peak_kind = measured_peaks()
+    rev_bytes = B_REV_ITER * rev_pi + B_REV_LAUNCH * rev_pl
+    achieved = rev_bytes / (rev_ms * 1e-3) / 1e9 if rev_ms > 0 else None
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak if achieved else None,
+        "traffic": profiled_rev_traffic(rev_bytes / max(rev_n, 1)),
+        "kernel": "k_rev_tiled (reverse pass: 4 reversed iterations per launch, 32x32 tiles, "
+                  "4-pixel halo)",
+        "peak_source": f"{peak_kind} hbm_gbs", "avg_launch_us": rev_ms * 1e3 / max(rev_n, 1),
+        "launches_timed": rev_n, "bytes_per_launch": rev_bytes / max(rev_n, 1)}
     line = {
         "metric": METRIC, "value": solves / (ms * 1e-3), "unit": "differentiated packet solves/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -669,8 +716,13 @@ def run_diff_bench(args):
                                "packets, 30 unrolled iterations, checkpoints every 10, L2 loss "
                                "vs ground-truth frames, gradients w.r.t. lambda, C and f",
                    "timing": "CUDA events around the whole step (one batched forward + "
-                             "backward of the 64 packets per step, autograd on the host)"},
+                             "backward of the 64 packets per step, autograd on the host)",
+                   "l2": "no flush: the working set is larger than L2 (the tape of one "
+                         "checkpoint segment alone is 10 x 5 planes x 11 MB = 0.55 GB)"},
         "wall_s": wall,
+        "roofline": roofline,
+        "clocks": clocks,
+        "gpu_launches": launches,
         "grad": {"lambda": float(lam.grad), "C": float(C.grad)},
     }
     print(json.dumps(line), flush=True)

@@ -350,6 +350,20 @@ int evr_unrolled_backward(const float* tx, const float* ty, const float* f, int 
                           const float* gp_K, float* gu0, float* gp0, float* gf,
                           double* glambda_dev, void* cuda_stream);
 
+/* Launch accounting of the differentiation calls, for benchmarks (process-wide, not
+ * thread-safe).  evr_unrolled_timing_start clears the counters and starts counting every
+ * kernel that evr_unrolled_forward/backward and evr_data_image(_backward) launch, and
+ * recording a CUDA event pair on the call's stream around each of the first 16384
+ * reverse-pass launches (the tiled kernel that walks the adjoint back a few iterations at a
+ * time).  evr_unrolled_timing_stop waits for the recorded events and returns their summed
+ * device time in ms, the number of recorded reverse-pass launches, their reversed
+ * pixel-iterations and pixels x launches (for algorithmic byte counts), and the number of
+ * all launches; then it stops.  Errors: EVR_ERR_OOM, EVR_ERR_CUDA, EVR_ERR_INVALID_ARG
+ * (null pointer). */
+int evr_unrolled_timing_start(void);
+int evr_unrolled_timing_stop(double* rev_ms, long long* rev_launches, long long* rev_px_iters,
+                             long long* rev_px_launches, long long* launches);
+
 /* Data image f = u_prev exp(Delta+ n+ - Delta- n-) (Eq. intensity_update, one factor
  * per event, compounded) from the packet's event counts. */
 int evr_data_image(const float* u_prev, const int32_t* npos, const int32_t* nneg, int W, int H,

@@ -10,6 +10,8 @@
 // back to back (plane stride pitch * H).
 #include <cuda_runtime.h>
 
+#include <new>
+
 #include "../../include/evr.h"
 #include "evr_internal.cuh"
 
@@ -17,6 +19,24 @@ namespace {
 
 constexpr int kRedBlocks = 256;
 constexpr int kRedThreads = 1024;
+
+// Launch accounting of the calls below for benchmarks (process-wide, not thread-safe):
+// while on, every kernel launch is counted and the first kMaxTimed reverse-pass launches
+// are bracketed by CUDA events on their stream.
+constexpr int kMaxTimed = 16384;
+struct LaunchTiming {
+  bool on = false;
+  long long launches = 0;
+  int n = 0;                     // recorded reverse-pass launches
+  long long px_iters = 0;        // their reversed pixel-iterations
+  long long px_launches = 0;     // their pixels x launches
+  cudaEvent_t* ev = nullptr;     // 2 kMaxTimed events, created on the first start
+};
+LaunchTiming g_timing;
+
+inline void counted(int k = 1) {
+  if (g_timing.on) g_timing.launches += k;
+}
 
 // n images of W x Hm stacked vertically into one W x (n Hm) image (H = n Hm): the
 // forward differences and divergences use the row within the member, so the members
@@ -471,6 +491,7 @@ int tiled_pass(evr::Planes P, const State& a, const State& b, int iters, int pas
   P.p1[1] = b.p[0];
   P.p2[1] = b.p[1];
   P.p3[1] = b.p[2];
+  counted();
   return evr::launch_tiled_tape(P, kUnrolledR, 0, iters, pass, sc, tape, (long long)fpl,
                                 tape_first, st);
 }
@@ -533,6 +554,7 @@ extern "C" int evr_unrolled_forward(const float* tx, const float* ty, const floa
   // of segment j
   k_copy<<<grd, blk, 0, st>>>(g, u0, w.ck, 1);
   for (int k = 0; k < 3; ++k) k_copy<<<grd, blk, 0, st>>>(g, p0 + k * g.plane, w.ck + (1 + k) * fpl, 1);
+  counted(5);
   const evr::Planes P = unrolled_planes(W, H, Hm, pitch, tx, ty, f, w.iG, w.sG);
   const evr::SolveConsts sc{tau, sigma, lambda, u_min, u_max, 0};
   const State out{u_out, {p_out, p_out + g.plane, p_out + 2 * g.plane}};
@@ -568,6 +590,7 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
   k_metric<<<grd, blk, 0, st>>>(g, tx, ty, w.iG, w.sG);
   const Met m{tx, ty, w.iG, w.sG};
   k_zero<<<grd, blk, 0, st>>>(g, gf, 1);
+  counted(2);
   const evr::Planes PR = unrolled_planes(W, H, Hm, pitch, tx, ty, f, w.iG, w.sG);
   const evr::SolveConsts sc{tau, sigma, lambda, u_min, u_max, 0};
   // the reverse passes: the first reads the given adjoints (gu_K, and gp_K as a_p of the
@@ -608,18 +631,30 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
         ra.a_out[q] = adj[nxt] + q * fpl;
       }
       if (k - r < 0 && gu0) ra.a_out[0] = gu0;  // the last launch: dL/du0 itself
+      const bool timed = g_timing.on && g_timing.n < kMaxTimed;
+      if (timed) cudaEventRecord(g_timing.ev[2 * g_timing.n], st);
       k_rev_tiled<<<ra.tiles_total, dim3(32, kRevNTY), 0, st>>>(ra);
+      counted();
+      if (timed) {
+        cudaEventRecord(g_timing.ev[2 * g_timing.n + 1], st);
+        ++g_timing.n;
+        g_timing.px_iters += (long long)W * H * r;
+        g_timing.px_launches += (long long)W * H;
+      }
       cur = nxt;
       k -= r;
     }
   }
-  if (gp0)  // the adjoint of p_0 from the reversed iteration 0
+  if (gp0) {  // the adjoint of p_0 from the reversed iteration 0
     k_b_pupdate<<<grd, blk, 0, st>>>(g4, m, adj[cur] + fpl, adj[cur] + 4 * fpl, gp0, g.plane);
+    counted();
+  }
   // dL/dlambda: the K x tiles sums, in index order
   const long long nl = (long long)K * (long long)lam_slots(W, H);
   Geo gd{(int)nl, 1, (int)nl, 0, 1};
   k_red_partial<<<kRedBlocks, kRedThreads, 0, st>>>(gd, w.glam, 1, w.partials);
   k_red_final<<<1, kRedBlocks, 0, st>>>(w.partials, 1, glambda_dev);
+  counted(2);
   return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
 }
 
@@ -630,6 +665,7 @@ extern "C" int evr_data_image(const float* u_prev, const int32_t* npos, const in
     return EVR_ERR_INVALID_ARG;
   Geo g{W, H, pitch, (size_t)pitch * H, H};
   dim3 blk(32, 8), grd((W + 31) / 32, (H + 7) / 8);
+  counted();
   k_data_image<<<grd, blk, 0, (cudaStream_t)cuda_stream>>>(g, u_prev, npos, nneg, delta_pos,
                                                            delta_neg, f_out);
   return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
@@ -651,5 +687,48 @@ extern "C" int evr_data_image_backward(const float* f, const float* u_prev, cons
                                         g_uprev, scratch);
   k_red_partial<<<kRedBlocks, kRedThreads, 0, st>>>(g, scratch, 2, scratch + 2 * g.plane);
   k_red_final<<<1, kRedBlocks, 0, st>>>(scratch + 2 * g.plane, 2, g_delta_dev);
+  counted(3);
   return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}
+
+extern "C" int evr_unrolled_timing_start(void) {
+  if (!g_timing.ev) {
+    g_timing.ev = new (std::nothrow) cudaEvent_t[2 * kMaxTimed];
+    if (!g_timing.ev) return EVR_ERR_OOM;
+    for (int i = 0; i < 2 * kMaxTimed; ++i)
+      if (cudaEventCreate(&g_timing.ev[i]) != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(g_timing.ev[j]);
+        delete[] g_timing.ev;
+        g_timing.ev = nullptr;
+        return EVR_ERR_CUDA;
+      }
+  }
+  g_timing.on = true;
+  g_timing.launches = 0;
+  g_timing.n = 0;
+  g_timing.px_iters = 0;
+  g_timing.px_launches = 0;
+  return EVR_OK;
+}
+
+extern "C" int evr_unrolled_timing_stop(double* rev_ms, long long* rev_launches,
+                                        long long* rev_px_iters, long long* rev_px_launches,
+                                        long long* launches) {
+  if (!rev_ms || !rev_launches || !rev_px_iters || !rev_px_launches || !launches)
+    return EVR_ERR_INVALID_ARG;
+  double ms = 0.0;
+  for (int i = 0; i < g_timing.n; ++i) {
+    float t = 0.0f;
+    if (cudaEventSynchronize(g_timing.ev[2 * i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, g_timing.ev[2 * i], g_timing.ev[2 * i + 1]) != cudaSuccess)
+      return EVR_ERR_CUDA;
+    ms += t;
+  }
+  *rev_ms = ms;
+  *rev_launches = g_timing.n;
+  *rev_px_iters = g_timing.px_iters;
+  *rev_px_launches = g_timing.px_launches;
+  *launches = g_timing.launches;
+  g_timing.on = false;
+  return EVR_OK;
 }

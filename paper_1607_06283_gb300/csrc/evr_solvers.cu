@@ -302,28 +302,27 @@ struct Tile {
 
   // Tape mode: the dual state p_k the iteration starts from (before it), then its primal
   // argument v and ubar (after it), into one slot of 5 FP32 planes p1 p2 p3 v ubar of
-  // `plane` floats each (pitched like the stream's planes; owned pixels).
-  __device__ __forceinline__ void store_tape_p(float* slot, long long plane, const Planes& P) {
+  // `plane` floats each, at the owned pixels' indices ti[k] (~0u: not written).
+  __device__ __forceinline__ void store_tape_p(float* slot, unsigned plane,
+                                               const unsigned* ti) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int j = k >> 1, h = k & 1;
-      if (owned(k) && on(k, P.W, P.H)) {
-        const size_t i = gidx(P, k);
-        slot[i] = el(p1[j], h);
-        slot[plane + i] = el(p2[j], h);
-        slot[2 * plane + i] = el(p3[j], h);
+      if (ti[k] != ~0u) {
+        slot[ti[k]] = el(p1[j], h);
+        slot[plane + ti[k]] = el(p2[j], h);
+        slot[2 * plane + ti[k]] = el(p3[j], h);
       }
     }
   }
-  __device__ __forceinline__ void store_tape_vub(float* slot, long long plane,
-                                                 const Planes& P) {
+  __device__ __forceinline__ void store_tape_vub(float* slot, unsigned plane,
+                                                 const unsigned* ti) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int j = k >> 1, h = k & 1;
-      if (owned(k) && on(k, P.W, P.H)) {
-        const size_t i = gidx(P, k);
-        slot[3 * plane + i] = el(vs[j], h);
-        slot[4 * plane + i] = el(ubs[j], h);
+      if (ti[k] != ~0u) {
+        slot[3 * plane + ti[k]] = el(vs[j], h);
+        slot[4 * plane + ti[k]] = el(ubs[j], h);
       }
     }
   }
@@ -502,8 +501,10 @@ constexpr int kTiledMinBlocks =
 // MODE 2 (tape, FP32 only): iteration it of this launch also writes the p it starts
 // from, its v and its ubar into tape slot tape_first + it (5 planes, slot stride
 // 5 tape_plane floats), for the reverse pass of the unrolled solve.
+// The tape mode's tile is held to two resident CTAs per SM (64 registers), as the plain
+// passes of the same tile reach without a cap.
 template <int KX, int KY, int NTY, typename ST, int MODE>
-__global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>))
+__global__ void __launch_bounds__(32 * NTY, (MODE == 2 ? 2 : kTiledMinBlocks<KX, KY, NTY, ST>))
     k_tiled(Planes P, int src, int iters, int R, SolveConsts c, int tiles_x, BatchRef B,
             int pass, PrologueConsts pc, float* tape, long long tape_plane, int tape_first) {
   constexpr bool FRONT = MODE == 1;
@@ -546,14 +547,20 @@ __global__ void __launch_bounds__(32 * NTY, (kTiledMinBlocks<KX, KY, NTY, ST>))
     T.load_state(sP, src);
   }
   if constexpr (MODE == 2) {
+    // the owned pixels' tape indices, computed once (a tape plane holds < 2^31 floats)
+    unsigned ti[Tile<KX, KY, NTY, ST>::K];
+#pragma unroll
+    for (int k = 0; k < Tile<KX, KY, NTY, ST>::K; ++k)
+      ti[k] = (T.owned(k) && T.on(k, sP.W, sP.H)) ? (unsigned)T.gidx(sP, k) : ~0u;
+    const unsigned pl = (unsigned)tape_plane;
     for (int it = 0; it < iters; ++it) {
       float* slot = tape + (long long)(tape_first + it) * 5 * tape_plane;
-      T.store_tape_p(slot, tape_plane, sP);
+      T.store_tape_p(slot, pl, ti);
       if (c.data_term)
         T.template iterate<true, true>(sm, c);
       else
         T.template iterate<false, true>(sm, c);
-      T.store_tape_vub(slot, tape_plane, sP);
+      T.store_tape_vub(slot, pl, ti);
     }
   } else {
     if (c.data_term)

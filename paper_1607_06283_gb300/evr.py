@@ -102,6 +102,8 @@ def _load():
         "evr_unrolled_backward": ([vp] * 3 + [i, i, i, i] + [ctypes.c_float] * 5 + [i, i] +
                                   [vp] * 8, i),
         "evr_data_image": ([vp] * 3 + [i, i, i, ctypes.c_float, ctypes.c_float, vp, vp], i),
+        "evr_unrolled_timing_start": ([], i),
+        "evr_unrolled_timing_stop": ([vp] * 5, i),
         "evr_batch_create": ([i, vp, vp, vp, vp], i),
         "evr_batch_get_images_async": ([vp, vp, sz, ctypes.POINTER(ctypes.c_uint64)], i),
         "evr_batch_wait_images": ([vp, ctypes.c_uint64], i),
@@ -332,6 +334,21 @@ def evr_kernel_time(h):
 
 def evr_solver_name(h) -> str:
     return _lib.evr_solver_name(h).decode()
+
+
+def evr_unrolled_timing_start() -> None:
+    _check(_lib.evr_unrolled_timing_start(), "evr_unrolled_timing_start")
+
+
+def evr_unrolled_timing_stop():
+    """(reverse-pass ms, reverse-pass launches, their pixel-iterations, their pixels x
+    launches, all launches of the differentiation calls) since the start."""
+    ms = ctypes.c_double()
+    n, pi, pl, la = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.evr_unrolled_timing_stop(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(pi),
+                                         ctypes.byref(pl), ctypes.byref(la)),
+           "evr_unrolled_timing_stop")
+    return ms.value, n.value, pi.value, pl.value, la.value
 
 
 class Stream:
