@@ -479,6 +479,12 @@ State ws_state(float* base, size_t fpl) {
   return State{base, {base + fpl, base + 2 * fpl, base + 3 * fpl}};
 }
 
+// The forward's passes (no tape) run on the solver's 32 x 48 tile with two pixel pairs
+// per thread (384 threads, two CTAs per SM); the tape passes on the 32 x 32 one-pair tile.
+// Both compute each pixel with the same explicitly rounded operations, so the replayed
+// states equal the forward's bit for bit.
+constexpr evr::SolverCfg kForwardCfg{1, 6, kUnrolledR};
+
 // One tiled pass of `iters` iterations from state a into state b (a is only read).
 int tiled_pass(evr::Planes P, const State& a, const State& b, int iters, int pass,
                const evr::SolveConsts& sc, float* tape, size_t fpl, int tape_first,
@@ -492,6 +498,7 @@ int tiled_pass(evr::Planes P, const State& a, const State& b, int iters, int pas
   P.p2[1] = b.p[1];
   P.p3[1] = b.p[2];
   counted();
+  if (!tape) return evr::launch_tiled_pass(P, kForwardCfg, 0, iters, pass, sc, st);
   return evr::launch_tiled_tape(P, kUnrolledR, 0, iters, pass, sc, tape, (long long)fpl,
                                 tape_first, st);
 }

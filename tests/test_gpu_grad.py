@@ -218,3 +218,24 @@ def test_batched_call_rejects_bad_sizes(T):
     assert E._lib.evr_unrolled_workspace_bytes(16, 8, 16, 0, 10, 5) == 0
     assert E._lib.evr_unrolled_workspace_bytes(16, 8, 16, 70000, 10, 5) == 0
     assert E._lib.evr_unrolled_workspace_bytes(16, 8, 16, 4, 10, 5) > 0
+
+
+def test_launch_timing_counts_every_launch(T):
+    """evr_unrolled_timing_start/stop: every kernel of the differentiation calls counted,
+    every reverse-pass launch timed (4 reversed iterations per launch)."""
+    torch, AG, E = T
+    H, W, K, every = 23, 37, 30, 10
+    tx, ty, f, u0, p0, w = problem(11, H, W)
+    ttx, tty, tf, tu0, tp0, tw = cuda(torch, tx, ty, f, u0, p0, w)
+    tf.requires_grad_(True)
+    E.evr_unrolled_timing_start()
+    u, _ = AG.packet_solve(tf, 30.0, tu0, tp0, ttx, tty, K, every)
+    (u * tw).sum().backward()
+    ms, n_rev, px_iters, px_launches, launches = E.evr_unrolled_timing_stop()
+    segs, passes, revs = K // every, -(-every // 5), -(-every // 4)
+    assert n_rev == segs * revs
+    assert px_iters == H * W * K and px_launches == H * W * n_rev
+    # forward: metric, 4 copies, the passes; backward: metric, zero, replay passes and
+    # reverse launches per segment, dL/dp0, the two-stage lambda reduction
+    assert launches == (5 + segs * passes) + (2 + segs * (passes + revs) + 1 + 2)
+    assert ms > 0.0
