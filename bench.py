@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="blobs346")
+    ap.add_argument("--every", type=int, default=10,
+                    help="diff64: checkpoint spacing of the unrolled solve (>= 30: whole tape "
+                         "kept from the forward, no recomputation)")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solver", type=int, default=0, help="evr_params.solver")
@@ -638,7 +641,8 @@ def run_diff_bench(args):
     from paper_1607_06283_gb300 import autograd as AG
     from paper_1607_06283_gb300 import evr as E
     from evsim.configs import StreamConfig, make_batch
-    n_streams, W, H, packet, K, every = 64, 240, 180, 2000, 30, 10
+    n_streams, W, H, packet, K = 64, 240, 180, 2000, 30
+    every = args.every
     cfgs = [StreamConfig(f"diff{s}", W, H, "rects", 40, 5000 + s, 2 * packet, packet, K,
                          speed=120.0, noise=0.01, dt_us=250.0) for s in range(n_streams)]
     streams = make_batch(cfgs)
@@ -713,12 +717,13 @@ def run_diff_bench(args):
         "gpix_iter_per_s_fwd_bwd": solves * W * H * K / (ms * 1e-3) / 1e9,
         "events_per_s": solves * packet / (ms * 1e-3),
         "config": {"workload": "diff64: 64 streams of 240x180 rectangles scenes, 2000-event "
-                               "packets, 30 unrolled iterations, checkpoints every 10, L2 loss "
-                               "vs ground-truth frames, gradients w.r.t. lambda, C and f",
+                               f"packets, 30 unrolled iterations, checkpoints every {every}, L2 "
+                               "loss vs ground-truth frames, gradients w.r.t. lambda, C and f",
                    "timing": "CUDA events around the whole step (one batched forward + "
                              "backward of the 64 packets per step, autograd on the host)",
                    "l2": "no flush: the working set is larger than L2 (the tape of one "
-                         "checkpoint segment alone is 10 x 5 planes x 11 MB = 0.55 GB)"},
+                         f"checkpoint segment alone is {min(every, K)} x 5 planes x 11 MB = "
+                         f"{min(every, K) * 5 * 11e6 / 1e9:.2f} GB)"},
         "wall_s": wall,
         "roofline": roofline,
         "clocks": clocks,

@@ -327,9 +327,12 @@ size_t evr_unrolled_workspace_bytes(int W, int H, int pitch, int n, int K, int e
 
 /* K iterations from (u0, p0), storing (u, p) checkpoints every `every` iterations in
  * `workspace`; result in u_out, p_out.  The iterations are the solver's tiled FP32 passes
- * (MUFU reciprocal square root and reciprocal, a few ulp); evr_unrolled_backward
- * recomputes each segment with the same passes, so it sees the same states bit for bit
- * for any checkpoint spacing. */
+ * (MUFU reciprocal square root and reciprocal, a few ulp); the last checkpoint segment's
+ * passes also write that segment's tape (p, v and ubar of every iteration) to the
+ * workspace.  evr_unrolled_backward recomputes the other segments with the same
+ * arithmetic, so it sees the same states bit for bit for any checkpoint spacing; with
+ * every >= K it recomputes nothing (the workspace then holds the whole tape,
+ * 5 planes per iteration). */
 int evr_unrolled_forward(const float* tx, const float* ty, const float* f, const float* u0,
                          const float* p0, int W, int H, int pitch, int n, float lambda,
                          float tau, float sigma, float u_min, float u_max, int K, int every,

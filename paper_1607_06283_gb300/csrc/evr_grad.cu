@@ -398,8 +398,8 @@ __global__ void k_data_image_bwd(Geo g, const float* f, const float* u_prev, con
 
 struct Workspace {
   float* ck;       // n_ck checkpoints x 4 planes
-  float* tape;     // `every` slots x 5 planes: p1 p2 p3 of the state an iteration starts
-                   // from, then its v and ubar
+  float* tape;     // min(every, K) slots x 5 planes: p1 p2 p3 of the state an iteration
+                   // starts from, then its v and ubar
   float* adj;      // 2 x 5 planes: ping-pong adjoint states (a_u, a_pt, tau a_v)
   float* xs;       // 2 states x 4 planes: ping-pong buffers of the passes
   float* iG;       // 1 plane: 1/G
@@ -435,7 +435,7 @@ size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspac
   };
   Workspace t;
   t.ck = (float*)take(fpl * 4 * (size_t)(n_ck > 0 ? n_ck : 1));
-  t.tape = (float*)take(fpl * 5 * (size_t)every);
+  t.tape = (float*)take(fpl * 5 * (size_t)(every < K ? every : K));
   t.adj = (float*)take(fpl * 10);
   t.xs = (float*)take(fpl * 8);
   t.iG = (float*)take(fpl);
@@ -565,11 +565,15 @@ extern "C" int evr_unrolled_forward(const float* tx, const float* ty, const floa
   const evr::Planes P = unrolled_planes(W, H, Hm, pitch, tx, ty, f, w.iG, w.sG);
   const evr::SolveConsts sc{tau, sigma, lambda, u_min, u_max, 0};
   const State out{u_out, {p_out, p_out + g.plane, p_out + 2 * g.plane}};
+  // the last segment's passes also write its tape, which the backward then uses as is
+  // (with every >= K: the whole tape, and the backward replays nothing)
   for (int k0 = 0, seg = 0; k0 < K; k0 += every, ++seg) {
     const int len = (K - k0 < every) ? K - k0 : every;
+    const bool last = k0 + len == K;
     const State from = ws_state(w.ck + (size_t)seg * 4 * fpl, fpl);
-    const State to = (k0 + len < K) ? ws_state(w.ck + (size_t)(seg + 1) * 4 * fpl, fpl) : out;
-    if (segment_passes(P, from, &to, len, sc, w.xs, nullptr, fpl, st)) return EVR_ERR_CUDA;
+    const State to = last ? out : ws_state(w.ck + (size_t)(seg + 1) * 4 * fpl, fpl);
+    if (segment_passes(P, from, &to, len, sc, w.xs, last ? w.tape : nullptr, fpl, st))
+      return EVR_ERR_CUDA;
   }
   return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
 }
@@ -621,9 +625,9 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
     const int k0 = cseg * every, k1 = (k0 + every < K) ? k0 + every : K;
     // replay iterations k0 .. k1-1 from the checkpoint, every iteration writing the p it
     // starts from, its v and its ubar to tape slot k - k0 (the states themselves go to
-    // the ping-pong buffers only)
+    // the ping-pong buffers only); the last segment's tape is the forward's
     const State from = ws_state(w.ck + (size_t)cseg * 4 * fpl, fpl);
-    if (segment_passes(PR, from, nullptr, k1 - k0, sc, w.xs, w.tape, fpl, st))
+    if (cseg < n_ck - 1 && segment_passes(PR, from, nullptr, k1 - k0, sc, w.xs, w.tape, fpl, st))
       return EVR_ERR_CUDA;
     // reverse the segment's iterations, kRevR per launch
     for (int k = k1 - 1; k >= k0;) {

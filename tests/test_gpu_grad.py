@@ -235,7 +235,8 @@ def test_launch_timing_counts_every_launch(T):
     segs, passes, revs = K // every, -(-every // 5), -(-every // 4)
     assert n_rev == segs * revs
     assert px_iters == H * W * K and px_launches == H * W * n_rev
-    # forward: metric, 4 copies, the passes; backward: metric, zero, replay passes and
-    # reverse launches per segment, dL/dp0, the two-stage lambda reduction
-    assert launches == (5 + segs * passes) + (2 + segs * (passes + revs) + 1 + 2)
+    # forward: metric, 4 copies, the passes (the last segment's writing its tape);
+    # backward: metric, zero, the replay passes of all but the last segment, the reverse
+    # launches, dL/dp0, the two-stage lambda reduction
+    assert launches == (5 + segs * passes) + (2 + (segs - 1) * passes + segs * revs + 1 + 2)
     assert ms > 0.0
