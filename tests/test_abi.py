@@ -60,10 +60,29 @@ def test_ptxas_reports_no_spills_in_the_iteration_kernels(evr):
     """Register pressure check on the built kernels (from nvcc -Xptxas -v)."""
     import os
     text = ""
-    for f in ("evr_kernels.ptxas.txt", "evr_solvers.ptxas.txt"):
+    for f in ("evr_kernels.ptxas.txt", "evr_solvers.ptxas.txt", "evr_grad.ptxas.txt"):
         text += open(os.path.join(os.path.dirname(build.LIB), f)).read()
     blocks = text.split("Compiling entry function")
     for b in blocks[1:]:
         name = b.split("'")[1]
-        if "k_tiled" in name or "k_prologue" in name or "k_push" in name:
+        if ("k_tiled" in name or "k_prologue" in name or "k_push" in name or
+                "k_rev_tiled" in name):
             assert "0 bytes spill stores" in b, name
+
+
+def test_unrolled_workspace_sizing_needs_no_gpu(evr):
+    """Workspace of the differentiation calls: checkpoints every `every` iterations plus a
+    tape of min(every, K) iterations (5 planes each); invalid sizes give 0."""
+    E = evr
+    ws = E._lib.evr_unrolled_workspace_bytes
+    W, H, n, K = 37, 23, 3, 30
+    plane = (W * H * n * 4 + 255) // 256 * 256
+    # every >= K: one checkpoint and the whole tape, whatever `every` is
+    assert ws(W, H, W, n, K, K) == ws(W, H, W, n, K, 2 * K) == ws(W, H, W, n, K, 1000)
+    # every 10 -> 30: 2 checkpoints (4 planes each) fewer, 20 tape slots (5 planes) more
+    assert ws(W, H, W, n, K, 30) - ws(W, H, W, n, K, 10) == (20 * 5 - 2 * 4) * plane
+    # a larger pitch grows every plane
+    assert ws(W, H, W + 64, n, K, 10) > ws(W, H, W, n, K, 10)
+    for bad in [(0, H, W, n, K, 10), (W, H, W - 1, n, K, 10), (W, H, W, 0, K, 10),
+                (W, H, W, n, 0, 10), (W, H, W, n, K, 0)]:
+        assert ws(*bad) == 0, bad
