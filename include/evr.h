@@ -332,19 +332,23 @@ size_t evr_unrolled_workspace_bytes(int W, int H, int pitch, int n, int K, int e
  * workspace.  evr_unrolled_backward recomputes the other segments with the same
  * arithmetic, so it sees the same states bit for bit for any checkpoint spacing; with
  * every >= K it recomputes nothing (the workspace then holds the whole tape,
- * 5 planes per iteration). */
+ * 5 planes per iteration; with every < K it holds the last segment's tape and a second
+ * tape of `every` iterations for the recomputation). */
 int evr_unrolled_forward(const float* tx, const float* ty, const float* f, const float* u0,
                          const float* p0, int W, int H, int pitch, int n, float lambda,
                          float tau, float sigma, float u_min, float u_max, int K, int every,
                          void* workspace, float* u_out, float* p_out, void* cuda_stream);
 
 /* Reverse mode after evr_unrolled_forward with the same arguments and workspace:
- * from gu_K = dL/du_K and gp_K = dL/dp_K (NULL means 0), recompute each checkpoint
- * segment (states, primal arguments v and ubar of every iteration, kept in the
- * workspace) and walk the adjoint back on tiled passes of a few iterations each: gu0 =
- * dL/du0 and gp0 = dL/dp0 (either may be NULL), gf = dL/df, and glambda_dev[0] =
- * dL/dlambda summed over the n images (device double: FP32 sums over 64 pixels per
- * iteration, reduced in FP64 in a fixed order).  Clamped pixels and the projection are
+ * from gu_K = dL/du_K and gp_K = dL/dp_K (NULL means 0), walk the adjoint back one
+ * checkpoint segment at a time, last segment first, on tiled passes of a few iterations
+ * each.  Each segment but the last (whose tape the forward wrote) is first recomputed
+ * from its checkpoint into a second tape area of the workspace (p, v and ubar of every
+ * iteration).  The checkpoints and the forward's tape are only read, so the call may be
+ * repeated.  Outputs: gu0 = dL/du0 and gp0 =
+ * dL/dp0 (either may be NULL), gf = dL/df, and glambda_dev[0] = dL/dlambda summed over
+ * the n images (device double: FP32 sums over each reverse tile's pixels per iteration,
+ * reduced in FP64 in a fixed order).  Clamped pixels and the projection are
  * differentiated on their active side; 1/|p| and 1/s of the KL root are MUFU reciprocal
  * square roots (a few ulp). */
 int evr_unrolled_backward(const float* tx, const float* ty, const float* f, int W, int H,

@@ -398,8 +398,11 @@ __global__ void k_data_image_bwd(Geo g, const float* f, const float* u_prev, con
 
 struct Workspace {
   float* ck;       // n_ck checkpoints x 4 planes
-  float* tape;     // min(every, K) slots x 5 planes: p1 p2 p3 of the state an iteration
-                   // starts from, then its v and ubar
+  float* tape_last;  // the last checkpoint segment's tape, written by the forward: one
+                     // slot of 5 planes per iteration (p1 p2 p3 of the state it starts
+                     // from, then its v and ubar)
+  float* tape;       // the backward's replay of one earlier segment (every slots), or
+                     // NULL with a single segment
   float* adj;      // 2 x 5 planes: ping-pong adjoint states (a_u, a_pt, tau a_v)
   float* xs;       // 2 states x 4 planes: ping-pong buffers of the passes
   float* iG;       // 1 plane: 1/G
@@ -435,7 +438,9 @@ size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspac
   };
   Workspace t;
   t.ck = (float*)take(fpl * 4 * (size_t)(n_ck > 0 ? n_ck : 1));
-  t.tape = (float*)take(fpl * 5 * (size_t)(every < K ? every : K));
+  const int len_last = K - (n_ck - 1) * every;
+  t.tape_last = (float*)take(fpl * 5 * (size_t)len_last);
+  t.tape = n_ck > 1 ? (float*)take(fpl * 5 * (size_t)every) : nullptr;
   t.adj = (float*)take(fpl * 10);
   t.xs = (float*)take(fpl * 8);
   t.iG = (float*)take(fpl);
@@ -572,7 +577,7 @@ extern "C" int evr_unrolled_forward(const float* tx, const float* ty, const floa
     const bool last = k0 + len == K;
     const State from = ws_state(w.ck + (size_t)seg * 4 * fpl, fpl);
     const State to = last ? out : ws_state(w.ck + (size_t)(seg + 1) * 4 * fpl, fpl);
-    if (segment_passes(P, from, &to, len, sc, w.xs, last ? w.tape : nullptr, fpl, st))
+    if (segment_passes(P, from, &to, len, sc, w.xs, last ? w.tape_last : nullptr, fpl, st))
       return EVR_ERR_CUDA;
   }
   return cudaGetLastError() == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
@@ -612,7 +617,6 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
   ra.c = c;
   ra.m = m;
   ra.f = f;
-  ra.tape = w.tape;
   ra.gf = gf;
   ra.glam = w.glam;
   rev_tiles(W, H, &ra.tiles_x, &ra.tiles_total);
@@ -623,12 +627,15 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
   const int n_ck = (K + every - 1) / every;
   for (int cseg = n_ck - 1; cseg >= 0; --cseg) {
     const int k0 = cseg * every, k1 = (k0 + every < K) ? k0 + every : K;
-    // replay iterations k0 .. k1-1 from the checkpoint, every iteration writing the p it
-    // starts from, its v and its ubar to tape slot k - k0 (the states themselves go to
-    // the ping-pong buffers only); the last segment's tape is the forward's
+    // the last segment's tape is the forward's; an earlier one is replayed from its
+    // checkpoint, every iteration writing the p it starts from, its v and its ubar to
+    // slot k - k0 of the replay tape (the states themselves go to the ping-pong buffers
+    // only).  Checkpoints and the forward's tape stay as they are: the call can repeat.
+    const bool last = cseg == n_ck - 1;
     const State from = ws_state(w.ck + (size_t)cseg * 4 * fpl, fpl);
-    if (cseg < n_ck - 1 && segment_passes(PR, from, nullptr, k1 - k0, sc, w.xs, w.tape, fpl, st))
+    if (!last && segment_passes(PR, from, nullptr, k1 - k0, sc, w.xs, w.tape, fpl, st))
       return EVR_ERR_CUDA;
+    ra.tape = last ? w.tape_last : w.tape;
     // reverse the segment's iterations, kRevR per launch
     for (int k = k1 - 1; k >= k0;) {
       const int r = (k - k0 + 1) < kRevR ? (k - k0 + 1) : kRevR;

@@ -71,16 +71,19 @@ def test_ptxas_reports_no_spills_in_the_iteration_kernels(evr):
 
 
 def test_unrolled_workspace_sizing_needs_no_gpu(evr):
-    """Workspace of the differentiation calls: checkpoints every `every` iterations plus a
-    tape of min(every, K) iterations (5 planes each); invalid sizes give 0."""
+    """Workspace of the differentiation calls: checkpoints every `every` iterations, the
+    forward's tape of the last segment and, with several segments, a replay tape of
+    `every` iterations (5 planes per tape iteration); invalid sizes give 0."""
     E = evr
     ws = E._lib.evr_unrolled_workspace_bytes
     W, H, n, K = 37, 23, 3, 30
     plane = (W * H * n * 4 + 255) // 256 * 256
     # every >= K: one checkpoint and the whole tape, whatever `every` is
     assert ws(W, H, W, n, K, K) == ws(W, H, W, n, K, 2 * K) == ws(W, H, W, n, K, 1000)
-    # every 10 -> 30: 2 checkpoints (4 planes each) fewer, 20 tape slots (5 planes) more
-    assert ws(W, H, W, n, K, 30) - ws(W, H, W, n, K, 10) == (20 * 5 - 2 * 4) * plane
+    # every 10: 3 checkpoints, 10 + 10 tape slots; every 30: 1 checkpoint, 30 tape slots
+    assert ws(W, H, W, n, K, 30) - ws(W, H, W, n, K, 10) == ((4 + 150) - (12 + 100)) * plane
+    # every 7 (segments 7, 7, 7, 7, 2): 5 checkpoints, the last segment's 2 slots + 7
+    assert ws(W, H, W, n, K, 10) - ws(W, H, W, n, K, 7) == ((12 + 100) - (20 + 45)) * plane
     # a larger pitch grows every plane
     assert ws(W, H, W + 64, n, K, 10) > ws(W, H, W, n, K, 10)
     for bad in [(0, H, W, n, K, 10), (W, H, W - 1, n, K, 10), (W, H, W, 0, K, 10),

@@ -245,3 +245,20 @@ def test_launch_timing_counts_every_launch(T):
     # wrote its tape), the reverse launches, dL/dp0, the two-stage lambda reduction
     assert bwd == 2 + (segs - 1) * passes + n_rev + 1 + 2
     assert ms > 0.0
+
+
+def test_backward_can_repeat(T):
+    """The backward leaves the checkpoints and the forward's tape intact: a second
+    backward through the same graph gives the same gradients bit for bit."""
+    torch, AG, E = T
+    H, W, K, every = 21, 19, 25, 7
+    tx, ty, f, u0, p0, w = problem(13, H, W)
+    ttx, tty, tu0, tp0, tw = cuda(torch, tx, ty, u0, p0, w)
+    tf = torch.from_numpy(f).cuda().requires_grad_(True)
+    u, _ = AG.packet_solve(tf, 30.0, tu0, tp0, ttx, tty, K, every)
+    loss = (u * tw).sum()
+    loss.backward(retain_graph=True)
+    g1 = tf.grad.clone()
+    tf.grad = None
+    loss.backward()
+    assert torch.equal(tf.grad, g1)
