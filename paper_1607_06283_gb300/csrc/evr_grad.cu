@@ -428,7 +428,7 @@ size_t lam_slots(int W, int H) {
 
 size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspace* w) {
   const size_t plane = (size_t)pitch * H;
-  const size_t fpl = (plane * 4 + 255) / 256 * 256;
+  const size_t bpl = (plane * 4 + 255) / 256 * 256;  // bytes per plane slot
   const int n_ck = (K + every - 1) / every;
   size_t off = 0;
   auto take = [&](size_t b) {
@@ -437,14 +437,14 @@ size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspac
     return base ? base + o : nullptr;
   };
   Workspace t;
-  t.ck = (float*)take(fpl * 4 * (size_t)(n_ck > 0 ? n_ck : 1));
+  t.ck = (float*)take(bpl * 4 * (size_t)(n_ck > 0 ? n_ck : 1));
   const int len_last = K - (n_ck - 1) * every;
-  t.tape_last = (float*)take(fpl * 5 * (size_t)len_last);
-  t.tape = n_ck > 1 ? (float*)take(fpl * 5 * (size_t)every) : nullptr;
-  t.adj = (float*)take(fpl * 10);
-  t.xs = (float*)take(fpl * 8);
-  t.iG = (float*)take(fpl);
-  t.sG = (float*)take(fpl);
+  t.tape_last = (float*)take(bpl * 5 * (size_t)len_last);
+  t.tape = n_ck > 1 ? (float*)take(bpl * 5 * (size_t)every) : nullptr;
+  t.adj = (float*)take(bpl * 10);
+  t.xs = (float*)take(bpl * 8);
+  t.iG = (float*)take(bpl);
+  t.sG = (float*)take(bpl);
   t.glam = (double*)take(sizeof(double) * (size_t)K * lam_slots(W, H));
   t.partials = (double*)take(sizeof(double) * 4 * kRedBlocks);
   if (w) *w = t;
@@ -452,9 +452,9 @@ size_t ws_layout(int W, int H, int pitch, int K, int every, char* base, Workspac
 }
 
 // The iterations of the forward pass and of the reverse pass's recomputation run as the
-// solver's tiled passes (FP32, one pixel pair per thread, a kUnrolledR-pixel halo) over
-// the stacked images; their per-pixel arithmetic does not depend on how the iterations
-// are split into launches, so the recomputed states equal the forward's bit for bit.
+// solver's tiled passes (FP32, a kUnrolledR-pixel halo) over the stacked images; their
+// per-pixel arithmetic does not depend on how the iterations are split into launches,
+// so the recomputed states equal the forward's bit for bit.
 constexpr int kUnrolledR = 5;
 
 // The packet's planes as the tiled passes' descriptor (the state buffers are set per pass).
