@@ -33,7 +33,10 @@ static_assert((long long)kChunk * kStaticChunks == EVR_GAP_STATIC_MAX_PIXELS,
 static __device__ __align__(256) double g_gap_partials[3 * kStaticChunks];
 
 // Host-side device address of g_gap_partials for each device (the symbol's name in
-// host code is only a stand-in and must never be passed to a kernel).
+// host code is only a stand-in and must never be passed to a kernel), looked up by the
+// first call on that device.  A device reset (cudaDeviceReset) unloads the module, so
+// the address cached here is stale afterwards: the entry point must not be called on
+// a device after it was reset.
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {nullptr};
 
@@ -49,11 +52,15 @@ int scratch_address(int dev, double** out) {
 }
 
 // Per pixel, in FP64 from FP32 planes (Eq. 5 and the dual of Eq. primal_dual_energy):
-// the g-tensor norm term sqrt(G)|L_g u|, the data term sqrt(G)(u - f log u), and
-// min over the box of a (u - f log u) + w u with a = lambda sqrt(G), w = -div_g p.
+// the g-tensor norm term sqrt(G)|L_g u|, and with a = lambda sqrt(G), w = -div_g p
+//   KL data term (data_term 0): sqrt(G)(u - f log u) and the dual term
+//     min over the box of a (u - f log u) + w u;
+//   L2 data term of Eq. 7 (data_term 1, no box): sqrt(G)(u - f)^2 / 2 and the dual
+//     term min over u of (a/2)(u - f)^2 + w u = w f - w^2 / (2a).
+// These are the terms evr_gap reduces for a stream with the same data term.
 struct GapIn {
   const float *u, *p1, *p2, *p3, *f, *tx, *ty;
-  int W, H, pitch;
+  int W, H, pitch, data_term;
   double lambda, u_min, u_max;
 };
 
@@ -82,16 +89,23 @@ __global__ void __launch_bounds__(kThreads) k_gap_static_partial(GapIn g, double
     double g2 = ((1.0 + a * a) * uy - a * b * ux) / G;
     double g3 = (a * ux + b * uy) / G;
     reg += sqrt(G * (g1 * g1 + g2 * g2 + g3 * g3));
-    dat += (u - (f == 0.0 ? 0.0 : f * log(u))) * sG;
+    if (g.data_term)
+      dat += 0.5 * (u - f) * (u - f) * sG;
+    else
+      dat += (u - (f == 0.0 ? 0.0 : f * log(u))) * sG;
     double q1, q2, q1m = 0.0, q2m = 0.0, d;
     mtp(g, i, q1, q2);
     if (x > 0) mtp(g, i - 1, q1m, d);
     if (y > 0) mtp(g, i - g.pitch, d, q2m);
     double div = ((x < g.W - 1) ? q1 : 0.0) - q1m + ((y < g.H - 1) ? q2 : 0.0) - q2m;
     double aa = g.lambda * sG, w = -div;
-    double us = (aa + w > 0.0) ? aa * f / (aa + w) : g.u_max;
-    us = fmin(fmax(us, g.u_min), g.u_max);
-    dua += aa * (us - (f == 0.0 ? 0.0 : f * log(us))) + w * us;
+    if (g.data_term) {
+      dua += w * f - w * w / (2.0 * aa);
+    } else {
+      double us = (aa + w > 0.0) ? aa * f / (aa + w) : g.u_max;
+      us = fmin(fmax(us, g.u_min), g.u_max);
+      dua += aa * (us - (f == 0.0 ? 0.0 : f * log(us))) + w * us;
+    }
   }
   s[0][threadIdx.x] = reg;
   s[1][threadIdx.x] = dat;
@@ -129,9 +143,10 @@ __global__ void __launch_bounds__(kStaticChunks) k_gap_static_final(const double
 
 extern "C" int evr_gap_static(const float* u, const float* p1, const float* p2, const float* p3,
                               const float* f, const float* tx, const float* ty, int W, int H,
-                              int pitch, float lambda, float u_min, float u_max, double* out_dev,
-                              void* cuda_stream) {
+                              int pitch, float lambda, float u_min, float u_max, int data_term,
+                              double* out_dev, void* cuda_stream) {
   if (!u || !p1 || !p2 || !p3 || !f || !tx || !ty || !out_dev) return EVR_ERR_INVALID_ARG;
+  if (data_term != 0 && data_term != 1) return EVR_ERR_INVALID_ARG;
   if (W <= 0 || H <= 0 || pitch < W) return EVR_ERR_INVALID_ARG;
   if ((long long)W * H > EVR_GAP_STATIC_MAX_PIXELS) return EVR_ERR_INVALID_ARG;
   if (!(lambda > 0.f) || !(u_min > 0.f) || !(u_min < u_max)) return EVR_ERR_INVALID_ARG;
@@ -140,7 +155,8 @@ extern "C" int evr_gap_static(const float* u, const float* p1, const float* p2, 
   double* partials = nullptr;
   int rc = scratch_address(dev, &partials);
   if (rc) return rc;
-  GapIn g{u, p1, p2, p3, f, tx, ty, W, H, pitch, (double)lambda, (double)u_min, (double)u_max};
+  GapIn g{u, p1, p2, p3, f, tx, ty, W, H, pitch, data_term, (double)lambda, (double)u_min,
+          (double)u_max};
   const int chunks = (int)(((long long)W * H + kChunk - 1) / kChunk);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   k_gap_static_partial<<<chunks, kThreads, 0, st>>>(g, partials);
