@@ -7,6 +7,11 @@
  * step and no blocking or fusion, so that it can be checked against the paper by
  * eye.  Built with -O2 -ffp-contract=off (no fused multiply-add).
  *
+ * The per-pixel loops of one step carry "omp parallel for": their iterations are
+ * independent (each writes only its own pixel, reading the previous step's arrays),
+ * so a build with -fopenmp computes the same bits on any number of threads; without
+ * -fopenmp the pragmas are ignored.  Only the CPU-baseline timing uses that build.
+ *
  * Readings taken where the paper is silent (all are parameters, shared with the
  * CUDA library by value, never by code):
  *  - t(x,y) is the time since the pixel's last event (Sec. 3.1), scaled by
@@ -32,6 +37,7 @@
  * finite differences after Chambolle 2004: forward difference, zero on the last
  * column for L_x and on the last row for L_y). */
 void orc_grad(int W, int H, const double* a, double* ax, double* ay) {
+#pragma omp parallel for
   for (int y = 0; y < H; ++y) {
     for (int x = 0; x < W; ++x) {
       int i = y * W + x;
@@ -46,6 +52,7 @@ void orc_grad(int W, int H, const double* a, double* ax, double* ay) {
  * G = det g = 1 + t_x^2 + t_y^2, with t_x = L_x t, t_y = L_y t (after Eq. 3). */
 void orc_metric(int W, int H, const double* t, double* tx, double* ty, double* G) {
   orc_grad(W, H, t, tx, ty);
+#pragma omp parallel for
   for (int i = 0; i < W * H; ++i) G[i] = 1.0 + tx[i] * tx[i] + ty[i] * ty[i];
 }
 
@@ -57,6 +64,7 @@ void orc_Lg(int W, int H, const double* tx, const double* ty, const double* G,
   double* ux = (double*)malloc(sizeof(double) * (size_t)n);
   double* uy = (double*)malloc(sizeof(double) * (size_t)n);
   orc_grad(W, H, u, ux, uy);
+#pragma omp parallel for
   for (int i = 0; i < n; ++i) {
     double a = tx[i], b = ty[i];
     g1[i] = ((1.0 + b * b) * ux[i] - a * b * uy[i]) / G[i];
@@ -77,12 +85,14 @@ void orc_divg(int W, int H, const double* tx, const double* ty, const double* G,
   int n = W * H;
   double* q1 = (double*)malloc(sizeof(double) * (size_t)n);
   double* q2 = (double*)malloc(sizeof(double) * (size_t)n);
+#pragma omp parallel for
   for (int i = 0; i < n; ++i) {
     double a = tx[i], b = ty[i];
     /* column 1 and column 2 of M, dotted with (p1, p2, p3) */
     q1[i] = ((1.0 + b * b) * p1[i] - a * b * p2[i] + a * p3[i]) / G[i];
     q2[i] = (-a * b * p1[i] + (1.0 + a * a) * p2[i] + b * p3[i]) / G[i];
   }
+#pragma omp parallel for
   for (int y = 0; y < H; ++y) {
     for (int x = 0; x < W; ++x) {
       int i = y * W + x;
@@ -196,15 +206,18 @@ void orc_pd_iterations_dt(int W, int H, const double* tx, const double* ty, cons
   for (int k = 0; k < K; ++k) {
     /* primal: argument u_k - tau L_g^* p_k */
     orc_divg(W, H, tx, ty, G, p1, p2, p3, dv);
+#pragma omp parallel for
     for (int i = 0; i < n; ++i) {
       double v = u[i] + tau * dv[i];
       double beta = tau * lambda * sqrt(G[i]);
       un[i] = data_term ? orc_prox_l2(v, beta, f[i]) : orc_prox_kl(v, beta, f[i], u_min, u_max);
     }
     /* over-relaxation 2 u_{k+1} - u_k */
+#pragma omp parallel for
     for (int i = 0; i < n; ++i) ub[i] = 2.0 * un[i] - u[i];
     /* dual: ascent on L_g of the extrapolated primal, then projection */
     orc_Lg(W, H, tx, ty, G, ub, g1, g2, g3);
+#pragma omp parallel for
     for (int i = 0; i < n; ++i) {
       double out[3];
       orc_project(p1[i] + sigma * g1[i], p2[i] + sigma * g2[i], p3[i] + sigma * g3[i],
@@ -213,6 +226,7 @@ void orc_pd_iterations_dt(int W, int H, const double* tx, const double* ty, cons
       p2[i] = out[1];
       p3[i] = out[2];
     }
+#pragma omp parallel for
     for (int i = 0; i < n; ++i) u[i] = un[i];
   }
   free(dv);

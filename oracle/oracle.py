@@ -23,8 +23,10 @@ _SRC = os.path.join(_HERE, "evr_oracle.c")
 _HDR = os.path.join(_HERE, "evr_oracle.h")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liborc.so")
+_OMP_PATH = os.path.join(_OUT_DIR, "liborc_omp.so")  # same source, OpenMP over pixels
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 ORC_OK = 0
 ORC_ERR_INVALID_ARG = -1
@@ -36,18 +38,22 @@ ORC_ERR_OOM = -5
 U, P1, P2, P3, F, TAU, G, TLAST, NPOS, NNEG, TREF, TINIT, TX, TY = range(14)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/_build/liborc.so (gcc, no FMA contraction)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liborc.so (gcc, no FMA contraction), or with
+    omp=True into liborc_omp.so: the same source with its per-pixel loops spread over the
+    host's cores by OpenMP (bit-identical results; used to time the CPU baseline)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
+    path = _OMP_PATH if omp else _LIB_PATH
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= newest:
+        return path
+    tmp = path + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC",
-           "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
+           "-shared", "-Wall", "-Wno-unknown-pragmas", *(["-fopenmp"] if omp else []),
+           "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 class _Params(ctypes.Structure):
@@ -75,11 +81,11 @@ class _Params(ctypes.Structure):
 _D = ctypes.POINTER(ctypes.c_double)
 
 
-def _lib_handle():
-    global _lib
+def _lib_handle(omp: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+        if (_lib_omp if omp else _lib) is None:
+            lib = ctypes.CDLL(build(omp=omp))
             vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
             lib.orc_grad.argtypes = [i, i, _D, _D, _D]
             lib.orc_metric.argtypes = [i, i, _D, _D, _D, _D]
@@ -107,8 +113,11 @@ def _lib_handle():
             lib.orc_get.argtypes = [vp, i, vp]
             lib.orc_set.argtypes = [vp, i, vp]
             lib.orc_stream_energy.argtypes = [vp, _D, _D]
-            _lib = lib
-        return _lib
+            if omp:
+                _lib_omp = lib
+            else:
+                _lib = lib
+        return _lib_omp if omp else _lib
 
 
 def _dp(a: np.ndarray):
@@ -279,18 +288,19 @@ class OracleParams:
 class OracleStream:
     """One event stream of a W x H sensor, solved by the FP64 oracle."""
 
-    def __init__(self, W: int, H: int, params: OracleParams | None = None):
+    def __init__(self, W: int, H: int, params: OracleParams | None = None, omp: bool = False):
+        """omp=True: the OpenMP build (same results, the host's cores; CPU baseline)."""
         self.W, self.H = int(W), int(H)
         self.params = params or OracleParams()
         self._c_params = self.params._c()
-        lib = _lib_handle()
+        self._lib = lib = _lib_handle(omp)
         self._h = lib.orc_create(self.W, self.H, ctypes.byref(self._c_params))
         if not self._h:
             raise ValueError("oracle rejected the sensor size or parameters")
 
     def close(self):
         if getattr(self, "_h", None):
-            _lib_handle().orc_destroy(self._h)
+            self._lib.orc_destroy(self._h)
             self._h = None
 
     __del__ = close
@@ -303,11 +313,11 @@ class OracleStream:
         n = len(x)
         if not (len(y) == len(t) == len(pol) == n):
             raise ValueError("event arrays differ in length")
-        return _lib_handle().orc_push(self._h, x.ctypes.data, y.ctypes.data, t.ctypes.data,
+        return self._lib.orc_push(self._h, x.ctypes.data, y.ctypes.data, t.ctypes.data,
                                       pol.ctypes.data, n)
 
     def solve(self, K: int) -> int:
-        return _lib_handle().orc_solve(self._h, int(K))
+        return self._lib.orc_solve(self._h, int(K))
 
     _DT = {U: np.float64, P1: np.float64, P2: np.float64, P3: np.float64, F: np.float64,
            TAU: np.float64, G: np.float64, TX: np.float64, TY: np.float64,
@@ -318,7 +328,7 @@ class OracleStream:
             out = np.zeros(1, dtype=np.int64)
         else:
             out = np.empty((self.H, self.W), dtype=self._DT[which])
-        rc = _lib_handle().orc_get(self._h, which, out.ctypes.data)
+        rc = self._lib.orc_get(self._h, which, out.ctypes.data)
         if rc:
             raise ValueError(f"orc_get({which}) -> {rc}")
         return out[0] if which in (TREF, TINIT) else out
@@ -328,7 +338,7 @@ class OracleStream:
             arr = np.array([value], dtype=np.int64)
         else:
             arr = np.ascontiguousarray(value, dtype=self._DT[which]).reshape(self.H, self.W)
-        rc = _lib_handle().orc_set(self._h, which, arr.ctypes.data)
+        rc = self._lib.orc_set(self._h, which, arr.ctypes.data)
         if rc:
             raise ValueError(f"orc_set({which}) -> {rc}")
 
@@ -347,5 +357,5 @@ class OracleStream:
 
     def energy(self):
         pr, du = ctypes.c_double(), ctypes.c_double()
-        _lib_handle().orc_stream_energy(self._h, ctypes.byref(pr), ctypes.byref(du))
+        self._lib.orc_stream_energy(self._h, ctypes.byref(pr), ctypes.byref(du))
         return pr.value, du.value

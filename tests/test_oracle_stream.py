@@ -193,3 +193,34 @@ def test_invalid_parameters_rejected():
             O.OracleStream(4, 4, O.OracleParams(**bad))
     with pytest.raises(ValueError):
         O.OracleStream(0, 4)
+
+
+def test_openmp_build_is_bit_identical_to_the_serial_oracle():
+    """The CPU baseline's OpenMP build (per-pixel loops over the host's cores) computes the
+    same bits as the serial oracle: its loops write only their own pixel."""
+    import os
+    import subprocess
+    import sys
+    code = r"""
+import numpy as np
+from evsim import CONFIGS, make_stream
+from oracle import oracle as O
+cfg = CONFIGS["rects128"].with_events(3000)
+st = make_stream(cfg)
+outs = []
+for omp in (False, True):
+    o = O.OracleStream(cfg.W, cfg.H, omp=omp)
+    for a in range(0, len(st), cfg.packet):
+        s = st.slice(a, a + cfg.packet)
+        assert o.push(s.x, s.y, s.t, s.pol) == 0
+        o.solve(cfg.iters)
+    outs.append((o.u.copy(), o.get(O.P1).copy(), o.get(O.P3).copy()))
+for a, b in zip(*outs):
+    assert np.array_equal(a, b)
+print("identical")
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="4")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and "identical" in r.stdout, r.stderr[-2000:]
