@@ -230,20 +230,41 @@ int evr_gap(evr_stream* s, double* primal, double* dual);
  * it exists for callers that may not allocate once they are running -- a real-time
  * loop that cannot afford cudaMalloc's implicit device synchronisation, or a host
  * application that owns all device memory through its own pool.
- *   u, p1, p2, p3, f, tx, ty: device planes of H rows of `pitch` floats (pitch >= W,
+ *   u, p1, p2, p3, f, tx, ty: device planes of H rows of `pitch` FP32 values (pitch >= W,
  *     row-major, x the column), as read back from a stream (u, p, f, L_x t, L_y t);
+ *     each must hold at least pitch*H floats;
  *   lambda, u_min, u_max: the model's parameters;
+ *   data_term: 0 the generalised KL term with the box [u_min, u_max] (Eq. 5), 1 the L2
+ *     term of Eq. 7 (no box; u_min, u_max still validated, otherwise unused) -- the
+ *     value of evr_params.data_term of the stream the planes come from;
  *   out_dev: device memory for 2 doubles, receives {primal, dual};
  *   cuda_stream: cudaStream_t to queue on (NULL: the legacy default stream).
  * Asynchronous.  The reduction's scratch is one fixed 24 KiB device array inside the
  * library (held by every GPU that loads it until the process exits) and shared by
- * all calls: calls whose work overlaps on the GPU race on it.  The first call on a
- * device looks up the array's address; make that first call before any stream
- * capture.  Errors: EVR_ERR_INVALID_ARG (null pointer, W or H <= 0, pitch < W,
- * W*H > EVR_GAP_STATIC_MAX_PIXELS, lambda <= 0, bad box), EVR_ERR_CUDA. */
+ * all calls: each call overwrites the partials it uses before reading them, and calls
+ * whose work overlaps on the GPU race on it.  The first call on a device looks up
+ * the array's address and caches it; make that first call before any stream
+ * capture.  A device reset (cudaDeviceReset) invalidates the cached address: do not
+ * call the entry point on a device after resetting it.  Errors: EVR_ERR_INVALID_ARG
+ * (null pointer, W or H <= 0, pitch < W, W*H > EVR_GAP_STATIC_MAX_PIXELS, lambda <= 0,
+ * bad box, data_term not 0 or 1), EVR_ERR_CUDA. */
 int evr_gap_static(const float* u, const float* p1, const float* p2, const float* p3,
                    const float* f, const float* tx, const float* ty, int W, int H, int pitch,
-                   float lambda, float u_min, float u_max, double* out_dev, void* cuda_stream);
+                   float lambda, float u_min, float u_max, int data_term, double* out_dev,
+                   void* cuda_stream);
+
+/* ---- measurement support (the paper has no counterpart) ----
+ * Measured bandwidth of one memory level of this GPU, the denominator of a roofline:
+ *   level 0: L2 -- a copy between two 16 MiB device buffers that stay resident in L2,
+ *            bytes read + written per second;
+ *   level 1: shared memory -- conflict-free 16-byte reads by one 1024-thread CTA per SM,
+ *            aggregate over all SMs (a kernel on k SMs is bounded by k / SMs of it).
+ * *gbs receives GB/s (1e9 bytes per second), the best of five timed launches (CUDA
+ * events on cuda_stream, NULL: the legacy default stream) after one warm-up.
+ * Allocates and frees 32 MiB of device memory (level 0) or a few bytes (level 1) and
+ * synchronises.  Errors: EVR_ERR_INVALID_ARG (null gbs, unknown level), EVR_ERR_OOM,
+ * EVR_ERR_CUDA. */
+int evr_measure_peak(int level, double* gbs, void* cuda_stream);
 
 /* ---- batching: many independent streams solved together ----
  * A batch holds n streams of possibly different sizes sharing one evr_params.  A step
@@ -409,14 +430,30 @@ int evr_kernel_time(evr_stream* s, double* ms, int64_t* launches, int64_t* pixel
  * under a second.  Synchronises. */
 int evr_selftest_wait_timeout(evr_stream* s);
 
+/* Self-test of the cluster solver's bounded waits (the paper has no counterpart): runs
+ * a few iterations of a cluster configuration (kind 3, at least two CTAs, one that fits
+ * the sensor) in which one CTA of every cluster never sends its edges, so its
+ * neighbours' waits run out; the state is saved first and restored afterwards.
+ * Returns the status the device reported (EVR_ERR_TIMEOUT when detection works),
+ * EVR_ERR_NOT_SUPPORTED when no cluster configuration fits the sensor.  Takes well
+ * under a second.  Synchronises. */
+int evr_selftest_cluster_wait_timeout(evr_stream* s);
+
 /* Fault injection for tests (the paper has no counterpart): the n-th library
  * allocation of device or page-locked host memory after this call fails as if memory
  * were exhausted (the calls that make it then return EVR_ERR_OOM or EVR_ERR_CUDA and
  * release what they had allocated); n <= 0 disables.  Returns EVR_OK. */
 int evr_test_fail_alloc_after(int n);
 
-/* Description of the solver in use, e.g. "tiled 32x32 R4"; static storage. */
+/* Description of the solver in use, e.g. "tiled 32x32 R4" or "cluster 4x4 of 32x32 R0";
+ * static storage. */
 const char* evr_solver_name(evr_stream* s);
+
+/* 1 when the solver configuration is settled (EVR_SOLVER_AUTO: the first solve has tuned
+ * and the online refinement over the next solves has decided; fixed configurations:
+ * always), 0 while later solves may still change it, EVR_ERR_INVALID_ARG for a null
+ * handle. */
+int evr_solver_settled(evr_stream* s);
 
 /* Static description of a return code. */
 const char* evr_strerror(int code);

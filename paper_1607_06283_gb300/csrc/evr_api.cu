@@ -204,9 +204,16 @@ void set_name(evr_stream* s) {
   } else {
     const SolverCfg& c = kSolverCfgs[s->cfg];
     const TileShape& t = kTileShapes[c.shape];
-    std::snprintf(s->name, sizeof(s->name), "%s %dx%d R%d (%d threads, %d CTAs)",
-                  c.kind == 2 ? "persistent" : "tiled", t.EW, t.EH, c.R, 32 * t.NTY,
-                  solver_cfg_ctas(s->P, c));
+    if (c.kind == 3)
+      std::snprintf(s->name, sizeof(s->name), "cluster %dx%d of %dx%d R%d (%d threads, %d CTAs)",
+                    c.cx, c.cy, t.EW, t.EH, c.R, 32 * t.NTY, solver_cfg_ctas(s->P, c));
+    else if (c.kind == 4)
+      std::snprintf(s->name, sizeof(s->name), "staged %dx%d R%d (%d threads, %d CTAs)", t.EW,
+                    t.EH, c.R, 32 * t.NTY, solver_cfg_ctas(s->P, c));
+    else
+      std::snprintf(s->name, sizeof(s->name), "%s %dx%d R%d (%d threads, %d CTAs)",
+                    c.kind == 2 ? "persistent" : "tiled", t.EW, t.EH, c.R, 32 * t.NTY,
+                    solver_cfg_ctas(s->P, c));
   }
 }
 
@@ -303,13 +310,26 @@ int enqueue_iterations(evr_stream* s, int iters, int cur, cudaStream_t st, int* 
     return cur;
   }
   const SolverCfg& cfg = kSolverCfgs[s->cfg];
+  if (cfg.kind == 3 && cfg.R == 0) {  // one cluster over the sensor: one launch
+    if (launch_cluster(s->P, cfg, cur, iters, 0, c, st, front, nullptr)) return -1;
+    *launches = 1;
+    return 1 - cur;
+  }
   for (int done = 0, pass = 0; done < iters; done += cfg.R, ++pass) {
     int it = iters - done < cfg.R ? iters - done : cfg.R;
-    if (launch_tiled_pass(s->P, cfg, cur, it, pass, c, st, front)) return -1;
+    const int e = cfg.kind == 3   ? launch_cluster(s->P, cfg, cur, it, pass, c, st, front, nullptr)
+                  : cfg.kind == 4 ? launch_staged(s->P, cfg, cur, it, pass, c, st)
+                                  : launch_tiled_pass(s->P, cfg, cur, it, pass, c, st, front);
+    if (e) return -1;
     cur = 1 - cur;
     *launches += 1;
   }
   return cur;
+}
+
+// Passes of one packet's solve with configuration cfg (kind 1 or 3).
+int solve_passes(const SolverCfg& cfg, int iters) {
+  return (cfg.kind == 3 && cfg.R == 0) ? 1 : (iters + cfg.R - 1) / cfg.R;
 }
 
 // Run one packet's iterations with configuration index `ci` (kind 1 or 2) directly
@@ -351,8 +371,11 @@ void autotune(evr_stream* s, int iters) {
   int best_cfg = 0;
   std::vector<std::pair<float, int>> timed;  // (ms, configuration) of kind-1 trials
   for (int ci = 0; ci < kNumSolverCfgs; ++ci) {
-    if (!solver_cfg_usable(s->P, kSolverCfgs[ci])) continue;
+    // the persistent configurations were measured slower than relaunching on every
+    // workload (their L2 flag exchange); they stay selectable through tile_config
+    if (kSolverCfgs[ci].kind == 2) continue;
     if (s->P.storage != 0 && kSolverCfgs[ci].kind != 1) continue;  // 16-bit p: kind 1 only
+    if (!solver_cfg_usable(s->P, kSolverCfgs[ci])) continue;
     s->cfg = ci;
     clear_flags(s);
     bool ok = run_cfg_direct(s, ci, iters) == 0;  // warm-up (module load)
@@ -370,22 +393,21 @@ void autotune(evr_stream* s, int iters) {
       cudaMemset(&s->P.sc->status, 0, sizeof(int));
     }
     if (cudaGetLastError() == cudaSuccess && ok) {
-      if (kSolverCfgs[ci].kind == 1) timed.emplace_back(ms, ci);
+      timed.emplace_back(ms, ci);
       if (ms < best) {
         best = ms;
         best_cfg = ci;
       }
     }
   }
-  // candidates for the online refinement: kind-1 configurations within 25 % of the best
+  // candidates for the online refinement: configurations within 25 % of the best
   // back-to-back time (these trials run warm and without the packet's front launches;
   // real solves decide among them)
   std::sort(timed.begin(), timed.end());
   s->n_cand = 0;
   s->refine_done = 0;
-  if (kSolverCfgs[best_cfg].kind == 1)
-    for (const auto& t : timed)
-      if (s->n_cand < kRefineCands && t.first <= 1.25f * best) s->cand[s->n_cand++] = t.second;
+  for (const auto& t : timed)
+    if (s->n_cand < kRefineCands && t.first <= 1.25f * best) s->cand[s->n_cand++] = t.second;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   float* dst[4] = {s->P.u[cur0], s->P.p1[cur0], s->P.p2[cur0], s->P.p3[cur0]};
@@ -739,9 +761,18 @@ namespace {
 bool front_fused(const evr_stream* s, int iters) {
   if (s->cfg < 0) return false;
   const SolverCfg& cfg = kSolverCfgs[s->cfg];
-  if (cfg.kind != 1 || !tiled_front_fusable(cfg, s->P.storage)) return false;
   if (s->prm.data_mode != 0 || (s->prm.tvl1_iters > 0 && s->prm.manifold)) return false;
+  if (cfg.kind == 3) return cfg.R == 0 || (iters + cfg.R - 1) / cfg.R >= 2;
+  if (cfg.kind != 1 || !tiled_front_fusable(cfg, s->P.storage)) return false;  // kind 4 too
   return (iters + cfg.R - 1) / cfg.R >= 2;
+}
+
+// Whether the packet's push runs inside the solver's one launch (one cluster over the
+// sensor, front fused, a packet the single-launch push takes).
+bool push_in_solver(const evr_stream* s, size_t n, int iters) {
+  if (s->cfg < 0) return false;
+  const SolverCfg& cfg = kSolverCfgs[s->cfg];
+  return cfg.kind == 3 && cfg.R == 0 && n > 0 && n <= 32768 && front_fused(s, iters);
 }
 }  // namespace
 
@@ -826,7 +857,7 @@ int evr_solve(evr_stream* s, int iters) {
     if (s->cfg < 0) {
       launches += 2 * iters;
     } else {
-      const int passes = (iters + kSolverCfgs[s->cfg].R - 1) / kSolverCfgs[s->cfg].R;
+      const int passes = solve_passes(kSolverCfgs[s->cfg], iters);
       launches += passes;
       end_cur = (passes % 2) ? 1 - s->cur : s->cur;
     }
@@ -884,7 +915,10 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
                const uint16_t* x, const uint16_t* y, const long long* t, const int8_t* pol) {
   cudaStream_t st = s->stream;
   const bool fuse = front_fused(s, iters);  // the prologue inside the first pass
+  // one cluster over the sensor: the push runs inside the solver's single launch
+  const bool in_solver = push_in_solver(s, (size_t)n, iters);
   const PrologueConsts pc = prologue_consts(s);
+  const PushArgs pa{x, y, t, pol, n};
   GraphKey key{iters, s->cur, copy_src ? 3 : 2, s->cfg};
   auto it = s->fused.find(key);
   evr_stream::Fused* fg = nullptr;
@@ -897,12 +931,18 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
     if (copy_src && cudaMemcpyAsync(s->dstage, copy_src, copy_bytes, cudaMemcpyHostToDevice,
                                     s->cap_stream) != cudaSuccess)
       r = -1;
-    if (r == 0 && launch_push(s->P, x, y, t, pol, n, s->cap_stream)) r = -1;
-    if (r == 0 && !fuse) r = enqueue_front(s, s->cap_stream);
-    // enqueue_iterations returns the buffer holding the result, or -1
-    if (r == 0 && enqueue_iterations(s, iters, s->cur, s->cap_stream, &captured,
-                                     fuse ? &pc : nullptr) < 0)
-      r = -1;
+    if (in_solver) {
+      if (r == 0 && launch_cluster(s->P, kSolverCfgs[s->cfg], s->cur, iters, 0,
+                                   solve_consts(s), s->cap_stream, &pc, &pa))
+        r = -1;
+    } else {
+      if (r == 0 && launch_push(s->P, x, y, t, pol, n, s->cap_stream)) r = -1;
+      if (r == 0 && !fuse) r = enqueue_front(s, s->cap_stream);
+      // enqueue_iterations returns the buffer holding the result, or -1
+      if (r == 0 && enqueue_iterations(s, iters, s->cur, s->cap_stream, &captured,
+                                       fuse ? &pc : nullptr) < 0)
+        r = -1;
+    }
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &nf.graph);
     size_t roots = 1, deps = 1;
     cudaGraphNode_t root = nullptr;
@@ -929,17 +969,22 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
                                                        copy_bytes, cudaMemcpyHostToDevice) !=
                         cudaSuccess)
       return EVR_ERR_CUDA;
-    // this call's packet: the push node's arguments (Planes, x, y, t, pol, n)
-    cudaKernelNodeParams kp;
-    if (cudaGraphKernelNodeGetParams(fg->push, &kp) != cudaSuccess) return EVR_ERR_CUDA;
-    void* args[6] = {(void*)&s->P, (void*)&x, (void*)&y, (void*)&t, (void*)&pol, (void*)&n};
-    kp.kernelParams = args;
-    kp.extra = nullptr;
-    if (cudaGraphExecKernelNodeSetParams(fg->exec, fg->push, &kp) != cudaSuccess)
-      return EVR_ERR_CUDA;
+    if (in_solver) {  // the cluster launch's arguments with this call's packet
+      if (cluster_node_set_push(fg->exec, fg->push, s->P, kSolverCfgs[s->cfg], s->cur, iters,
+                                solve_consts(s), pc, pa))
+        return EVR_ERR_CUDA;
+    } else {
+      // this call's packet: the push node's arguments (Planes, x, y, t, pol, n)
+      cudaKernelNodeParams kp;
+      if (cudaGraphKernelNodeGetParams(fg->push, &kp) != cudaSuccess) return EVR_ERR_CUDA;
+      void* args[6] = {(void*)&s->P, (void*)&x, (void*)&y, (void*)&t, (void*)&pol, (void*)&n};
+      kp.kernelParams = args;
+      kp.extra = nullptr;
+      if (cudaGraphExecKernelNodeSetParams(fg->exec, fg->push, &kp) != cudaSuccess)
+        return EVR_ERR_CUDA;
+    }
   }
-  const int passes =
-      (s->cfg < 0) ? 0 : (iters + kSolverCfgs[s->cfg].R - 1) / kSolverCfgs[s->cfg].R;
+  const int passes = (s->cfg < 0) ? 0 : solve_passes(kSolverCfgs[s->cfg], iters);
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (s->timing) {
     if ((int)s->ev_used.size() >= kMaxTimingPairs) resolve_timing(s);
@@ -958,7 +1003,7 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
     s->ev_used.push_back(ev);
     const int front =
         fuse ? 0 : 1 + ((s->prm.tvl1_iters > 0 && s->prm.manifold) ? 1 + 2 * s->prm.tvl1_iters : 0);
-    s->ev_launches.push_back(1 + front + (s->cfg < 0 ? 2 * iters : passes));
+    s->ev_launches.push_back((in_solver ? 0 : 1) + front + (s->cfg < 0 ? 2 * iters : passes));
     s->ev_pixiters.push_back((long long)s->W * s->H * iters);
   }
   if (s->cfg >= 0 && passes % 2) s->cur = 1 - s->cur;
@@ -1241,7 +1286,45 @@ int evr_selftest_wait_timeout(evr_stream* s) {
   return rc;
 }
 
+int evr_selftest_cluster_wait_timeout(evr_stream* s) {
+  if (!s) return EVR_ERR_INVALID_ARG;
+  int ci = -1;  // a cluster configuration of at least two CTAs that fits the sensor
+  for (int k = 0; k < kNumSolverCfgs && ci < 0; ++k)
+    if (kSolverCfgs[k].kind == 3 && kSolverCfgs[k].cx * kSolverCfgs[k].cy >= 2 &&
+        solver_cfg_usable(s->P, kSolverCfgs[k]))
+      ci = k;
+  if (ci < 0) return EVR_ERR_NOT_SUPPORTED;
+  int rc = sync_status(s);  // report nothing stale as the test's result
+  if (rc != EVR_OK && rc != EVR_ERR_TIMEOUT) return rc;
+  const size_t plane = (size_t)s->pitch * s->H * sizeof(float);
+  float* save = nullptr;
+  if (dev_alloc((void**)&save, 4 * plane) != cudaSuccess) return EVR_ERR_OOM;
+  const int cur0 = s->cur;
+  float* live[4] = {s->P.u[cur0], s->P.p1[cur0], s->P.p2[cur0], s->P.p3[cur0]};
+  for (int k = 0; k < 4; ++k)
+    cudaMemcpyAsync((char*)save + k * plane, live[k], plane, cudaMemcpyDeviceToDevice, s->stream);
+  const SolverCfg& cfg = kSolverCfgs[ci];
+  // rank 0 of every cluster sends nothing: its neighbours' waits for its edges run out
+  const int iters = cfg.R > 0 ? cfg.R : 3;
+  int e = launch_cluster(s->P, cfg, cur0, iters, 2, solve_consts(s), s->stream, nullptr,
+                         nullptr, 0);
+  rc = e ? EVR_ERR_CUDA : sync_status(s);  // reads and clears the status
+  for (int k = 0; k < 4; ++k)
+    cudaMemcpyAsync(live[k], (char*)save + k * plane, plane, cudaMemcpyDeviceToDevice, s->stream);
+  cudaStreamSynchronize(s->stream);
+  cudaFree(save);
+  s->cur = cur0;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return EVR_ERR_CUDA;
+  return rc;
+}
+
 const char* evr_solver_name(evr_stream* s) { return s ? s->name : ""; }
+
+int evr_solver_settled(evr_stream* s) {
+  if (!s) return EVR_ERR_INVALID_ARG;
+  const bool refining = s->n_cand > 1 && s->refine_done < s->n_cand * kRefineReps;
+  return (s->tuned && !refining) ? 1 : 0;
+}
 
 int evr_test_fail_alloc_after(int n) {
   g_fail_countdown.store(n > 0 ? n : 0);

@@ -103,16 +103,24 @@ __device__ __forceinline__ float data_image(float base, int np, int nn,
 // configuration is a template, a halo width R and a kind:
 //   kind 1: one launch per R iterations (state in HBM/L2 between launches);
 //   kind 2: one cooperative launch per packet, state in registers, R-wide halo bands
-//           exchanged with the 8 neighbouring CTAs through L2 every R iterations.
+//           exchanged with the 8 neighbouring CTAs through L2 every R iterations;
+//   kind 3: thread-block clusters of cx x cy CTAs whose tiles form one super-tile; the
+//           CTAs exchange their edge values every iteration through distributed shared
+//           memory, and only the super-tile carries an R-pixel halo.  R = 0: one cluster
+//           covers the sensor and runs every iteration of a packet (with the packet's
+//           push and prologue) in one launch;
+//   kind 4: as kind 1, with a persistent grid whose CTAs walk the tiles and stage each
+//           tile's planes in shared memory with tensor copies, one tile ahead.
 struct TileShape {
   int EW, EH, NTY;
 };
 struct SolverCfg {
   int kind, shape, R;
+  int cx, cy;  // kind 3: cluster shape in CTAs
 };
 constexpr int kNumTileShapes = 8;
 extern const TileShape kTileShapes[kNumTileShapes];
-constexpr int kNumSolverCfgs = 46;
+constexpr int kNumSolverCfgs = 70;
 extern const SolverCfg kSolverCfgs[kNumSolverCfgs];
 
 constexpr int kGapBlocks = 304;   // fixed: the reduction order does not depend on W, H
@@ -179,6 +187,38 @@ int launch_tiled_pass_batch(const BatchRef& B, int n_work, const SolverCfg& cfg,
 // its neighbours' bounded waits run out and the launch ends with EVR_ERR_TIMEOUT.
 int launch_persistent(const Planes& P, const SolverCfg& cfg, int cur, int iters, int base,
                       const SolveConsts& c, void* stream, int silent_cta = -1);
+// kind 3 (evr_cluster.cu): `iters` iterations from buffer src into 1 - src, at most R per
+// launch (R = 0: all of them).  front != NULL: the packet's front is fused (R = 0: the
+// one launch computes the prologue's constants and clears the event counts; R > 0: as
+// kind 1, pass 0 computes them and pass 1 clears the counts).  push != NULL (R = 0 only):
+// the launch first validates and integrates the packet x, y, t, pol of n events
+// (n <= 32768).  silent_rank >= 0 (wait self-test only): that CTA of the cluster sends
+// nothing, so its neighbours' bounded waits run out and the launch ends with
+// EVR_ERR_TIMEOUT.
+struct PushArgs {
+  const uint16_t *x, *y;
+  const long long* t;
+  const int8_t* pol;
+  int n;
+};
+int launch_cluster(const Planes& P, const SolverCfg& cfg, int src, int iters, int pass,
+                   const SolveConsts& c, void* stream, const PrologueConsts* front,
+                   const PushArgs* push, int silent_rank = -1);
+// Updates the kernel node `node` of an instantiated graph, captured by launch_cluster with
+// a push, to push the packet `push` instead (all other arguments as captured).
+int cluster_node_set_push(void* graph_exec, void* node, const Planes& P, const SolverCfg& cfg,
+                          int src, int iters, const SolveConsts& c, const PrologueConsts& front,
+                          const PushArgs& push);
+bool cluster_cfg_usable(const Planes& P, const SolverCfg& cfg);
+int cluster_cfg_ctas(const Planes& P, const SolverCfg& cfg);
+// kind 4 (evr_staged.cu, FP32): a persistent pass of `iters` <= R iterations from buffer
+// src into 1 - src whose CTAs stage each tile's planes with tensor copies one tile ahead
+// (the packet's prologue runs as its own launch before the first pass).
+int launch_staged(const Planes& P, const SolverCfg& cfg, int src, int iters, int pass,
+                  const SolveConsts& c, void* stream);
+bool staged_cfg_usable(const Planes& P, const SolverCfg& cfg);
+int staged_cfg_ctas(const Planes& P, const SolverCfg& cfg);
+
 // Whether the configuration can run on this sensor (tile fits, grid co-resident).
 bool solver_cfg_usable(const Planes& P, const SolverCfg& cfg);
 int solver_cfg_ctas(const Planes& P, const SolverCfg& cfg);

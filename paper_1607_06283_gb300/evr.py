@@ -91,11 +91,14 @@ def _load():
         "evr_enable_kernel_timing": ([vp, i], i),
         "evr_kernel_time": ([vp, vp, vp, vp], i),
         "evr_solver_name": ([vp], ctypes.c_char_p),
+        "evr_solver_settled": ([vp], i),
         "evr_selftest_wait_timeout": ([vp], i),
+        "evr_selftest_cluster_wait_timeout": ([vp], i),
         "evr_strerror": ([i], ctypes.c_char_p),
         "evr_test_fail_alloc_after": ([i], i),
+        "evr_measure_peak": ([i, vp, vp], i),
         "evr_gap_static": ([vp] * 7 + [i, i, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                                       vp, vp], i),
+                                       i, vp, vp], i),
         "evr_unrolled_workspace_bytes": ([i, i, i, i, i, i], sz),
         "evr_unrolled_forward": ([vp] * 5 + [i, i, i, i] + [ctypes.c_float] * 5 + [i, i] +
                                  [vp] * 4, i),
@@ -305,13 +308,35 @@ EVR_GAP_STATIC_MAX_PIXELS = 4194304
 
 
 def evr_gap_static(u, p1, p2, p3, f, tx, ty, W: int, H: int, pitch: int, lam: float,
-                   u_min: float, u_max: float, out, stream_handle: int = 0) -> int:
+                   u_min: float, u_max: float, out, stream_handle: int = 0,
+                   data_term: int = 0) -> int:
     """Gap of caller-provided device planes (torch CUDA tensors) into `out`
     (a CUDA float64 tensor of 2 elements); allocates no device memory.  Returns the
-    library's code."""
+    library's code.  Raises ValueError before calling the library when a plane is not
+    a contiguous CUDA float32 tensor of at least pitch*H elements on out's device, or
+    `out` is not a contiguous CUDA float64 tensor of at least 2 elements."""
+    import torch
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+            and out.is_contiguous() and out.numel() >= 2):
+        raise ValueError("out must be a contiguous CUDA float64 tensor of >= 2 elements")
+    need = int(pitch) * int(H)
+    for a in (u, p1, p2, p3, f, tx, ty):
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float32
+                and a.is_contiguous() and a.device == out.device and a.numel() >= need):
+            raise ValueError(f"each plane must be a contiguous CUDA float32 tensor of >= "
+                             f"pitch*H = {need} elements on {out.device}")
     ptrs = [a.data_ptr() for a in (u, p1, p2, p3, f, tx, ty)]
     return _lib.evr_gap_static(*ptrs, int(W), int(H), int(pitch), float(lam), float(u_min),
-                               float(u_max), out.data_ptr(), ctypes.c_void_p(int(stream_handle)))
+                               float(u_max), int(data_term), out.data_ptr(),
+                               ctypes.c_void_p(int(stream_handle)))
+
+
+def evr_measure_peak(level: int, stream_handle: int = 0) -> float:
+    """Measured GB/s of memory level `level` (0 L2, 1 shared memory, all SMs)."""
+    g = ctypes.c_double()
+    _check(_lib.evr_measure_peak(int(level), ctypes.byref(g), ctypes.c_void_p(int(stream_handle))),
+           "evr_measure_peak")
+    return g.value
 
 
 def evr_synchronize(h) -> int:
@@ -334,6 +359,13 @@ def evr_kernel_time(h):
 
 def evr_solver_name(h) -> str:
     return _lib.evr_solver_name(h).decode()
+
+
+def evr_solver_settled(h) -> bool:
+    rc = _lib.evr_solver_settled(h)
+    if rc < 0:
+        _check(rc, "evr_solver_settled")
+    return rc == 1
 
 
 def evr_unrolled_timing_start() -> None:

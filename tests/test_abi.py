@@ -89,3 +89,16 @@ def test_unrolled_workspace_sizing_needs_no_gpu(evr):
     for bad in [(0, H, W, n, K, 10), (W, H, W - 1, n, K, 10), (W, H, W, 0, K, 10),
                 (W, H, W, n, 0, 10), (W, H, W, n, K, 0)]:
         assert ws(*bad) == 0, bad
+
+
+def test_gap_static_binding_refuses_planes_before_the_call(evr):
+    # host tensors, wrong dtypes or short planes never reach the library (no GPU needed:
+    # the binding raises before calling it)
+    import torch
+    W, H = 8, 4
+    planes = [torch.zeros(W * H, dtype=torch.float32) for _ in range(7)]
+    out = torch.zeros(2, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        evr.evr_gap_static(*planes, W, H, W, 90.0, 0.05, 20.0, out)
+    with pytest.raises(ValueError):
+        evr.evr_gap_static(*planes, W, H, W, 90.0, 0.05, 20.0, out.float())

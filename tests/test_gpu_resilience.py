@@ -92,6 +92,35 @@ def test_wait_timeout_is_detected_and_the_stream_recovers(E):
     np.testing.assert_array_equal(a.image(), twin.image())  # solver works after the test
 
 
+# tile_config 47: one cluster of 4 x 4 CTAs over the sensor (evr_params.tile_config)
+@pytest.mark.parametrize("tile", [0, 47])
+def test_cluster_wait_timeout_is_detected_and_the_stream_recovers(E, tile):
+    """One CTA of the cluster never sends its edges: its neighbours' bounded waits run out,
+    the launch reports EVR_ERR_TIMEOUT, and the stream (state saved and restored) goes on
+    bit-identically to a twin that never ran the test."""
+    W, H = 100, 60
+    pk = packets(3, W, H, 6, 500)
+    a = E.Stream(W, H, solver=2, tile_config=tile)
+    twin = E.Stream(W, H, solver=2, tile_config=tile)
+    for g in (a, twin):
+        for x, y, t, p in pk[:3]:
+            assert g.push(x, y, t, p) == 0
+            g.solve(15)
+    t0 = time.perf_counter()
+    rc = E._lib.evr_selftest_cluster_wait_timeout(a.h)
+    dt = time.perf_counter() - t0
+    assert rc == E.EVR_ERR_TIMEOUT, rc
+    assert dt < 10.0
+    assert a.synchronize() == 0  # reported once
+    np.testing.assert_array_equal(a.image(), twin.image())  # state restored
+    for g in (a, twin):
+        for x, y, t, p in pk[3:]:
+            assert g.push(x, y, t, p) == 0
+            g.solve(15)
+    assert a.synchronize() == 0
+    np.testing.assert_array_equal(a.image(), twin.image())
+
+
 def _free_bytes():
     import torch
     torch.cuda.synchronize()

@@ -37,8 +37,9 @@ def dev(torch, pk):
             for a in (x, y, t, p)]
 
 
+# tile_config 55: clusters of 4 x 4 32 x 32 tiles as super-tiles with a 6-pixel halo
 @pytest.mark.parametrize("over", [{}, dict(tile_config=45), dict(solver=1),
-                                  dict(tvl1_iters=3)])
+                                  dict(tvl1_iters=3), dict(tile_config=55)])
 def test_step_equals_push_then_solve(T, over):
     torch, E = T
     W, H = 150, 97
@@ -57,10 +58,12 @@ def test_step_equals_push_then_solve(T, over):
         assert a.solver_name == b.solver_name  # the results do not depend on it
 
 
-def test_step_with_empty_and_large_packets_and_a_rejection(T):
+# tile_config 47: one 4 x 4 cluster over the sensor, the push inside its single launch
+@pytest.mark.parametrize("tile", [45, 47])
+def test_step_with_empty_and_large_packets_and_a_rejection(T, tile):
     torch, E = T
     W, H = 64, 40
-    a, b = E.Stream(W, H, tile_config=45), E.Stream(W, H, tile_config=45)
+    a, b = E.Stream(W, H, tile_config=tile), E.Stream(W, H, tile_config=tile)
     pk = packets(2, W, H, 3, 500)
     big = packets(3, W, H, 1, 40000)[0]  # above one CTA's packet: the two-call path
     big = (big[0], big[1], big[2] + pk[-1][2][-1], big[3])
@@ -79,7 +82,8 @@ def test_step_with_empty_and_large_packets_and_a_rejection(T):
     assert int(a.state(E.EVR_STATE_CLOCK)) == int(b.state(E.EVR_STATE_CLOCK))
 
 
-@pytest.mark.parametrize("over", [{}, dict(tile_config=45)])
+@pytest.mark.parametrize("over", [{}, dict(tile_config=45), dict(tile_config=47),
+                                  dict(tile_config=47, data_term=1)])
 def test_host_step_equals_push_then_solve(T, over):
     """evr_step (host arrays, staging copy inside the graph) against evr_push_events +
     evr_solve; the host-side checks reject a bad packet before anything is queued."""
