@@ -175,69 +175,67 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the device code the DRAM counters depend on (the solve graph's kernels)."""
+def kernel_source_hash(files=("evr_kernels.cu", "evr_solvers.cu", "evr_cluster.cu",
+                              "evr_tile.cuh", "evr_push.cuh", "evr_internal.cuh")):
+    """Hash of the device code the profiled counters depend on."""
     h = hashlib.sha256()
-    for f in ("evr_kernels.cu", "evr_solvers.cu", "evr_internal.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1607_06283_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(config, solver_name, launches_per_step):
-    """DRAM bytes per launch of the packet's step graph from the committed ncu summary
-    (profiles/k_tiled_<config>.md: the DRAM bytes of one step's launches, captured in
-    the benchmark's own sequence), if it was taken on the current kernel source with
-    the same solver configuration; else None."""
-    p = os.path.join(ROOT, "profiles", f"k_tiled_{config}.md")
+def profiled(workload, solver_name, source_sha):
+    """ncu counters of the dominant kernel for this workload and solver configuration
+    (profiles/counters.json, written by paper_1607_06283_gb300/profiling.py from the
+    captures its summaries describe), if they were taken on the current kernel source;
+    else None."""
+    p = os.path.join(ROOT, "profiles", "counters.json")
     if not os.path.exists(p):
         return None
-    import re
     with open(p) as fh:
-        text = fh.read()
-    for m in re.finditer(r"step_traffic_bytes: (\d+) launches_per_step: (\d+) "
-                         r"kernel_source_sha: (\w+) solver: (.+)", text):
-        if (m.group(3) == kernel_source_hash() and m.group(4).strip() == solver_name and
-                int(m.group(2)) == round(launches_per_step)):
-            return int(m.group(1)) / int(m.group(2))
+        entries = json.load(fh)
+    for e in entries:
+        if (e.get("workload") == workload and e.get("solver") == solver_name and
+                e.get("source_sha") == source_sha):
+            return e
     return None
 
 
-def rev_kernel_hash():
-    """Hash of the reverse-pass kernel's source (the DRAM counters of its summary)."""
-    with open(os.path.join(ROOT, "paper_1607_06283_gb300", "csrc", "evr_grad.cu")) as fh:
-        t = fh.read()
-    a, b = t.index("// ---- the reverse pass, tiled ----"), t.index("// The adjoint of p_0:")
-    return hashlib.sha256(t[a:b].encode()).hexdigest()[:16]
+def cpu_info():
+    """Host core count and CPU model (lscpu's "Model name", which Arm hosts report there
+    and not in /proc/cpuinfo)."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(),
+            "cpu_model": f"{model or platform.processor() or 'unknown'} ({platform.machine()})"}
 
 
-def profiled_rev_traffic(bytes_per_launch):
-    """DRAM bytes of an average reverse-pass launch: the committed ncu capture of one
-    launch (profiles/k_rev_tiled_diff64.md), scaled by the algorithmic bytes of the
-    average launch (traffic grows with the pixel-iterations), if it was taken on the
-    current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "k_rev_tiled_diff64.md")
-    if not os.path.exists(p):
-        return None
-    import re
-    with open(p) as fh:
-        m = re.search(r"rev_launch_traffic_bytes: (\d+) rev_launch_alg_bytes: (\d+) "
-                      r"rev_kernel_sha: (\w+)", fh.read())
-    if not m or m.group(3) != rev_kernel_hash():
-        return None
-    return int(m.group(1)) * bytes_per_launch / int(m.group(2))
-
-
-def cpu_baseline(cfg, stream, budget_s, max_packets=None):
-    """The FP64 oracle, as it stands, on this host's cores: packets of the same stream
-    until the time budget is spent."""
+def _oracle_rate(cfg, stream, budget_s, omp, shift_steps=None):
     from oracle import oracle as O
-    o = O.OracleStream(cfg.W, cfg.H)
+    o = O.OracleStream(cfg.W, cfg.H, omp=omp)
     t0 = time.perf_counter()
     done = ev = 0
     while True:
         a = done * cfg.packet
-        if a >= len(stream) or (max_packets and done >= max_packets):
+        if a >= len(stream):
             break
         b = min(a + cfg.packet, len(stream))
         o.push(stream.x[a:b], stream.y[a:b], stream.t[a:b], stream.pol[a:b])
@@ -247,10 +245,26 @@ def cpu_baseline(cfg, stream, budget_s, max_packets=None):
         if time.perf_counter() - t0 > budget_s and done >= 3:
             break
     dt = time.perf_counter() - t0
-    return {"value": ev / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
-            "gpix_iter_per_s": done * cfg.W * cfg.H * cfg.iters / dt / 1e9,
-            "sample": f"first {done} packets ({ev} events) of the same stream, FP64, "
-                      f"single thread, {dt:.1f} s"}
+    return ev / dt, done, ev, dt
+
+
+def cpu_baseline(cfg, stream, budget_s):
+    """The FP64 oracle, as it stands, on this host's cores: packets of the same stream
+    until the time budget is spent, once on one thread and once with its per-pixel loops
+    spread over every core by OpenMP (the same source and results)."""
+    info = cpu_info()
+    v1, d1, e1, t1 = _oracle_rate(cfg, stream, budget_s / 2, omp=False)
+    vn, dn, en, tn = _oracle_rate(cfg, stream, budget_s / 2, omp=True)
+    threads = int(os.environ.get("OMP_NUM_THREADS", info["nproc"]))
+    return {"value": vn, "unit": "events/s", "cores": threads, "kind": "oracle",
+            "gpix_iter_per_s": dn * cfg.W * cfg.H * cfg.iters / tn / 1e9,
+            "sample": f"first {dn} packets ({en} events) of the same stream, FP64, OpenMP "
+                      f"over pixels on {threads} threads, {tn:.1f} s",
+            "nproc": info["nproc"], "cpu_model": info["cpu_model"],
+            "single_thread": {"value": v1, "unit": "events/s", "cores": 1,
+                              "gpix_iter_per_s": d1 * cfg.W * cfg.H * cfg.iters / t1 / 1e9,
+                              "sample": f"first {d1} packets ({e1} events), FP64, one "
+                                        f"thread, {t1:.1f} s"}}
 
 
 def error_vs_oracle(E, cfg, stream, p):
@@ -294,7 +308,9 @@ def run_reference(args):
     cfg, stream = workload(args.config, 0,
                            max_packets=args.warmup + args.steps if big else None)
     from oracle import oracle as O
-    o = O.OracleStream(cfg.W, cfg.H)
+    o = O.OracleStream(cfg.W, cfg.H, omp=True)  # per-pixel loops on every host core
+    info = cpu_info()
+    threads = int(os.environ.get("OMP_NUM_THREADS", info["nproc"]))
     steps = list(packet_slices(stream, cfg, args.warmup + args.steps))
     for a, b, sh in steps[:args.warmup]:
         o.push(stream.x[a:b], stream.y[a:b], stream.t[a:b] + sh, stream.pol[a:b])
@@ -312,7 +328,8 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = ev / dt
     sample = (f"{done} of {args.steps} timed packets (time budget {budget:.0f} s), "
-              f"after {args.warmup} warm-up packets; FP64 oracle, single thread")
+              f"after {args.warmup} warm-up packets; FP64 oracle, OpenMP over pixels on "
+              f"{threads} threads")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "events/s",
             "n_gpus": 1, "steps": done, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / max(1, done), "higher_is_better": True,
@@ -320,8 +337,9 @@ def run_reference(args):
             "gpix_iter_per_s": done * cfg.W * cfg.H * cfg.iters / dt / 1e9,
             "config": {"workload": describe(cfg), "sensor": f"{cfg.W}x{cfg.H}",
                        "packet": cfg.packet, "iters": cfg.iters},
-            "cpu_baseline": {"value": v, "unit": "events/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "events/s", "cores": threads,
+                             "kind": "oracle", "sample": sample, "nproc": info["nproc"],
+                             "cpu_model": info["cpu_model"]},
             "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -329,6 +347,25 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------- our arm
+SETTLE_MAX = 12  # untimed packets at most before the solver configuration is settled
+
+
+def roofline_level(solver_name, n_sms, l2_gbs, smem_gbs):
+    """The memory level that holds the iterated state between the iterations of a packet,
+    and its measured peak.  A cluster over the whole sensor (R0) keeps u, p and the packet
+    constants in registers and shared memory for all iterations: its bound is the
+    shared-memory bandwidth of the SMs it occupies.  The multi-launch solvers keep the state
+    on chip within a launch and in L2 between launches: their bound is L2."""
+    import re
+    m = re.search(r"R(\d+) \((\d+) threads, (\d+) CTAs\)", solver_name)
+    if solver_name.startswith("cluster") and m and int(m.group(1)) == 0:
+        ctas = int(m.group(3))
+        return "smem", smem_gbs * min(ctas, n_sms) / n_sms, (
+            f"shared memory of the {min(ctas, n_sms)} SMs the cluster occupies: "
+            f"{min(ctas, n_sms)}/{n_sms} of the aggregate measured in this run")
+    return "l2", l2_gbs, "L2, measured in this run (evr_measure_peak level 0)"
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -349,8 +386,10 @@ def run_ours(args):
     from paper_1607_06283_gb300 import evr as E
 
     big = args.config != "blobs346"
-    cfg, stream = workload(args.config, rank,
-                           max_packets=args.warmup + args.steps if big else None)
+    # packets: up to SETTLE_MAX to settle the solver, the warm-up, the timed steps and as
+    # many again for the kernel-timing pass
+    n_all = SETTLE_MAX + args.warmup + 2 * args.steps
+    cfg, stream = workload(args.config, rank, max_packets=n_all if big else None)
     cur = torch.cuda.Stream()  # one non-default stream for the library and the timing events
     torch.cuda.set_stream(cur)
     p = E.evr_default_params()
@@ -358,10 +397,10 @@ def run_ours(args):
     p.tile_config = args.tile
     p.storage = args.storage
     p.tvl1_iters = args.tvl1
-    g = E.Stream(cfg.W, cfg.H, p)
-    E.evr_set_cuda_stream(g.h, cur.cuda_stream)
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    l2_gbs = E.evr_measure_peak(0, cur.cuda_stream)
+    smem_gbs = E.evr_measure_peak(1, cur.cuda_stream)
 
-    n_all = args.warmup + args.steps
     steps = list(packet_slices(stream, cfg, n_all))
     # device-resident inputs: the whole (time-shifted) event sequence of the run
     t_all = np.concatenate([stream.t[a:b] + sh for a, b, sh in steps])
@@ -373,23 +412,39 @@ def run_ours(args):
     offs = np.concatenate([[0], np.cumsum([b - a for a, b, _ in steps])])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    g = E.Stream(cfg.W, cfg.H, p)
+    E.evr_set_cuda_stream(g.h, cur.cuda_stream)
+
     def step(k):  # push (device arrays) and solve: one graph per packet once settled
         s, e = int(offs[k]), int(offs[k + 1])
         rc = E.evr_step_device(g.h, dx[s:e], dy[s:e], dt_[s:e], dp[s:e], cfg.iters)
         if rc:
             raise RuntimeError(f"step failed: {rc}")
 
-    for k in range(args.warmup):
+    # the first packet of a new stream tunes the solver (autotuner): its latency to the
+    # image, then untimed packets until the online refinement has decided
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step(0)
+    assert g.synchronize() == 0
+    first_ms = (time.perf_counter() - t0) * 1e3
+    k = 1
+    while not E.evr_solver_settled(g.h) and k < SETTLE_MAX:
         step(k)
+        k += 1
+    settled = E.evr_solver_settled(g.h)
+    k0 = SETTLE_MAX  # first warm-up packet
+    for j in range(args.warmup):
+        step(k0 + j)
     assert g.synchronize() == 0
     torch.cuda.synchronize()
+    k1 = k0 + args.warmup  # first timed packet
 
     clk = ClockSampler(local)
     if rank == 0:
         clk.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
-    E.evr_enable_kernel_timing(g.h, True)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -397,20 +452,33 @@ def run_ours(args):
     for j in range(args.steps):
         flush.fill_(float(j))  # L2 flush between timed steps (outside the events)
         evs[j][0].record(cur)
-        step(args.warmup + j)
+        step(k1 + j)
         evs[j][1].record(cur)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if pg:
         pg.barrier()
-    clocks = clk.stop() if rank == 0 else None
     ms_steps = sum(a.elapsed_time(b) for a, b in evs)
+
+    # the dominant kernels alone: the same packets' solves (front fused into the iteration
+    # kernels) bracketed by the library's CUDA events on this stream, each push queued
+    # before them and outside the events
+    k2 = k1 + args.steps
+    E.evr_enable_kernel_timing(g.h, True)
+    for j in range(args.steps):
+        flush.fill_(float(j))
+        s_, e_ = int(offs[k2 + j]), int(offs[k2 + j + 1])
+        if E.evr_push_events_device(g.h, dx[s_:e_], dy[s_:e_], dt_[s_:e_], dp[s_:e_]):
+            raise RuntimeError("push failed")
+        g.solve(cfg.iters)
+    torch.cuda.synchronize()
     k_ms, k_launches, k_pixiters = E.evr_kernel_time(g.h)
     E.evr_enable_kernel_timing(g.h, False)
+    clocks = clk.stop() if rank == 0 else None
     status = g.synchronize()
     if status:
         raise RuntimeError(f"device-side rejection during the run: {status}")
-    ev_timed = int(offs[n_all] - offs[args.warmup])
+    ev_timed = int(offs[k1 + args.steps] - offs[k1])
     from paper_1607_06283_gb300.shard import reduce_timing
     t_max, ev_total = reduce_timing(ms_steps, ev_timed, pg, "cuda")
     value = ev_total / (t_max * 1e-3)
@@ -443,15 +511,19 @@ def run_ours(args):
         if rc:
             raise RuntimeError(f"wait_image: {rc}")
 
-    for k in range(args.warmup):
+    k = 0
+    while k < SETTLE_MAX and (k == 0 or not E.evr_solver_settled(g2.h)):
         wait(step_host(k, k % depth))
+        k += 1
+    for j in range(args.warmup):
+        wait(step_host(k0 + j, j % depth))
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     pending = []
     for j in range(args.steps):
-        pending.append(step_host(args.warmup + j, j % depth))
+        pending.append(step_host(k1 + j, j % depth))
         if len(pending) == depth:
             wait(pending.pop(0))
     for t in pending:
@@ -461,16 +533,20 @@ def run_ours(args):
     e2e_val = ev_total / e2e_s
 
     if rank == 0:
-        peak, peak_kind = measured_peaks()
-        # the timed region of each step: one graph per packet with the push, the front
-        # launches (prologue, TV-L1) and the iteration kernels
+        hbm, hbm_kind = measured_peaks()
+        # the solve graphs: the iteration kernels, the first of them computing the packet's
+        # metric and data image (the fused front; a separate prologue launch where it is
+        # not fused is counted with them)
         avg_launch_ms = k_ms / max(1, k_launches)
         alg_bytes = (b_alg(args.storage) * k_pixiters +
-                     (B_PROLOGUE + B_TVL1_ITER * args.tvl1) * cfg.W * cfg.H * args.steps +
-                     B_PUSH_EVENT * ev_timed)
+                     (B_PROLOGUE + B_TVL1_ITER * args.tvl1) * cfg.W * cfg.H * args.steps)
         bytes_per_launch = alg_bytes / max(1, k_launches)
         achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
-        launches_per_step = k_launches / args.steps
+        bound, peak, peak_src = roofline_level(g.solver_name, n_sms, l2_gbs, smem_gbs)
+        src_sha = kernel_source_hash()
+        prof = profiled(cfg.name, g.solver_name, src_sha)
+        kernel = ("k_cluster" if g.solver_name.startswith("cluster") else
+                  "k_tiled" if g.solver_name.startswith("tiled") else "iteration kernels")
         line = {
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -485,23 +561,37 @@ def run_ours(args):
                        "tvl1_iters": args.tvl1,
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "inputs": "device-resident event arrays (evr_step_device: push "
-                                 "and solve)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                 "and solve)",
+                       "settled": bool(settled),
+                       "untimed_before_warmup": "first packet (autotuner) + packets until "
+                                                "the solver configuration is settled"},
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": profiled_traffic(cfg.name, g.solver_name,
-                                                     k_launches / args.steps),
-                         "kernel": "packet step graph: push + prologue + iteration "
-                                   "kernels (" + g.solver_name + ")",
-                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "traffic": (prof["dram_bytes_per_launch"] if prof else None),
+                         "kernel": f"{kernel}: the solve's iteration launches "
+                                   f"({g.solver_name}), prologue fused",
+                         "peak_source": peak_src,
+                         "frac_hbm": achieved / hbm, "hbm_peak": hbm,
+                         "hbm_peak_source": f"{hbm_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                         "l2_gbs": l2_gbs, "smem_gbs_all_sms": smem_gbs,
+                         "issue_active": (prof.get("issue_active") if prof else None),
                          "avg_launch_us": avg_launch_ms * 1e3,
-                         "launches_per_step": k_launches / args.steps,
-                         "bytes_per_launch": bytes_per_launch},
+                         "launches_per_solve": k_launches / args.steps,
+                         "bytes_per_launch": bytes_per_launch,
+                         "timing": "CUDA events around each solve graph on the launching "
+                                   "stream, a second pass over as many packets as the "
+                                   "timed steps (pushes outside the events)"},
             "e2e": {"value": e2e_val, "unit": "events/s",
                     "h2d_bytes_per_step": cfg.packet * (2 + 2 + 8 + 1),
                     "d2h_bytes_per_step": cfg.W * cfg.H * 4 + 4,  # image + status word
                     "calls": "evr_step (host arrays: push and solve) + "
                              "evr_get_image_async into pinned memory, three steps in flight"},
-            "gpu_launches": int(round(launches_per_step * args.steps)),
+            # the timed steps' graphs: the solve's launches, plus the push kernel unless
+            # the single-launch cluster solver pushes the packet itself
+            "gpu_launches": int(round(k_launches + args.steps *
+                                      (0 if (" R0 " in g.solver_name and args.tvl1 == 0 and
+                                             g.solver_name.startswith("cluster")) else 1))),
+            "first_image_ms": first_ms,
             "clocks": clocks,
             "wall_s_timed": wall,
         }
@@ -520,15 +610,28 @@ def run_ours(args):
 
 # ----------------------------------------------------------------------- batched streams
 def run_batch_bench(args):
-    """256 independent streams of mixed sizes, one packet per active stream per step."""
+    """256 independent streams of mixed sizes, one packet per active stream per step.
+    Under torchrun the streams are split over the ranks by their work (shard.batch_share):
+    strong scaling of the one batched workload, no data-path collective."""
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
     from paper_1607_06283_gb300 import build
-    build.build()
+    if rank == 0:
+        build.build()
+    if pg:
+        pg.barrier()
     from paper_1607_06283_gb300 import evr as E
+    from paper_1607_06283_gb300.shard import batch_share, reduce_timing
     from evsim.configs import batch_configs, batch_step_arrays, make_batch
-    cfgs = batch_configs()
+    all_cfgs = batch_configs()
+    mine = batch_share(all_cfgs, world, rank)
+    cfgs = [all_cfgs[i] for i in mine]
     # every stream holds at least 20 packets and at most 400: past step 400 the batch
     # would be idle, so the timed steps are capped (the line reports the count used)
     args.steps = min(args.steps, 60)
@@ -553,8 +656,11 @@ def run_batch_bench(args):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     clk = ClockSampler(local)
-    clk.start()
+    if rank == 0:
+        clk.start()
     b.enable_kernel_timing(True)
+    if pg:
+        pg.barrier()
     torch.cuda.synchronize()
     for j in range(args.steps):
         flush.fill_(float(j))
@@ -562,7 +668,9 @@ def run_batch_bench(args):
         b.step_device(*dev[args.warmup + j], iters)
         evs[j][1].record(cur)
     torch.cuda.synchronize()
-    clocks = clk.stop()
+    if pg:
+        pg.barrier()
+    clocks = clk.stop() if rank == 0 else None
     ms = sum(a.elapsed_time(c) for a, c in evs)
     k_ms, k_launches, _ = b.kernel_time()
     assert b.synchronize() == (0, -1)
@@ -573,6 +681,9 @@ def run_batch_bench(args):
         cnt = np.diff(off)
         ev += int(cnt.sum())
         pxit += sum(w * h for (w, h), c in zip(sizes, cnt) if c > 0) * iters
+    ms_local, ev_local, pxit_local = ms, ev, pxit
+    ms, ev = reduce_timing(ms_local, ev_local, pg, "cuda")
+    _, pxit = reduce_timing(ms_local, pxit_local, pg, "cuda")
     value = ev / (ms * 1e-3)
     # end to end: host arrays in, all images out into pinned memory, every step; two
     # steps in flight (the next step is queued before the previous images are waited for)
@@ -593,13 +704,23 @@ def run_batch_bench(args):
         prev = t
     b2.wait_images(prev)
     e2e_s = time.perf_counter() - t0
+    e2e_s, _ = reduce_timing(e2e_s, 0.0, pg, "cuda")
     peak, peak_kind = measured_peaks()
-    # the step graph: prologue (B_PROLOGUE per pixel of an active stream) + passes
-    achieved = (b_alg(args.storage) * pxit + B_PROLOGUE * pxit / iters) / (k_ms * 1e-3) / 1e9
+    # the step graph: prologue (B_PROLOGUE per pixel of an active stream) + passes, this
+    # rank's kernels on this rank's launching stream
+    achieved = ((b_alg(args.storage) * pxit_local + B_PROLOGUE * pxit_local / iters) /
+                (k_ms * 1e-3) / 1e9)
+    if rank != 0:
+        b.close()
+        b2.close()
+        pg.barrier()
+        pg.destroy_process_group()
+        return 0
     line = {
-        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
         "dtype": ["f32", "f32 (p, ubar stored f16)", "f32 (p, ubar stored bf16)"][args.storage],
         "data": "synthetic",
         "gpix_iter_per_s": pxit / (ms * 1e-3) / 1e9,
@@ -607,6 +728,9 @@ def run_batch_bench(args):
                                "64 x 346x260), rects/blobs scenes, packets U[20,400], "
                                "500-event packets, 50 iterations",
                    "solver": b.solver_name, "steps_timed": "one packet per active stream",
+                   "parallelism": (f"streams split over {world} ranks by work "
+                                   f"(rank 0: {len(mine)} streams)" if world > 1 else
+                                   "one GPU"),
                    "l2": "flushed between timed steps (256 MiB write, outside the events)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
@@ -625,6 +749,9 @@ def run_batch_bench(args):
     print(json.dumps(line), flush=True)
     b.close()
     b2.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
     return 0
 
 
@@ -701,10 +828,18 @@ def run_diff_bench(args):
     peak, peak_kind = measured_peaks()
     rev_bytes = B_REV_ITER * rev_pi + B_REV_LAUNCH * rev_pl
     achieved = rev_bytes / (rev_ms * 1e-3) / 1e9 if rev_ms > 0 else None
+    # the captured launch's DRAM bytes, scaled to the average launch by algorithmic bytes
+    # (traffic grows with the reversed pixel-iterations)
+    prof = profiled("diff64", "k_rev_tiled", kernel_source_hash(("evr_grad.cu",)))
+    traffic = None
+    if prof and prof.get("alg_bytes_per_launch"):
+        traffic = (prof["dram_bytes_per_launch"] * (rev_bytes / max(rev_n, 1)) /
+                   prof["alg_bytes_per_launch"])
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak if achieved else None,
-        "traffic": profiled_rev_traffic(rev_bytes / max(rev_n, 1)),
+        "traffic": traffic,
+        "issue_active": prof.get("issue_active") if prof else None,
         "kernel": "k_rev_tiled (reverse pass: 4 reversed iterations per launch, 32x32 tiles, "
                   "4-pixel halo)",
         "peak_source": f"{peak_kind} hbm_gbs", "avg_launch_us": rev_ms * 1e3 / max(rev_n, 1),

@@ -26,6 +26,13 @@ def assign_streams(costs, world: int) -> list:
     return [sorted(o) for o in out]
 
 
+def batch_share(cfgs, world: int, rank: int) -> list:
+    """Indices of the batched streams rank `rank` of `world` solves: the streams are
+    balanced by their work (pixels x iterations x packets) with assign_streams."""
+    costs = [c.W * c.H * c.iters * c.n_packets for c in cfgs]
+    return assign_streams(costs, world)[rank]
+
+
 def stream_seed(base_seed: int, rank: int) -> int:
     """Seed of rank `rank`'s own stream in a weak-scaling run (rank 0 keeps the base)."""
     return base_seed + 7 * rank

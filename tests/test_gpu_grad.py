@@ -159,6 +159,83 @@ def test_fit_lambda_and_threshold_to_target(T):
     assert abs(math.log(l_fit / 25.0)) < abs(math.log(60.0 / 25.0))
 
 
+def test_diff64_shape_gradients_match_oracle(T):
+    """The differentiation workload's shape: 64 stacked 240 x 180 packets, 30 unrolled
+    iterations, checkpoints every 10.  Two members' dL/df and dL/du0 against the FP64
+    oracle adjoint of those members alone, and dL/dlambda summed over all 64 members
+    against the sum of the oracle's."""
+    torch, AG, E = T
+    n, H, W, K, every, lam = 64, 180, 240, 30, 10, 90.0
+    probs = [problem(5000 + b, H, W) for b in range(n)]
+    stk = [np.stack([pr[k] for pr in probs]) for k in range(6)]
+    ttx, tty, tf, tu0, tp0, tw = cuda(torch, *stk)
+    tf.requires_grad_(True)
+    tu0.requires_grad_(True)
+    tlam = torch.tensor(lam, dtype=torch.float32, device="cuda", requires_grad=True)
+    u, _ = AG.packet_solve(tf, tlam, tu0, tp0, ttx, tty, K, every)
+    (u * tw).sum().backward()
+    gl_sum = 0.0
+    for b, (tx, ty, f, u0, p0, w) in enumerate(probs):
+        otx, oty, oG = oracle_metric(tx, ty)
+        gu0, _, gf, gl = O.pd_grad(otx, oty, oG, f, u0, p0, K, TAU, TAU, lam, UMIN, UMAX, w)
+        gl_sum += gl
+        if b in (0, n - 1):
+            uo, _ = O.pd_iterations(otx, oty, oG, f, u0, p0, K, TAU, TAU, lam, UMIN, UMAX)
+            assert np.max(np.abs(u[b].detach().cpu().numpy() - uo)) <= 1e-4
+            assert rel_err(tf.grad[b].cpu().numpy(), gf) <= GRAD_RTOL, b
+            assert rel_err(tu0.grad[b].cpu().numpy(), gu0) <= GRAD_RTOL, b
+    assert float(tlam.grad) == pytest.approx(gl_sum, rel=GRAD_RTOL, abs=1e-6)
+
+
+def test_fit_to_ground_truth_frames_of_a_simulated_scene(T):
+    """(lambda, C) fitted by gradient descent through the GPU adjoint to the simulator's
+    ground-truth frames of a rectangles scene: each packet starts from the true image at
+    its first event, its events give f = u_prev exp(C (n+ - n-)) and the metric, and the
+    loss is the mean square error against the true image at its last event.  The loss
+    falls and the fitted contrast threshold moves towards the simulator's C = 0.15."""
+    torch, AG, E = T
+    from evsim.configs import StreamConfig, make_stream
+    W, H, K, per, n_pk = 64, 48, 30, 1500, 4
+    cfg = StreamConfig("fit", W, H, "rects", 8, 4242, per * (n_pk + 1), per, K, speed=60.0,
+                       noise=0.0, dt_us=100.0)
+    st = make_stream(cfg)
+    o = O.OracleStream(W, H)
+    items = []
+    a0 = per  # the first packet sets the time surface up
+    s = st.slice(0, a0)
+    assert o.push(s.x, s.y, s.t, s.pol) == 0
+    o.solve(0)
+    L0 = st.log_frame(float(st.t[0]))
+    for k in range(n_pk):
+        a, b = a0 + k * per, a0 + (k + 1) * per
+        s = st.slice(a, b)
+        assert o.push(s.x, s.y, s.t, s.pol) == 0
+        npos, nneg = o.get(O.NPOS).copy(), o.get(O.NNEG).copy()
+        o.solve(0)  # metric of this packet (oracle prologue)
+        u_prev = np.exp(st.log_frame(float(st.t[a])) - L0)
+        target = np.exp(st.log_frame(float(st.t[b - 1])) - L0)
+        items.append((u_prev, npos, nneg, o.get(O.TX), o.get(O.TY), target))
+    u_prev, npos, nneg, tx, ty, target = [
+        torch.from_numpy(np.ascontiguousarray(np.stack([it[j] for it in items]).astype(
+            np.int32 if j in (1, 2) else np.float32))).cuda() for j in range(6)]
+    p0 = torch.zeros((n_pk, 3, H, W), device="cuda")
+    logl = torch.tensor(math.log(30.0), device="cuda", requires_grad=True)
+    C = torch.tensor(0.06, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([logl, C], lr=0.03)
+    losses, cs = [], []
+    for _ in range(80):
+        opt.zero_grad()
+        f = AG.data_image(u_prev, npos, nneg, C, C)
+        u, _ = AG.packet_solve(f, logl.exp(), u_prev, p0, tx, ty, K, 10)
+        loss = ((u - target) ** 2).mean()
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.detach()))
+        cs.append(float(C.detach()))
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+    assert abs(cs[-1] - 0.15) < 0.5 * abs(0.06 - 0.15), cs[-1]
+
+
 def test_batched_solve_equals_single_solves_bit_for_bit(T):
     """n packets in one call: each image's forward state and every gradient are those of
     the same packet solved alone; dL/dlambda is the sum over the batch."""

@@ -69,3 +69,44 @@ def test_two_ranks_gloo():
     for _, _, t, w in res:
         assert t == 11.0
         assert w == float(sum(costs))
+
+
+def _batch_worker(rank, world, port, q):
+    import torch.distributed as dist
+    from evsim.configs import batch_configs
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        cfgs = batch_configs()
+        mine = shard.batch_share(cfgs, world, rank)
+        work = sum(cfgs[i].W * cfgs[i].H * cfgs[i].iters * cfgs[i].n_packets for i in mine)
+        dist.barrier()
+        t, w = shard.reduce_timing(5.0 + rank, work, dist)
+        q.put((rank, mine, work, t, w))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_batched_streams_split_over_two_gloo_ranks():
+    """The 256-stream batched workload split over two ranks: every stream on exactly one
+    rank, the work balanced, the timing reduced to the maximum and the work summed."""
+    import torch.multiprocessing as mp
+    from evsim.configs import batch_configs
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batch_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    cfgs = batch_configs()
+    costs = [c.W * c.H * c.iters * c.n_packets for c in cfgs]
+    assert sorted(res[0][1] + res[1][1]) == list(range(256))
+    assert abs(res[0][2] - res[1][2]) <= max(costs)
+    for _, _, _, t, w in res:
+        assert t == 6.0
+        assert w == float(sum(costs))
