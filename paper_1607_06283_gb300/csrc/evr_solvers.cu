@@ -67,13 +67,13 @@ const SolverCfg kSolverCfgs[kNumSolverCfgs] = {
 // then waits for the previous pass to complete before reading (u, p), and only then
 // lets the next pass launch -- so no pass can run ahead of the prologue.  Pass 0
 // loads everything after its wait.
-// Resident CTAs per SM the register budget is sized for: FP32 tiles with two pixel pairs
-// per thread get as many CTAs as fit at 80 registers (no spills; three of 256 threads,
-// two of 384), so that more warps hide latency and the next pass's CTAs can become
-// resident while the current pass runs; one otherwise.
+// Resident CTAs per SM the register budget is sized for: tiles with two pixel pairs per
+// thread get as many CTAs as fit at 80 registers (three of 256 threads, two of 384; no
+// spills in FP32 and BF16, 4 bytes in FP16), so that more warps hide latency and the
+// next pass's CTAs can become resident while the current pass runs; one otherwise.
 template <int KX, int KY, int NTY, typename ST>
 constexpr int kTiledMinBlocks =
-    (KX * KY == 4 && sizeof(ST) == 4 && 65536 / (32 * NTY * 80) > 1) ? 65536 / (32 * NTY * 80)
+    (KX * KY == 4 && 65536 / (32 * NTY * 80) > 1) ? 65536 / (32 * NTY * 80)
                                                                       : 1;
 
 // MODE 0: plain passes.  MODE 1 (FRONT): the packet's front launch is fused into the

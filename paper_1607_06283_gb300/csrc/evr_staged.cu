@@ -4,10 +4,9 @@
 // shared memory with tensor-memory-access (TMA) copies, one tile ahead.
 //
 // A pass of R iterations reads, per tile, the extended tile (owned pixels plus an
-// R-pixel halo) of seven planes: u, p1, p2, p3 of the current buffer and the packet's
-// L_x t, L_y t and f (1/G and sqrt G are recomputed from L_x t and L_y t with the
-// prologue's own arithmetic, so they equal the planes bit for bit).  One thread of each
-// CTA issues the seven 2-D tensor copies of the next tile into the second of two
+// R-pixel halo) of nine planes: u, p1, p2, p3 of the current buffer and the packet's
+// L_x t, L_y t, f, 1/G and sqrt G.  One thread of each
+// CTA issues the nine 2-D tensor copies of the next tile into the second of two
 // shared-memory stages as soon as every thread has moved the current tile into
 // registers; the copies then run while the current tile iterates, and an mbarrier's
 // transaction count says when they have landed.  The per-pixel arithmetic is that of
@@ -37,12 +36,12 @@ namespace {
 
 constexpr int kErrTimeoutSt = -7;              // EVR_ERR_TIMEOUT
 constexpr unsigned kStageSpin = 1u << 22;      // polls of an mbarrier before giving up
-constexpr int kStagePlanes = 7;                // u, p1, p2, p3, L_x t, L_y t, f
+constexpr int kStagePlanes = 9;  // u, p1, p2, p3, L_x t, L_y t, f, 1/G, sqrt G
 constexpr int kStageAlign = 8;                 // elements: 32 bytes, a multiple of 16
 
 struct StageMaps {
   CUtensorMap m[2][4];  // [buffer][u, p1, p2, p3]
-  CUtensorMap tx, ty, f;
+  CUtensorMap tx, ty, f, iG, sG;
 };
 
 struct StageArgs {
@@ -137,6 +136,8 @@ __global__ void __launch_bounds__(32 * NTY, (kStagedMinBlocks<KX, KY, NTY>))
     tma_load_2d(dst + 4 * SS::PLANE * 4u, &M.tx, x0, gy0, mb);
     tma_load_2d(dst + 5 * SS::PLANE * 4u, &M.ty, x0, gy0, mb);
     tma_load_2d(dst + 6 * SS::PLANE * 4u, &M.f, x0, gy0, mb);
+    tma_load_2d(dst + 7 * SS::PLANE * 4u, &M.iG, x0, gy0, mb);
+    tma_load_2d(dst + 8 * SS::PLANE * 4u, &M.sG, x0, gy0, mb);
   };
   const int first = blockIdx.x;
   if (tid == 0 && first < a.n_tiles) issue(first, 0);
@@ -173,10 +174,8 @@ __global__ void __launch_bounds__(32 * NTY, (kStagedMinBlocks<KX, KY, NTY>))
           av = st[4 * SS::PLANE + o];
           bv = st[5 * SS::PLANE + o];
           f = st[6 * SS::PLANE + o];
-          // 1/G and sqrt(G) as the prologue computes them
-          const float G = metric_G(av, bv);
-          ig = 1.0f / G;
-          sg = sqrtf(G);
+          ig = st[7 * SS::PLANE + o];
+          sg = st[8 * SS::PLANE + o];
           mx = (T.gx0 + T.lx(k) < P.W - 1) ? 1.0f : 0.0f;
           const int gy = T.gy0 + T.ly(k);
           my = ((P.Hm == P.H ? gy : gy % P.Hm) < P.Hm - 1) ? 1.0f : 0.0f;
@@ -285,7 +284,10 @@ int launch_t(const Planes& P, int R, int src, int iters, int pass, const SolveCo
       if (!encode_plane(&M.m[b][k], q[k], P, SS::BW, SS::EH)) return (int)cudaErrorInvalidValue;
   }
   if (!encode_plane(&M.tx, P.tx, P, SS::BW, SS::EH) ||
-      !encode_plane(&M.ty, P.ty, P, SS::BW, SS::EH) || !encode_plane(&M.f, P.f, P, SS::BW, SS::EH))
+      !encode_plane(&M.ty, P.ty, P, SS::BW, SS::EH) ||
+      !encode_plane(&M.f, P.f, P, SS::BW, SS::EH) ||
+      !encode_plane(&M.iG, P.iG, P, SS::BW, SS::EH) ||
+      !encode_plane(&M.sG, P.sG, P, SS::BW, SS::EH))
     return (int)cudaErrorInvalidValue;
   StageArgs a{P, c, src, iters, R, tx, tx * ty};
   const int n = tx * ty;
