@@ -243,14 +243,8 @@ struct ClusterArgs {
   int silent;     // wait self-test: this rank sends nothing (-1: none)
 };
 
-// The 512-thread tile with one pixel pair per thread is held to 64 registers, so that two
-// of its CTAs fit on an SM when clusters share SMs; the others run one CTA per SM.
 template <int KX, int KY, int NTY>
-constexpr int kClusterMinBlocks = (NTY == 16 && KX * KY == 2) ? 2 : 1;
-
-template <int KX, int KY, int NTY>
-__global__ void __launch_bounds__(32 * NTY, (kClusterMinBlocks<KX, KY, NTY>))
-    k_cluster(const __grid_constant__ ClusterArgs a) {
+__global__ void __launch_bounds__(32 * NTY, 1) k_cluster(const __grid_constant__ ClusterArgs a) {
   using TT = Tile<KX, KY, NTY, float>;
   __shared__ TileSmem<KX, KY, NTY, float> sm;
   __shared__ __align__(8) unsigned long long s_mb[2];

@@ -57,17 +57,29 @@ def test_argument_errors_need_no_gpu(evr):
 
 
 def test_ptxas_reports_no_spills_in_the_iteration_kernels(evr):
-    """Register pressure check on the built kernels (from nvcc -Xptxas -v)."""
+    """Register pressure check on the built kernels (from nvcc -Xptxas -v).  Two
+    instantiations are allowed a few bytes: the two-pair FP16 tile held to 80 registers
+    (two CTAs per SM; measured faster than one CTA without the spill) and the cluster
+    solver's 1024-thread tile (64 registers is the most a 1024-thread CTA can have)."""
     import os
+    import re
+    allowed = {"ILi1ELi4ELi12E6__half": 8, "ILi1ELi4ELi8E6__half": 8,
+               "k_clusterILi1ELi2ELi32E": 8}
     text = ""
-    for f in ("evr_kernels.ptxas.txt", "evr_solvers.ptxas.txt", "evr_grad.ptxas.txt"):
+    for f in ("evr_kernels.ptxas.txt", "evr_solvers.ptxas.txt", "evr_grad.ptxas.txt",
+              "evr_cluster.ptxas.txt", "evr_staged.ptxas.txt"):
         text += open(os.path.join(os.path.dirname(build.LIB), f)).read()
     blocks = text.split("Compiling entry function")
+    seen = 0
     for b in blocks[1:]:
         name = b.split("'")[1]
-        if ("k_tiled" in name or "k_prologue" in name or "k_push" in name or
-                "k_rev_tiled" in name):
-            assert "0 bytes spill stores" in b, name
+        if any(k in name for k in ("k_tiled", "k_prologue", "k_push", "k_rev_tiled",
+                                   "k_cluster", "k_staged")):
+            seen += 1
+            spill = int(re.search(r"(\d+) bytes spill stores", b).group(1))
+            limit = max([v for k, v in allowed.items() if k in name], default=0)
+            assert spill <= limit, (name, spill)
+    assert seen >= 40
 
 
 def test_unrolled_workspace_sizing_needs_no_gpu(evr):
