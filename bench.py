@@ -16,7 +16,6 @@ bracketed by a barrier and the time is the maximum over ranks.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -175,21 +174,13 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash(files=("evr_kernels.cu", "evr_solvers.cu", "evr_cluster.cu",
-                              "evr_tile.cuh", "evr_push.cuh", "evr_internal.cuh")):
-    """Hash of the device code the profiled counters depend on."""
-    h = hashlib.sha256()
-    for f in files:
-        with open(os.path.join(ROOT, "paper_1607_06283_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
-def profiled(workload, solver_name, source_sha):
+def profiled(workload, solver_name):
     """ncu counters of the dominant kernel for this workload and solver configuration
     (profiles/counters.json, written by paper_1607_06283_gb300/profiling.py from the
     captures its summaries describe), if they were taken on the current kernel source;
     else None."""
+    from paper_1607_06283_gb300.profiling import source_hash, sources_for
+    source_sha = source_hash(sources_for(solver_name))
     p = os.path.join(ROOT, "profiles", "counters.json")
     if not os.path.exists(p):
         return None
@@ -543,8 +534,7 @@ def run_ours(args):
         bytes_per_launch = alg_bytes / max(1, k_launches)
         achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
         bound, peak, peak_src = roofline_level(g.solver_name, n_sms, l2_gbs, smem_gbs)
-        src_sha = kernel_source_hash()
-        prof = profiled(cfg.name, g.solver_name, src_sha)
+        prof = profiled(cfg.name, g.solver_name)
         kernel = ("k_cluster" if g.solver_name.startswith("cluster") else
                   "k_tiled" if g.solver_name.startswith("tiled") else "iteration kernels")
         line = {
@@ -830,7 +820,7 @@ def run_diff_bench(args):
     achieved = rev_bytes / (rev_ms * 1e-3) / 1e9 if rev_ms > 0 else None
     # the captured launch's DRAM bytes, scaled to the average launch by algorithmic bytes
     # (traffic grows with the reversed pixel-iterations)
-    prof = profiled("diff64", "k_rev_tiled", kernel_source_hash(("evr_grad.cu",)))
+    prof = profiled("diff64", "k_rev_tiled")
     traffic = None
     if prof and prof.get("alg_bytes_per_launch"):
         traffic = (prof["dram_bytes_per_launch"] * (rev_bytes / max(rev_n, 1)) /

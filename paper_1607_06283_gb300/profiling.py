@@ -33,9 +33,21 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1607_06283_gb300", "csrc")
 # the device sources the counters of the iteration kernels depend on (bench.py hashes the
-# same list)
+# same lists, through sources_for)
 SOLVER_SOURCES = ("evr_kernels.cu", "evr_solvers.cu", "evr_cluster.cu", "evr_tile.cuh",
                   "evr_push.cuh", "evr_internal.cuh")
+STAGED_SOURCES = SOLVER_SOURCES + ("evr_staged.cu", "evr_tma.cuh")
+REVERSE_SOURCES = ("evr_grad.cu", "evr_tma.cuh")
+
+
+def sources_for(solver: str):
+    """The device sources whose hash keys the counters of `solver` (a solver name as the
+    library reports it, or k_rev_tiled)."""
+    if solver.startswith("staged"):
+        return STAGED_SOURCES
+    if solver.startswith("k_rev_tiled"):
+        return REVERSE_SOURCES
+    return SOLVER_SOURCES
 
 
 def source_hash(files=SOLVER_SOURCES) -> str:
@@ -177,8 +189,7 @@ def main(argv=None):
                     help="algorithmic bytes of one captured launch, recorded with the entry")
     ap.add_argument("--exclude", default="",
                     help="launches: comma-separated name parts of kernels to leave out")
-    ap.add_argument("--sources", default=",".join(SOLVER_SOURCES),
-                    help="device sources whose hash keys the entry (comma-separated)")
+
     a = ap.parse_args(argv)
     if a.what == "launches":
         print(launch_table(a.csv, tuple(e for e in a.exclude.split(",") if e)))
@@ -201,7 +212,7 @@ def main(argv=None):
         print(f"mean DRAM bytes per launch: {summary['dram_bytes_per_launch']:.0f}")
     if a.update:
         entry = dict(summary, workload=a.workload, solver=a.solver,
-                     source_sha=source_hash(tuple(a.sources.split(","))),
+                     source_sha=source_hash(sources_for(a.solver)),
                      dram_scale=a.scale, command=a.command, alg_bytes_per_launch=a.alg_bytes)
         update_json(a.update, entry)
         print(f"recorded {a.workload} / {a.solver} in {a.update}")
