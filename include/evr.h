@@ -49,11 +49,12 @@ extern "C" {
 #define EVR_T_INIT_FIRST INT64_MIN
 
 /* Solver variants (evr_params.solver). */
-#define EVR_SOLVER_AUTO 0      /* pick the tiled solver, tile shape from the autotuner: at
-                                  the first solve every configuration is timed on the
-                                  sensor (state saved and restored); the up to three
-                                  closest then take turns on the next nine solves, timed
-                                  with CUDA events, and the fastest is kept */
+#define EVR_SOLVER_AUTO 0      /* pick the solver configuration with the autotuner: at
+                                  the first solve every candidate is timed once on the
+                                  sensor and the six fastest three more times (state
+                                  saved and restored); the up to three closest then take
+                                  turns on the next nine solves, timed with CUDA events,
+                                  and the fastest is kept (evr_solver_settled) */
 #define EVR_SOLVER_UNFUSED 1   /* two kernels per iteration (primal step, dual step) */
 #define EVR_SOLVER_TILED 2     /* temporally blocked tiles, several iterations per launch */
 

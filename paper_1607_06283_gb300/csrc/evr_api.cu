@@ -96,6 +96,7 @@ struct GraphKey {
   }
 };
 
+constexpr int kScreenKeep = 6;   // configurations re-timed after the autotuner's screen
 constexpr int kRefineCands = 3;  // configurations refined on real solves
 constexpr int kRefineReps = 3;   // real solves per candidate
 
@@ -367,20 +368,14 @@ void autotune(evr_stream* s, int iters) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int best_cfg = 0;
-  std::vector<std::pair<float, int>> timed;  // (ms, configuration) of kind-1 trials
-  for (int ci = 0; ci < kNumSolverCfgs; ++ci) {
-    // the persistent configurations were measured slower than relaunching on every
-    // workload (their L2 flag exchange); they stay selectable through tile_config
-    if (kSolverCfgs[ci].kind == 2) continue;
-    if (s->P.storage != 0 && kSolverCfgs[ci].kind != 1) continue;  // 16-bit p: kind 1 only
-    if (!solver_cfg_usable(s->P, kSolverCfgs[ci])) continue;
+  // time `reps` back-to-back solves of configuration ci (after `warm` untimed ones);
+  // < 0: the configuration failed (launch error or a timed-out wait)
+  auto trial = [&](int ci, int warm, int reps) -> float {
     s->cfg = ci;
     clear_flags(s);
-    bool ok = run_cfg_direct(s, ci, iters) == 0;  // warm-up (module load)
+    bool ok = true;
+    for (int r = 0; r < warm && ok; ++r) ok = run_cfg_direct(s, ci, iters) == 0;
     cudaEventRecord(e0, s->stream);
-    const int reps = 3;
     for (int r = 0; r < reps && ok; ++r) ok = run_cfg_direct(s, ci, iters) == 0;
     cudaEventRecord(e1, s->stream);
     if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
@@ -392,18 +387,33 @@ void autotune(evr_stream* s, int iters) {
       ok = false;
       cudaMemset(&s->P.sc->status, 0, sizeof(int));
     }
-    if (cudaGetLastError() == cudaSuccess && ok) {
-      timed.emplace_back(ms, ci);
-      if (ms < best) {
-        best = ms;
-        best_cfg = ci;
-      }
-    }
+    if (cudaGetLastError() != cudaSuccess) ok = false;
+    return ok ? ms / (float)reps : -1.0f;
+  };
+  // screen: every usable configuration once (after one untimed solve that loads its
+  // kernel); then the kScreenKeep fastest three more times each, keeping the best time
+  std::vector<std::pair<float, int>> timed;  // (ms per solve, configuration)
+  for (int ci = 0; ci < kNumSolverCfgs; ++ci) {
+    // the persistent configurations were measured slower than relaunching on every
+    // workload (their L2 flag exchange); they stay selectable through tile_config
+    if (kSolverCfgs[ci].kind == 2) continue;
+    if (s->P.storage != 0 && kSolverCfgs[ci].kind != 1) continue;  // 16-bit p: kind 1 only
+    if (!solver_cfg_usable(s->P, kSolverCfgs[ci])) continue;
+    const float ms = trial(ci, 1, 1);
+    if (ms >= 0.f) timed.emplace_back(ms, ci);
   }
+  std::sort(timed.begin(), timed.end());
+  if (timed.size() > (size_t)kScreenKeep) timed.resize(kScreenKeep);
+  for (auto& t : timed) {
+    const float ms = trial(t.second, 0, 3);
+    if (ms >= 0.f && ms < t.first) t.first = ms;
+  }
+  std::sort(timed.begin(), timed.end());
+  float best = timed.empty() ? 0.f : timed[0].first;
+  int best_cfg = timed.empty() ? 0 : timed[0].second;
   // candidates for the online refinement: configurations within 25 % of the best
   // back-to-back time (these trials run warm and without the packet's front launches;
   // real solves decide among them)
-  std::sort(timed.begin(), timed.end());
   s->n_cand = 0;
   s->refine_done = 0;
   for (const auto& t : timed)

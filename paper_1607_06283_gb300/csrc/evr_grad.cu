@@ -14,8 +14,11 @@
 
 #include "../../include/evr.h"
 #include "evr_internal.cuh"
+#include "evr_tma.cuh"
 
 namespace {
+
+namespace tma = evr::tma;
 
 constexpr int kRedBlocks = 256;
 constexpr int kRedThreads = 1024;
@@ -109,7 +112,9 @@ __global__ void k_metric(Geo g, const float* tx, const float* ty, float* iG, flo
 // L_g) and the new a_pt at x-1 and y-1 (in div_g), so, as in the forward, the values
 // stay exact on the tile shrunk by one pixel per side and iteration.  The adjoint state
 // (a_u, a_pt, tau a_v and the accumulated dL/df) stays in registers across the launch's
-// iterations; per iteration only the tape's p, v and ubar are read.
+// iterations; per iteration only the tape's p, v and ubar are read, from a shared-memory
+// copy of the slot staged one iteration ahead where the tape's rows are a multiple of 16
+// bytes (the pitch a multiple of 4), else directly.
 //
 // Reversing iteration k (state k = tape slot, adjoints of u_{k+1}, p_{k+1} given):
 //   a_p(k+1) = a_pt(k+1) - L_g(tau a_v(k+1))   (the given one if k = K-1)
@@ -126,6 +131,17 @@ __global__ void k_metric(Geo g, const float* tx, const float* ty, float* iG, flo
 // (GB300 issues FP64 arithmetic at a small fraction of the FP32 rate).
 constexpr int kRevR = 4;
 constexpr int kRevNTY = 16;
+// Where the tape's rows are a multiple of 16 bytes, the tape slot of each reversed
+// iteration is staged in shared memory by one tensor copy
+// (x, row, plane) issued one iteration ahead into the second of two stages: a box of
+// 5 planes x (2 kRevNTY + 1) rows x (32 + 8) columns, starting at the tile's x rounded
+// down to 8 elements (the 16-byte rule of tensor copies) and one row longer than the tile
+// for the y + 1 neighbour of its last row.
+constexpr int kRevBW = 40, kRevBH = 2 * kRevNTY + 1;
+constexpr int kRevPlaneF = kRevBW * kRevBH;                  // floats per staged plane
+constexpr int kRevStageF = (5 * kRevPlaneF + 31) / 32 * 32;  // 128-byte aligned stages
+constexpr size_t kRevSmem = 2 * sizeof(float) * kRevStageF;
+constexpr unsigned kRevSpin = 1u << 22;  // polls of a stage's mbarrier before giving up
 
 struct RevArgs {
   Geo g;
@@ -142,15 +158,20 @@ struct RevArgs {
   float* gf;
   double* glam;       // per (iteration, tile) lambda sums
   int tiles_x, tiles_total;
+  int staged;  // 1: the tape slots come through tape_map (rows of a multiple of 16 bytes)
 };
 
-__global__ void __launch_bounds__(32 * kRevNTY, 2) k_rev_tiled(RevArgs A) {
+__global__ void __launch_bounds__(32 * kRevNTY, 2)
+    k_rev_tiled(RevArgs A, const __grid_constant__ CUtensorMap tape_map) {
   constexpr int NT = kRevNTY, EW = 32, EH = 2 * NT, R = kRevR;
   constexpr int OW = EW - 2 * R, OH = EH - 2 * R;
+  extern __shared__ __align__(128) float rstage[];  // [2][kRevStageF]: tape slots
   __shared__ float tv[EH + 1][EW + 1];  // tau a_v; column EW and row EH: zero pads
   __shared__ float q1s[EH][EW + 1];     // (M^T sigma a_pt)_1 masked; column 0: zero pad
   __shared__ float q2s[EH + 1][EW];     // (M^T sigma a_pt)_2 masked; row 0: zero pad
   __shared__ float lsum[NT];            // the warps' lambda sums of an iteration
+  __shared__ __align__(8) unsigned long long s_mb[2];
+  __shared__ int s_bail;
   const Geo& g = A.g;
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int tile = blockIdx.x;
@@ -201,30 +222,76 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2) k_rev_tiled(RevArgs A) {
     q2s[0][i] = 0.0f;
   }
   for (int i = tid; i < EH; i += 32 * NT) q1s[i][0] = 0.0f;
+  const int sx0 = gx0 & ~7;  // the staged box's first column
+  auto issue = [&](int it, int b) {  // thread 0: the tape slot of reversed iteration it
+    const uint32_t mb = tma::smem_u32(&s_mb[b]);
+    tma::mbar_arm(mb, 5u * kRevPlaneF * 4u);
+    tma::load_3d(tma::smem_u32(rstage + b * kRevStageF), &tape_map, sx0, gy0,
+                 5 * (A.slot_hi - it), mb);
+  };
+  if (tid == 0) {
+    s_bail = 0;
+    if (A.staged) {
+      tma::mbar_init1(tma::smem_u32(&s_mb[0]));
+      tma::mbar_init1(tma::smem_u32(&s_mb[1]));
+      tma::mbar_init_fence();
+      issue(0, 0);
+    }
+  }
   __syncthreads();
   const float tl = tau * A.c.lambda;
   const unsigned PL = (unsigned)g.plane;  // plane stride (< 2^31 floats, checked)
-  // x + 1 neighbour offset where the x-difference exists (else the pixel itself: that
-  // difference is masked out); y + 1: pixel 1 of the pair for pixel 0, the next thread
-  // row for pixel 1, where the y-difference exists
+  // x + 1 neighbour where the x-difference exists (else the pixel itself: that difference
+  // is masked out); y + 1: pixel 1 of the pair for pixel 0, the next row for pixel 1,
+  // where the y-difference exists
   const unsigned ox = x < g.W - 1 ? 1u : 0u;
   const unsigned oy1 = (ydiff & 2u) ? (unsigned)g.pitch : 0u;
   for (int it = 0; it < A.iters; ++it) {
-    const float* slot = A.tape + (size_t)(A.slot_hi - it) * 5 * g.plane;  // uniform
-    // the iteration's tape values of both pixels, all loads issued together
     float p1[2], p2[2], p3[2], ub[2], ubx[2], vk[2];
     float uby1 = 0.0f;
-    for (int h = 0; h < 2; ++h) {
-      p1[h] = p2[h] = p3[h] = ub[h] = ubx[h] = vk[h] = 0.0f;
-      if (in[h]) {
-        const unsigned i = idx[h];
-        p1[h] = slot[i];
-        p2[h] = slot[PL + i];
-        p3[h] = slot[2 * PL + i];
-        vk[h] = slot[3 * PL + i];
-        ub[h] = slot[4 * PL + i];
-        ubx[h] = slot[4 * PL + i + ox];
-        if (h == 1) uby1 = slot[4 * PL + i + oy1];
+    if (A.staged) {
+      // the next iteration's slot into the other stage (read one iteration ago, by every
+      // thread before that iteration's barriers), then wait for this one's (bounded)
+      if (tid == 0 && it + 1 < A.iters) {
+        tma::fence_proxy_async();
+        issue(it + 1, (it + 1) & 1);
+      }
+      const uint32_t mb = tma::smem_u32(&s_mb[it & 1]);
+      for (unsigned n = 0; !tma::mbar_done(mb, (uint32_t)(it >> 1) & 1u);)
+        if (++n > kRevSpin) {
+          s_bail = 1;
+          break;
+        }
+      const float* slot = rstage + (it & 1) * kRevStageF;
+      // the iteration's tape values of both pixels from the staged slot
+      for (int h = 0; h < 2; ++h) {
+        p1[h] = p2[h] = p3[h] = ub[h] = ubx[h] = vk[h] = 0.0f;
+        if (in[h]) {
+          const int o = (2 * ty + h) * kRevBW + lane + (gx0 - sx0);
+          p1[h] = slot[o];
+          p2[h] = slot[kRevPlaneF + o];
+          p3[h] = slot[2 * kRevPlaneF + o];
+          vk[h] = slot[3 * kRevPlaneF + o];
+          ub[h] = slot[4 * kRevPlaneF + o];
+          ubx[h] = slot[4 * kRevPlaneF + o + (int)ox];
+          if (h == 1) uby1 = slot[4 * kRevPlaneF + o + ((ydiff & 2u) ? kRevBW : 0)];
+        }
+      }
+    } else {
+      const float* slot = A.tape + (size_t)(A.slot_hi - it) * 5 * g.plane;  // uniform
+      // the iteration's tape values of both pixels, all loads issued together
+      for (int h = 0; h < 2; ++h) {
+        p1[h] = p2[h] = p3[h] = ub[h] = ubx[h] = vk[h] = 0.0f;
+        if (in[h]) {
+          const unsigned i = idx[h];
+          p1[h] = slot[i];
+          p2[h] = slot[PL + i];
+          p3[h] = slot[2 * PL + i];
+          vk[h] = slot[3 * PL + i];
+          ub[h] = slot[4 * PL + i];
+          ubx[h] = slot[4 * PL + i + ox];
+          if (h == 1) uby1 = slot[4 * PL + i + oy1];
+        }
       }
     }
     float q1o[2], q2o[2];  // this thread's own (M^T sigma a_pt) entries
@@ -303,15 +370,20 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2) k_rev_tiled(RevArgs A) {
       if (lane == 0) A.glam[(size_t)(A.k_hi - it) * A.tiles_total + tile] = (double)t;
     }
   }
+  // a stage wait that ran out poisons this tile's outputs (NaN), so that a failed copy
+  // cannot pass for a gradient
+  __syncthreads();
+  const bool bail = s_bail != 0;
   for (int h = 0; h < 2; ++h) {
     if (!own[h]) continue;
     const unsigned i = idx[h];
-    A.a_out[0][i] = au[h];
-    A.a_out[1][i] = a1[h];
-    A.a_out[2][i] = a2[h];
-    A.a_out[3][i] = a3[h];
-    A.a_out[4][i] = tav[h];
-    A.gf[i] = gfa[h];
+    const float nan = __int_as_float(0x7fc00000);
+    A.a_out[0][i] = bail ? nan : au[h];
+    A.a_out[1][i] = bail ? nan : a1[h];
+    A.a_out[2][i] = bail ? nan : a2[h];
+    A.a_out[3][i] = bail ? nan : a3[h];
+    A.a_out[4][i] = bail ? nan : tav[h];
+    A.gf[i] = bail ? nan : gfa[h];
   }
 }
 
@@ -621,6 +693,11 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
   ra.glam = w.glam;
   rev_tiles(W, H, &ra.tiles_x, &ra.tiles_total);
   float* adj[2] = {w.adj, w.adj + 5 * fpl};
+  // the two staged tape slots exceed the default 48 KiB of dynamic shared memory
+  if (cudaFuncSetAttribute((const void*)k_rev_tiled,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRevSmem) !=
+      cudaSuccess)
+    return EVR_ERR_CUDA;
   const float* given[5] = {gu_K, gp_K, gp_K ? gp_K + g.plane : nullptr,
                            gp_K ? gp_K + 2 * g.plane : nullptr, nullptr};
   int cur = -1;  // the adjoint state's buffer; -1: the given adjoints
@@ -650,8 +727,20 @@ extern "C" int evr_unrolled_backward(const float* tx, const float* ty, const flo
       }
       if (k - r < 0 && gu0) ra.a_out[0] = gu0;  // the last launch: dL/du0 itself
       const bool timed = g_timing.on && g_timing.n < kMaxTimed;
+      // the tape as a 3-D tensor (x, row, plane) over the slots this launch reads, where
+      // its rows are a multiple of 16 bytes (a tensor copy's stride rule); else the
+      // launch reads the tape directly
+      CUtensorMap tape_map{};
+      const uint64_t dims[3] = {(uint64_t)W, (uint64_t)H, 5ull * (uint64_t)(ra.slot_hi + 1)};
+      const uint32_t box[3] = {(uint32_t)kRevBW, (uint32_t)kRevBH, 5u};
+      ra.staged = (pitch % 4 == 0) &&
+                  tma::encode_f32(&tape_map, ra.tape, 3, dims, (uint64_t)pitch * sizeof(float),
+                                  (uint64_t)fpl * sizeof(float), box)
+                      ? 1
+                      : 0;
       if (timed) cudaEventRecord(g_timing.ev[2 * g_timing.n], st);
-      k_rev_tiled<<<ra.tiles_total, dim3(32, kRevNTY), 0, st>>>(ra);
+      k_rev_tiled<<<ra.tiles_total, dim3(32, kRevNTY), ra.staged ? kRevSmem : 0, st>>>(ra,
+                                                                                  tape_map);
       counted();
       if (timed) {
         cudaEventRecord(g_timing.ev[2 * g_timing.n + 1], st);

@@ -21,14 +21,13 @@
 // Every wait on an mbarrier is bounded; a wait that runs out sets EVR_ERR_TIMEOUT in the
 // stream's status and the CTA stops taking tiles (after waiting, again bounded, for its
 // copies still in flight).
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "evr_internal.cuh"
 #include "evr_tile.cuh"
+#include "evr_tma.cuh"
 
 namespace evr {
 
@@ -50,38 +49,11 @@ struct StageArgs {
   int src, iters, R, tiles_x, n_tiles;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init1(uint32_t mb) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-}
-__device__ __forceinline__ void mbar_arm(uint32_t mb, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_done(uint32_t mb, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(mb), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// 2-D tensor copy of the box at (x, y) of `map` into shared memory at `dst`, completing
-// its bytes on the mbarrier `mb`
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint32_t mb) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(mb)
-      : "memory");
-}
+using tma::fence_proxy_async;
+using tma::mbar_arm;
+using tma::mbar_done;
+using tma::mbar_init1;
+using tma::smem_u32;
 
 template <int KX, int KY, int NTY>
 struct StageShape {
@@ -118,7 +90,7 @@ __global__ void __launch_bounds__(32 * NTY, (kStagedMinBlocks<KX, KY, NTY>))
     s_bail = 0;
     mbar_init1(smem_u32(&s_mb[0]));
     mbar_init1(smem_u32(&s_mb[1]));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tma::mbar_init_fence();
   }
   __syncthreads();
   // the previous pass wrote (u, p) of buffer src: wait for it before the first copy
@@ -132,12 +104,12 @@ __global__ void __launch_bounds__(32 * NTY, (kStagedMinBlocks<KX, KY, NTY>))
     const uint32_t dst = smem_u32(stage + (size_t)b * SS::STAGE);
     mbar_arm(mb, SS::BYTES);
     for (int q = 0; q < 4; ++q)
-      tma_load_2d(dst + q * SS::PLANE * 4u, &M.m[a.src][q], x0, gy0, mb);
-    tma_load_2d(dst + 4 * SS::PLANE * 4u, &M.tx, x0, gy0, mb);
-    tma_load_2d(dst + 5 * SS::PLANE * 4u, &M.ty, x0, gy0, mb);
-    tma_load_2d(dst + 6 * SS::PLANE * 4u, &M.f, x0, gy0, mb);
-    tma_load_2d(dst + 7 * SS::PLANE * 4u, &M.iG, x0, gy0, mb);
-    tma_load_2d(dst + 8 * SS::PLANE * 4u, &M.sG, x0, gy0, mb);
+      tma::load_2d(dst + q * SS::PLANE * 4u, &M.m[a.src][q], x0, gy0, mb);
+    tma::load_2d(dst + 4 * SS::PLANE * 4u, &M.tx, x0, gy0, mb);
+    tma::load_2d(dst + 5 * SS::PLANE * 4u, &M.ty, x0, gy0, mb);
+    tma::load_2d(dst + 6 * SS::PLANE * 4u, &M.f, x0, gy0, mb);
+    tma::load_2d(dst + 7 * SS::PLANE * 4u, &M.iG, x0, gy0, mb);
+    tma::load_2d(dst + 8 * SS::PLANE * 4u, &M.sG, x0, gy0, mb);
   };
   const int first = blockIdx.x;
   if (tid == 0 && first < a.n_tiles) issue(first, 0);
@@ -191,7 +163,7 @@ __global__ void __launch_bounds__(32 * NTY, (kStagedMinBlocks<KX, KY, NTY>))
     __syncthreads();
     if (s_bail) break;
     if (tid == 0 && tile + (int)gridDim.x < a.n_tiles) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      fence_proxy_async();
       issue(tile + gridDim.x, b ^ 1);
     }
     if (a.c.data_term)
@@ -208,34 +180,10 @@ __global__ void __launch_bounds__(32 * NTY, (kStagedMinBlocks<KX, KY, NTY>))
 }
 
 // ---------------------------------------------------------------- host side
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    else
-      cudaGetLastError();
-  }
-  return fn;
-}
-
 bool encode_plane(CUtensorMap* m, const float* base, const Planes& P, int BW, int EH) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)P.W, (cuuint64_t)P.H};
-  const cuuint64_t strides[1] = {(cuuint64_t)P.pitch * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)BW, (cuuint32_t)EH};
-  const cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  const uint64_t dims[2] = {(uint64_t)P.W, (uint64_t)P.H};
+  const uint32_t box[2] = {(uint32_t)BW, (uint32_t)EH};
+  return tma::encode_f32(m, base, 2, dims, (uint64_t)P.pitch * sizeof(float), 0, box);
 }
 
 template <int KX, int KY, int NTY>
@@ -307,7 +255,7 @@ int launch_t(const Planes& P, int R, int src, int iters, int pass, const SolveCo
 template <int KX, int KY, int NTY>
 bool usable_t(const Planes& P, int R) {
   int tx, ty;
-  return P.storage == 0 && tiles<KX, KY, NTY>(P, R, &tx, &ty) && encode_fn() != nullptr &&
+  return P.storage == 0 && tiles<KX, KY, NTY>(P, R, &tx, &ty) && tma::encode_fn() != nullptr &&
          resident_ctas<KX, KY, NTY>() > 0;
 }
 
