@@ -438,6 +438,9 @@ def run_ours(args):
            for _ in range(args.steps)]
     if pg:
         pg.barrier()
+    # the library records each step graph's launches (its events around the graph launch
+    # sit inside ours)
+    E.evr_enable_kernel_timing(g.h, True)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for j in range(args.steps):
@@ -450,6 +453,8 @@ def run_ours(args):
     if pg:
         pg.barrier()
     ms_steps = sum(a.elapsed_time(b) for a, b in evs)
+    _, step_launches, _ = E.evr_kernel_time(g.h)
+    E.evr_enable_kernel_timing(g.h, False)
 
     # the dominant kernels alone: the same packets' solves (front fused into the iteration
     # kernels) bracketed by the library's CUDA events on this stream, each push queued
@@ -576,11 +581,10 @@ def run_ours(args):
                     "d2h_bytes_per_step": cfg.W * cfg.H * 4 + 4,  # image + status word
                     "calls": "evr_step (host arrays: push and solve) + "
                              "evr_get_image_async into pinned memory, three steps in flight"},
-            # the timed steps' graphs: the solve's launches, plus the push kernel unless
-            # the single-launch cluster solver pushes the packet itself
-            "gpu_launches": int(round(k_launches + args.steps *
-                                      (0 if (" R0 " in g.solver_name and args.tvl1 == 0 and
-                                             g.solver_name.startswith("cluster")) else 1))),
+            # the timed steps' graphs, as the library counted them: the solve's launches,
+            # plus the push kernel unless the solver's first launch integrates the packet
+            "gpu_launches": int(step_launches),
+            "launches_per_step": step_launches / args.steps,
             "first_image_ms": first_ms,
             "clocks": clocks,
             "wall_s_timed": wall,
