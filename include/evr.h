@@ -339,6 +339,11 @@ const char* evr_batch_solver_name(evr_batch* b);
  * ((n, H, pitch) contiguous), a dual variable p is 3 such fields back to back
  * ((3, n, H, pitch) contiguous, component stride n*pitch*H).  The images are coupled by
  * nothing: image b's result is bit-identical to a call with n = 1 on image b alone.
+ * Images of different sizes cannot share a call (one call per size; a caller may pad
+ * smaller images into a larger W x H itself, which changes their border terms).  Where
+ * pitch is a multiple of 4 (rows of a multiple of 16 bytes) the reverse pass stages its
+ * tape slots in shared memory by tensor copies; otherwise it reads them directly (same
+ * results).
  * tx, ty are L_x t, L_y t of the packet (evr_get_state EVR_STATE_TX / EVR_STATE_TY).
  * All work is queued on cuda_stream (NULL: legacy default stream).  Errors:
  * EVR_ERR_INVALID_ARG (null pointer, W or H <= 0, pitch < W, n < 1, n*H > 524280,

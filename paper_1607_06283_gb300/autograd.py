@@ -146,6 +146,24 @@ def packet_solve(f, lam, u0, p0, tx, ty, iters: int, every: int = 10, tau: float
                              d.u_max if u_max is None else u_max)
 
 
+def packet_solve_many(members, lam, iters: int, every: int = 10, **kw):
+    """Differentiable solves of packets of different sensor sizes: `members` is a list of
+    (f, u0, p0, tx, ty) tuples ((H, W) images, (3, H, W) dual variables).  Members of one
+    size are stacked and solved by one library call per size (each member's result is
+    that of its own call: the stacked images are independent); returns [(u_K, p_K)] in
+    the members' order.  lambda is shared, so dL/dlambda sums over every member."""
+    groups = {}
+    for k, m in enumerate(members):
+        groups.setdefault(tuple(m[0].shape), []).append(k)
+    out = [None] * len(members)
+    for idx in groups.values():
+        stk = [torch.stack([members[k][j] for k in idx]) for j in range(5)]
+        u, p = packet_solve(stk[0], lam, stk[1], stk[2], stk[3], stk[4], iters, every, **kw)
+        for b, k in enumerate(idx):
+            out[k] = (u[b], p[b])
+    return out
+
+
 def data_image(u_prev, npos, nneg, delta_pos, delta_neg):
     """Differentiable data image of one packet or a batch of packets."""
     return DataImage.apply(u_prev, npos, nneg, delta_pos, delta_neg)

@@ -300,7 +300,7 @@ int clear_flags(evr_stream* s) {
 // The multi-launch iteration launches of one packet (unfused or kind 1):
 // `iters` iterations from buffer `cur`.  Returns the buffer holding the result.
 int enqueue_iterations(evr_stream* s, int iters, int cur, cudaStream_t st, int* launches,
-                       const PrologueConsts* front = nullptr) {
+                       const PrologueConsts* front = nullptr, const PushArgs* push = nullptr) {
   SolveConsts c = solve_consts(s);
   *launches = 0;
   if (s->cfg < 0) {
@@ -320,7 +320,7 @@ int enqueue_iterations(evr_stream* s, int iters, int cur, cudaStream_t st, int* 
     int it = iters - done < cfg.R ? iters - done : cfg.R;
     const int e = cfg.kind == 3   ? launch_cluster(s->P, cfg, cur, it, pass, c, st, front, nullptr)
                   : cfg.kind == 4 ? launch_staged(s->P, cfg, cur, it, pass, c, st)
-                                  : launch_tiled_pass(s->P, cfg, cur, it, pass, c, st, front);
+                                  : launch_tiled_pass(s->P, cfg, cur, it, pass, c, st, front, push);
     if (e) return -1;
     cur = 1 - cur;
     *launches += 1;
@@ -925,11 +925,15 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
                const uint16_t* x, const uint16_t* y, const long long* t, const int8_t* pol) {
   cudaStream_t st = s->stream;
   const bool fuse = front_fused(s, iters);  // the prologue inside the first pass
-  // one cluster over the sensor: the push runs inside the solver's single launch
+  // one cluster over the sensor: the push runs inside the solver's single launch; a
+  // multi-launch tiled solve with its front fused takes a small packet into pass 0
   const bool in_solver = push_in_solver(s, (size_t)n, iters);
+  const bool in_pass0 = !in_solver && fuse && n <= kTiledPushMax &&
+                        kSolverCfgs[s->cfg].kind == 1 &&
+                        tiled_push_fusable(kSolverCfgs[s->cfg], s->P.storage);
   const PrologueConsts pc = prologue_consts(s);
   const PushArgs pa{x, y, t, pol, n};
-  GraphKey key{iters, s->cur, copy_src ? 3 : 2, s->cfg};
+  GraphKey key{iters, s->cur, (copy_src ? 3 : 2) + (in_pass0 ? 10 : 0), s->cfg};
   auto it = s->fused.find(key);
   evr_stream::Fused* fg = nullptr;
   if (it == s->fused.end()) {
@@ -944,6 +948,9 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
     if (in_solver) {
       if (r == 0 && launch_cluster(s->P, kSolverCfgs[s->cfg], s->cur, iters, 0,
                                    solve_consts(s), s->cap_stream, &pc, &pa))
+        r = -1;
+    } else if (in_pass0) {
+      if (r == 0 && enqueue_iterations(s, iters, s->cur, s->cap_stream, &captured, &pc, &pa) < 0)
         r = -1;
     } else {
       if (r == 0 && launch_push(s->P, x, y, t, pol, n, s->cap_stream)) r = -1;
@@ -983,6 +990,10 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
       if (cluster_node_set_push(fg->exec, fg->push, s->P, kSolverCfgs[s->cfg], s->cur, iters,
                                 solve_consts(s), pc, pa))
         return EVR_ERR_CUDA;
+    } else if (in_pass0) {  // pass 0's arguments with this call's packet
+      if (tiled_node_set_push(fg->exec, fg->push, s->P, kSolverCfgs[s->cfg], s->cur, iters,
+                              solve_consts(s), pc, pa))
+        return EVR_ERR_CUDA;
     } else {
       // this call's packet: the push node's arguments (Planes, x, y, t, pol, n)
       cudaKernelNodeParams kp;
@@ -1013,7 +1024,8 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
     s->ev_used.push_back(ev);
     const int front =
         fuse ? 0 : 1 + ((s->prm.tvl1_iters > 0 && s->prm.manifold) ? 1 + 2 * s->prm.tvl1_iters : 0);
-    s->ev_launches.push_back((in_solver ? 0 : 1) + front + (s->cfg < 0 ? 2 * iters : passes));
+    s->ev_launches.push_back((in_solver || in_pass0 ? 0 : 1) + front +
+                             (s->cfg < 0 ? 2 * iters : passes));
     s->ev_pixiters.push_back((long long)s->W * s->H * iters);
   }
   if (s->cfg >= 0 && passes % 2) s->cur = 1 - s->cur;

@@ -23,6 +23,10 @@ struct DevScalars {
   int status;        // first device-side error code (rejection or timeout), 0 if none
   int first_bad;     // multi-CTA validation: lowest index of an invalid event
   int abort;         // persistent solver: set by a CTA whose neighbour wait timed out
+  // a packet integrated inside the first tiled pass (every CTA reads the clock there):
+  // its clock and t_init, committed by the second pass
+  long long clock_next, t_init_next;
+  int commit_pending;
 };
 
 // Persistent solver: at most this many CTAs (one progress flag each).
@@ -98,6 +102,14 @@ __device__ __forceinline__ float data_image(float base, int np, int nn,
 }
 #endif
 
+// A packet of n events (device arrays) that a solver launch integrates itself.
+struct PushArgs {
+  const uint16_t *x, *y;
+  const long long* t;
+  const int8_t* pol;
+  int n;
+};
+
 // Tiled solvers.  A tile template is an extended tile of EW x EH pixels (an owned
 // tile plus an R-pixel halo on every side) processed by 32 x NTY threads.  A solver
 // configuration is a template, a halo width R and a kind:
@@ -163,7 +175,19 @@ int launch_unfused_iteration(const Planes& P, int cur, const SolveConsts& c, voi
 // computes the prologue's constants itself (data_mode 0, no TV-L1 plane) and pass 1
 // clears the event counts; the caller runs at least two passes.
 int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters, int pass,
-                      const SolveConsts& c, void* stream, const PrologueConsts* front = nullptr);
+                      const SolveConsts& c, void* stream, const PrologueConsts* front = nullptr,
+                      const PushArgs* push = nullptr);
+// With front and push (FP32 tiles that fuse the front, packets of at most
+// kTiledPushMax events): pass 0 also validates and integrates the packet itself -- every
+// CTA scans it and merges the events of its extended tile from a shared-memory map, the
+// owned pixels' t_last is written back, and pass 1 commits the stream clock.  The
+// pass-0 node of a captured graph of an `iters`-iteration solve takes a new packet
+// through tiled_node_set_push.
+constexpr int kTiledPushMax = 2048;
+bool tiled_push_fusable(const SolverCfg& cfg, int storage);
+int tiled_node_set_push(void* graph_exec, void* node, const Planes& P, const SolverCfg& cfg,
+                        int src, int iters, const SolveConsts& c, const PrologueConsts& front,
+                        const PushArgs& push);
 // Whether launch_tiled_pass supports a fused front for this configuration and storage
 // (tiles without a register cap).
 int tiled_front_fusable(const SolverCfg& cfg, int storage);
@@ -195,12 +219,6 @@ int launch_persistent(const Planes& P, const SolverCfg& cfg, int cur, int iters,
 // (n <= 32768).  silent_rank >= 0 (wait self-test only): that CTA of the cluster sends
 // nothing, so its neighbours' bounded waits run out and the launch ends with
 // EVR_ERR_TIMEOUT.
-struct PushArgs {
-  const uint16_t *x, *y;
-  const long long* t;
-  const int8_t* pol;
-  int n;
-};
 int launch_cluster(const Planes& P, const SolverCfg& cfg, int src, int iters, int pass,
                    const SolveConsts& c, void* stream, const PrologueConsts* front,
                    const PushArgs* push, int silent_rank = -1);

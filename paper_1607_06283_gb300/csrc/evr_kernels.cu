@@ -70,6 +70,9 @@ __global__ void k_init(Planes P, float u_init, long long clock0, long long t_ini
     P.sc->status = 0;
     P.sc->first_bad = INT_MAX;
     P.sc->abort = 0;
+    P.sc->clock_next = clock0;
+    P.sc->t_init_next = t_init;
+    P.sc->commit_pending = 0;
   }
   if (P.flags && y == 0 && x < kMaxCtas) P.flags[x] = 0;  // solo streams only
   if (x >= P.pitch || y >= P.H) return;

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "evr_internal.cuh"
+#include "evr_push.cuh"
 #include "evr_tile.cuh"
 
 namespace evr {
@@ -69,25 +70,97 @@ const SolverCfg kSolverCfgs[kNumSolverCfgs] = {
 // loads everything after its wait.
 // Resident CTAs per SM the register budget is sized for: tiles with two pixel pairs per
 // thread get as many CTAs as fit at 80 registers (three of 256 threads, two of 384; no
-// spills in FP32 and BF16, 4 bytes in FP16), so that more warps hide latency and the
-// next pass's CTAs can become resident while the current pass runs; one otherwise.
+// spills in FP32 and BF16, 4 bytes in FP16), tiles with one pair as many as fit at 64
+// (four of 256 threads, two of 512, one of 1024; no spills), so that more warps hide
+// latency and the next pass's CTAs can become resident while the current pass runs.
 template <int KX, int KY, int NTY, typename ST>
 constexpr int kTiledMinBlocks =
-    (KX * KY == 4 && 65536 / (32 * NTY * 80) > 1) ? 65536 / (32 * NTY * 80)
-                                                                      : 1;
+    (KX * KY == 4 && 65536 / (32 * NTY * 80) > 1)   ? 65536 / (32 * NTY * 80)
+    : (KX * KY == 2 && 65536 / (32 * NTY * 64) > 1) ? 65536 / (32 * NTY * 64)
+                                                    : 1;
+// Tiles whose passes can take the packet's front (its computation needs the registers of
+// an uncapped two-pair tile; one-pair tiles fit it in 64)
+template <int KX, int KY, int NTY, typename ST>
+constexpr bool kTiledFront = kTiledMinBlocks<KX, KY, NTY, ST> == 1 || KX * KY == 2;
 
 // MODE 0: plain passes.  MODE 1 (FRONT): the packet's front launch is fused into the
-// passes (instantiated only for tiles without a register cap, kTiledMinBlocks == 1).
+// passes (instantiated for the tiles of kTiledFront).
 // MODE 2 (tape, FP32 only): iteration it of this launch also writes the p it starts
 // from, its v and its ubar into tape slot tape_first + it (5 planes, slot stride
 // 5 tape_plane floats), for the reverse pass of the unrolled solve.
 // The tape mode's tile is held to two resident CTAs per SM (64 registers), as the plain
 // passes of the same tile reach without a cap.
+// MODE 3 (FRONT and push, FP32 only): as MODE 1, and pass 0 integrates the packet
+// itself.  Every CTA validates the whole packet (the same verdict everywhere; the
+// stream's clock is read, never written, in pass 0), merges the events that fall into
+// its extended tile plus one column and row into shared-memory maps (dynamic shared
+// memory), forms the packet constants from the planes and the maps, and writes back its
+// owned pixels' t_last (a pixel read as halo by another CTA gives that CTA the same
+// value before or after the write: t_last only grows by the maximum).  CTA 0 records the
+// packet's clock for pass 1, which commits it.
+template <int KX, int KY, int NTY>
+constexpr size_t tiled_push_smem() {
+  return (size_t)(32 * KX + 1) * (NTY * KY + 1) * (sizeof(long long) + sizeof(int));
+}
+
+template <class TT>
+__device__ __forceinline__ void push_front(TT& T, const Planes& P, const SolveConsts& c,
+                                           const PrologueConsts& pc, const PushArgs& ev) {
+  constexpr int MW = TT::EW + 1, MH = TT::EH + 1;
+  const int NT = (int)(blockDim.x * blockDim.y);
+  extern __shared__ __align__(16) unsigned char push_smem[];
+  long long* mt = reinterpret_cast<long long*>(push_smem);
+  int* mc = reinterpret_cast<int*>(mt + MW * MH);
+  __shared__ int s_bad;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const long long clock0 = P.sc->clock;
+  const int have = P.sc->t_init_set;
+  const long long t_init0 = P.sc->t_init;
+  if (tid == 0) s_bad = ev.n;
+  for (int m = tid; m < MW * MH; m += NT) {
+    mt[m] = kNeverFired;
+    mc[m] = 0;
+  }
+  __syncthreads();
+  for (int i = tid; i < ev.n; i += NT)
+    if (event_code(ev.x, ev.y, ev.t, ev.pol, i, P.W, P.H, clock0, have) != 0)
+      atomicMin(&s_bad, i);
+  __syncthreads();
+  const bool valid = s_bad >= ev.n;
+  if (valid) {
+    for (int i = tid; i < ev.n; i += NT) {
+      const int lx = (int)ev.x[i] - T.gx0, ly = (int)ev.y[i] - T.gy0;
+      if (lx >= 0 && lx < MW && ly >= 0 && ly < MH) {
+        atomicMax(&mt[ly * MW + lx], ev.t[i]);
+        atomicAdd(&mc[ly * MW + lx], ev.pol[i] > 0 ? 1 : (1 << 16));
+      }
+    }
+  }
+  __syncthreads();
+  long long clock = clock0, t_init = have ? t_init0 : clock0;
+  if (valid && ev.n > 0) {
+    clock = max(clock0, ev.t[ev.n - 1]);
+    t_init = have ? t_init0 : ev.t[0];
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    if (!valid) {
+      atomicCAS(&P.sc->status, 0,
+                event_code(ev.x, ev.y, ev.t, ev.pol, s_bad, P.W, P.H, clock0, have));
+    } else if (ev.n > 0) {
+      P.sc->clock_next = clock;
+      P.sc->t_init_next = t_init;
+      P.sc->commit_pending = 1;
+    }
+  }
+  T.front_consts_push(P, c, pc, mt, mc, clock, t_init);
+}
+
 template <int KX, int KY, int NTY, typename ST, int MODE>
 __global__ void __launch_bounds__(32 * NTY, (MODE == 2 ? 2 : kTiledMinBlocks<KX, KY, NTY, ST>))
     k_tiled(Planes P, int src, int iters, int R, SolveConsts c, int tiles_x, BatchRef B,
-            int pass, PrologueConsts pc, float* tape, long long tape_plane, int tape_first) {
-  constexpr bool FRONT = MODE == 1;
+            int pass, PrologueConsts pc, float* tape, long long tape_plane, int tape_first,
+            PushArgs ev) {
+  constexpr bool FRONT = MODE == 1 || MODE == 3;
   __shared__ TileSmem<KX, KY, NTY, ST> sm;
   __shared__ Planes sP;  // this CTA's stream, staged once (no per-thread local copy)
   int tile = blockIdx.x;
@@ -114,7 +187,21 @@ __global__ void __launch_bounds__(32 * NTY, (MODE == 2 ? 2 : kTiledMinBlocks<KX,
   if (early) T.load_consts(sP, c);
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" :::);
-  if constexpr (FRONT) {
+  if constexpr (MODE == 3) {
+    T.load_state(sP, src);  // the front takes f from the current u
+    if (pass == 0) {
+      push_front(T, sP, c, pc, ev);
+    } else if (!early) {
+      T.load_consts(sP, c);
+      T.clear_counts(sP);
+      if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0 && sP.sc->commit_pending) {
+        sP.sc->clock = sP.sc->clock_next;  // the packet integrated by pass 0
+        sP.sc->t_init = sP.sc->t_init_next;
+        sP.sc->t_init_set = 1;
+        sP.sc->commit_pending = 0;
+      }
+    }
+  } else if constexpr (FRONT) {
     T.load_state(sP, src);  // front_consts takes f from the current u
     if (pass == 0) {
       T.front_consts(sP, c, pc);
@@ -240,44 +327,83 @@ static int tiles_of(const Planes& P, int R, int* tx, int* ty) {
   return 1;
 }
 
+// Whether the push can be fused into pass 0 for this tile (MODE 3 instantiated: FP32,
+// no register cap); sets the kernel's dynamic shared-memory limit for its event maps.
+template <int KX, int KY, int NTY>
+static bool push_fusable_t() {
+  if constexpr (kTiledMinBlocks<KX, KY, NTY, float> == 1) {
+    static int ok = -1;
+    if (ok < 0) {
+      ok = cudaFuncSetAttribute((const void*)k_tiled<KX, KY, NTY, float, 3>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tiled_push_smem<KX, KY, NTY>()) == cudaSuccess;
+      if (!ok) cudaGetLastError();
+    }
+    return ok == 1;
+  } else {
+    return false;
+  }
+}
+
 template <int KX, int KY, int NTY, typename ST>
 static cudaError_t launch_k_tiled_st(cudaLaunchConfig_t* lc, const Planes& P, int src,
                                      int iters, int R, const SolveConsts& c, int tx,
-                                     const BatchRef& B, int pass, const PrologueConsts* front) {
+                                     const BatchRef& B, int pass, const PrologueConsts* front,
+                                     const PushArgs* push) {
+  const PushArgs none{nullptr, nullptr, nullptr, nullptr, 0};
+  if (front && push) {
+    if constexpr (kTiledMinBlocks<KX, KY, NTY, ST> == 1 && sizeof(ST) == 4) {
+      if (push->n < 0 || push->n > kTiledPushMax) return cudaErrorInvalidValue;
+      lc->dynamicSmemBytes = tiled_push_smem<KX, KY, NTY>();
+      return cudaLaunchKernelEx(lc, k_tiled<KX, KY, NTY, ST, 3>, P, src, iters, R, c, tx, B,
+                                pass, *front, (float*)nullptr, 0LL, 0,
+                                pass == 0 ? *push : none);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   if (front) {
-    if constexpr (kTiledMinBlocks<KX, KY, NTY, ST> == 1)
+    if constexpr (kTiledFront<KX, KY, NTY, ST>)
       return cudaLaunchKernelEx(lc, k_tiled<KX, KY, NTY, ST, 1>, P, src, iters, R, c, tx, B,
-                                pass, *front, (float*)nullptr, 0LL, 0);
+                                pass, *front, (float*)nullptr, 0LL, 0, none);
     else
       return cudaErrorInvalidValue;
   }
   return cudaLaunchKernelEx(lc, k_tiled<KX, KY, NTY, ST, 0>, P, src, iters, R, c, tx, B, pass,
-                            PrologueConsts{}, (float*)nullptr, 0LL, 0);
+                            PrologueConsts{}, (float*)nullptr, 0LL, 0, none);
+}
+
+template <int KX, int KY, int NTY>
+static void tiled_config(cudaLaunchConfig_t* lc, cudaLaunchAttribute* at, int blocks,
+                         cudaStream_t st) {
+  *lc = cudaLaunchConfig_t{};
+  lc->gridDim = dim3(blocks);
+  lc->blockDim = dim3(32, NTY);
+  lc->stream = st;
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc->attrs = at;
+  lc->numAttrs = 1;
 }
 
 template <int KX, int KY, int NTY>
 static int launch_k_tiled(int blocks, const Planes& P, int src, int iters, int R,
                           const SolveConsts& c, int tx, const BatchRef& B, int pass,
-                          int storage, cudaStream_t st, const PrologueConsts* front) {
-  cudaLaunchConfig_t lc = {};
-  lc.gridDim = dim3(blocks);
-  lc.blockDim = dim3(32, NTY);
-  lc.stream = st;
+                          int storage, cudaStream_t st, const PrologueConsts* front,
+                          const PushArgs* push = nullptr) {
+  cudaLaunchConfig_t lc;
   cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  lc.attrs = at;
-  lc.numAttrs = 1;
+  tiled_config<KX, KY, NTY>(&lc, at, blocks, st);
   switch (storage) {
     case 0:
       return (int)launch_k_tiled_st<KX, KY, NTY, float>(&lc, P, src, iters, R, c, tx, B, pass,
-                                                        front);
+                                                        front, push);
     case 1:
       return (int)launch_k_tiled_st<KX, KY, NTY, __half>(&lc, P, src, iters, R, c, tx, B, pass,
-                                                         front);
+                                                         front, push);
     case 2:
       return (int)launch_k_tiled_st<KX, KY, NTY, __nv_bfloat16>(&lc, P, src, iters, R, c, tx, B,
-                                                                pass, front);
+                                                                pass, front, push);
     default:
       return (int)cudaErrorInvalidValue;
   }
@@ -286,22 +412,56 @@ static int launch_k_tiled(int blocks, const Planes& P, int src, int iters, int R
 template <int KX, int KY, int NTY>
 static bool front_fusable(int storage) {
   switch (storage) {
-    case 0: return kTiledMinBlocks<KX, KY, NTY, float> == 1;
-    case 1: return kTiledMinBlocks<KX, KY, NTY, __half> == 1;
-    case 2: return kTiledMinBlocks<KX, KY, NTY, __nv_bfloat16> == 1;
+    case 0: return kTiledFront<KX, KY, NTY, float>;
+    case 1: return kTiledFront<KX, KY, NTY, __half>;
+    case 2: return kTiledFront<KX, KY, NTY, __nv_bfloat16>;
     default: return false;
   }
 }
 
 template <int KX, int KY, int NTY>
 static int run_tiled(const Planes& P, int R, int src, int iters, int pass,
-                     const SolveConsts& c, cudaStream_t st, const PrologueConsts* front) {
+                     const SolveConsts& c, cudaStream_t st, const PrologueConsts* front,
+                     const PushArgs* push) {
   int tx, ty;
   if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters > R || iters < 1)
     return (int)cudaErrorInvalidValue;
   return launch_k_tiled<KX, KY, NTY>(tx * ty, P, src, iters, R, c, tx,
                                      BatchRef{nullptr, nullptr, nullptr, nullptr}, pass,
-                                     P.storage, st, front);
+                                     P.storage, st, front, push);
+}
+
+// The pass-0 node of a captured push-fused graph of a packet solve of `iters` iterations,
+// given the next packet: the arguments launch_tiled_pass gave pass 0 (min(iters, R)
+// iterations from buffer src), with this push.
+template <int KX, int KY, int NTY>
+static int set_push_node(cudaGraphExec_t exec, cudaGraphNode_t node, const Planes& P, int R,
+                         int src, int iters, const SolveConsts& c, const PrologueConsts& front,
+                         const PushArgs& push) {
+  int tx, ty;
+  if constexpr (kTiledMinBlocks<KX, KY, NTY, float> == 1) {
+    if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters < 1 || push.n < 0 ||
+        push.n > kTiledPushMax)
+      return (int)cudaErrorInvalidValue;
+    Planes Pc = P;
+    SolveConsts cc = c;
+    BatchRef B{nullptr, nullptr, nullptr, nullptr};
+    PrologueConsts pc = front;
+    PushArgs ev = push;
+    int srcv = src, itv = iters < R ? iters : R, Rv = R, txv = tx, pass = 0;
+    float* tape = nullptr;
+    long long tp = 0;
+    int tf = 0;
+    void* args[] = {&Pc, &srcv, &itv, &Rv, &cc, &txv, &B, &pass, &pc, &tape, &tp, &tf, &ev};
+    cudaKernelNodeParams kp;
+    cudaError_t e = cudaGraphKernelNodeGetParams(node, &kp);
+    if (e != cudaSuccess) return (int)e;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    return (int)cudaGraphExecKernelNodeSetParams(exec, node, &kp);
+  } else {
+    return (int)cudaErrorInvalidValue;
+  }
 }
 
 template <int KX, int KY, int NTY>
@@ -358,9 +518,26 @@ static int run_persist(const Planes& P, int R, int cur, int iters, int base, int
   }
 
 int launch_tiled_pass(const Planes& P, const SolverCfg& cfg, int src, int iters, int pass,
-                      const SolveConsts& c, void* stream, const PrologueConsts* front) {
+                      const SolveConsts& c, void* stream, const PrologueConsts* front,
+                      const PushArgs* push) {
   cudaStream_t st = (cudaStream_t)stream;
-  EVR_SHAPE_DISPATCH(run_tiled, P, cfg.R, src, iters, pass, c, st, front)
+  EVR_SHAPE_DISPATCH(run_tiled, P, cfg.R, src, iters, pass, c, st, front, push)
+  return (int)cudaErrorInvalidValue;
+}
+
+bool tiled_push_fusable(const SolverCfg& cfg, int storage) {
+  if (cfg.kind != 1 || storage != 0) return false;
+  EVR_SHAPE_DISPATCH(push_fusable_t)
+  return false;
+}
+
+int tiled_node_set_push(void* graph_exec, void* node, const Planes& P, const SolverCfg& cfg,
+                        int src, int iters, const SolveConsts& c, const PrologueConsts& front,
+                        const PushArgs& push) {
+  if (cfg.kind != 1) return (int)cudaErrorInvalidValue;
+  cudaGraphExec_t ex = (cudaGraphExec_t)graph_exec;
+  cudaGraphNode_t nd = (cudaGraphNode_t)node;
+  EVR_SHAPE_DISPATCH(set_push_node, ex, nd, P, cfg.R, src, iters, c, front, push)
   return (int)cudaErrorInvalidValue;
 }
 
@@ -390,10 +567,12 @@ int launch_tiled_tape(const Planes& P, int R, int src, int iters, int pass,
   if (tape)
     return (int)cudaLaunchKernelEx(&lc, k_tiled<kTapeKX, kTapeKY, kTapeNTY, float, 2>, P, src,
                                    iters, R, c, tx, BatchRef{nullptr, nullptr, nullptr, nullptr},
-                                   pass, PrologueConsts{}, tape, tape_plane, tape_first);
+                                   pass, PrologueConsts{}, tape, tape_plane, tape_first,
+                                   PushArgs{nullptr, nullptr, nullptr, nullptr, 0});
   return (int)cudaLaunchKernelEx(&lc, k_tiled<kTapeKX, kTapeKY, kTapeNTY, float, 0>, P, src,
                                  iters, R, c, tx, BatchRef{nullptr, nullptr, nullptr, nullptr},
-                                 pass, PrologueConsts{}, (float*)nullptr, 0LL, 0);
+                                 pass, PrologueConsts{}, (float*)nullptr, 0LL, 0,
+                                 PushArgs{nullptr, nullptr, nullptr, nullptr, 0});
 }
 
 int tiled_front_fusable(const SolverCfg& cfg, int storage) {

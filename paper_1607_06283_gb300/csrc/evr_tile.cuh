@@ -283,6 +283,56 @@ struct Tile {
     }
   }
 
+  // As front_consts, for a packet that is not yet in the planes: its events over the
+  // extended tile plus one column and one row (mw = EW + 1 per map row) are merged from
+  // shared-memory maps -- mt the latest event time of each pixel (kNeverFired: none),
+  // mc its event counts (positive in the low, negative in the high 16 bits) -- with the
+  // t_last and counts already in the planes, exactly as the push followed by the
+  // prologue would leave them (max and sum do not depend on the order).  clock and t_init
+  // are the stream's after the packet.  The owned pixels' merged t_last is written back.
+  __device__ __forceinline__ void front_consts_push(const Planes& P, const SolveConsts& c,
+                                                    const PrologueConsts& pc,
+                                                    const long long* mt, const int* mc,
+                                                    long long clock, long long t_init) {
+    constexpr int MW = EW + 1;
+    const float tl = c.tau * c.lambda;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float a = 0.0f, b = 0.0f, ig = 1.0f, sg = 1.0f, f = 1.0f, mx = 0.0f, my = 0.0f;
+      if (on(k, P.W, P.H)) {
+        const size_t i = gidx(P, k);
+        const int gx = gx0 + lx(k), gy = gy0 + ly(k), m = ly(k) * MW + lx(k);
+        const long long t_own = max(P.t_last[i], mt[m]);
+        const float t0 = time_surface(t_own, clock, t_init, pc);
+        a = (gx < P.W - 1)
+                ? surface_diff(time_surface(max(P.t_last[i + 1], mt[m + 1]), clock, t_init, pc),
+                               t0)
+                : 0.0f;
+        b = (gy < P.H - 1) ? surface_diff(time_surface(max(P.t_last[i + P.pitch], mt[m + MW]),
+                                                       clock, t_init, pc),
+                                          t0)
+                           : 0.0f;
+        const float G = metric_G(a, b);
+        ig = 1.0f / G;
+        sg = sqrtf(G);
+        const int cnt = mc[m];
+        f = data_image(el(u[k >> 1], k & 1), P.npos[i] + (cnt & 0xffff), P.nneg[i] + (cnt >> 16),
+                       pc);
+        mx = (gx < P.W - 1) ? 1.0f : 0.0f;
+        my = (gy % P.Hm < P.Hm - 1) ? 1.0f : 0.0f;
+        if (owned(k)) {
+          P.tx[i] = a;
+          P.ty[i] = b;
+          P.iG[i] = ig;
+          P.sG[i] = sg;
+          P.f[i] = f;
+          if (mt[m] > P.t_last[i]) P.t_last[i] = t_own;
+        }
+      }
+      set_consts(k, a, b, ig, sg, f, mx, my, tl, c);
+    }
+  }
+
   // The owned pixels' event counts, consumed by the previous pass's front_consts.
   __device__ __forceinline__ void clear_counts(const Planes& P) const {
 #pragma unroll

@@ -271,6 +271,38 @@ def test_batched_solve_equals_single_solves_bit_for_bit(T):
     assert float(tlam.grad) == pytest.approx(sum(s[5] for s in single), rel=1e-5)
 
 
+def test_mixed_size_members_equal_their_own_calls(T):
+    """packet_solve_many groups members by size (one library call per size); every
+    member's forward result and gradients are those of its own call, and dL/dlambda is
+    the sum over the members."""
+    torch, AG, E = T
+    K, every, lam = 17, 5, 30.0
+    shapes = [(19, 23), (12, 40), (19, 23), (12, 40), (19, 23)]
+    probs = [problem(900 + b, H, W) for b, (H, W) in enumerate(shapes)]
+    single = []
+    for tx, ty, f, u0, p0, w in probs:
+        ttx, tty, tf, tu0, tp0, tw = cuda(torch, tx, ty, f, u0, p0, w)
+        tf.requires_grad_(True)
+        tlam = torch.tensor(lam, device="cuda", requires_grad=True)
+        u, p = AG.packet_solve(tf, tlam, tu0, tp0, ttx, tty, K, every)
+        (u * tw).sum().backward()
+        single.append((u.detach().cpu().numpy(), tf.grad.cpu().numpy(), float(tlam.grad)))
+    members, ws, fs = [], [], []
+    for tx, ty, f, u0, p0, w in probs:
+        ttx, tty, tf, tu0, tp0, tw = cuda(torch, tx, ty, f, u0, p0, w)
+        tf.requires_grad_(True)
+        members.append((tf, tu0, tp0, ttx, tty))
+        ws.append(tw)
+        fs.append(tf)
+    tlam = torch.tensor(lam, device="cuda", requires_grad=True)
+    res = AG.packet_solve_many(members, tlam, K, every)
+    sum((u * w).sum() for (u, _), w in zip(res, ws)).backward()
+    for b, ((u, _), tf) in enumerate(zip(res, fs)):
+        np.testing.assert_array_equal(u.detach().cpu().numpy(), single[b][0])
+        np.testing.assert_array_equal(tf.grad.cpu().numpy(), single[b][1])
+    assert float(tlam.grad) == pytest.approx(sum(s[2] for s in single), rel=1e-5)
+
+
 def test_batched_gradients_match_oracle_on_a_ragged_member(T):
     """A batch of 3 images of 1 row each (every row is a member's first and last row):
     no y-coupling between members, gradients against the FP64 oracle per member."""
