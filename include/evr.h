@@ -157,8 +157,12 @@ int evr_step_device(evr_stream* s, const uint16_t* x, const uint16_t* y, const i
                     const int8_t* pol, size_t n, int iters);
 
 /* The same with host arrays: evr_push_events followed by evr_solve, with the same checks
- * and results; when fused, the staging copy, the push, the front launches and the
- * iteration kernels form one graph.  The arrays may be reused when the call returns. */
+ * and results.  The packet is packed into one of the handle's pinned staging slots and
+ * copied, on a library-owned copy stream, into that slot's device buffer while the
+ * earlier packets still solve; the packet's graph (push, front launches, iteration
+ * kernels) waits for the copy on the handle's stream.  The arrays may be reused when the
+ * call returns.  Errors: as evr_push_events (nothing is queued on a rejected packet or
+ * EVR_ERR_OOM), EVR_ERR_CUDA. */
 int evr_step(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t* t_us,
              const int8_t* pol, size_t n, int iters);
 

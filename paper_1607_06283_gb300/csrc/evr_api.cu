@@ -79,8 +79,13 @@ struct Packed {
 struct StageSlot {
   size_t cap = 0;            // events
   char* h = nullptr;         // pinned, 13 * cap bytes
-  cudaEvent_t done = nullptr;  // recorded after the slot's host-to-device copy
+  cudaEvent_t done = nullptr;  // recorded after the work that reads the slot
   bool pending = false;
+  // evr_step: the slot's own device copy of the packet, filled on the handle's copy
+  // stream ahead of the packet's graph (which waits for `copied`)
+  size_t dcap = 0;           // events
+  char* d = nullptr;         // device, 13 * dcap bytes
+  cudaEvent_t copied = nullptr;
 };
 
 constexpr int kImgRing = 16;  // asynchronous image readbacks in flight per handle
@@ -122,6 +127,7 @@ struct evr_stream {
   int flag_base = 0;                  // persistent solver: progress-flag count
   // host-to-device event staging
   StageSlot slot[kStageSlots];
+  cudaStream_t h2d_stream = nullptr;  // evr_step: packet copies ahead of their graphs
   int next_slot = 0;
   size_t dcap = 0;           // events
   char* dstage = nullptr;    // device, 13 * dcap bytes
@@ -149,7 +155,6 @@ struct evr_stream {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphNode_t push = nullptr;
-    cudaGraphNode_t copy = nullptr;  // host-array steps: the staging copy before the push
   };
   std::map<GraphKey, Fused> fused;
   // kernel timing
@@ -219,9 +224,16 @@ void set_name(evr_stream* s) {
 }
 
 void free_stage(evr_stream* s) {
+  if (s->h2d_stream) {
+    cudaStreamSynchronize(s->h2d_stream);
+    cudaStreamDestroy(s->h2d_stream);
+    s->h2d_stream = nullptr;
+  }
   for (auto& sl : s->slot) {
     if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.copied) cudaEventDestroy(sl.copied);
     if (sl.h) cudaFreeHost(sl.h);
+    if (sl.d) cudaFree(sl.d);
     sl = StageSlot{};
   }
   if (s->dstage) cudaFree(s->dstage);
@@ -246,8 +258,8 @@ void free_stage(evr_stream* s) {
   s->h_img_status = nullptr;
 }
 
-// Grow the pinned slot and the device staging buffer to hold n events.
-int ensure_stage(evr_stream* s, StageSlot& sl, size_t n) {
+// Grow the pinned slot to hold n events.
+int ensure_stage(StageSlot& sl, size_t n) {
   if (sl.cap < n) {
     if (sl.done) cudaEventSynchronize(sl.done);
     if (sl.h) cudaFreeHost(sl.h);
@@ -262,6 +274,12 @@ int ensure_stage(evr_stream* s, StageSlot& sl, size_t n) {
     if (!sl.done && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
       return EVR_ERR_CUDA;
   }
+  return EVR_OK;
+}
+
+// evr_push_events: grow the handle's device staging buffer (read by the push on the
+// handle's stream) to hold n events.
+int ensure_dstage(evr_stream* s, size_t n) {
   if (s->dcap < n) {
     if (s->dstage) {
       cudaStreamSynchronize(s->stream);
@@ -274,6 +292,33 @@ int ensure_stage(evr_stream* s, StageSlot& sl, size_t n) {
       return EVR_ERR_OOM;
     }
     s->dcap = cap;
+  }
+  return EVR_OK;
+}
+
+// evr_step: the slot's device copy of n events, its copy event and the handle's copy
+// stream.  The caller has waited for the slot's previous packet (stage_host), so the old
+// device buffer is no longer read.
+int ensure_slot_device(evr_stream* s, StageSlot& sl, size_t n) {
+  if (!s->h2d_stream &&
+      cudaStreamCreateWithFlags(&s->h2d_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    s->h2d_stream = nullptr;
+    return EVR_ERR_CUDA;
+  }
+  if (!sl.copied && cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming) != cudaSuccess) {
+    sl.copied = nullptr;
+    return EVR_ERR_CUDA;
+  }
+  if (sl.dcap < n) {
+    if (sl.d) cudaFree(sl.d);
+    sl.d = nullptr;
+    sl.dcap = 0;
+    const size_t cap = ((n < 4096 ? 4096 : n + n / 2) + 63) / 64 * 64;
+    if (dev_alloc((void**)&sl.d, cap * 13) != cudaSuccess) {
+      sl.d = nullptr;
+      return EVR_ERR_OOM;
+    }
+    sl.dcap = cap;
   }
   return EVR_OK;
 }
@@ -689,7 +734,7 @@ int stage_host(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_
     if (cudaEventSynchronize(sl.done) != cudaSuccess) return EVR_ERR_CUDA;
     sl.pending = false;
   }
-  int rc = ensure_stage(s, sl, n);
+  int rc = ensure_stage(sl, n);
   if (rc) return rc;
   const Packed L(n);
   std::memcpy(sl.h, x, n * 2);
@@ -720,6 +765,7 @@ int evr_push_events(evr_stream* s, const uint16_t* x, const uint16_t* y, const i
   StageSlot* sl = nullptr;
   long long clock = 0;
   int rc = stage_host(s, x, y, t_us, pol, n, &sl, &clock);
+  if (rc == EVR_OK) rc = ensure_dstage(s, n);
   if (rc) return rc;
   const Packed L(n);
   cudaStream_t st = s->stream;
@@ -917,12 +963,12 @@ bool fused_ok(const evr_stream* s, size_t n, int iters) {
          !(s->cfg >= 0 && kSolverCfgs[s->cfg].kind == 2);
 }
 
-// One packet as one graph: [staging copy (host arrays: copy_src, copy_bytes)], push of the
-// events at x, y, t, pol (device), the front launches and the iteration kernels.  The
-// graph is cached per (iters, buffer, kind, configuration); later calls update the copy
-// and push nodes.
-int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t copy_bytes,
-               const uint16_t* x, const uint16_t* y, const long long* t, const int8_t* pol) {
+// One packet as one graph: push of the events at x, y, t, pol (device arrays), the front
+// launches and the iteration kernels (the push inside the first launch where the solver
+// takes it).  The graph is cached per (iters, buffer, push form, configuration); later
+// calls update the node that pushes.
+int fused_step(evr_stream* s, int iters, int n, const uint16_t* x, const uint16_t* y,
+               const long long* t, const int8_t* pol) {
   cudaStream_t st = s->stream;
   const bool fuse = front_fused(s, iters);  // the prologue inside the first pass
   // one cluster over the sensor: the push runs inside the solver's single launch; a
@@ -933,7 +979,7 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
                         tiled_push_fusable(kSolverCfgs[s->cfg], s->P.storage);
   const PrologueConsts pc = prologue_consts(s);
   const PushArgs pa{x, y, t, pol, n};
-  GraphKey key{iters, s->cur, (copy_src ? 3 : 2) + (in_pass0 ? 10 : 0), s->cfg};
+  GraphKey key{iters, s->cur, in_pass0 ? 12 : 2, s->cfg};
   auto it = s->fused.find(key);
   evr_stream::Fused* fg = nullptr;
   if (it == s->fused.end()) {
@@ -942,9 +988,6 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
     if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return EVR_ERR_CUDA;
     int r = 0;
-    if (copy_src && cudaMemcpyAsync(s->dstage, copy_src, copy_bytes, cudaMemcpyHostToDevice,
-                                    s->cap_stream) != cudaSuccess)
-      r = -1;
     if (in_solver) {
       if (r == 0 && launch_cluster(s->P, kSolverCfgs[s->cfg], s->cur, iters, 0,
                                    solve_consts(s), s->cap_stream, &pc, &pa))
@@ -961,20 +1004,12 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
         r = -1;
     }
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &nf.graph);
-    size_t roots = 1, deps = 1;
+    size_t roots = 1;
     cudaGraphNode_t root = nullptr;
     if (r == 0 && e == cudaSuccess) e = cudaGraphGetRootNodes(nf.graph, &root, &roots);
-    if (r == 0 && e == cudaSuccess && roots == 1) {
-      if (copy_src) {
-        nf.copy = root;
-        e = cudaGraphNodeGetDependentNodes(root, &nf.push, nullptr, &deps);
-      } else {
-        nf.push = root;
-      }
-    }
-    if (r == 0 && e == cudaSuccess && roots == 1 && deps == 1)
-      e = cudaGraphInstantiate(&nf.exec, nf.graph, 0);
-    if (r < 0 || e != cudaSuccess || roots != 1 || deps != 1 || !nf.exec) {
+    if (r == 0 && e == cudaSuccess && roots == 1) nf.push = root;
+    if (r == 0 && e == cudaSuccess && roots == 1) e = cudaGraphInstantiate(&nf.exec, nf.graph, 0);
+    if (r < 0 || e != cudaSuccess || roots != 1 || !nf.exec) {
       if (nf.exec) cudaGraphExecDestroy(nf.exec);
       if (nf.graph) cudaGraphDestroy(nf.graph);
       return EVR_ERR_CUDA;
@@ -982,10 +1017,6 @@ int fused_step(evr_stream* s, int iters, int n, const char* copy_src, size_t cop
     fg = &(s->fused[key] = nf);
   } else {
     fg = &it->second;
-    if (copy_src && cudaGraphExecMemcpyNodeSetParams1D(fg->exec, fg->copy, s->dstage, copy_src,
-                                                       copy_bytes, cudaMemcpyHostToDevice) !=
-                        cudaSuccess)
-      return EVR_ERR_CUDA;
     if (in_solver) {  // the cluster launch's arguments with this call's packet
       if (cluster_node_set_push(fg->exec, fg->push, s->P, kSolverCfgs[s->cfg], s->cur, iters,
                                 solve_consts(s), pc, pa))
@@ -1045,7 +1076,7 @@ int evr_step_device(evr_stream* s, const uint16_t* x, const uint16_t* y, const i
     int rc = n ? evr_push_events_device(s, x, y, t_us, pol, n) : EVR_OK;
     return rc ? rc : evr_solve(s, iters);
   }
-  int rc = fused_step(s, iters, (int)n, nullptr, 0, x, y, (const long long*)t_us, pol);
+  int rc = fused_step(s, iters, (int)n, x, y, (const long long*)t_us, pol);
   if (rc == EVR_OK) s->h_clock_valid = false;
   return rc;
 }
@@ -1064,13 +1095,20 @@ int evr_step(evr_stream* s, const uint16_t* x, const uint16_t* y, const int64_t*
   long long clock = 0;
   int rc = stage_host(s, x, y, t_us, pol, n, &sl, &clock);
   if (rc) return rc;
+  if ((rc = ensure_slot_device(s, *sl, n)) != EVR_OK) return rc;
   const Packed L(n);
-  char* d = s->dstage;
-  rc = fused_step(s, iters, (int)n, sl->h, L.bytes, (const uint16_t*)d,
-                  (const uint16_t*)(d + L.off_y), (const long long*)(d + L.off_t),
-                  (const int8_t*)(d + L.off_p));
+  // the packet's copy runs on the copy stream while earlier packets still solve; the
+  // packet's graph (on the handle's stream) waits for it
+  cudaError_t e =
+      cudaMemcpyAsync(sl->d, sl->h, L.bytes, cudaMemcpyHostToDevice, s->h2d_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(sl->copied, s->h2d_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, sl->copied, 0);
+  if (e != cudaSuccess) return EVR_ERR_CUDA;
+  char* d = sl->d;
+  rc = fused_step(s, iters, (int)n, (const uint16_t*)d, (const uint16_t*)(d + L.off_y),
+                  (const long long*)(d + L.off_t), (const int8_t*)(d + L.off_p));
   if (rc) return rc;
-  // the slot is free again once this packet's graph has run
+  // the slot (pinned and device copies) is free again once this packet's graph has run
   if (cudaEventRecord(sl->done, s->stream) != cudaSuccess) return EVR_ERR_CUDA;
   sl->pending = true;
   note_clock(s, clock);

@@ -188,3 +188,29 @@ def test_push_staging_allocation_failure_leaves_the_stream_unchanged(E):
         assert g.push(*big) == 0
         g.solve(10)
     np.testing.assert_array_equal(a.image(), twin.image())
+
+
+@pytest.mark.parametrize("fail_at", [1, 2])
+def test_step_slot_allocation_failure_leaves_the_stream_unchanged(E, fail_at):
+    """evr_step grows a staging slot's pinned buffer (first allocation) and then its device
+    buffer (second) for a large packet; when either fails the packet is not queued and
+    the stream goes on as its twin."""
+    W, H = 80, 40
+    smalls = packets(7, W, H, 4, 200)  # four packets: every staging slot holds a buffer
+    big = packets(8, W, H, 1, 6000)[0]  # past the slot's first 4096 events
+    big = (big[0], big[1], big[2] + smalls[-1][2][-1], big[3])
+    a, twin = E.Stream(W, H), E.Stream(W, H)
+    for g in (a, twin):
+        for pk in smalls:
+            assert E.evr_step(g.h, *pk, 10) == 0
+    E._lib.evr_test_fail_alloc_after(fail_at)
+    rc = E._lib.evr_step(a.h, big[0].ctypes.data, big[1].ctypes.data, big[2].ctypes.data,
+                         big[3].ctypes.data, len(big[0]), 10)
+    E._lib.evr_test_fail_alloc_after(0)
+    assert rc == E.EVR_ERR_OOM
+    for g in (a, twin):
+        g.solve(10)
+    np.testing.assert_array_equal(a.image(), twin.image())
+    for g in (a, twin):  # and the stream takes the packet afterwards
+        assert E.evr_step(g.h, *big, 10) == 0
+    np.testing.assert_array_equal(a.image(), twin.image())

@@ -85,8 +85,9 @@ def test_step_with_empty_and_large_packets_and_a_rejection(T, tile):
 @pytest.mark.parametrize("over", [{}, dict(tile_config=45), dict(tile_config=47),
                                   dict(tile_config=47, data_term=1)])
 def test_host_step_equals_push_then_solve(T, over):
-    """evr_step (host arrays, staging copy inside the graph) against evr_push_events +
-    evr_solve; the host-side checks reject a bad packet before anything is queued."""
+    """evr_step (host arrays, copied on the copy stream ahead of the packet's graph) against
+    evr_push_events + evr_solve; the host-side checks reject a bad packet before anything
+    is queued."""
     torch, E = T
     W, H = 120, 77
     pk = packets(4, W, H, 12, 900)
