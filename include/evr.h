@@ -276,11 +276,12 @@ int evr_measure_peak(int level, double* gbs, void* cuda_stream);
  * takes at most one packet per stream (streams with no events in the step are left
  * untouched), validates and integrates every packet (one CTA per stream), then runs
  * the packet prologue and `iters` iterations for every stream that had events, as one
- * CUDA graph over a (stream, tile) work list.  Each stream's results are bit-identical
- * to a single stream (evr_create) fed the same packets with the same tile_config; the
- * tiled configuration is autotuned over the whole batch at the first step unless
- * tile_config selects one (multi-launch configurations only).  Per-stream packets
- * above 32768 events are rejected with EVR_ERR_INVALID_ARG. */
+ * CUDA graph over a (stream, tile) work list, cut into groups of streams that fit L2
+ * (evr_batch_set_grouping).  Each stream's results are bit-identical to a single stream
+ * (evr_create) fed the same packets with the same tile_config; the tiled configuration
+ * is autotuned over the whole batch at the first step unless tile_config selects one
+ * (multi-launch configurations only).  Per-stream packets above 32768 events are
+ * rejected with EVR_ERR_INVALID_ARG. */
 typedef struct evr_batch evr_batch; /* opaque handle */
 
 /* Create n streams of sizes W[s] x H[s].  Errors as evr_create; EVR_ERR_NOT_SUPPORTED
@@ -289,6 +290,19 @@ int evr_batch_create(int n, const int* W, const int* H, const evr_params* params
                      evr_batch** out);
 void evr_batch_destroy(evr_batch* b);
 int evr_batch_set_cuda_stream(evr_batch* b, void* cuda_stream);
+
+/* Order of a step's work (results are bit-identical for every setting).  The streams
+ * are cut, in index order, into groups whose pass working set ((u, p) of both buffers
+ * and the five constant planes, pitch x H pixels each) stays within budget_bytes (a
+ * larger stream is a group of its own); the step graph runs each group's prologue and
+ * all its iteration passes before the next group, so that the group's state stays in
+ * L2 across its passes; with branches = k (1 to 4) group g runs on graph branch g mod k,
+ * k groups side by side.  budget_bytes = 0: one group (every pass over all streams);
+ * budget_bytes < 0 (the default): chosen with the tiled configuration by the autotuner
+ * at the next step with iterations, from 8 to 64 MB and one to four branches, against
+ * one group.  Synchronises the batch's stream.  Errors: EVR_ERR_INVALID_ARG (null
+ * handle, branches outside 1..4), EVR_ERR_CUDA. */
+int evr_batch_set_grouping(evr_batch* b, long long budget_bytes, int branches);
 
 /* One step.  Events of all streams concatenated (structure of arrays, device
  * pointers); stream s owns events [offsets[s], offsets[s+1]) (offsets: device int64
@@ -326,9 +340,10 @@ int evr_batch_get_state(evr_batch* b, int s, int which, void* out_host, size_t b
  * *stream_out if not NULL, -1 if none) and clear all pending rejections. */
 int evr_batch_synchronize(evr_batch* b, int* stream_out);
 
-/* Kernel timing of the steps' graphs (prologue + iteration passes), as
- * evr_enable_kernel_timing / evr_kernel_time; pixel_iters counts every stream as
- * active in every timed step. */
+/* Kernel timing of the steps' graphs (per group the prologue and the iteration passes;
+ * the buffer flip), as evr_enable_kernel_timing / evr_kernel_time; launches counts
+ * every kernel of the graphs; pixel_iters counts every stream as active in every timed
+ * step. */
 int evr_batch_enable_kernel_timing(evr_batch* b, int enable);
 int evr_batch_kernel_time(evr_batch* b, double* ms, int64_t* launches, int64_t* pixel_iters);
 const char* evr_batch_solver_name(evr_batch* b);

@@ -8,6 +8,11 @@
 // work list of (stream, tile) pairs.  The tiled kernel is the same instantiation the
 // single-stream solver uses, so each stream's result is bit-identical to solving it
 // alone with the same solver configuration.
+//
+// The streams can be cut into groups whose pass working set fits L2: the graph then runs
+// each group's prologue and all its passes before the next group (optionally two groups
+// at a time on two graph branches), so that a group's (u, p) and constants stay in L2
+// across its passes instead of every pass sweeping the whole batch through HBM.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,9 +46,22 @@ struct evr_batch {
   int n_work_pro = 0;
   int2* d_work_tile = nullptr;
   int n_work_tile = 0;
+  std::vector<int> pro_off, tile_off;  // per stream: first work item (n + 1 entries)
   int cfg = -1;
   bool tuned = false;
+  // L2 grouping of a step's work: pass working set per group (0: one group of all
+  // streams), graph branches running groups side by side; auto: chosen by the autotuner
+  long long group_budget = 0;
+  int branches = 1;
+  bool group_auto = true, group_tuned = false;
+  struct Group {
+    int tile0, ntile, pro0, npro;
+  };
+  std::vector<Group> groups;
   cudaStream_t stream = nullptr, own_stream = nullptr, cap_stream = nullptr;
+  static constexpr int kMaxBranches = 4;
+  cudaStream_t side[kMaxBranches - 1] = {};  // the other branches (capture and tuning)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::map<int, cudaGraphExec_t> graphs;  // by iteration count
   // host-pointer steps: packed pinned staging (two slots) and device staging
   size_t stage_cap = 0;
@@ -109,8 +127,36 @@ PrologueConsts pconsts(const evr_batch* b) {
                         (long long)b->prm.t_max_us, b->prm.manifold, b->prm.data_mode, nullptr};
 }
 
-BatchRef bref(const evr_batch* b, bool tiles) {
-  return BatchRef{b->d_descs, tiles ? b->d_work_tile : b->d_work_pro, b->d_curs, b->d_active};
+BatchRef bref(const evr_batch* b, bool tiles, int first = 0) {
+  return BatchRef{b->d_descs, (tiles ? b->d_work_tile : b->d_work_pro) + first, b->d_curs,
+                  b->d_active};
+}
+
+// Bytes one pass reads and writes of stream s: (u, p) of both buffers and the five
+// constant planes (tx, ty, 1/G, sqrt G, f).
+long long pass_bytes(const evr_batch* b, int s) {
+  const long long ps = b->prm.storage ? 2 : 4;
+  return (long long)b->planes[s].pitch * b->planes[s].H * (2 * (4 + 3 * ps) + 5 * 4);
+}
+
+// Cut the streams, in index order, into groups whose pass bytes stay within
+// group_budget (a stream larger than the budget is a group of its own); budget 0: one
+// group.  Needs the work offsets of the current tile work list.
+void build_groups(evr_batch* b) {
+  b->groups.clear();
+  int s0 = 0;
+  long long acc = 0;
+  for (int s = 0; s <= b->n; ++s) {
+    const long long sb = s < b->n ? pass_bytes(b, s) : 0;
+    const bool cut = s == b->n || (b->group_budget > 0 && s > s0 && acc + sb > b->group_budget);
+    if (cut) {
+      b->groups.push_back(evr_batch::Group{b->tile_off[s0], b->tile_off[s] - b->tile_off[s0],
+                                           b->pro_off[s0], b->pro_off[s] - b->pro_off[s0]});
+      s0 = s;
+      acc = 0;
+    }
+    acc += sb;
+  }
 }
 
 // (stream, tile) work items of configuration ci for every stream.
@@ -119,10 +165,14 @@ int build_tile_work(evr_batch* b, int ci) {
   const TileShape& t = kTileShapes[c.shape];
   const int OW = t.EW - 2 * c.R, OH = t.EH - 2 * c.R;
   std::vector<int2> w;
+  b->tile_off.assign(b->n + 1, 0);
   for (int s = 0; s < b->n; ++s) {
     const int tx = (b->planes[s].W + OW - 1) / OW, ty = (b->planes[s].H + OH - 1) / OH;
+    b->tile_off[s] = (int)w.size();
     for (int k = 0; k < tx * ty; ++k) w.push_back(make_int2(s, k));
   }
+  b->tile_off[b->n] = (int)w.size();
+  build_groups(b);
   if (b->d_work_tile) cudaFree(b->d_work_tile);
   b->d_work_tile = nullptr;
   if (dev_alloc((void**)&b->d_work_tile, sizeof(int2) * w.size()) != cudaSuccess)
@@ -146,51 +196,130 @@ void set_name(evr_batch* b) {
   }
   const SolverCfg& c = kSolverCfgs[b->cfg];
   const TileShape& t = kTileShapes[c.shape];
-  std::snprintf(b->name, sizeof(b->name), "batch of %d: tiled %dx%d R%d (%d threads, %d CTAs)",
-                b->n, t.EW, t.EH, c.R, 32 * t.NTY, b->n_work_tile);
+  const int n = std::snprintf(b->name, sizeof(b->name),
+                              "batch of %d: tiled %dx%d R%d (%d threads, %d CTAs)", b->n, t.EW,
+                              t.EH, c.R, 32 * t.NTY, b->n_work_tile);
+  if (b->groups.size() > 1 && n > 0 && n < (int)sizeof(b->name))
+    std::snprintf(b->name + n, sizeof(b->name) - n, ", %d L2 groups of <= %lld MB x %d",
+                  (int)b->groups.size(), b->group_budget >> 20, b->branches);
 }
 
-// Time each multi-launch tiled configuration over the whole batch: single passes that
-// read each stream's current buffer and write the other one (no live state changes).
-// Time every multi-launch configuration on the whole batch with the packet's iteration
-// count (its passes, the last one shorter) and keep the fastest (best of two runs).  Every
-// timing launch reads the live buffer and writes the other one, which the step graph
-// overwrites anyway, so the live state is untouched.
-void autotune(evr_batch* b, int iters) {
-  SolveConsts c = consts(b);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+// A step's work for configuration ci, group by group: group g on branch g mod
+// `branches`, branch 0 being q and the others the batch's side streams (fork and join
+// through events, so the same code serves stream capture and direct launches).  step:
+// each group's prologue, then its passes with their indices in the step; otherwise
+// (timing) the passes only, all with index 0 (each reads the live buffer and writes the
+// other one, which a step overwrites anyway).
+int enqueue_groups(evr_batch* b, int ci, int iters, bool step, cudaStream_t q) {
+  const SolverCfg& cfg = kSolverCfgs[ci];
+  const SolveConsts c = consts(b);
+  const int nb = std::min<int>(b->branches, (int)b->groups.size());
+  int bad = 0;
+  if (nb > 1) bad |= cudaEventRecord(b->ev_fork, q) != cudaSuccess;
+  for (int k = 1; k < nb; ++k) bad |= cudaStreamWaitEvent(b->side[k - 1], b->ev_fork, 0) != cudaSuccess;
+  for (size_t g = 0; g < b->groups.size(); ++g) {
+    const evr_batch::Group& G = b->groups[g];
+    cudaStream_t st = g % nb ? b->side[g % nb - 1] : q;
+    if (step) bad |= launch_prologue_batch(bref(b, false, G.pro0), G.npro, pconsts(b), st);
+    for (int done = 0, j = 0; done < iters; done += cfg.R, ++j) {
+      const int k = iters - done < cfg.R ? iters - done : cfg.R;
+      bad |= launch_tiled_pass_batch(bref(b, true, G.tile0), G.ntile, cfg, step ? j : 0, k, c,
+                                     b->prm.storage, st);
+    }
+  }
+  for (int k = 1; k < nb; ++k) {  // each wait takes the event's latest record
+    bad |= cudaEventRecord(b->ev_join, b->side[k - 1]) != cudaSuccess;
+    bad |= cudaStreamWaitEvent(q, b->ev_join, 0) != cudaSuccess;
+  }
+  return bad;
+}
+
+// Milliseconds of the passes of a step (best of `reps` after one warm-up), or -1.
+float time_passes(evr_batch* b, int ci, int iters, int reps, cudaEvent_t e0, cudaEvent_t e1) {
+  float best = -1.f;
+  if (enqueue_groups(b, ci, iters, false, b->stream)) return -1.f;
+  for (int rep = 0; rep < reps; ++rep) {
+    cudaEventRecord(e0, b->stream);
+    const int bad = enqueue_groups(b, ci, iters, false, b->stream);
+    cudaEventRecord(e1, b->stream);
+    float ms = 0.f;
+    if (bad || cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      return -1.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0.f || ms < best) best = ms;
+  }
+  return best;
+}
+
+// Fastest multi-launch configuration under the current grouping (every configuration
+// timed on the whole batch with the packet's iteration count, best of two runs), or -1.
+int screen_configs(evr_batch* b, int iters, cudaEvent_t e0, cudaEvent_t e1, float* best_ms) {
   float best = 1e30f;
   int best_cfg = -1;
   for (int ci = 0; ci < kNumSolverCfgs; ++ci) {
     if (kSolverCfgs[ci].kind != 1) continue;
     if (build_tile_work(b, ci)) continue;
-    const int R = kSolverCfgs[ci].R;
-    const int passes = (iters + R - 1) / R;
-    BatchRef B = bref(b, true);
-    launch_tiled_pass_batch(B, b->n_work_tile, kSolverCfgs[ci], 0, R, c, b->prm.storage,
-                            b->stream);  // warm-up
-    for (int rep = 0; rep < 2; ++rep) {
-      cudaEventRecord(e0, b->stream);
-      for (int j = 0; j < passes; ++j)
-        launch_tiled_pass_batch(B, b->n_work_tile, kSolverCfgs[ci], 0,
-                                j + 1 < passes ? R : iters - j * R, c, b->prm.storage,
-                                b->stream);
-      cudaEventRecord(e1, b->stream);
-      float ms = 0.f;
-      if (cudaEventSynchronize(e1) == cudaSuccess && cudaGetLastError() == cudaSuccess) {
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-          best = ms;
-          best_cfg = ci;
+    const float ms = time_passes(b, ci, iters, 2, e0, e1);
+    if (ms >= 0.f && ms < best) {
+      best = ms;
+      best_cfg = ci;
+    }
+  }
+  *best_ms = best;
+  return best_cfg;
+}
+
+// The step's tiled configuration and L2 grouping.  configs: the configuration is
+// screened with one group.  Unless the grouping was set: every budget from 64 MB down to
+// 8 MB of pass working set per group with one to four branches is timed against one
+// group for that configuration, and with configs the configurations are screened again
+// under the best grouping.  The timing launches read the live buffer and write the other
+// one, so the live state is untouched.
+void autotune(evr_batch* b, int iters, bool configs) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const long long budget = b->group_budget;
+  const int branches = b->branches;
+  float ms = 0.f;
+  if (configs) {
+    b->group_budget = 0;
+    b->branches = 1;
+    const int ci = screen_configs(b, iters, e0, e1, &ms);
+    b->cfg = ci < 0 ? 0 : ci;
+    b->group_budget = budget;
+    b->branches = branches;
+  }
+  if (b->group_auto) {
+    static const long long kBudgetsMB[] = {64, 48, 32, 24, 16, 12, 8};
+    long long best_budget = 0;
+    int best_branches = 1;
+    b->group_budget = 0;
+    b->branches = 1;
+    float best = build_tile_work(b, b->cfg) ? -1.f : time_passes(b, b->cfg, iters, 2, e0, e1);
+    for (long long mb : kBudgetsMB)
+      for (int br = 1; br <= evr_batch::kMaxBranches && best >= 0.f; ++br) {
+        b->group_budget = mb << 20;
+        b->branches = br;
+        build_groups(b);
+        if ((int)b->groups.size() < std::max(2, br)) continue;
+        const float t = time_passes(b, b->cfg, iters, 2, e0, e1);
+        if (t >= 0.f && t < best) {
+          best = t;
+          best_budget = b->group_budget;
+          best_branches = br;
         }
       }
+    b->group_budget = best_budget;
+    b->branches = best_branches;
+    b->group_tuned = true;
+    if (configs && best_budget > 0) {
+      const int ci = screen_configs(b, iters, e0, e1, &ms);
+      if (ci >= 0 && ms < best) b->cfg = ci;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->cfg = best_cfg < 0 ? 0 : best_cfg;
   build_tile_work(b, b->cfg);
 }
 
@@ -219,17 +348,10 @@ int step_graph(evr_batch* b, int iters, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return EVR_ERR_CUDA;
-  int bad = launch_prologue_batch(bref(b, false), b->n_work_pro, pconsts(b), b->cap_stream);
-  int passes = 0;
+  int bad = enqueue_groups(b, b->cfg, iters, true, b->cap_stream);
   if (iters > 0) {
-    const SolverCfg& cfg = kSolverCfgs[b->cfg];
-    SolveConsts c = consts(b);
-    for (int done = 0; done < iters; done += cfg.R, ++passes) {
-      int k = iters - done < cfg.R ? iters - done : cfg.R;
-      bad |= launch_tiled_pass_batch(bref(b, true), b->n_work_tile, cfg, passes, k, c,
-                                     b->prm.storage, b->cap_stream);
-    }
-    bad |= launch_batch_flip(b->d_curs, b->d_active, b->n, passes, b->cap_stream);
+    const int R = kSolverCfgs[b->cfg].R;
+    bad |= launch_batch_flip(b->d_curs, b->d_active, b->n, (iters + R - 1) / R, b->cap_stream);
   }
   cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
   if (bad || e != cudaSuccess) {
@@ -290,13 +412,16 @@ int evr_batch_create(int n, const int* W, const int* H, const evr_params* params
   }
   b->planes.resize(n);
   std::vector<int2> pro;
+  b->pro_off.assign(n + 1, 0);
   for (int s = 0; s < n; ++s) {
     carve_state(b->dev + off[s], W[s], H[s], false, &b->planes[s]);
     b->planes[s].storage = params->storage;
     const int nb = ((W[s] + 31) / 32) * ((H[s] + 7) / 8);
+    b->pro_off[s] = (int)pro.size();
     for (int k = 0; k < nb; ++k) pro.push_back(make_int2(s, k));
     b->px_total += (long long)W[s] * H[s];
   }
+  b->pro_off[n] = (int)pro.size();
   b->d_descs = (Planes*)(b->dev + tail);
   b->d_curs = (int*)(b->dev + tail + (sizeof(Planes) * n + 255) / 256 * 256);
   b->d_active = b->d_curs + n;
@@ -309,6 +434,10 @@ int evr_batch_create(int n, const int* W, const int* H, const evr_params* params
   b->n_work_pro = (int)pro.size();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  for (auto& q : b->side)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = host_alloc((void**)&b->h_sc, sizeof(DevScalars) * n);
   if (e == cudaSuccess) e = host_alloc((void**)&b->h_curs, sizeof(int) * n);
   b->stream = b->own_stream;
@@ -366,8 +495,28 @@ void evr_batch_destroy(evr_batch* b) {
   if (b->h_curs) cudaFreeHost(b->h_curs);
   if (b->own_stream) cudaStreamDestroy(b->own_stream);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (auto& q : b->side)
+    if (q) {
+      cudaStreamSynchronize(q);
+      cudaStreamDestroy(q);
+    }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   if (b->dev) cudaFree(b->dev);
   delete b;
+}
+
+int evr_batch_set_grouping(evr_batch* b, long long budget_bytes, int branches) {
+  if (!b || branches < 1 || branches > evr_batch::kMaxBranches) return EVR_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return EVR_ERR_CUDA;
+  b->group_auto = budget_bytes < 0;
+  b->group_tuned = false;
+  b->group_budget = budget_bytes > 0 ? budget_bytes : 0;
+  b->branches = budget_bytes < 0 ? 1 : branches;
+  if (b->cfg >= 0 && !b->tile_off.empty()) build_groups(b);
+  drop_graphs(b);
+  set_name(b);
+  return EVR_OK;
 }
 
 int evr_batch_set_cuda_stream(evr_batch* b, void* cuda_stream) {
@@ -390,8 +539,8 @@ int evr_batch_step_device(evr_batch* b, const uint16_t* x, const uint16_t* y,
   if (launch_push_batch(b->d_descs, b->n, x, y, (const long long*)t_us, pol,
                         (const long long*)offsets, b->d_active, st))
     return EVR_ERR_CUDA;
-  if (iters > 0 && !b->tuned) {
-    autotune(b, iters);
+  if (iters > 0 && (!b->tuned || (b->group_auto && !b->group_tuned))) {
+    autotune(b, iters, !b->tuned);
     drop_graphs(b);  // the tile work list may have moved
     b->tuned = true;
     set_name(b);
@@ -418,8 +567,9 @@ int evr_batch_step_device(evr_batch* b, const uint16_t* x, const uint16_t* y,
   if (b->timing) {
     cudaEventRecord(ev.second, st);
     b->ev_used.push_back(ev);
-    const int R = kSolverCfgs[b->cfg].R;
-    b->ev_launches.push_back(iters > 0 ? (iters + R - 1) / R : 0);
+    const int R = kSolverCfgs[b->cfg].R, groups = (int)b->groups.size();
+    // every launch of the graph: per group the prologue and the passes; the flip
+    b->ev_launches.push_back(iters > 0 ? groups * (1 + (iters + R - 1) / R) + 1 : groups);
     b->ev_pixiters.push_back(b->px_total * iters);  // upper bound: every stream active
   }
   return EVR_OK;

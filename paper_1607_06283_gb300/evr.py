@@ -112,6 +112,7 @@ def _load():
         "evr_batch_wait_images": ([vp, ctypes.c_uint64], i),
         "evr_batch_destroy": ([vp], None),
         "evr_batch_set_cuda_stream": ([vp, vp], i),
+        "evr_batch_set_grouping": ([vp, ctypes.c_longlong, i], i),
         "evr_batch_step_device": ([vp] * 6 + [i], i),
         "evr_batch_step": ([vp] * 6 + [i], i),
         "evr_batch_get_image": ([vp, i, vp, sz], i),
@@ -479,6 +480,12 @@ class Batch:
     def set_cuda_stream(self, handle) -> None:
         arg = handle if isinstance(handle, ctypes.c_void_p) else ctypes.c_void_p(int(handle))
         _check(_lib.evr_batch_set_cuda_stream(self.h, arg), "evr_batch_set_cuda_stream")
+
+    def set_grouping(self, budget_bytes: int, branches: int = 1) -> None:
+        """L2 grouping of a step's work: budget_bytes of pass working set per group
+        (0: one group, < 0: autotuned), one to four graph branches."""
+        _check(_lib.evr_batch_set_grouping(self.h, int(budget_bytes), int(branches)),
+               "evr_batch_set_grouping")
 
     def step(self, x, y, t, pol, offsets, iters: int) -> None:
         """Host arrays: all streams' events concatenated; offsets (n+1) int64."""

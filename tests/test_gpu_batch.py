@@ -42,8 +42,10 @@ def streams():
     return out
 
 
-def run_batch(E, streams, tile, steps, iters=30):
+def run_batch(E, streams, tile, steps, iters=30, grouping=None):
     b = E.Batch(SIZES, tile_config=tile)
+    if grouping is not None:
+        b.set_grouping(*grouping)
     for k in range(steps):
         x, y, t, p, off = batch_step_arrays(streams, 300, k)
         b.step(x, y, t, p, off, iters)
@@ -75,6 +77,36 @@ def test_batch_equals_solo_bit_for_bit(E, streams, tile):
             np.testing.assert_array_equal(b.state(s, w), g.state(w), err_msg=f"stream {s} {w}")
         assert int(b.state(s, E.EVR_STATE_CLOCK)) == int(g.state(E.EVR_STATE_CLOCK))
         g.close()
+    b.close()
+
+
+@pytest.mark.parametrize("budget,branches", [(1 << 20, 1), (1 << 20, 2), (3 << 20, 2),
+                                             (1 << 20, 4)])
+def test_l2_groups_equal_one_group_bit_for_bit(E, streams, budget, branches):
+    """Streams cut into groups of at most `budget` bytes of pass working set (the 240 x 180
+    stream, 2.4 MB, a group of its own), each group's prologue and passes run before the
+    next, on one to four graph branches: every stream's state equals the one-group run."""
+    steps = max(COUNTS)
+    ref = run_batch(E, streams, 6, steps, grouping=(0, 1))
+    b = run_batch(E, streams, 6, steps, grouping=(budget, branches))
+    assert "L2 groups" in b.solver_name and "L2 groups" not in ref.solver_name
+    for g in (ref, b):
+        rc, bad = g.synchronize()
+        assert rc == 0 and bad == -1
+    for s in range(len(SIZES)):
+        for w in (E.EVR_STATE_U, E.EVR_STATE_P1, E.EVR_STATE_P2, E.EVR_STATE_P3,
+                  E.EVR_STATE_F, E.EVR_STATE_TLAST):
+            np.testing.assert_array_equal(b.state(s, w), ref.state(s, w),
+                                          err_msg=f"stream {s} {w}")
+    ref.close()
+    b.close()
+
+
+def test_grouping_rejects_bad_branches(E):
+    b = E.Batch(SIZES[:3])
+    for br in (0, 5):
+        with pytest.raises(E.EvrError):
+            b.set_grouping(1 << 20, br)
     b.close()
 
 
