@@ -464,6 +464,17 @@ int evr_selftest_wait_timeout(evr_stream* s);
  * under a second.  Synchronises. */
 int evr_selftest_cluster_wait_timeout(evr_stream* s);
 
+/* Self-test of the resident solver's bounded grid-barrier wait (the paper has no
+ * counterpart): sets the barrier's arrival count far below any target, then runs two
+ * barrier intervals of a resident configuration (kind 5, at least two CTAs, one that fits
+ * the sensor): every CTA's first wait runs out, one sets the abort flag the others poll,
+ * the status records EVR_ERR_TIMEOUT and all CTAs return.  The state is saved first and
+ * restored afterwards and the barrier words are cleared, so the stream stays usable.
+ * Returns the status the device reported (EVR_ERR_TIMEOUT when detection works),
+ * EVR_ERR_NOT_SUPPORTED when no resident configuration fits the sensor.  Takes well under
+ * a second.  Synchronises. */
+int evr_selftest_resident_wait_timeout(evr_stream* s);
+
 /* Fault injection for tests (the paper has no counterpart): the n-th library
  * allocation of device or page-locked host memory after this call fails as if memory
  * were exhausted (the calls that make it then return EVR_ERR_OOM or EVR_ERR_CUDA and

@@ -218,7 +218,8 @@ void set_name(evr_stream* s) {
                     t.EH, c.R, 32 * t.NTY, solver_cfg_ctas(s->P, c));
     else
       std::snprintf(s->name, sizeof(s->name), "%s %dx%d R%d (%d threads, %d CTAs)",
-                    c.kind == 2 ? "persistent" : "tiled", t.EW, t.EH, c.R, 32 * t.NTY,
+                    c.kind == 2 ? "persistent" : c.kind == 5 ? "resident" : "tiled", t.EW,
+                    t.EH, c.R, 32 * t.NTY,
                     solver_cfg_ctas(s->P, c));
   }
 }
@@ -337,10 +338,12 @@ void drop_graphs(evr_stream* s) {
 // changes and after an aborted launch).
 int clear_flags(evr_stream* s) {
   s->flag_base = 0;
-  cudaError_t e = cudaMemsetAsync(s->P.flags, 0, sizeof(int) * kMaxCtas, s->stream);
+  cudaError_t e = cudaMemsetAsync(s->P.flags, 0, sizeof(int) * (kMaxCtas + 2), s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(&s->P.sc->abort, 0, sizeof(int), s->stream);
   return cuda_err(e);
 }
+
+int solve_passes(const SolverCfg& cfg, int iters);
 
 // The multi-launch iteration launches of one packet (unfused or kind 1):
 // `iters` iterations from buffer `cur`.  Returns the buffer holding the result.
@@ -361,6 +364,11 @@ int enqueue_iterations(evr_stream* s, int iters, int cur, cudaStream_t st, int* 
     *launches = 1;
     return 1 - cur;
   }
+  if (cfg.kind == 5) {  // resident: one cooperative launch
+    if (launch_resident(s->P, cfg, cur, iters, c, st, front, push)) return -1;
+    *launches = 1;
+    return cur ^ (solve_passes(cfg, iters) & 1);
+  }
   for (int done = 0, pass = 0; done < iters; done += cfg.R, ++pass) {
     int it = iters - done < cfg.R ? iters - done : cfg.R;
     const int e = cfg.kind == 3   ? launch_cluster(s->P, cfg, cur, it, pass, c, st, front, nullptr)
@@ -376,6 +384,11 @@ int enqueue_iterations(evr_stream* s, int iters, int cur, cudaStream_t st, int* 
 // Passes of one packet's solve with configuration cfg (kind 1 or 3).
 int solve_passes(const SolverCfg& cfg, int iters) {
   return (cfg.kind == 3 && cfg.R == 0) ? 1 : (iters + cfg.R - 1) / cfg.R;
+}
+
+// Kernel launches of one packet's solve (the front not counted).
+int solve_launches(const SolverCfg& cfg, int iters) {
+  return cfg.kind == 5 ? 1 : solve_passes(cfg, iters);
 }
 
 // Run one packet's iterations with configuration index `ci` (kind 1 or 2) directly
@@ -530,7 +543,7 @@ size_t state_bytes(int W, int H, bool solo) {
   size_t total = 16 * fb + lb + al256(sizeof(DevScalars));
   if (solo)
     total += al256(sizeof(double) * 3 * kGapBlocks) + al256(sizeof(double) * 2) +
-             al256(sizeof(int) * kMaxCtas);
+             al256(sizeof(int) * (kMaxCtas + 2));
   return total;
 }
 
@@ -572,7 +585,7 @@ char* carve_state(char* base, int W, int H, bool solo, Planes* out) {
   if (solo) {
     P.partials = (double*)take(al256(sizeof(double) * 3 * kGapBlocks));
     gap = take(al256(sizeof(double) * 2));
-    P.flags = (int*)take(al256(sizeof(int) * kMaxCtas));
+    P.flags = (int*)take(al256(sizeof(int) * (kMaxCtas + 2)));
   }
   *out = P;
   return solo ? gap : q;
@@ -819,15 +832,17 @@ bool front_fused(const evr_stream* s, int iters) {
   const SolverCfg& cfg = kSolverCfgs[s->cfg];
   if (s->prm.data_mode != 0 || (s->prm.tvl1_iters > 0 && s->prm.manifold)) return false;
   if (cfg.kind == 3) return cfg.R == 0 || (iters + cfg.R - 1) / cfg.R >= 2;
+  if (cfg.kind == 5) return s->P.storage == 0;
   if (cfg.kind != 1 || !tiled_front_fusable(cfg, s->P.storage)) return false;  // kind 4 too
   return (iters + cfg.R - 1) / cfg.R >= 2;
 }
 
 // Whether the packet's push runs inside the solver's one launch (one cluster over the
-// sensor, front fused, a packet the single-launch push takes).
+// sensor, or the resident solver; front fused, a packet the single-launch push takes).
 bool push_in_solver(const evr_stream* s, size_t n, int iters) {
   if (s->cfg < 0) return false;
   const SolverCfg& cfg = kSolverCfgs[s->cfg];
+  if (cfg.kind == 5) return n > 0 && n <= (size_t)kTiledPushMax && front_fused(s, iters);
   return cfg.kind == 3 && cfg.R == 0 && n > 0 && n <= 32768 && front_fused(s, iters);
 }
 }  // namespace
@@ -914,7 +929,7 @@ int evr_solve(evr_stream* s, int iters) {
       launches += 2 * iters;
     } else {
       const int passes = solve_passes(kSolverCfgs[s->cfg], iters);
-      launches += passes;
+      launches += solve_launches(kSolverCfgs[s->cfg], iters);
       end_cur = (passes % 2) ? 1 - s->cur : s->cur;
     }
     if (cudaGraphLaunch(exec, st) != cudaSuccess) return EVR_ERR_CUDA;
@@ -988,7 +1003,11 @@ int fused_step(evr_stream* s, int iters, int n, const uint16_t* x, const uint16_
     if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return EVR_ERR_CUDA;
     int r = 0;
-    if (in_solver) {
+    if (in_solver && kSolverCfgs[s->cfg].kind == 5) {
+      if (launch_resident(s->P, kSolverCfgs[s->cfg], s->cur, iters, solve_consts(s),
+                          s->cap_stream, &pc, &pa))
+        r = -1;
+    } else if (in_solver) {
       if (r == 0 && launch_cluster(s->P, kSolverCfgs[s->cfg], s->cur, iters, 0,
                                    solve_consts(s), s->cap_stream, &pc, &pa))
         r = -1;
@@ -1017,7 +1036,11 @@ int fused_step(evr_stream* s, int iters, int n, const uint16_t* x, const uint16_
     fg = &(s->fused[key] = nf);
   } else {
     fg = &it->second;
-    if (in_solver) {  // the cluster launch's arguments with this call's packet
+    if (in_solver && kSolverCfgs[s->cfg].kind == 5) {  // the resident launch's arguments
+      if (resident_node_set_push(fg->exec, fg->push, s->P, kSolverCfgs[s->cfg], s->cur, iters,
+                                 solve_consts(s), pc, pa))
+        return EVR_ERR_CUDA;
+    } else if (in_solver) {  // the cluster launch's arguments with this call's packet
       if (cluster_node_set_push(fg->exec, fg->push, s->P, kSolverCfgs[s->cfg], s->cur, iters,
                                 solve_consts(s), pc, pa))
         return EVR_ERR_CUDA;
@@ -1056,7 +1079,7 @@ int fused_step(evr_stream* s, int iters, int n, const uint16_t* x, const uint16_
     const int front =
         fuse ? 0 : 1 + ((s->prm.tvl1_iters > 0 && s->prm.manifold) ? 1 + 2 * s->prm.tvl1_iters : 0);
     s->ev_launches.push_back((in_solver || in_pass0 ? 0 : 1) + front +
-                             (s->cfg < 0 ? 2 * iters : passes));
+                             (s->cfg < 0 ? 2 * iters : solve_launches(kSolverCfgs[s->cfg], iters)));
     s->ev_pixiters.push_back((long long)s->W * s->H * iters);
   }
   if (s->cfg >= 0 && passes % 2) s->cur = 1 - s->cur;
@@ -1341,6 +1364,41 @@ int evr_selftest_wait_timeout(evr_stream* s) {
   cudaStreamSynchronize(s->stream);
   cudaFree(save);
   clear_flags(s);
+  s->cur = cur0;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return EVR_ERR_CUDA;
+  return rc;
+}
+
+int evr_selftest_resident_wait_timeout(evr_stream* s) {
+  if (!s) return EVR_ERR_INVALID_ARG;
+  int ci = -1;  // a resident configuration of at least two CTAs that fits the sensor
+  for (int k = 0; k < kNumSolverCfgs && ci < 0; ++k)
+    if (kSolverCfgs[k].kind == 5 && solver_cfg_usable(s->P, kSolverCfgs[k]) &&
+        solver_cfg_ctas(s->P, kSolverCfgs[k]) >= 2)
+      ci = k;
+  if (ci < 0) return EVR_ERR_NOT_SUPPORTED;
+  int rc = sync_status(s);  // report nothing stale as the test's result
+  if (rc != EVR_OK && rc != EVR_ERR_TIMEOUT) return rc;
+  const size_t plane = (size_t)s->pitch * s->H * sizeof(float);
+  float* save = nullptr;
+  if (dev_alloc((void**)&save, 4 * plane) != cudaSuccess) return EVR_ERR_OOM;
+  const int cur0 = s->cur;
+  float* live[4] = {s->P.u[cur0], s->P.p1[cur0], s->P.p2[cur0], s->P.p3[cur0]};
+  for (int k = 0; k < 4; ++k)
+    cudaMemcpyAsync((char*)save + k * plane, live[k], plane, cudaMemcpyDeviceToDevice, s->stream);
+  const SolverCfg& cfg = kSolverCfgs[ci];
+  // the barrier's arrival word starts far below any target (every byte 0x80: a large
+  // negative count), so the first barrier's wait runs out in every CTA
+  cudaError_t ce = cudaMemsetAsync(s->P.flags + kMaxCtas, 0x80, sizeof(int), s->stream);
+  int e = ce != cudaSuccess ? 1
+                            : launch_resident(s->P, cfg, cur0, 2 * cfg.R, solve_consts(s),
+                                              s->stream, nullptr, nullptr);
+  rc = e ? EVR_ERR_CUDA : sync_status(s);  // reads and clears the status and the flags
+  if (rc != EVR_ERR_TIMEOUT && clear_flags(s) != EVR_OK) rc = EVR_ERR_CUDA;
+  for (int k = 0; k < 4; ++k)
+    cudaMemcpyAsync(live[k], (char*)save + k * plane, plane, cudaMemcpyDeviceToDevice, s->stream);
+  cudaStreamSynchronize(s->stream);
+  cudaFree(save);
   s->cur = cur0;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return EVR_ERR_CUDA;
   return rc;

@@ -51,7 +51,8 @@ struct Planes {
   int* nneg;
   DevScalars* sc;
   double* partials;
-  int* flags;  // persistent solver: passes completed by each CTA (monotonic)
+  int* flags;  // persistent solver: passes completed by each CTA (monotonic), then the
+               // resident solver's barrier words (arrivals, leaves): kMaxCtas + 2 ints
   int storage; // format of the p planes: 0 FP32, 1 FP16, 2 BF16 (tiled solver only)
 };
 
@@ -63,6 +64,17 @@ struct BatchRef {
   const int* curs;      // per-stream buffer holding the current (u, p)
   const int* active;    // per-stream: 1 when the stream has a packet in this step
 };
+
+// Copy a stream's plane descriptor (a __grid_constant__ kernel parameter or an element of
+// a device array) into shared memory with the 32 lanes of one warp, word by word: the
+// copy by a single thread was a serial chain of loads (about 1 us on GB300) that every CTA
+// of every pass waited for at its first barrier.
+__device__ __forceinline__ void stage_planes(Planes* dst, const Planes* src, int lane) {
+  static_assert(sizeof(Planes) % 4 == 0, "the descriptor is copied in 4-byte words");
+  const unsigned* s = reinterpret_cast<const unsigned*>(src);
+  unsigned* d = reinterpret_cast<unsigned*>(dst);
+  for (int i = lane; i < (int)(sizeof(Planes) / 4); i += 32) d[i] = s[i];
+}
 
 struct SolveConsts {
   float tau, sigma, lambda, u_min, u_max;
@@ -132,7 +144,7 @@ struct SolverCfg {
 };
 constexpr int kNumTileShapes = 8;
 extern const TileShape kTileShapes[kNumTileShapes];
-constexpr int kNumSolverCfgs = 70;
+constexpr int kNumSolverCfgs = 80;
 extern const SolverCfg kSolverCfgs[kNumSolverCfgs];
 
 constexpr int kGapBlocks = 304;   // fixed: the reduction order does not depend on W, H
@@ -211,6 +223,21 @@ int launch_tiled_pass_batch(const BatchRef& B, int n_work, const SolverCfg& cfg,
 // its neighbours' bounded waits run out and the launch ends with EVR_ERR_TIMEOUT.
 int launch_persistent(const Planes& P, const SolverCfg& cfg, int cur, int iters, int base,
                       const SolveConsts& c, void* stream, int silent_cta = -1);
+// kind 5: one cooperative launch of all `iters` iterations from buffer cur; the result
+// lands in buffer cur ^ (ceil(iters / R) & 1).  front != NULL: the packet's front is
+// computed in the launch and the event counts are cleared (data_mode 0, no TV-L1 plane);
+// push != NULL as well: the launch first validates and integrates the packet (n <=
+// kTiledPushMax) and commits the stream clock.  FP32 storage; needs the solo state's
+// flags (two barrier words after kMaxCtas progress flags).  Returns
+// cudaErrorCooperativeLaunchTooLarge when the grid cannot be co-resident.
+int launch_resident(const Planes& P, const SolverCfg& cfg, int cur, int iters,
+                    const SolveConsts& c, void* stream, const PrologueConsts* front,
+                    const PushArgs* push);
+// Updates the kernel node of an instantiated graph, captured by launch_resident with a
+// push, to push the packet `push` instead (all other arguments as captured).
+int resident_node_set_push(void* graph_exec, void* node, const Planes& P, const SolverCfg& cfg,
+                           int cur, int iters, const SolveConsts& c, const PrologueConsts& front,
+                           const PushArgs& push);
 // kind 3 (evr_cluster.cu): `iters` iterations from buffer src into 1 - src, at most R per
 // launch (R = 0: all of them).  front != NULL: the packet's front is fused (R = 0: the
 // one launch computes the prologue's constants and clears the event counts; R > 0: as

@@ -251,8 +251,8 @@ __device__ __forceinline__ void prologue_px_body(const Planes& P, int cur, const
 // f = base * exp(Delta+ n+ - Delta- n-) (Eq. intensity_update, one factor per event);
 // the counts are then cleared.  One kernel serves a single stream (B.descs null,
 // blocks numbered over its image) and a batch (one work item per CTA).
-__global__ void __launch_bounds__(256) k_prologue(Planes P, int cur, PrologueConsts c,
-                                                  BatchRef B) {
+__global__ void __launch_bounds__(256) k_prologue(const __grid_constant__ Planes P, int cur,
+                                                  PrologueConsts c, BatchRef B) {
   // Launched as a programmatic dependent of the push (in the fused push-and-solve
   // graph): wait for its completion before reading the pixel state (a no-op when
   // launched without that relation).  The first iteration pass may launch now; it
@@ -267,9 +267,9 @@ __global__ void __launch_bounds__(256) k_prologue(Planes P, int cur, PrologueCon
     if (!B.active[w.x]) return;
     cur = B.curs[w.x];
     blk = w.y;
-    if (threadIdx.x == 0 && threadIdx.y == 0) sP = B.descs[w.x];
-  } else if (threadIdx.x == 0 && threadIdx.y == 0) {
-    sP = P;
+    if (threadIdx.y == 0) stage_planes(&sP, &B.descs[w.x], threadIdx.x);
+  } else if (threadIdx.y == 0) {
+    stage_planes(&sP, &P, threadIdx.x);
   }
   __syncthreads();
   prologue_px_body(sP, cur, c, blk);

@@ -14,7 +14,11 @@
 //     CTAs' bands through L2, synchronised by per-CTA progress flags.  Every wait is
 //     bounded; a wait that runs out sets an abort flag and EVR_ERR_TIMEOUT and the
 //     kernel returns.
+//   kind 5 (k_resident): as kind 2 with the exchange behind one grid-wide barrier (an
+//     arrival counter), the packet's front -- and its push -- at the start of the same
+//     launch, and the launch captured in the packet's graph: one launch per packet.
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -59,6 +63,9 @@ const SolverCfg kSolverCfgs[kNumSolverCfgs] = {
     {3, 1, 6, 2, 4}, {3, 7, 8, 4, 2}, {3, 6, 6, 4, 2},
     // kind 4: persistent passes with tensor-copy staging of each tile
     {4, 1, 4}, {4, 1, 6}, {4, 1, 8}, {4, 0, 4}, {4, 0, 6}, {4, 6, 4}, {4, 6, 5}, {4, 6, 6},
+    // kind 5: one resident cooperative launch per packet, grid barrier every R iterations
+    {5, 7, 6}, {5, 7, 8}, {5, 7, 9}, {5, 7, 10}, {5, 1, 4}, {5, 1, 6}, {5, 1, 8}, {5, 0, 4},
+    {5, 0, 6}, {5, 6, 5},
 };
 
 // ---------------------------------------------------------------- kind 1
@@ -157,7 +164,8 @@ __device__ __forceinline__ void push_front(TT& T, const Planes& P, const SolveCo
 
 template <int KX, int KY, int NTY, typename ST, int MODE>
 __global__ void __launch_bounds__(32 * NTY, (MODE == 2 ? 2 : kTiledMinBlocks<KX, KY, NTY, ST>))
-    k_tiled(Planes P, int src, int iters, int R, SolveConsts c, int tiles_x, BatchRef B,
+    k_tiled(const __grid_constant__ Planes P, int src, int iters, int R, SolveConsts c,
+            int tiles_x, BatchRef B,
             int pass, PrologueConsts pc, float* tape, long long tape_plane, int tape_first,
             PushArgs ev) {
   constexpr bool FRONT = MODE == 1 || MODE == 3;
@@ -169,9 +177,9 @@ __global__ void __launch_bounds__(32 * NTY, (MODE == 2 ? 2 : kTiledMinBlocks<KX,
     if (!B.active[w.x]) return;
     src = B.curs[w.x] ^ (pass & 1);
     tile = w.y;
-    if (threadIdx.x == 0 && threadIdx.y == 0) sP = B.descs[w.x];
-  } else if (threadIdx.x == 0 && threadIdx.y == 0) {
-    sP = P;
+    if (threadIdx.y == 0) stage_planes(&sP, &B.descs[w.x], threadIdx.x);
+  } else if (threadIdx.y == 0) {
+    stage_planes(&sP, &P, threadIdx.x);
   }
   __syncthreads();
   if (B.descs) tiles_x = (sP.W + (32 * KX - 2 * R) - 1) / (32 * KX - 2 * R);
@@ -314,6 +322,115 @@ __global__ void __launch_bounds__(32 * NTY) k_persist(Planes P, int cur, int ite
     __syncthreads();
     if (s_bail) return;
     T.reload_halo(P, buf);
+  }
+}
+
+// ---------------------------------------------------------------- kind 5
+// Grid-wide barrier of a cooperative launch: the CTA's earlier global writes (issued
+// before the call by any of its threads) are visible to every CTA after it.  `arrive`
+// counts arrivals from 0 within the launch; the j-th barrier (j = 1, 2, ...) waits for
+// j * ctas of them.  The wait is bounded: it gives up when the stream's abort flag is set
+// or after kSpinLimit polls (then it sets the flag and EVR_ERR_TIMEOUT).  Returns false
+// (in every thread of the CTA) if it gave up.
+__device__ __forceinline__ bool grid_barrier(int* arrive, int target, DevScalars* sc, int tid,
+                                             int* s_bail) {
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(arrive), "r"(1) : "memory");
+    bool ok = true;
+    unsigned n = 0;
+    while (ld_acquire(arrive) < target) {
+      if ((++n & 31) == 0 && (*(volatile int*)&sc->abort || n > kSpinLimit)) {
+        ok = false;
+        break;
+      }
+    }
+    if (!ok) {
+      atomicExch(&sc->abort, 1);
+      atomicCAS(&sc->status, 0, kErrTimeout);
+    }
+    *s_bail = ok ? 0 : 1;
+  }
+  __syncthreads();
+  return *s_bail == 0;
+}
+
+// One packet's solve in one cooperative launch of one CTA per tile (all resident).
+// FM (the front): 0 -- the packet constants come from the planes (the prologue ran
+// before); 1 -- computed here as the prologue computes them; 3 -- as 1 after validating
+// and integrating the packet `ev` here (the same code as pass 0 of the push-fused
+// passes: every CTA scans the packet into shared-memory maps of its extended tile).
+// Then `iters` iterations from buffer `cur`: after every R of them (and after the first R
+// only if FM > 0 and they are all) the CTA writes its band into buffer cur ^ (j + 1 & 1),
+// passes a grid barrier and reads its halo back; after the first barrier the owned event
+// counts are cleared and CTA 0 commits the packet's stream clock (FM 3).  The last pass
+// writes every owned pixel into buffer cur ^ (passes & 1).  The barrier words live after
+// the persistent solver's flags: an arrival count and a leave count; the last CTA to
+// leave resets both, so every launch starts from 0.  One-pair tiles take the
+// multi-launch tile's register budget (64: several CTAs per SM where the block size
+// allows them); two-pair tiles, whose front needs more, are not capped.
+template <int KX, int KY, int NTY>
+constexpr int kResidentMinBlocks = KX * KY == 2 ? kTiledMinBlocks<KX, KY, NTY, float> : 1;
+
+template <int KX, int KY, int NTY, int FM>
+__global__ void __launch_bounds__(32 * NTY, (kResidentMinBlocks<KX, KY, NTY>))
+    k_resident(const __grid_constant__ Planes P, int cur, int iters, int R, SolveConsts c,
+               int tiles_x, int tiles_y, PrologueConsts pc, PushArgs ev) {
+  using TT = Tile<KX, KY, NTY>;
+  __shared__ TileSmem<KX, KY, NTY> sm;
+  __shared__ Planes sP;
+  __shared__ int s_bail;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int nct = tiles_x * tiles_y;
+  if (threadIdx.y == 0) stage_planes(&sP, &P, threadIdx.x);
+  if (tid == 0) s_bail = 0;
+  __syncthreads();
+  TT T;
+  T.setup(blockIdx.x, tiles_x, R);
+  TT::zero_pads(sm);
+  if constexpr (FM == 3) {
+    T.load_state(sP, cur);  // the front takes f from the current u
+    push_front(T, sP, c, pc, ev);
+  } else if constexpr (FM == 1) {
+    T.load_state(sP, cur);
+    T.front_consts(sP, c, pc);
+  } else {
+    T.load_consts(sP, c);
+    T.load_state(sP, cur);
+  }
+  int* arrive = sP.flags + kMaxCtas;
+  int* leave = arrive + 1;
+  const int passes = (iters + R - 1) / R;
+  bool settled = FM == 0;  // event counts cleared and clock committed
+  int bars = 0;
+  for (int j = 0; j < passes; ++j) {
+    const int r = min(R, iters - j * R);
+    if (c.data_term)
+      for (int it = 0; it < r; ++it) T.template iterate<true>(sm, c);
+    else
+      for (int it = 0; it < r; ++it) T.template iterate<false>(sm, c);
+    const int buf = cur ^ ((j + 1) & 1);
+    const bool last = j == passes - 1;
+    T.store(sP, buf, !last);
+    if (last && settled) break;
+    if (!grid_barrier(arrive, ++bars * nct, sP.sc, tid, &s_bail)) return;
+    if (!settled) {  // every CTA's front has read the counts and the clock
+      T.clear_counts(sP);
+      if (blockIdx.x == 0 && tid == 0 && sP.sc->commit_pending) {
+        sP.sc->clock = sP.sc->clock_next;
+        sP.sc->t_init = sP.sc->t_init_next;
+        sP.sc->t_init_set = 1;
+        sP.sc->commit_pending = 0;
+      }
+      settled = true;
+    }
+    if (last) break;
+    T.reload_halo(sP, buf);
+  }
+  if (tid == 0 && atomicAdd(leave, 1) == nct - 1) {  // every CTA has left every barrier
+    *arrive = 0;
+    *leave = 0;
   }
 }
 
@@ -504,6 +621,97 @@ static int run_persist(const Planes& P, int R, int cur, int iters, int base, int
                                           dim3(32, NTY), args, 0, st);
 }
 
+template <int KX, int KY, int NTY, int FM>
+static int resident_per_sm() {
+  static int per = -1;
+  if (per < 0) {
+    const size_t dyn = FM == 3 ? tiled_push_smem<KX, KY, NTY>() : 0;
+    if (FM == 3 && cudaFuncSetAttribute((const void*)k_resident<KX, KY, NTY, 3>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)dyn) != cudaSuccess) {
+      cudaGetLastError();
+      return per = 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_resident<KX, KY, NTY, FM>, 32 * NTY,
+                                                      dyn) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    per = n;
+  }
+  return per;
+}
+
+// Whether all tiles of the resident solver are co-resident (in every front form).
+template <int KX, int KY, int NTY>
+static bool resident_fits(const Planes& P, int R, int* nctas) {
+  int tx, ty;
+  if (!P.flags || P.storage != 0 || !tiles_of<KX, KY, NTY>(P, R, &tx, &ty)) return false;
+  *nctas = tx * ty;
+  if (tx * ty > kMaxCtas) return false;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  const int per = std::min(resident_per_sm<KX, KY, NTY, 0>(),
+                           std::min(resident_per_sm<KX, KY, NTY, 1>(),
+                                    resident_per_sm<KX, KY, NTY, 3>()));
+  return tx * ty <= sms * per;
+}
+
+template <int KX, int KY, int NTY>
+static int run_resident(const Planes& P, int R, int cur, int iters, const SolveConsts& c,
+                        cudaStream_t st, const PrologueConsts* front, const PushArgs* push) {
+  int tx, ty, n;
+  if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters < 1) return (int)cudaErrorInvalidValue;
+  if (!resident_fits<KX, KY, NTY>(P, R, &n)) return (int)cudaErrorCooperativeLaunchTooLarge;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(tx * ty);
+  lc.blockDim = dim3(32, NTY);
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  const PushArgs none{nullptr, nullptr, nullptr, nullptr, 0};
+  if (front && push) {
+    if (push->n < 0 || push->n > kTiledPushMax) return (int)cudaErrorInvalidValue;
+    lc.dynamicSmemBytes = tiled_push_smem<KX, KY, NTY>();
+    return (int)cudaLaunchKernelEx(&lc, k_resident<KX, KY, NTY, 3>, P, cur, iters, R, c, tx, ty,
+                                   *front, *push);
+  }
+  if (front)
+    return (int)cudaLaunchKernelEx(&lc, k_resident<KX, KY, NTY, 1>, P, cur, iters, R, c, tx, ty,
+                                   *front, none);
+  return (int)cudaLaunchKernelEx(&lc, k_resident<KX, KY, NTY, 0>, P, cur, iters, R, c, tx, ty,
+                                 PrologueConsts{}, none);
+}
+
+// The resident launch node of a captured push-fused graph, given the next packet.
+template <int KX, int KY, int NTY>
+static int set_resident_push_node(cudaGraphExec_t exec, cudaGraphNode_t node, const Planes& P,
+                                  int R, int cur, int iters, const SolveConsts& c,
+                                  const PrologueConsts& front, const PushArgs& push) {
+  int tx, ty;
+  if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters < 1 || push.n < 0 ||
+      push.n > kTiledPushMax)
+    return (int)cudaErrorInvalidValue;
+  Planes Pc = P;
+  SolveConsts cc = c;
+  PrologueConsts pc = front;
+  PushArgs ev = push;
+  int curv = cur, itv = iters, Rv = R, txv = tx, tyv = ty;
+  void* args[] = {&Pc, &curv, &itv, &Rv, &cc, &txv, &tyv, &pc, &ev};
+  cudaKernelNodeParams kp;
+  cudaError_t e = cudaGraphKernelNodeGetParams(node, &kp);
+  if (e != cudaSuccess) return (int)e;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  return (int)cudaGraphExecKernelNodeSetParams(exec, node, &kp);
+}
+
 #define EVR_SHAPE_DISPATCH(FN, ...)                                  \
   switch (cfg.shape) {                                               \
     case 0: return FN<1, 4, 8>(__VA_ARGS__);                         \
@@ -590,6 +798,25 @@ int tiled_front_fusable(const SolverCfg& cfg, int storage) {
   }
 }
 
+int launch_resident(const Planes& P, const SolverCfg& cfg, int cur, int iters,
+                    const SolveConsts& c, void* stream, const PrologueConsts* front,
+                    const PushArgs* push) {
+  if (cfg.kind != 5) return (int)cudaErrorInvalidValue;
+  cudaStream_t st = (cudaStream_t)stream;
+  EVR_SHAPE_DISPATCH(run_resident, P, cfg.R, cur, iters, c, st, front, push)
+  return (int)cudaErrorInvalidValue;
+}
+
+int resident_node_set_push(void* graph_exec, void* node, const Planes& P, const SolverCfg& cfg,
+                           int cur, int iters, const SolveConsts& c, const PrologueConsts& front,
+                           const PushArgs& push) {
+  if (cfg.kind != 5) return (int)cudaErrorInvalidValue;
+  cudaGraphExec_t ex = (cudaGraphExec_t)graph_exec;
+  cudaGraphNode_t nd = (cudaGraphNode_t)node;
+  EVR_SHAPE_DISPATCH(set_resident_push_node, ex, nd, P, cfg.R, cur, iters, c, front, push)
+  return (int)cudaErrorInvalidValue;
+}
+
 int launch_persistent(const Planes& P, const SolverCfg& cfg, int cur, int iters, int base,
                       const SolveConsts& c, void* stream, int silent_cta) {
   cudaStream_t st = (cudaStream_t)stream;
@@ -602,6 +829,7 @@ static bool usable(const Planes& P, const SolverCfg& cfg) {
   int tx, ty, n;
   if (cfg.kind == 1) return tiles_of<KX, KY, NTY>(P, cfg.R, &tx, &ty) != 0;
   if (cfg.kind == 2) return persist_fits<KX, KY, NTY>(P, cfg.R, &n);
+  if (cfg.kind == 5) return resident_fits<KX, KY, NTY>(P, cfg.R, &n);
   return false;
 }
 

@@ -94,6 +94,7 @@ def _load():
         "evr_solver_settled": ([vp], i),
         "evr_selftest_wait_timeout": ([vp], i),
         "evr_selftest_cluster_wait_timeout": ([vp], i),
+        "evr_selftest_resident_wait_timeout": ([vp], i),
         "evr_strerror": ([i], ctypes.c_char_p),
         "evr_test_fail_alloc_after": ([i], i),
         "evr_measure_peak": ([i, vp, vp], i),

@@ -74,7 +74,7 @@ def test_ptxas_reports_no_spills_in_the_iteration_kernels(evr):
     for b in blocks[1:]:
         name = b.split("'")[1]
         if any(k in name for k in ("k_tiled", "k_prologue", "k_push", "k_rev_tiled",
-                                   "k_cluster", "k_staged")):
+                                   "k_cluster", "k_staged", "k_resident")):
             seen += 1
             spill = int(re.search(r"(\d+) bytes spill stores", b).group(1))
             limit = max([v for k, v in allowed.items() if k in name], default=0)

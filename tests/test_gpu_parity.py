@@ -38,7 +38,7 @@ def oracle_params(p, **kw):
         tvl1_iters=int(p.tvl1_iters), tvl1_lambda=float(np.float32(p.tvl1_lambda)), **kw)
 
 
-N_CFGS = 70  # solver configurations selectable with evr_params.tile_config = 1..N_CFGS
+N_CFGS = 80  # solver configurations selectable with evr_params.tile_config = 1..N_CFGS
 SOLVERS = [("unfused", 1, 0)] + [(f"cfg{k}", 2, k) for k in range(1, N_CFGS + 1)]
 # tile_config of the cluster solver: one 4 x 4 cluster of 32 x 32 tiles over a sensor of
 # up to 128 x 128 (one launch per packet), and 2 x 2 clusters as super-tiles with a
@@ -49,6 +49,10 @@ CLUSTER_SUPER = 59
 # halo (512 threads) and 32 x 48 tiles with a 5-pixel halo (384 threads)
 STAGED_32 = 63
 STAGED_48 = 69
+# tile_config of the resident solver (one cooperative launch per packet, grid barrier
+# every R iterations): 32 x 64 tiles with a 9-pixel halo, 32 x 32 tiles with 6
+RESIDENT_64 = 73
+RESIDENT_32 = 76
 
 
 def make_pair(E, W, H, solver=2, tile=0, **over):
@@ -198,7 +202,8 @@ def test_free_running_drift_rects128(E, rects128):
 @pytest.mark.parametrize("name,solver,tile", [SOLVERS[0], SOLVERS[1], SOLVERS[11], SOLVERS[20],
                                               SOLVERS[24], SOLVERS[CLUSTER_ONE],
                                               SOLVERS[CLUSTER_SUPER], SOLVERS[STAGED_32],
-                                              SOLVERS[STAGED_48]])
+                                              SOLVERS[STAGED_48], SOLVERS[RESIDENT_64],
+                                              SOLVERS[RESIDENT_32]])
 def test_ragged_sizes(E, W, H, name, solver, tile):
     rng = np.random.default_rng(W * 1000 + H)
     g, o = make_pair(E, W, H, solver=solver, tile=tile)

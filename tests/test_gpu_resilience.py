@@ -121,6 +121,36 @@ def test_cluster_wait_timeout_is_detected_and_the_stream_recovers(E, tile):
     np.testing.assert_array_equal(a.image(), twin.image())
 
 
+# tile_config 73: the resident solver, 32 x 64 tiles with a 9-pixel halo (evr_params)
+@pytest.mark.parametrize("tile", [0, 73])
+def test_resident_wait_timeout_is_detected_and_the_stream_recovers(E, tile):
+    """The resident solver's grid barrier never completes (its arrival count starts far
+    below the target): every CTA's bounded wait runs out, the launch reports
+    EVR_ERR_TIMEOUT, and the stream (state restored, barrier words cleared) goes on
+    bit-identically to a twin that never ran the test."""
+    W, H = 100, 60
+    pk = packets(4, W, H, 6, 500)
+    a = E.Stream(W, H, solver=2, tile_config=tile)
+    twin = E.Stream(W, H, solver=2, tile_config=tile)
+    for g in (a, twin):
+        for x, y, t, p in pk[:3]:
+            assert g.push(x, y, t, p) == 0
+            g.solve(20)
+    t0 = time.perf_counter()
+    rc = E._lib.evr_selftest_resident_wait_timeout(a.h)
+    dt = time.perf_counter() - t0
+    assert rc == E.EVR_ERR_TIMEOUT, rc
+    assert dt < 10.0
+    assert a.synchronize() == 0  # reported once
+    np.testing.assert_array_equal(a.image(), twin.image())  # state restored
+    for g in (a, twin):
+        for x, y, t, p in pk[3:]:
+            assert g.push(x, y, t, p) == 0
+            g.solve(20)
+    assert a.synchronize() == 0
+    np.testing.assert_array_equal(a.image(), twin.image())
+
+
 def _free_bytes():
     import torch
     torch.cuda.synchronize()

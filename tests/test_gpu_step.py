@@ -37,9 +37,11 @@ def dev(torch, pk):
             for a in (x, y, t, p)]
 
 
-# tile_config 55: clusters of 4 x 4 32 x 32 tiles as super-tiles with a 6-pixel halo
+# tile_config 55: clusters of 4 x 4 32 x 32 tiles as super-tiles with a 6-pixel halo;
+# 73: the resident solver (one cooperative launch, the push inside it)
 @pytest.mark.parametrize("over", [{}, dict(tile_config=45), dict(solver=1),
-                                  dict(tvl1_iters=3), dict(tile_config=55)])
+                                  dict(tvl1_iters=3), dict(tile_config=55),
+                                  dict(tile_config=73), dict(tile_config=73, data_mode=1)])
 def test_step_equals_push_then_solve(T, over):
     torch, E = T
     W, H = 150, 97
@@ -58,8 +60,9 @@ def test_step_equals_push_then_solve(T, over):
         assert a.solver_name == b.solver_name  # the results do not depend on it
 
 
-# tile_config 47: one 4 x 4 cluster over the sensor, the push inside its single launch
-@pytest.mark.parametrize("tile", [45, 47])
+# tile_config 47: one 4 x 4 cluster over the sensor, the push inside its single launch;
+# 73: the resident solver
+@pytest.mark.parametrize("tile", [45, 47, 73])
 def test_step_with_empty_and_large_packets_and_a_rejection(T, tile):
     torch, E = T
     W, H = 64, 40
@@ -82,9 +85,13 @@ def test_step_with_empty_and_large_packets_and_a_rejection(T, tile):
     assert int(a.state(E.EVR_STATE_CLOCK)) == int(b.state(E.EVR_STATE_CLOCK))
 
 
-@pytest.mark.parametrize("over", [{}, dict(tile_config=45), dict(tile_config=47),
-                                  dict(tile_config=47, data_term=1)])
-def test_host_step_equals_push_then_solve(T, over):
+@pytest.mark.parametrize("over,iters", [({}, 25), (dict(tile_config=45), 25),
+                                        (dict(tile_config=47), 25),
+                                        (dict(tile_config=47, data_term=1), 25),
+                                        (dict(tile_config=73), 25), (dict(tile_config=73), 7),
+                                        (dict(tile_config=76, data_term=1), 25),
+                                        (dict(tile_config=78), 8)])
+def test_host_step_equals_push_then_solve(T, over, iters):
     """evr_step (host arrays, copied on the copy stream ahead of the packet's graph) against
     evr_push_events + evr_solve; the host-side checks reject a bad packet before anything
     is queued."""
@@ -93,13 +100,13 @@ def test_host_step_equals_push_then_solve(T, over):
     pk = packets(4, W, H, 12, 900)
     a, b = E.Stream(W, H, **over), E.Stream(W, H, **over)
     for k, (x, y, t, p) in enumerate(pk):
-        assert E.evr_step(a.h, x, y, t, p, 25) == 0
+        assert E.evr_step(a.h, x, y, t, p, iters) == 0
         assert b.push(x, y, t, p) == 0
-        b.solve(25)
+        b.solve(iters)
         if k in (0, 6, 11):
             np.testing.assert_array_equal(a.image(), b.image(), err_msg=f"packet {k}")
     x, y, t, p = packets(5, W, H, 1, 50)[0]
     x = x.copy()
     x[3] = W
-    assert E.evr_step(a.h, x, y, t + pk[-1][2][-1], p, 25) == E.EVR_ERR_OUT_OF_RANGE
+    assert E.evr_step(a.h, x, y, t + pk[-1][2][-1], p, iters) == E.EVR_ERR_OUT_OF_RANGE
     np.testing.assert_array_equal(a.image(), b.image())
