@@ -101,10 +101,11 @@ constexpr bool kTiledFront = kTiledMinBlocks<KX, KY, NTY, ST> == 1 || KX * KY ==
 // itself.  Every CTA validates the whole packet (the same verdict everywhere; the
 // stream's clock is read, never written, in pass 0), merges the events that fall into
 // its extended tile plus one column and row into shared-memory maps (dynamic shared
-// memory), forms the packet constants from the planes and the maps, and writes back its
-// owned pixels' t_last (a pixel read as halo by another CTA gives that CTA the same
-// value before or after the write: t_last only grows by the maximum).  CTA 0 records the
-// packet's clock for pass 1, which commits it.
+// memory) that start from the planes' t_last, forms the packet constants from the maps
+// and the planes' counts, and writes back the t_last of its owned pixels that events hit
+// (a pixel read as halo by another CTA gives that CTA the same value before or after the
+// write: t_last only grows by the maximum).  CTA 0 records the packet's clock for pass 1,
+// which commits it.
 template <int KX, int KY, int NTY>
 constexpr size_t tiled_push_smem() {
   return (size_t)(32 * KX + 1) * (NTY * KY + 1) * (sizeof(long long) + sizeof(int));
@@ -120,34 +121,58 @@ __device__ __forceinline__ void push_front(TT& T, const Planes& P, const SolveCo
   int* mc = reinterpret_cast<int*>(mt + MW * MH);
   __shared__ int s_bad;
   const int tid = threadIdx.y * 32 + threadIdx.x;
+  // Every global read the front needs that does not depend on the packet's verdict, in
+  // one round: the stream's clock, this thread's first event (and the timestamp before
+  // it), the packet's first and last timestamps, the counts of the thread's pixels, and
+  // the t_last of the map's pixels (the map starts from them, so the merged surface
+  // needs no second read).
+  const bool mine = tid < ev.n;
+  int x0 = 0, y0 = 0, p0 = 1;
+  long long t0 = 0, tp0 = 0;
+  if (mine) {
+    x0 = ev.x[tid];
+    y0 = ev.y[tid];
+    t0 = ev.t[tid];
+    p0 = ev.pol[tid];
+    if (tid > 0) tp0 = ev.t[tid - 1];
+  }
   const long long clock0 = P.sc->clock;
   const int have = P.sc->t_init_set;
   const long long t_init0 = P.sc->t_init;
+  const long long t_first = ev.n > 0 ? ev.t[0] : 0, t_end = ev.n > 0 ? ev.t[ev.n - 1] : 0;
+  int np[TT::K], nn[TT::K];
+  T.load_counts(P, np, nn);
   if (tid == 0) s_bad = ev.n;
   for (int m = tid; m < MW * MH; m += NT) {
-    mt[m] = kNeverFired;
+    const int gx = T.gx0 + m % MW, gy = T.gy0 + m / MW;
+    mt[m] = (gx >= 0 && gx < P.W && gy >= 0 && gy < P.H) ? P.t_last[(size_t)gy * P.pitch + gx]
+                                                          : kNeverFired;
     mc[m] = 0;
   }
   __syncthreads();
-  for (int i = tid; i < ev.n; i += NT)
+  if (mine && event_code_of(x0, y0, t0, tp0, p0, tid == 0, P.W, P.H, clock0, have) != 0)
+    atomicMin(&s_bad, tid);
+  for (int i = tid + NT; i < ev.n; i += NT)
     if (event_code(ev.x, ev.y, ev.t, ev.pol, i, P.W, P.H, clock0, have) != 0)
       atomicMin(&s_bad, i);
   __syncthreads();
   const bool valid = s_bad >= ev.n;
   if (valid) {
-    for (int i = tid; i < ev.n; i += NT) {
-      const int lx = (int)ev.x[i] - T.gx0, ly = (int)ev.y[i] - T.gy0;
+    auto merge = [&](int xe, int ye, long long te, int pe) {
+      const int lx = xe - T.gx0, ly = ye - T.gy0;
       if (lx >= 0 && lx < MW && ly >= 0 && ly < MH) {
-        atomicMax(&mt[ly * MW + lx], ev.t[i]);
-        atomicAdd(&mc[ly * MW + lx], ev.pol[i] > 0 ? 1 : (1 << 16));
+        atomicMax(&mt[ly * MW + lx], te);
+        atomicAdd(&mc[ly * MW + lx], pe > 0 ? 1 : (1 << 16));
       }
-    }
+    };
+    if (mine) merge(x0, y0, t0, p0);
+    for (int i = tid + NT; i < ev.n; i += NT) merge(ev.x[i], ev.y[i], ev.t[i], ev.pol[i]);
   }
   __syncthreads();
   long long clock = clock0, t_init = have ? t_init0 : clock0;
   if (valid && ev.n > 0) {
-    clock = max(clock0, ev.t[ev.n - 1]);
-    t_init = have ? t_init0 : ev.t[0];
+    clock = max(clock0, t_end);
+    t_init = have ? t_init0 : t_first;
   }
   if (blockIdx.x == 0 && tid == 0) {
     if (!valid) {
@@ -159,7 +184,7 @@ __device__ __forceinline__ void push_front(TT& T, const Planes& P, const SolveCo
       P.sc->commit_pending = 1;
     }
   }
-  T.front_consts_push(P, c, pc, mt, mc, clock, t_init);
+  T.front_consts_push(P, c, pc, mt, mc, np, nn, clock, t_init);
 }
 
 template <int KX, int KY, int NTY, typename ST, int MODE>

@@ -290,9 +290,29 @@ struct Tile {
   // t_last and counts already in the planes, exactly as the push followed by the
   // prologue would leave them (max and sum do not depend on the order).  clock and t_init
   // are the stream's after the packet.  The owned pixels' merged t_last is written back.
+  // The event counts of this thread's pixels (0 off the sensor).
+  __device__ __forceinline__ void load_counts(const Planes& P, int* np, int* nn) const {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      np[k] = 0;
+      nn[k] = 0;
+      if (on(k, P.W, P.H)) {
+        const size_t i = gidx(P, k);
+        np[k] = P.npos[i];
+        nn[k] = P.nneg[i];
+      }
+    }
+  }
+
+  // front_consts with the packet integrated in shared memory (the push fused into the
+  // first pass): mt holds the merged t_last of the extended tile plus one column and row
+  // (row stride EW + 1), mc the packet's events per pixel (positive in the low 16 bits,
+  // negative in the high), np and nn the counts before the packet.  The owned pixels'
+  // constants are written to the planes, and their t_last where events hit them.
   __device__ __forceinline__ void front_consts_push(const Planes& P, const SolveConsts& c,
                                                     const PrologueConsts& pc,
                                                     const long long* mt, const int* mc,
+                                                    const int* np, const int* nn,
                                                     long long clock, long long t_init) {
     constexpr int MW = EW + 1;
     const float tl = c.tau * c.lambda;
@@ -302,22 +322,17 @@ struct Tile {
       if (on(k, P.W, P.H)) {
         const size_t i = gidx(P, k);
         const int gx = gx0 + lx(k), gy = gy0 + ly(k), m = ly(k) * MW + lx(k);
-        const long long t_own = max(P.t_last[i], mt[m]);
+        const long long t_own = mt[m];
         const float t0 = time_surface(t_own, clock, t_init, pc);
-        a = (gx < P.W - 1)
-                ? surface_diff(time_surface(max(P.t_last[i + 1], mt[m + 1]), clock, t_init, pc),
-                               t0)
-                : 0.0f;
-        b = (gy < P.H - 1) ? surface_diff(time_surface(max(P.t_last[i + P.pitch], mt[m + MW]),
-                                                       clock, t_init, pc),
-                                          t0)
+        a = (gx < P.W - 1) ? surface_diff(time_surface(mt[m + 1], clock, t_init, pc), t0)
+                           : 0.0f;
+        b = (gy < P.H - 1) ? surface_diff(time_surface(mt[m + MW], clock, t_init, pc), t0)
                            : 0.0f;
         const float G = metric_G(a, b);
         ig = 1.0f / G;
         sg = sqrtf(G);
         const int cnt = mc[m];
-        f = data_image(el(u[k >> 1], k & 1), P.npos[i] + (cnt & 0xffff), P.nneg[i] + (cnt >> 16),
-                       pc);
+        f = data_image(el(u[k >> 1], k & 1), np[k] + (cnt & 0xffff), nn[k] + (cnt >> 16), pc);
         mx = (gx < P.W - 1) ? 1.0f : 0.0f;
         my = (gy % P.Hm < P.Hm - 1) ? 1.0f : 0.0f;
         if (owned(k)) {
@@ -326,7 +341,7 @@ struct Tile {
           P.iG[i] = ig;
           P.sG[i] = sg;
           P.f[i] = f;
-          if (mt[m] > P.t_last[i]) P.t_last[i] = t_own;
+          if (cnt != 0) P.t_last[i] = t_own;
         }
       }
       set_consts(k, a, b, ig, sg, f, mx, my, tl, c);
