@@ -89,6 +89,10 @@ constexpr int kTiledMinBlocks =
 // an uncapped two-pair tile; one-pair tiles fit it in 64)
 template <int KX, int KY, int NTY, typename ST>
 constexpr bool kTiledFront = kTiledMinBlocks<KX, KY, NTY, ST> == 1 || KX * KY == 2;
+// Tiles whose pass 0 can also take the packet's push (FP32; the event maps in dynamic
+// shared memory): the front's tiles
+template <int KX, int KY, int NTY>
+constexpr bool kTiledPush = kTiledFront<KX, KY, NTY, float>;
 
 // MODE 0: plain passes.  MODE 1 (FRONT): the packet's front launch is fused into the
 // passes (instantiated for the tiles of kTiledFront).
@@ -470,10 +474,11 @@ static int tiles_of(const Planes& P, int R, int* tx, int* ty) {
 }
 
 // Whether the push can be fused into pass 0 for this tile (MODE 3 instantiated: FP32,
-// no register cap); sets the kernel's dynamic shared-memory limit for its event maps.
+// a tile that takes the front); sets the kernel's dynamic shared-memory limit for its
+// event maps.
 template <int KX, int KY, int NTY>
 static bool push_fusable_t() {
-  if constexpr (kTiledMinBlocks<KX, KY, NTY, float> == 1) {
+  if constexpr (kTiledPush<KX, KY, NTY>) {
     static int ok = -1;
     if (ok < 0) {
       ok = cudaFuncSetAttribute((const void*)k_tiled<KX, KY, NTY, float, 3>,
@@ -494,7 +499,7 @@ static cudaError_t launch_k_tiled_st(cudaLaunchConfig_t* lc, const Planes& P, in
                                      const PushArgs* push) {
   const PushArgs none{nullptr, nullptr, nullptr, nullptr, 0};
   if (front && push) {
-    if constexpr (kTiledMinBlocks<KX, KY, NTY, ST> == 1 && sizeof(ST) == 4) {
+    if constexpr (kTiledPush<KX, KY, NTY> && sizeof(ST) == 4) {
       if (push->n < 0 || push->n > kTiledPushMax) return cudaErrorInvalidValue;
       lc->dynamicSmemBytes = tiled_push_smem<KX, KY, NTY>();
       return cudaLaunchKernelEx(lc, k_tiled<KX, KY, NTY, ST, 3>, P, src, iters, R, c, tx, B,
@@ -581,7 +586,7 @@ static int set_push_node(cudaGraphExec_t exec, cudaGraphNode_t node, const Plane
                          int src, int iters, const SolveConsts& c, const PrologueConsts& front,
                          const PushArgs& push) {
   int tx, ty;
-  if constexpr (kTiledMinBlocks<KX, KY, NTY, float> == 1) {
+  if constexpr (kTiledPush<KX, KY, NTY>) {
     if (!tiles_of<KX, KY, NTY>(P, R, &tx, &ty) || iters < 1 || push.n < 0 ||
         push.n > kTiledPushMax)
       return (int)cudaErrorInvalidValue;

@@ -41,7 +41,8 @@ def dev(torch, pk):
 # 73: the resident solver (one cooperative launch, the push inside it)
 @pytest.mark.parametrize("over", [{}, dict(tile_config=45), dict(solver=1),
                                   dict(tvl1_iters=3), dict(tile_config=55),
-                                  dict(tile_config=73), dict(tile_config=73, data_mode=1)])
+                                  dict(tile_config=73), dict(tile_config=73, data_mode=1),
+                                  dict(tile_config=32), dict(tile_config=2)])
 def test_step_equals_push_then_solve(T, over):
     torch, E = T
     W, H = 150, 97
@@ -62,7 +63,7 @@ def test_step_equals_push_then_solve(T, over):
 
 # tile_config 47: one 4 x 4 cluster over the sensor, the push inside its single launch;
 # 73: the resident solver
-@pytest.mark.parametrize("tile", [45, 47, 73])
+@pytest.mark.parametrize("tile", [45, 47, 73, 32])
 def test_step_with_empty_and_large_packets_and_a_rejection(T, tile):
     torch, E = T
     W, H = 64, 40
