@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--storage", type=int, default=0, help="evr_params.storage (0 FP32, 1 FP16, "
                     "2 BF16)")
     ap.add_argument("--tvl1", type=int, default=0, help="evr_params.tvl1_iters")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "graph", "persistent"],
+                    help="batch256: evr_batch_set_schedule (default: autotuned)")
     ap.add_argument("--grouping", default=None,
                     help="batch256: BYTES[,BRANCHES] for evr_batch_set_grouping (default: "
                          "autotuned; 0 = one group)")
@@ -646,6 +648,9 @@ def run_batch_bench(args):
         parts = [int(v) for v in args.grouping.split(",")]
         grouping = (parts[0], parts[1] if len(parts) > 1 else 1)
         b.set_grouping(*grouping)
+    schedule = {"auto": E.EVR_BATCH_SCHEDULE_AUTO, "graph": E.EVR_BATCH_SCHEDULE_GRAPH,
+                "persistent": E.EVR_BATCH_SCHEDULE_PERSISTENT}[args.schedule]
+    b.set_schedule(schedule)
     l2_gbs = E.evr_measure_peak(0, cur.cuda_stream)
     steps = [batch_step_arrays(streams, packet, k) for k in range(n_steps)]
     dev = []
@@ -694,6 +699,7 @@ def run_batch_bench(args):
     b2.set_cuda_stream(cur.cuda_stream)
     if grouping is not None:
         b2.set_grouping(*grouping)
+    b2.set_schedule(schedule)
     n_img = sum(w * h for w, h in sizes)
     imgs = [torch.empty(n_img, dtype=torch.float32).pin_memory().numpy() for _ in range(2)]
     for k in range(args.warmup):
@@ -717,7 +723,8 @@ def run_batch_bench(args):
                 (k_ms * 1e-3) / 1e9)
     # cut into groups that fit L2, a group's state stays in L2 across its passes (the
     # level that bounds them); one group sweeps the whole batch through HBM every pass
-    grouped = "L2 groups" in b.solver_name
+    persistent = b.schedule == E.EVR_BATCH_SCHEDULE_PERSISTENT
+    grouped = "L2 groups" in b.solver_name or "windows of" in b.solver_name
     if grouped:
         level = {"bound": "l2", "peak": l2_gbs, "frac": achieved / l2_gbs,
                  "peak_source": "L2, measured in this run (evr_measure_peak level 0)"}
@@ -741,7 +748,8 @@ def run_batch_bench(args):
         "config": {"workload": "batch256: 256 streams (96 x 128x128, 96 x 240x180, "
                                "64 x 346x260), rects/blobs scenes, packets U[20,400], "
                                "500-event packets, 50 iterations",
-                   "solver": b.solver_name, "steps_timed": "one packet per active stream",
+                   "solver": b.solver_name, "schedule": args.schedule,
+                   "steps_timed": "one packet per active stream",
                    "parallelism": (f"streams split over {world} ranks by work "
                                    f"(rank 0: {len(mine)} streams)" if world > 1 else
                                    "one GPU"),
@@ -749,18 +757,22 @@ def run_batch_bench(args):
         "roofline": {"bound": level["bound"], "achieved": achieved, "peak": level["peak"],
                      "unit": "GB/s", "frac": level["frac"], "traffic": None,
                      "frac_hbm": achieved / peak,
-                     "kernel": "batched prologue + iteration passes (graph)",
+                     "kernel": ("k_batch_persist: the whole step (pushes, prologue, "
+                                "iteration passes) in one persistent launch" if persistent
+                                else "batched prologue + iteration passes (graph)"),
                      "peak_source": level["peak_source"],
-                     "graph_launches_per_step": k_launches / args.steps},
+                     "launches_per_step": (k_launches if persistent
+                                           else k_launches + args.steps) / args.steps},
         "e2e": {"value": ev / e2e_s, "unit": "events/s",
                 "h2d_bytes_per_step": int(13 * ev / args.steps) + 8 * (len(sizes) + 1),
                 "d2h_bytes_per_step": int(4 * n_img),
                 "calls": "evr_batch_step (host arrays) + evr_batch_get_images_async into "
                          "pinned memory, two steps in flight"},
         "clocks": clocks,
-        # per step: the push kernel, then the graph (per L2 group the prologue and the
-        # passes; the buffer flip), whose launches the library counts
-        "gpu_launches": int(k_launches) + args.steps,
+        # per step: the persistent launch, or the push kernel and then the graph (per L2
+        # group the prologue and the passes; the buffer flip); the library counts the
+        # launches it times (all but the graph schedule's push)
+        "gpu_launches": int(k_launches) + (0 if persistent else args.steps),
     }
     print(json.dumps(line), flush=True)
     b.close()

@@ -304,6 +304,33 @@ int evr_batch_set_cuda_stream(evr_batch* b, void* cuda_stream);
  * handle, branches outside 1..4), EVR_ERR_CUDA. */
 int evr_batch_set_grouping(evr_batch* b, long long budget_bytes, int branches);
 
+/* How a step runs once the tiled configuration is chosen.
+ *   EVR_BATCH_SCHEDULE_GRAPH: one push launch, then a CUDA graph of launches (per group
+ *     of streams the prologue and each iteration pass over the group's (stream, tile)
+ *     work list).
+ *   EVR_BATCH_SCHEDULE_PERSISTENT: the whole step -- every stream's push, prologue and
+ *     iteration passes -- is one persistent launch, captured as a one-node CUDA graph
+ *     whose arguments take each step's packets.  The grid holds as many CTAs as are
+ *     resident at once; they take (stream, item) work items in list order from a queue
+ *     and wait, bounded, until the item's stream has completed the items it depends on
+ *     (the batching of NEXT-2; the update rules are Eq. update_rules, run as in the
+ *     tiled passes).  The items of a window of streams whose pass working set fits the
+ *     grouping budget (evr_batch_set_grouping; 0: every stream) are listed pass after
+ *     pass, so the window's state stays in L2.  Tiles of 32 x 32 and 32 x 48 pixels only
+ *     (tile_config 1-5, 28-32, 35-42).  A wait that runs out (0.2 s) ends the launch
+ *     and is reported as EVR_ERR_TIMEOUT by evr_batch_synchronize.
+ *   EVR_BATCH_SCHEDULE_AUTO (the default): the autotuner times both with the chosen
+ *     configuration (and the persistent one over window budgets and its tiles) at the
+ *     next step with iterations and keeps the faster.
+ * Results are bit-identical under every schedule.  Synchronises the batch's stream.
+ * Errors: EVR_ERR_INVALID_ARG (null handle, unknown schedule), EVR_ERR_CUDA. */
+#define EVR_BATCH_SCHEDULE_AUTO (-1)
+#define EVR_BATCH_SCHEDULE_GRAPH 0
+#define EVR_BATCH_SCHEDULE_PERSISTENT 1
+int evr_batch_set_schedule(evr_batch* b, int schedule);
+/* The schedule steps use now (GRAPH or PERSISTENT; GRAPH before the first tuning). */
+int evr_batch_get_schedule(evr_batch* b, int* schedule);
+
 /* One step.  Events of all streams concatenated (structure of arrays, device
  * pointers); stream s owns events [offsets[s], offsets[s+1]) (offsets: device int64
  * array of n+1 entries, offsets[0] = 0, non-decreasing).  Validation is per stream
@@ -347,6 +374,16 @@ int evr_batch_synchronize(evr_batch* b, int* stream_out);
 int evr_batch_enable_kernel_timing(evr_batch* b, int enable);
 int evr_batch_kernel_time(evr_batch* b, double* ms, int64_t* launches, int64_t* pixel_iters);
 const char* evr_batch_solver_name(evr_batch* b);
+
+/* Self-test of the persistent step's bounded waits: one timing run of the current
+ * configuration's passes (reading the live state, writing only the other buffer) in
+ * which one work item waits for a count its stream never reaches; its wait runs out,
+ * every other CTA leaves at its next item or poll, and the last CTA resets the control
+ * words.  Returns the status the launch reported (EVR_ERR_TIMEOUT when detection
+ * works) after checking that the control words were reset (EVR_ERR_CUDA if not);
+ * EVR_ERR_NOT_SUPPORTED when the batch's tile has no persistent form.  Takes about
+ * 0.2 s; synchronises. */
+int evr_batch_selftest_persist_timeout(evr_batch* b);
 
 /* ---- differentiation of one packet's solve (no counterpart in the paper's text:
  * the adjoint of its iteration, Eq. cont_iterates with Eq. update_rules) ----

@@ -13,6 +13,12 @@
 // each group's prologue and all its passes before the next group (optionally two groups
 // at a time on two graph branches), so that a group's (u, p) and constants stay in L2
 // across its passes instead of every pass sweeping the whole batch through HBM.
+//
+// The other schedule runs a whole step -- every stream's push, prologue and passes -- as
+// one persistent launch working through an ordered list of (stream, item) pairs with
+// per-stream dependency counts (evr_persist.cu), captured as a one-node CUDA graph whose
+// arguments take each step's packets.  The autotuner times both schedules after choosing
+// the tile configuration and keeps the faster one.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +33,7 @@
 
 #include "../../include/evr.h"
 #include "evr_internal.cuh"
+#include "evr_persist.cuh"
 
 namespace evr {
 int check_params(const evr_params* p);
@@ -63,6 +70,23 @@ struct evr_batch {
   cudaStream_t side[kMaxBranches - 1] = {};  // the other branches (capture and tuning)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::map<int, cudaGraphExec_t> graphs;  // by iteration count
+  // persistent schedule (one launch per step): requested (-1 auto, 0 graph of launches,
+  // 1 persistent), chosen, its window budget (pass bytes of the streams whose passes are
+  // interleaved; 0: one window) and per iteration count its work list and graph
+  int sched_req = EVR_BATCH_SCHEDULE_AUTO;
+  bool persistent = false, sched_tuned = false;
+  long long win_budget = 0;
+  int pgrid = 0;
+  int* d_ctrl = nullptr;    // control words (evr_persist.cuh)
+  int* d_totals = nullptr;  // per stream: work items of a step
+  struct Plan {
+    int4* d_items = nullptr;
+    int n_items = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t node = nullptr;
+    cudaGraph_t graph = nullptr;
+  };
+  std::map<int, Plan> plans;  // by iteration count
   // host-pointer steps: packed pinned staging (two slots) and device staging
   size_t stage_cap = 0;
   char* d_stage = nullptr;
@@ -189,6 +213,272 @@ void drop_graphs(evr_batch* b) {
   b->graphs.clear();
 }
 
+// ---- persistent schedule (evr_persist.cu)
+
+void drop_plans(evr_batch* b) {
+  if (!b->plans.empty()) cudaStreamSynchronize(b->stream);
+  for (auto& kv : b->plans) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    if (kv.second.d_items) cudaFree(kv.second.d_items);
+  }
+  b->plans.clear();
+}
+
+// Tiles of stream s under configuration ci.
+int stream_tiles(const evr_batch* b, int s, int ci) {
+  const SolverCfg& c = kSolverCfgs[ci];
+  const TileShape& t = kTileShapes[c.shape];
+  const int OW = t.EW - 2 * c.R, OH = t.EH - 2 * c.R;
+  return ((b->planes[s].W + OW - 1) / OW) * ((b->planes[s].H + OH - 1) / OH);
+}
+
+// A step's work list for configuration ci with `passes` passes, window by window
+// (streams in index order whose pass bytes stay within budget; 0: one window): the
+// window's pushes and prologue bands, then pass after pass every stream's tiles, the
+// next window's pushes and bands placed before the last pass, so that they run while
+// this window drains.  Each item waits for the items of its stream listed before its own
+// group (the push for a band; the push, the bands and the earlier passes for a pass).
+// timing: passes only.  totals[s]: stream s's items.
+void persist_items(const evr_batch* b, int ci, int passes, bool timing, long long budget,
+                   std::vector<int4>* items, std::vector<int>* totals) {
+  items->clear();
+  totals->assign(b->n, 0);
+  std::vector<std::pair<int, int>> win;
+  int s0 = 0;
+  long long acc = 0;
+  for (int s = 0; s <= b->n; ++s) {
+    const long long sb = s < b->n ? pass_bytes(b, s) : 0;
+    const bool cut = s == b->n || (budget > 0 && s > s0 && acc + sb > budget);
+    if (cut && s > s0) {
+      win.emplace_back(s0, s);
+      s0 = s;
+      acc = 0;
+    }
+    acc += sb;
+  }
+  auto bands = [&](int q) { return (b->planes[q].H + kPersistProRows - 1) / kPersistProRows; };
+  auto front = [&](size_t g) {
+    if (timing || g >= win.size()) return;
+    for (int q = win[g].first; q < win[g].second; ++q)
+      items->push_back(make_int4(q, kItemPush, 0, 0));
+    for (int q = win[g].first; q < win[g].second; ++q)
+      for (int k = 0; k < bands(q); ++k) items->push_back(make_int4(q, kItemPrologue, k, 1));
+  };
+  auto pass = [&](size_t g, int j) {
+    for (int q = win[g].first; q < win[g].second; ++q) {
+      const int nt = stream_tiles(b, q, ci);
+      const int need = (timing ? 0 : 1 + bands(q)) + j * nt;
+      for (int k = 0; k < nt; ++k) items->push_back(make_int4(q, j, k, need));
+    }
+  };
+  front(0);
+  for (size_t g = 0; g < win.size(); ++g) {
+    for (int j = 0; j + 1 < passes; ++j) pass(g, j);
+    front(g + 1);
+    if (passes > 0) pass(g, passes - 1);
+    for (int q = win[g].first; q < win[g].second; ++q)
+      (*totals)[q] = (timing ? 0 : 1 + bands(q)) + passes * stream_tiles(b, q, ci);
+  }
+}
+
+// Work list and per-stream totals in one device buffer (items, then totals).
+int upload_items(const std::vector<int4>& items, const std::vector<int>& totals, int4** out) {
+  *out = nullptr;
+  const size_t ib = sizeof(int4) * items.size(), tb = sizeof(int) * totals.size();
+  if (dev_alloc((void**)out, ib + tb + 16) != cudaSuccess) {
+    *out = nullptr;
+    return EVR_ERR_OOM;
+  }
+  cudaError_t e = cudaMemcpy(*out, items.data(), ib, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy((char*)*out + ib, totals.data(), tb, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(*out);
+    *out = nullptr;
+    return EVR_ERR_CUDA;
+  }
+  return EVR_OK;
+}
+
+int ensure_ctrl(evr_batch* b) {
+  if (b->d_ctrl) return EVR_OK;
+  const size_t bytes = sizeof(int) * persist_ctrl_ints(b->n);
+  if (dev_alloc((void**)&b->d_ctrl, bytes) != cudaSuccess) {
+    b->d_ctrl = nullptr;
+    return EVR_ERR_OOM;
+  }
+  if (cudaMemset(b->d_ctrl, 0, bytes) != cudaSuccess) return EVR_ERR_CUDA;
+  return EVR_OK;
+}
+
+PersistArgs persist_args(const evr_batch* b, int ci, const int4* d_items, int n_items,
+                         int iters, bool timing) {
+  PersistArgs a{};
+  a.descs = b->d_descs;
+  a.curs = b->d_curs;
+  a.active = b->d_active;
+  a.items = d_items;
+  a.totals = (const int*)(d_items + n_items);
+  a.ctrl = b->d_ctrl;
+  a.n_items = n_items;
+  a.n_streams = b->n;
+  a.R = kSolverCfgs[ci].R;
+  a.iters = iters;
+  a.timing = timing ? 1 : 0;
+  a.c = consts(b);
+  a.pc = pconsts(b);
+  return a;
+}
+
+// Milliseconds of one persistent run of configuration ci's passes over the batch (timing
+// items: each pass reads the live buffer and writes the other one), best of `reps` after
+// one warm-up run, or -1.  need_bump > 0 (self-test): the first item waits for that
+// many more completions than its stream will ever reach.
+float time_persist(evr_batch* b, int ci, int iters, long long budget, int reps,
+                   cudaEvent_t e0, cudaEvent_t e1, int need_bump = 0) {
+  const SolverCfg& cfg = kSolverCfgs[ci];
+  if (!persist_supported(cfg, b->prm.storage) || ensure_ctrl(b)) return -1.f;
+  const int grid = persist_grid(cfg, b->prm.storage);
+  if (grid <= 0) return -1.f;
+  std::vector<int4> items;
+  std::vector<int> totals;
+  persist_items(b, ci, (iters + cfg.R - 1) / cfg.R, true, budget, &items, &totals);
+  if (items.empty()) return -1.f;
+  if (need_bump > 0) items[0].w += need_bump;
+  int4* d_items = nullptr;
+  if (upload_items(items, totals, &d_items)) return -1.f;
+  const PersistArgs a = persist_args(b, ci, d_items, (int)items.size(), iters, true);
+  float best = -1.f;
+  bool ok = need_bump > 0 ||
+            launch_batch_persist(cfg, b->prm.storage, a, grid, b->stream) == 0;
+  for (int rep = 0; ok && rep < reps; ++rep) {
+    cudaEventRecord(e0, b->stream);
+    ok = launch_batch_persist(cfg, b->prm.storage, a, grid, b->stream) == 0;
+    cudaEventRecord(e1, b->stream);
+    float ms = 0.f;
+    if (!ok || cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0.f || ms < best) best = ms;
+  }
+  cudaStreamSynchronize(b->stream);
+  cudaFree(d_items);
+  return ok ? best : -1.f;
+}
+
+float time_passes(evr_batch* b, int ci, int iters, int reps, cudaEvent_t e0, cudaEvent_t e1);
+
+// The persistent schedule against the graph of launches, after the graph's configuration
+// and grouping were chosen: window budgets for the chosen configuration (or the first
+// persistent-capable one), then (configs) every persistent-capable configuration under
+// the best budget.  Keeps the persistent schedule if it is faster (or requested).
+void tune_schedule(evr_batch* b, int iters, bool configs, cudaEvent_t e0, cudaEvent_t e1) {
+  const int storage = b->prm.storage;
+  const bool forced = b->sched_req == EVR_BATCH_SCHEDULE_PERSISTENT;
+  const float graph_ms = forced ? 1e30f : time_passes(b, b->cfg, iters, 2, e0, e1);
+  int pc = -1;
+  if (persist_supported(kSolverCfgs[b->cfg], storage)) {
+    pc = b->cfg;
+  } else if (configs) {
+    for (int ci = 0; ci < kNumSolverCfgs && pc < 0; ++ci)
+      if (persist_supported(kSolverCfgs[ci], storage)) pc = ci;
+  }
+  if (pc < 0) {
+    b->persistent = false;
+    b->sched_tuned = true;
+    return;
+  }
+  static const long long kWindowsMB[] = {0, 128, 96, 64, 48, 32, 24, 16};
+  long long best_budget = b->group_auto ? 0 : b->group_budget;
+  float best = -1.f;
+  if (b->group_auto) {
+    for (long long mb : kWindowsMB) {
+      const float t = time_persist(b, pc, iters, mb << 20, 2, e0, e1);
+      if (t >= 0.f && (best < 0.f || t < best)) {
+        best = t;
+        best_budget = mb << 20;
+      }
+    }
+  } else {
+    best = time_persist(b, pc, iters, best_budget, 2, e0, e1);
+  }
+  if (configs) {
+    for (int ci = 0; ci < kNumSolverCfgs; ++ci) {
+      if (ci == pc || !persist_supported(kSolverCfgs[ci], storage)) continue;
+      const float t = time_persist(b, ci, iters, best_budget, 2, e0, e1);
+      if (t >= 0.f && (best < 0.f || t < best)) {
+        best = t;
+        pc = ci;
+      }
+    }
+  }
+  b->sched_tuned = true;
+  if (best >= 0.f && (forced || best < graph_ms)) {
+    b->persistent = true;
+    b->win_budget = best_budget;
+    b->pgrid = persist_grid(kSolverCfgs[pc], storage);
+    if (pc != b->cfg) {
+      b->cfg = pc;
+      build_tile_work(b, b->cfg);
+    }
+  } else {
+    b->persistent = false;
+  }
+}
+
+// The persistent step of `iters` iterations with this call's packets: the plan's graph
+// (one kernel node) is captured at the first use, later calls set the node's arguments.
+int persist_step(evr_batch* b, const uint16_t* x, const uint16_t* y, const long long* t,
+                 const int8_t* pol, const long long* offsets, int iters) {
+  if (ensure_ctrl(b)) return EVR_ERR_OOM;
+  const SolverCfg& cfg = kSolverCfgs[b->cfg];
+  auto it = b->plans.find(iters);
+  evr_batch::Plan* pl = nullptr;
+  if (it == b->plans.end()) {
+    evr_batch::Plan np;
+    std::vector<int4> items;
+    std::vector<int> totals;
+    persist_items(b, b->cfg, (iters + cfg.R - 1) / cfg.R, false, b->win_budget, &items,
+                  &totals);
+    np.n_items = (int)items.size();
+    int rc = upload_items(items, totals, &np.d_items);
+    if (rc) return rc;
+    PersistArgs a = persist_args(b, b->cfg, np.d_items, np.n_items, iters, false);
+    a.x = x;
+    a.y = y;
+    a.t = t;
+    a.pol = pol;
+    a.offsets = offsets;
+    bool bad = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) !=
+               cudaSuccess;
+    if (!bad) bad = launch_batch_persist(cfg, b->prm.storage, a, b->pgrid, b->cap_stream) != 0;
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &np.graph);
+    size_t roots = 1;
+    if (!bad && e == cudaSuccess) e = cudaGraphGetRootNodes(np.graph, &np.node, &roots);
+    if (!bad && e == cudaSuccess && roots == 1) e = cudaGraphInstantiate(&np.exec, np.graph, 0);
+    if (bad || e != cudaSuccess || roots != 1 || !np.exec) {
+      if (np.exec) cudaGraphExecDestroy(np.exec);
+      if (np.graph) cudaGraphDestroy(np.graph);
+      cudaFree(np.d_items);
+      return EVR_ERR_CUDA;
+    }
+    pl = &(b->plans[iters] = np);
+  } else {
+    pl = &it->second;
+    PersistArgs a = persist_args(b, b->cfg, pl->d_items, pl->n_items, iters, false);
+    a.x = x;
+    a.y = y;
+    a.t = t;
+    a.pol = pol;
+    a.offsets = offsets;
+    if (persist_node_set(pl->exec, pl->node, a)) return EVR_ERR_CUDA;
+  }
+  return cudaGraphLaunch(pl->exec, b->stream) == cudaSuccess ? EVR_OK : EVR_ERR_CUDA;
+}
+
 void set_name(evr_batch* b) {
   if (b->cfg < 0) {
     std::snprintf(b->name, sizeof(b->name), "batch: untuned");
@@ -196,6 +486,16 @@ void set_name(evr_batch* b) {
   }
   const SolverCfg& c = kSolverCfgs[b->cfg];
   const TileShape& t = kTileShapes[c.shape];
+  if (b->persistent) {
+    const int n = std::snprintf(b->name, sizeof(b->name),
+                                "batch of %d: persistent step, tiled %dx%d R%d (%d threads, "
+                                "%d CTAs)",
+                                b->n, t.EW, t.EH, c.R, 32 * t.NTY, b->pgrid);
+    if (b->win_budget > 0 && n > 0 && n < (int)sizeof(b->name))
+      std::snprintf(b->name + n, sizeof(b->name) - n, ", windows of <= %lld MB",
+                    b->win_budget >> 20);
+    return;
+  }
   const int n = std::snprintf(b->name, sizeof(b->name),
                               "batch of %d: tiled %dx%d R%d (%d threads, %d CTAs)", b->n, t.EW,
                               t.EH, c.R, 32 * t.NTY, b->n_work_tile);
@@ -318,9 +618,15 @@ void autotune(evr_batch* b, int iters, bool configs) {
       if (ci >= 0 && ms < best) b->cfg = ci;
     }
   }
+  build_tile_work(b, b->cfg);
+  if (b->sched_req != EVR_BATCH_SCHEDULE_GRAPH) {
+    tune_schedule(b, iters, configs, e0, e1);
+  } else {
+    b->persistent = false;
+    b->sched_tuned = true;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  build_tile_work(b, b->cfg);
 }
 
 void resolve_timing(evr_batch* b) {
@@ -468,6 +774,8 @@ void evr_batch_destroy(evr_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   drop_graphs(b);
+  drop_plans(b);
+  if (b->d_ctrl) cudaFree(b->d_ctrl);
   resolve_timing(b);
   for (auto& e : b->ev_free) {
     cudaEventDestroy(e.first);
@@ -515,8 +823,60 @@ int evr_batch_set_grouping(evr_batch* b, long long budget_bytes, int branches) {
   b->branches = budget_bytes < 0 ? 1 : branches;
   if (b->cfg >= 0 && !b->tile_off.empty()) build_groups(b);
   drop_graphs(b);
+  drop_plans(b);
+  b->sched_tuned = false;  // the windows follow the grouping
   set_name(b);
   return EVR_OK;
+}
+
+int evr_batch_set_schedule(evr_batch* b, int schedule) {
+  if (!b || schedule < EVR_BATCH_SCHEDULE_AUTO || schedule > EVR_BATCH_SCHEDULE_PERSISTENT)
+    return EVR_ERR_INVALID_ARG;
+  if (schedule == EVR_BATCH_SCHEDULE_PERSISTENT && b->prm.tile_config > 0 &&
+      !persist_supported(kSolverCfgs[b->prm.tile_config - 1], b->prm.storage))
+    return EVR_ERR_NOT_SUPPORTED;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return EVR_ERR_CUDA;
+  b->sched_req = schedule;
+  b->sched_tuned = false;
+  b->persistent = false;
+  drop_plans(b);
+  set_name(b);
+  return EVR_OK;
+}
+
+int evr_batch_get_schedule(evr_batch* b, int* schedule) {
+  if (!b || !schedule) return EVR_ERR_INVALID_ARG;
+  *schedule = b->persistent ? EVR_BATCH_SCHEDULE_PERSISTENT : EVR_BATCH_SCHEDULE_GRAPH;
+  return EVR_OK;
+}
+
+int evr_batch_selftest_persist_timeout(evr_batch* b) {
+  if (!b) return EVR_ERR_INVALID_ARG;
+  int ci = b->cfg >= 0 && persist_supported(kSolverCfgs[b->cfg], b->prm.storage) ? b->cfg : -1;
+  for (int k = 0; k < kNumSolverCfgs && ci < 0; ++k)
+    if (persist_supported(kSolverCfgs[k], b->prm.storage)) ci = k;
+  if (ci < 0) return EVR_ERR_NOT_SUPPORTED;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return EVR_ERR_CUDA;
+  int rc = ensure_ctrl(b);
+  if (rc) return rc;
+  if (cudaMemset(b->d_ctrl + kCtrlStatus, 0, sizeof(int)) != cudaSuccess) return EVR_ERR_CUDA;
+  // every stream taken as active: the timing items ignore the active flags
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  time_persist(b, ci, kSolverCfgs[ci].R, 0, 1, e0, e1, 1 << 30);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::vector<int> ctrl(persist_ctrl_ints(b->n));
+  if (cudaMemcpy(ctrl.data(), b->d_ctrl, sizeof(int) * ctrl.size(), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return EVR_ERR_CUDA;
+  const int status = ctrl[kCtrlStatus];
+  bool clean = ctrl[kCtrlHead] == 0 && ctrl[kCtrlLeft] == 0 && ctrl[kCtrlAbort] == 0;
+  for (int s = 0; s < b->n; ++s) clean = clean && ctrl[kCtrlCount + s * kCtrlStride] == 0;
+  if (cudaMemset(b->d_ctrl + kCtrlStatus, 0, sizeof(int)) != cudaSuccess) return EVR_ERR_CUDA;
+  if (!clean) return EVR_ERR_CUDA;
+  return status;
 }
 
 int evr_batch_set_cuda_stream(evr_batch* b, void* cuda_stream) {
@@ -536,12 +896,36 @@ int evr_batch_step_device(evr_batch* b, const uint16_t* x, const uint16_t* y,
   if (!b || !offsets || iters < 0) return EVR_ERR_INVALID_ARG;
   if (!x || !y || !t_us || !pol) return EVR_ERR_INVALID_ARG;
   cudaStream_t st = b->stream;
+  const bool tuned = b->tuned && (!b->group_auto || b->group_tuned) && b->sched_tuned;
+  if (iters > 0 && tuned && b->persistent) {  // the whole step in one launch
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (b->timing) {
+      if (b->ev_free.empty()) {
+        cudaEventCreate(&ev.first);
+        cudaEventCreate(&ev.second);
+      } else {
+        ev = b->ev_free.back();
+        b->ev_free.pop_back();
+      }
+      cudaEventRecord(ev.first, st);
+    }
+    const int rc = persist_step(b, x, y, (const long long*)t_us, pol, (const long long*)offsets,
+                                iters);
+    if (b->timing) {
+      cudaEventRecord(ev.second, st);
+      b->ev_used.push_back(ev);
+      b->ev_launches.push_back(1);
+      b->ev_pixiters.push_back(b->px_total * iters);  // upper bound: every stream active
+    }
+    return rc;
+  }
   if (launch_push_batch(b->d_descs, b->n, x, y, (const long long*)t_us, pol,
                         (const long long*)offsets, b->d_active, st))
     return EVR_ERR_CUDA;
-  if (iters > 0 && (!b->tuned || (b->group_auto && !b->group_tuned))) {
+  if (iters > 0 && !tuned) {
     autotune(b, iters, !b->tuned);
     drop_graphs(b);  // the tile work list may have moved
+    drop_plans(b);
     b->tuned = true;
     set_name(b);
   }

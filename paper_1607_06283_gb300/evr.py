@@ -28,6 +28,7 @@ EVR_ERR_TIMEOUT = -7
 EVR_ERR_NOT_SUPPORTED = -8
 EVR_T_INIT_FIRST = -(2 ** 63)
 EVR_SOLVER_AUTO, EVR_SOLVER_UNFUSED, EVR_SOLVER_TILED = 0, 1, 2
+EVR_BATCH_SCHEDULE_AUTO, EVR_BATCH_SCHEDULE_GRAPH, EVR_BATCH_SCHEDULE_PERSISTENT = -1, 0, 1
 (EVR_STATE_U, EVR_STATE_P1, EVR_STATE_P2, EVR_STATE_P3, EVR_STATE_F, EVR_STATE_TLAST,
  EVR_STATE_NPOS, EVR_STATE_NNEG, EVR_STATE_CLOCK, EVR_STATE_TINIT, EVR_STATE_SQRTG,
  EVR_STATE_TX, EVR_STATE_TY) = range(13)
@@ -114,6 +115,9 @@ def _load():
         "evr_batch_destroy": ([vp], None),
         "evr_batch_set_cuda_stream": ([vp, vp], i),
         "evr_batch_set_grouping": ([vp, ctypes.c_longlong, i], i),
+        "evr_batch_set_schedule": ([vp, i], i),
+        "evr_batch_get_schedule": ([vp, vp], i),
+        "evr_batch_selftest_persist_timeout": ([vp], i),
         "evr_batch_step_device": ([vp] * 6 + [i], i),
         "evr_batch_step": ([vp] * 6 + [i], i),
         "evr_batch_get_image": ([vp, i, vp, sz], i),
@@ -487,6 +491,23 @@ class Batch:
         (0: one group, < 0: autotuned), one to four graph branches."""
         _check(_lib.evr_batch_set_grouping(self.h, int(budget_bytes), int(branches)),
                "evr_batch_set_grouping")
+
+    def set_schedule(self, schedule: int) -> None:
+        """EVR_BATCH_SCHEDULE_GRAPH (a graph of launches per step),
+        EVR_BATCH_SCHEDULE_PERSISTENT (one persistent launch per step) or
+        EVR_BATCH_SCHEDULE_AUTO (the faster, chosen at the next tuning)."""
+        _check(_lib.evr_batch_set_schedule(self.h, int(schedule)), "evr_batch_set_schedule")
+
+    @property
+    def schedule(self) -> int:
+        v = ctypes.c_int()
+        _check(_lib.evr_batch_get_schedule(self.h, ctypes.byref(v)), "evr_batch_get_schedule")
+        return v.value
+
+    def selftest_persist_timeout(self) -> int:
+        """Status of a persistent timing run whose first item waits for a count that is
+        never reached (EVR_ERR_TIMEOUT when the bounded waits work)."""
+        return _lib.evr_batch_selftest_persist_timeout(self.h)
 
     def step(self, x, y, t, pol, offsets, iters: int) -> None:
         """Host arrays: all streams' events concatenated; offsets (n+1) int64."""

@@ -60,21 +60,23 @@ def test_ptxas_reports_no_spills_in_the_iteration_kernels(evr):
     """Register pressure check on the built kernels (from nvcc -Xptxas -v).  Two
     instantiations are allowed a few bytes: the two-pair FP16 tile held to 80 registers
     (two CTAs per SM; measured faster than one CTA without the spill) and the cluster
-    solver's 1024-thread tile (64 registers is the most a 1024-thread CTA can have)."""
+    solver's 1024-thread tile (64 registers is the most a 1024-thread CTA can have); the
+    persistent batch step's two-pair FP16 tiles share the first allowance."""
     import os
     import re
     allowed = {"ILi1ELi4ELi12E6__half": 8, "ILi1ELi4ELi8E6__half": 8,
                "k_clusterILi1ELi2ELi32E": 8}
     text = ""
     for f in ("evr_kernels.ptxas.txt", "evr_solvers.ptxas.txt", "evr_grad.ptxas.txt",
-              "evr_cluster.ptxas.txt", "evr_staged.ptxas.txt"):
+              "evr_cluster.ptxas.txt", "evr_staged.ptxas.txt", "evr_persist.ptxas.txt"):
         text += open(os.path.join(os.path.dirname(build.LIB), f)).read()
     blocks = text.split("Compiling entry function")
     seen = 0
     for b in blocks[1:]:
         name = b.split("'")[1]
         if any(k in name for k in ("k_tiled", "k_prologue", "k_push", "k_rev_tiled",
-                                   "k_cluster", "k_staged", "k_resident")):
+                                   "k_cluster", "k_staged", "k_resident",
+                                   "k_batch_persist")):
             seen += 1
             spill = int(re.search(r"(\d+) bytes spill stores", b).group(1))
             limit = max([v for k, v in allowed.items() if k in name], default=0)

@@ -42,18 +42,20 @@ def streams():
     return out
 
 
-def run_batch(E, streams, tile, steps, iters=30, grouping=None):
-    b = E.Batch(SIZES, tile_config=tile)
+def run_batch(E, streams, tile, steps, iters=30, grouping=None, schedule=None, **kw):
+    b = E.Batch(SIZES, tile_config=tile, **kw)
     if grouping is not None:
         b.set_grouping(*grouping)
+    if schedule is not None:
+        b.set_schedule(schedule)
     for k in range(steps):
         x, y, t, p, off = batch_step_arrays(streams, 300, k)
         b.step(x, y, t, p, off, iters)
     return b
 
 
-def run_solo(E, st, tile, steps, iters=30):
-    g = E.Stream(st.W, st.H, solver=2, tile_config=tile)
+def run_solo(E, st, tile, steps, iters=30, **kw):
+    g = E.Stream(st.W, st.H, solver=2, tile_config=tile, **kw)
     for k in range(steps):
         a = k * 300
         if a >= len(st):
@@ -197,3 +199,117 @@ def test_gathered_and_async_readback_match_per_stream_images(E, streams):
         b.wait_images(99)
     b.close()
     r.close()
+
+
+# ---------------------------------------------------------------- persistent schedule
+# tile_config values whose tiles have a persistent form: 32x32 (256 threads) R2, 32x48
+# (384 threads) R4, 32x32 (512 threads) R6
+PERSIST_TILES = [1, 36, 31]
+
+
+@pytest.mark.parametrize("tile", PERSIST_TILES)
+@pytest.mark.parametrize("grouping", [(0, 1), (1 << 20, 1)])
+def test_persistent_step_equals_solo_bit_for_bit(E, streams, tile, grouping):
+    """One persistent launch per step (push, prologue and passes from a work queue, one
+    window of all streams or windows of at most 1 MB of pass working set): every stream
+    equals its solo run bit for bit.  The first step tunes (and runs as a graph); the
+    other seven run persistent, pushes included."""
+    steps = max(COUNTS)
+    b = run_batch(E, streams, tile, steps, grouping=grouping,
+                  schedule=E.EVR_BATCH_SCHEDULE_PERSISTENT)
+    assert b.schedule == E.EVR_BATCH_SCHEDULE_PERSISTENT
+    assert "persistent step" in b.solver_name
+    assert b.synchronize() == (0, -1)
+    for s, st in enumerate(streams):
+        g = run_solo(E, st, tile, steps)
+        for w in (E.EVR_STATE_U, E.EVR_STATE_P1, E.EVR_STATE_P2, E.EVR_STATE_P3,
+                  E.EVR_STATE_F, E.EVR_STATE_TLAST, E.EVR_STATE_SQRTG, E.EVR_STATE_NPOS):
+            np.testing.assert_array_equal(b.state(s, w), g.state(w), err_msg=f"stream {s} {w}")
+        assert int(b.state(s, E.EVR_STATE_CLOCK)) == int(g.state(E.EVR_STATE_CLOCK))
+        g.close()
+    b.close()
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_persistent_step_16bit_storage_equals_solo(E, streams, storage):
+    steps = 4
+    b = run_batch(E, streams, 36, steps, grouping=(0, 1),
+                  schedule=E.EVR_BATCH_SCHEDULE_PERSISTENT, storage=storage)
+    assert b.schedule == E.EVR_BATCH_SCHEDULE_PERSISTENT
+    for s in (0, 2, 4, 7):
+        g = run_solo(E, streams[s], 36, steps, storage=storage)
+        for w in (E.EVR_STATE_U, E.EVR_STATE_P1, E.EVR_STATE_P3):
+            np.testing.assert_array_equal(b.state(s, w), g.state(w), err_msg=f"stream {s} {w}")
+        g.close()
+    b.close()
+
+
+def test_persistent_step_rejection_is_per_stream_and_idle_streams_are_untouched(E, streams):
+    b = run_batch(E, streams, 36, 2, schedule=E.EVR_BATCH_SCHEDULE_PERSISTENT)
+    assert b.schedule == E.EVR_BATCH_SCHEDULE_PERSISTENT
+    before = [b.state(s, E.EVR_STATE_U).copy() for s in range(len(SIZES))]
+    t_before = b.state(4, E.EVR_STATE_TLAST).copy()
+    x, y, t, p, off = batch_step_arrays(streams, 300, 2)
+    a4 = off[4]
+    x = x.copy()
+    x[a4] = 1  # off the 1 x 1 sensor
+    keep = np.ones(len(x), bool)
+    keep[off[1]:off[2]] = False
+    cnt = np.diff(off)
+    cnt[1] = 0
+    off2 = np.concatenate([[0], np.cumsum(cnt)])
+    b.step(x[keep], y[keep], t[keep], p[keep], off2, 30)
+    rc, bad = b.synchronize()
+    assert rc == E.EVR_ERR_OUT_OF_RANGE and bad == 4
+    np.testing.assert_array_equal(b.state(1, E.EVR_STATE_U), before[1])
+    np.testing.assert_array_equal(b.state(4, E.EVR_STATE_TLAST), t_before)
+    assert b.synchronize() == (0, -1)
+    b.close()
+
+
+def test_persistent_step_is_one_launch_and_schedules_agree(E, streams):
+    """Kernel timing counts one launch per persistent step; the graph schedule of the same
+    tile gives the same bits; the autotuned schedule is one of the two."""
+    steps = 5
+    a = run_batch(E, streams, 36, 1, schedule=E.EVR_BATCH_SCHEDULE_PERSISTENT)
+    a.enable_kernel_timing(True)
+    for k in range(1, steps):
+        x, y, t, p, off = batch_step_arrays(streams, 300, k)
+        a.step(x, y, t, p, off, 30)
+    ms, launches, _ = a.kernel_time()
+    assert launches == steps - 1 and ms > 0
+    g = run_batch(E, streams, 36, steps, schedule=E.EVR_BATCH_SCHEDULE_GRAPH)
+    assert g.schedule == E.EVR_BATCH_SCHEDULE_GRAPH and "persistent" not in g.solver_name
+    for s in range(len(SIZES)):
+        np.testing.assert_array_equal(a.state(s, E.EVR_STATE_U), g.state(s, E.EVR_STATE_U))
+    auto = run_batch(E, streams, 0, 2)
+    assert auto.schedule in (E.EVR_BATCH_SCHEDULE_GRAPH, E.EVR_BATCH_SCHEDULE_PERSISTENT)
+    for b in (a, g, auto):
+        b.close()
+
+
+def test_persistent_schedule_rejects_a_tile_without_persistent_form(E):
+    b = E.Batch(SIZES[:3], tile_config=6)  # 32 x 64 tile
+    with pytest.raises(E.EvrError):
+        b.set_schedule(E.EVR_BATCH_SCHEDULE_PERSISTENT)
+    with pytest.raises(E.EvrError):
+        b.set_schedule(7)
+    b.close()
+
+
+def test_persistent_wait_timeout_is_reported_and_the_batch_continues(E, streams):
+    """A work item waits for a count its stream never reaches: its bounded wait runs out,
+    the launch reports EVR_ERR_TIMEOUT, the control words are reset (the self-test checks
+    them), and later steps still equal the solo runs bit for bit."""
+    steps = 4
+    b = run_batch(E, streams, 36, 2, schedule=E.EVR_BATCH_SCHEDULE_PERSISTENT)
+    assert b.selftest_persist_timeout() == E.EVR_ERR_TIMEOUT
+    for k in range(2, steps):
+        x, y, t, p, off = batch_step_arrays(streams, 300, k)
+        b.step(x, y, t, p, off, 30)
+    assert b.synchronize() == (0, -1)
+    for s in (0, 2, 7):
+        g = run_solo(E, streams[s], 36, steps)
+        np.testing.assert_array_equal(b.state(s, E.EVR_STATE_U), g.state(E.EVR_STATE_U))
+        g.close()
+    b.close()
