@@ -313,3 +313,20 @@ def test_persistent_wait_timeout_is_reported_and_the_batch_continues(E, streams)
         np.testing.assert_array_equal(b.state(s, E.EVR_STATE_U), g.state(E.EVR_STATE_U))
         g.close()
     b.close()
+
+
+@pytest.mark.parametrize("over", [dict(data_term=1), dict(data_mode=1), dict(manifold=0),
+                                  dict(t_max_us=0)])
+def test_persistent_step_model_variants_equal_solo(E, streams, over):
+    """The L2 data term of Eq. 7, the persistent data image, the flat manifold and the
+    unclamped time surface through the persistent step: each stream equals its solo run."""
+    steps = 4
+    b = run_batch(E, streams, 31, steps, grouping=(0, 1),
+                  schedule=E.EVR_BATCH_SCHEDULE_PERSISTENT, **over)
+    assert b.schedule == E.EVR_BATCH_SCHEDULE_PERSISTENT
+    for s in (0, 2, 5, 7):
+        g = run_solo(E, streams[s], 31, steps, **over)
+        for w in (E.EVR_STATE_U, E.EVR_STATE_P2, E.EVR_STATE_F):
+            np.testing.assert_array_equal(b.state(s, w), g.state(w), err_msg=f"stream {s} {w}")
+        g.close()
+    b.close()
