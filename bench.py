@@ -725,6 +725,11 @@ def run_batch_bench(args):
     # level that bounds them); one group sweeps the whole batch through HBM every pass
     persistent = b.schedule == E.EVR_BATCH_SCHEDULE_PERSISTENT
     grouped = "L2 groups" in b.solver_name or "windows of" in b.solver_name
+    # ncu counters of the persistent launch (one per step), keyed by its configuration
+    prof = None
+    if persistent and args.storage == 0 and world == 1:
+        key = b.solver_name.split(": ", 1)[-1].split(", windows")[0]
+        prof = profiled("batch256", key)
     if grouped:
         level = {"bound": "l2", "peak": l2_gbs, "frac": achieved / l2_gbs,
                  "peak_source": "L2, measured in this run (evr_measure_peak level 0)"}
@@ -755,7 +760,9 @@ def run_batch_bench(args):
                                    "one GPU"),
                    "l2": "flushed between timed steps (256 MiB write, outside the events)"},
         "roofline": {"bound": level["bound"], "achieved": achieved, "peak": level["peak"],
-                     "unit": "GB/s", "frac": level["frac"], "traffic": None,
+                     "unit": "GB/s", "frac": level["frac"],
+                     "traffic": prof["dram_bytes_per_launch"] if prof else None,
+                     "issue_active": prof["issue_active"] if prof else None,
                      "frac_hbm": achieved / peak,
                      "kernel": ("k_batch_persist: the whole step (pushes, prologue, "
                                 "iteration passes) in one persistent launch" if persistent

@@ -38,6 +38,7 @@ SOLVER_SOURCES = ("evr_kernels.cu", "evr_solvers.cu", "evr_cluster.cu", "evr_til
                   "evr_push.cuh", "evr_internal.cuh")
 STAGED_SOURCES = SOLVER_SOURCES + ("evr_staged.cu", "evr_tma.cuh")
 REVERSE_SOURCES = ("evr_grad.cu", "evr_tma.cuh")
+PERSIST_SOURCES = SOLVER_SOURCES + ("evr_persist.cu", "evr_persist.cuh")
 
 
 def sources_for(solver: str):
@@ -47,6 +48,8 @@ def sources_for(solver: str):
         return STAGED_SOURCES
     if solver.startswith("k_rev_tiled"):
         return REVERSE_SOURCES
+    if solver.startswith("persistent step"):
+        return PERSIST_SOURCES
     return SOLVER_SOURCES
 
 

@@ -330,3 +330,27 @@ def test_persistent_step_model_variants_equal_solo(E, streams, over):
             np.testing.assert_array_equal(b.state(s, w), g.state(w), err_msg=f"stream {s} {w}")
         g.close()
     b.close()
+
+
+def test_persistent_step_host_arrays_equal_device_arrays(E, streams):
+    """evr_batch_step (host arrays, copied through the library's pinned staging) and
+    evr_batch_step_device give the same persistent steps."""
+    import torch
+    steps = 4
+    a = E.Batch(SIZES, tile_config=36)
+    d = E.Batch(SIZES, tile_config=36)
+    for b in (a, d):
+        b.set_schedule(E.EVR_BATCH_SCHEDULE_PERSISTENT)
+    keep = []  # the device copies stay alive until the steps that read them are done
+    for k in range(steps):
+        x, y, t, p, off = batch_step_arrays(streams, 300, k)
+        a.step(x, y, t, p, off, 30)
+        dev = [torch.from_numpy(v.view(np.int16) if v.dtype == np.uint16 else v).cuda()
+               for v in (x, y, t, p, off)]
+        torch.cuda.synchronize()
+        d.step_device(*dev, 30)
+        keep.append(dev)
+    assert a.schedule == d.schedule == E.EVR_BATCH_SCHEDULE_PERSISTENT
+    np.testing.assert_array_equal(a.images(), d.images())
+    a.close()
+    d.close()
