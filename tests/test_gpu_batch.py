@@ -354,3 +354,29 @@ def test_persistent_step_host_arrays_equal_device_arrays(E, streams):
     np.testing.assert_array_equal(a.images(), d.images())
     a.close()
     d.close()
+
+
+def test_schedule_switch_mid_stream_keeps_every_stream_bit_identical(E, streams):
+    """The schedule switches every two steps (a switch re-tunes the schedule at the next
+    step, which runs as a graph; the step after it runs persistent when that was chosen):
+    the state equals a run that never switches."""
+    steps = 8
+    ref = run_batch(E, streams, 36, steps, grouping=(0, 1),
+                    schedule=E.EVR_BATCH_SCHEDULE_GRAPH)
+    b = E.Batch(SIZES, tile_config=36)
+    b.set_grouping(0, 1)
+    seen = set()
+    for k in range(steps):
+        if k % 2 == 0:
+            b.set_schedule(E.EVR_BATCH_SCHEDULE_PERSISTENT if k % 4 else
+                           E.EVR_BATCH_SCHEDULE_GRAPH)
+        x, y, t, p, off = batch_step_arrays(streams, 300, k)
+        b.step(x, y, t, p, off, 30)
+        seen.add(b.schedule)
+    assert seen == {E.EVR_BATCH_SCHEDULE_GRAPH, E.EVR_BATCH_SCHEDULE_PERSISTENT}
+    assert b.synchronize() == (0, -1)
+    for s in range(len(SIZES)):
+        for w in (E.EVR_STATE_U, E.EVR_STATE_P1, E.EVR_STATE_TLAST):
+            np.testing.assert_array_equal(b.state(s, w), ref.state(s, w), err_msg=f"{s} {w}")
+    ref.close()
+    b.close()
