@@ -313,8 +313,8 @@ int evr_batch_set_grouping(evr_batch* b, long long budget_bytes, int branches);
  *     whose arguments take each step's packets.  The grid holds as many CTAs as are
  *     resident at once; they take (stream, item) work items in list order from a queue
  *     and wait, bounded, until the item's stream has completed the items it depends on
- *     (the batching of NEXT-2; the update rules are Eq. update_rules, run as in the
- *     tiled passes).  The items of a window of streams whose pass working set fits the
+ *     (every tile runs the update rules of Eq. update_rules exactly as the tiled
+ *     passes do).  The items of a window of streams whose pass working set fits the
  *     grouping budget (evr_batch_set_grouping; 0: every stream) are listed pass after
  *     pass, so the window's state stays in L2.  Tiles of 32 x 32 and 32 x 48 pixels only
  *     (tile_config 1-5, 28-32, 35-42).  A wait that runs out (0.2 s) ends the launch
