@@ -380,3 +380,57 @@ def test_schedule_switch_mid_stream_keeps_every_stream_bit_identical(E, streams)
             np.testing.assert_array_equal(b.state(s, w), ref.state(s, w), err_msg=f"{s} {w}")
     ref.close()
     b.close()
+
+
+@pytest.fixture(scope="module")
+def batch256():
+    """The 256-stream batched workload at full size (96 x 128x128, 96 x 240x180,
+    64 x 346x260; 500-event packets, 50 iterations), its first three packets per stream."""
+    from evsim.configs import batch_configs, make_batch
+    cfgs = batch_configs()
+    return cfgs, make_batch(cfgs, max_packets=3)
+
+
+@pytest.mark.parametrize("schedule", ["graph", "persistent"])
+def test_full_size_batch256_sampled_streams_match_oracle(E, batch256, schedule):
+    """Full-size batch in the benchmark's launch configuration (autotuned tile; the graph
+    or the persistent schedule): three steps, the last one teacher-forced against the
+    FP64 oracle on sampled streams of every size (u within 1e-4, t_last bit-exact)."""
+    cfgs, streams = batch256
+    sizes = [(c.W, c.H) for c in cfgs]
+    iters = cfgs[0].iters
+    b = E.Batch(sizes)
+    b.set_schedule(E.EVR_BATCH_SCHEDULE_GRAPH if schedule == "graph"
+                   else E.EVR_BATCH_SCHEDULE_PERSISTENT)
+    sampled = [0, 95, 96, 191, 192, 255]
+    p = b.params
+    oracles = {}
+    for k in range(3):
+        x, y, t, pol, off = batch_step_arrays(streams, 500, k)
+        if k == 2:
+            for s in sampled:
+                W, H = sizes[s]
+                o = O.OracleStream(W, H, O.OracleParams(
+                    lam=float(p.lambda_), delta_pos=float(p.delta_pos),
+                    delta_neg=float(p.delta_neg), u_min=float(p.u_min), u_max=float(p.u_max),
+                    u_init=float(p.u_init), tau=float(p.tau), sigma=float(p.sigma),
+                    time_scale=float(np.float32(p.time_scale))))
+                o.set_up(b.state(s, E.EVR_STATE_U).astype(np.float64),
+                         np.stack([b.state(s, w) for w in (E.EVR_STATE_P1, E.EVR_STATE_P2,
+                                                           E.EVR_STATE_P3)]).astype(np.float64))
+                o.set(O.TLAST, b.state(s, E.EVR_STATE_TLAST))
+                o.set(O.TREF, int(b.state(s, E.EVR_STATE_CLOCK)))
+                o.set(O.TINIT, int(b.state(s, E.EVR_STATE_TINIT)))
+                a0, a1 = off[s], off[s + 1]
+                assert o.push(x[a0:a1], y[a0:a1], t[a0:a1], pol[a0:a1]) == 0
+                o.solve(iters)
+                oracles[s] = o
+        b.step(x, y, t, pol, off, iters)
+    assert b.synchronize() == (0, -1)
+    if schedule == "persistent":
+        assert b.schedule == E.EVR_BATCH_SCHEDULE_PERSISTENT
+    for s, o in oracles.items():
+        np.testing.assert_array_equal(b.state(s, E.EVR_STATE_TLAST), o.get(O.TLAST))
+        d = np.max(np.abs(b.image(s).astype(np.float64) - o.u))
+        assert d <= 1e-4, (s, sizes[s], d)
+    b.close()
