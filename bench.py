@@ -457,7 +457,8 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     if pg:
         pg.barrier()
-    ms_steps = sum(a.elapsed_time(b) for a, b in evs)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms_steps = sum(step_ms)
     _, step_launches, _ = E.evr_kernel_time(g.h)
     E.evr_enable_kernel_timing(g.h, False)
 
@@ -484,6 +485,14 @@ def run_ours(args):
     t_max, ev_total = reduce_timing(ms_steps, ev_timed, pg, "cuda")
     value = ev_total / (t_max * 1e-3)
     gpix = world * args.steps * cfg.W * cfg.H * cfg.iters / (t_max * 1e-3) / 1e9
+    # this rank's timed steps as five consecutive runs: events/s of each, and the median
+    runs = []
+    if args.steps >= 5:
+        bounds = np.linspace(0, args.steps, 6).astype(int)
+        for r in range(5):
+            a_, b_ = int(bounds[r]), int(bounds[r + 1])
+            ev_r = int(offs[k1 + b_] - offs[k1 + a_])
+            runs.append(ev_r / (sum(step_ms[a_:b_]) * 1e-3))
 
     # ---- end to end through the C ABI with host buffers (same number of steps): every
     # step pushes its packet from host arrays (the library stages it in pinned memory and
@@ -555,6 +564,8 @@ def run_ours(args):
                                            "f32 (p, ubar stored bf16)"][args.storage],
             "data": "synthetic",
             "gpix_iter_per_s": gpix,
+            "median_of_5_runs": ({"value": float(np.median(runs)), "unit": "events/s",
+                                  "runs": runs, "rank": 0} if runs else None),
             "config": {"workload": describe(cfg), "sensor": f"{cfg.W}x{cfg.H}",
                        "events_per_step": cfg.packet, "iters": cfg.iters,
                        "solver": g.solver_name, "parallelism": f"{world} independent streams",
