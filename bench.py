@@ -139,6 +139,13 @@ class ClockSampler:
         except OSError:
             self.proc = None
 
+    def wait_first(self, timeout=5.0):
+        """Block until nvidia-smi has produced its first sample (its start-up runs before
+        the timed region, not inside it)."""
+        t_end = time.perf_counter() + timeout
+        while self.proc and not self.rows and time.perf_counter() < t_end:
+            time.sleep(0.01)
+
     def _read(self):
         for line in self.proc.stdout:
             self.rows.append([c.strip() for c in line.split(",")])
@@ -429,23 +436,30 @@ def run_ours(args):
         step(k)
         k += 1
     settled = E.evr_solver_settled(g.h)
-    k0 = SETTLE_MAX  # first warm-up packet
-    for j in range(args.warmup):
-        step(k0 + j)
-    assert g.synchronize() == 0
-    torch.cuda.synchronize()
-    k1 = k0 + args.warmup  # first timed packet
-
+    # the clock sampler starts before the warm-up packets, so that its start-up is over
+    # and the GPU busy when the timed region begins
     clk = ClockSampler(local)
     if rank == 0:
         clk.start()
+        clk.wait_first()
+    # warm-up steps exactly as the timed ones: L2 flush, events, the library's own kernel
+    # timing (its events around each graph launch sit inside ours)
+    k0 = SETTLE_MAX  # first warm-up packet
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+           for _ in range(max(args.steps, args.warmup))]
+    E.evr_enable_kernel_timing(g.h, True)
+    for j in range(args.warmup):
+        flush.fill_(float(j))
+        evs[j][0].record(cur)
+        step(k0 + j)
+        evs[j][1].record(cur)
+    assert g.synchronize() == 0
+    torch.cuda.synchronize()
+    k1 = k0 + args.warmup  # first timed packet
+    evs = evs[:args.steps]
     if pg:
         pg.barrier()
-    # the library records each step graph's launches (its events around the graph launch
-    # sit inside ours)
-    E.evr_enable_kernel_timing(g.h, True)
+    E.evr_enable_kernel_timing(g.h, True)  # counts from here
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for j in range(args.steps):
@@ -668,16 +682,22 @@ def run_batch_bench(args):
     for x, y, t, p, off in steps:
         dev.append(tuple(torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).cuda()
                          for a in (x, y, t, p, off)))
-    for k in range(args.warmup):
-        b.step_device(*dev[k], iters)
-    assert b.synchronize() == (0, -1)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    clk = ClockSampler(local)
+    clk = ClockSampler(local)  # started (and running) before the warm-up steps
     if rank == 0:
         clk.start()
+        clk.wait_first()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(max(args.steps, args.warmup))]
     b.enable_kernel_timing(True)
+    for k in range(args.warmup):  # as the timed steps: flush, events, kernel timing
+        flush.fill_(float(k))
+        evs[k][0].record(cur)
+        b.step_device(*dev[k], iters)
+        evs[k][1].record(cur)
+    assert b.synchronize() == (0, -1)
+    evs = evs[:args.steps]
+    b.enable_kernel_timing(True)  # counts from here
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -853,11 +873,12 @@ def run_diff_bench(args):
         loss = ((u - target) ** 2).mean(dim=(1, 2)).sum()
         loss.backward()
 
+    clk = ClockSampler(local)  # started (and running) before the warm-up steps
+    clk.start()
+    clk.wait_first()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    clk.start()
     E.evr_unrolled_timing_start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
