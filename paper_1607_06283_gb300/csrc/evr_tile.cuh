@@ -112,7 +112,9 @@ struct NoExchange {
 // The extended tile held by one CTA.  Thread (tx, ty) holds pixels
 // (tx + 32 kx, KY ty + ky): pixel-local state in registers, vertical neighbours
 // inside the strip in registers, and only q1 (read at x-1), ubar (read at x+1) and
-// the strip ends in shared memory.  Pixels k = 2j and 2j + 1 (vertical neighbours in
+// the strip ends in shared memory -- for tiles one warp wide (KX = 1) without a
+// neighbour exchange, q1 and ubar of the x neighbours come from the adjacent lanes by
+// warp shuffles and only the strip ends go through shared memory.  Pixels k = 2j and 2j + 1 (vertical neighbours in
 // one strip, KY even) form pair j of every per-pixel array and are updated by paired
 // instructions.  The image-border rules (forward differences zero on the last
 // column/row, the matching divergence) are per-pixel 0/1 factors: q is zero where its
@@ -421,6 +423,8 @@ struct Tile {
   template <bool L2, bool SAVE = false, class X = NoExchange>
   __device__ __forceinline__ void iterate(TileSmem<KX, KY, NTY, ST>& sm, const SolveConsts& c,
                                           X* xc = nullptr) {
+    // one warp across the tile and no exchange with other CTAs: x neighbours by shuffles
+    constexpr bool kShfl = KX == 1 && !X::kOn;
     float2 q1r[KP], q2r[KP];
     const int ty0 = threadIdx.y;
     const float2 one_neg = dup2(-1.0f);
@@ -430,7 +434,7 @@ struct Tile {
       const int k0 = 2 * j, k1 = k0 + 1;
       q1r[j] = fma2(E3[j], p3[j], fma2(E2[j], p2[j], mul2(E1[j], p1[j])));
       q2r[j] = fma2(E6[j], p3[j], fma2(E5[j], p2[j], mul2(E4[j], p1[j])));
-      sm.q1[ly(k0) / 2][lx(k0) + 1] = q1r[j];
+      if constexpr (!kShfl) sm.q1[ly(k0) / 2][lx(k0) + 1] = q1r[j];
       if (k1 % KY == KY - 1) sm.q2last[ty0 + 1][lx(k1)] = q2r[j].y;
       if constexpr (X::kOn) xc->send_q(lx(k0), ly(k0) / 2, q1r[j], k1 % KY == KY - 1, lx(k1),
                                        q2r[j].y);
@@ -442,7 +446,14 @@ struct Tile {
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
       const int k0 = 2 * j;
-      const float2 q1m = sm.q1[ly(k0) / 2][lx(k0)];
+      float2 q1m;
+      if constexpr (kShfl) {  // x - 1 neighbour: the lane to the left (zero at lane 0)
+        q1m.x = __shfl_up_sync(0xffffffffu, q1r[j].x, 1);
+        q1m.y = __shfl_up_sync(0xffffffffu, q1r[j].y, 1);
+        if (threadIdx.x == 0) q1m = dup2(0.0f);
+      } else {
+        q1m = sm.q1[ly(k0) / 2][lx(k0)];
+      }
       // y - 1 neighbour: pixel k1's is k0; pixel k0's is the pair above or the strip above
       const float2 q2m = make_float2((k0 % KY == 0) ? sm.q2last[ty0][lx(k0)] : q2r[j - 1].y,
                                      q2r[j].x);
@@ -471,7 +482,7 @@ struct Tile {
       u[j] = un;
       q1r[j] = ub;  // from here on: ubar of pair j
       if constexpr (SAVE) ubs[j] = ub;
-      sm.ub[ly(k0) / 2][lx(k0)] = S::enc2(ub);
+      if constexpr (!kShfl) sm.ub[ly(k0) / 2][lx(k0)] = S::enc2(ub);
       if (k0 % KY == 0) sm.ubfirst[ty0][lx(k0)] = S::enc(ub.x);
       if constexpr (X::kOn) xc->send_u(lx(k0), ly(k0) / 2, ub, k0 % KY == 0);
     }
@@ -483,7 +494,14 @@ struct Tile {
     for (int j = 0; j < KP; ++j) {
       const int k0 = 2 * j, k1 = k0 + 1;
       const float2 ub = q1r[j];
-      const float2 ubx = S::dec2(sm.ub[ly(k0) / 2][lx(k0) + 1]);
+      float2 ubx;
+      if constexpr (kShfl) {  // x + 1 neighbour: the lane to the right (zero at lane 31)
+        ubx.x = __shfl_down_sync(0xffffffffu, ub.x, 1);
+        ubx.y = __shfl_down_sync(0xffffffffu, ub.y, 1);
+        if (threadIdx.x == 31) ubx = dup2(0.0f);
+      } else {
+        ubx = S::dec2(sm.ub[ly(k0) / 2][lx(k0) + 1]);
+      }
       // y + 1 neighbour: pixel k0's is k1; pixel k1's is the next pair or the strip below
       const float2 uby = make_float2(
           ub.y, (k1 % KY == KY - 1) ? S::dec(sm.ubfirst[ty0 + 1][lx(k1)]) : q1r[j + 1].x);
