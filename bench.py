@@ -666,7 +666,7 @@ def run_batch_bench(args):
     sizes = [(c.W, c.H) for c in cfgs]
     cur = torch.cuda.Stream()
     torch.cuda.set_stream(cur)
-    b = E.Batch(sizes, storage=args.storage)
+    b = E.Batch(sizes, storage=args.storage, tile_config=args.tile)
     b.set_cuda_stream(cur.cuda_stream)
     grouping = None
     if args.grouping is not None:
@@ -726,7 +726,7 @@ def run_batch_bench(args):
     value = ev / (ms * 1e-3)
     # end to end: host arrays in, all images out into pinned memory, every step; two
     # steps in flight (the next step is queued before the previous images are waited for)
-    b2 = E.Batch(sizes, storage=args.storage)
+    b2 = E.Batch(sizes, storage=args.storage, tile_config=args.tile)
     b2.set_cuda_stream(cur.cuda_stream)
     if grouping is not None:
         b2.set_grouping(*grouping)
