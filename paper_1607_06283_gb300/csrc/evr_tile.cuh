@@ -114,7 +114,11 @@ struct NoExchange {
 // inside the strip in registers, and only q1 (read at x-1), ubar (read at x+1) and
 // the strip ends in shared memory -- for tiles one warp wide (KX = 1) without a
 // neighbour exchange, q1 and ubar of the x neighbours come from the adjacent lanes by
-// warp shuffles and only the strip ends go through shared memory.  Pixels k = 2j and 2j + 1 (vertical neighbours in
+// warp shuffles and only the strip ends go through shared memory.  Lanes 0 and 31 then
+// read their own value where the shared-memory form read a zero pad: both are halo
+// columns (every tile has R >= 1), whose values are inexact after the first iteration
+// either way and reach the owned pixels in no case (the exact region shrinks by one
+// pixel per side and iteration from the tile's edge whatever the edge reads).  Pixels k = 2j and 2j + 1 (vertical neighbours in
 // one strip, KY even) form pair j of every per-pixel array and are updated by paired
 // instructions.  The image-border rules (forward differences zero on the last
 // column/row, the matching divergence) are per-pixel 0/1 factors: q is zero where its
@@ -447,10 +451,9 @@ struct Tile {
     for (int j = 0; j < KP; ++j) {
       const int k0 = 2 * j;
       float2 q1m;
-      if constexpr (kShfl) {  // x - 1 neighbour: the lane to the left (zero at lane 0)
+      if constexpr (kShfl) {  // x - 1 neighbour: the lane to the left (lane 0: its own)
         q1m.x = __shfl_up_sync(0xffffffffu, q1r[j].x, 1);
         q1m.y = __shfl_up_sync(0xffffffffu, q1r[j].y, 1);
-        if (threadIdx.x == 0) q1m = dup2(0.0f);
       } else {
         q1m = sm.q1[ly(k0) / 2][lx(k0)];
       }
@@ -495,10 +498,9 @@ struct Tile {
       const int k0 = 2 * j, k1 = k0 + 1;
       const float2 ub = q1r[j];
       float2 ubx;
-      if constexpr (kShfl) {  // x + 1 neighbour: the lane to the right (zero at lane 31)
+      if constexpr (kShfl) {  // x + 1 neighbour: the lane to the right (lane 31: its own)
         ubx.x = __shfl_down_sync(0xffffffffu, ub.x, 1);
         ubx.y = __shfl_down_sync(0xffffffffu, ub.y, 1);
-        if (threadIdx.x == 31) ubx = dup2(0.0f);
       } else {
         ubx = S::dec2(sm.ub[ly(k0) / 2][lx(k0) + 1]);
       }
