@@ -166,9 +166,10 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2)
   constexpr int NT = kRevNTY, EW = 32, EH = 2 * NT, R = kRevR;
   constexpr int OW = EW - 2 * R, OH = EH - 2 * R;
   extern __shared__ __align__(128) float rstage[];  // [2][kRevStageF]: tape slots
-  __shared__ float tv[EH + 1][EW + 1];  // tau a_v; column EW and row EH: zero pads
-  __shared__ float q1s[EH][EW + 1];     // (M^T sigma a_pt)_1 masked; column 0: zero pad
-  __shared__ float q2s[EH + 1][EW];     // (M^T sigma a_pt)_2 masked; row 0: zero pad
+  // neighbours in x are adjacent lanes (warp shuffles); in y the next thread row's
+  // first pixel (tau a_v) and the previous row's last (q2) go through shared memory
+  __shared__ float tv[EH + 1][EW];   // tau a_v of the even rows; row EH: zero pad
+  __shared__ float q2s[EH + 1][EW];  // (M^T sigma a_pt)_2 masked; row 0: zero pad
   __shared__ float lsum[NT];            // the warps' lambda sums of an iteration
   __shared__ __align__(8) unsigned long long s_mb[2];
   __shared__ int s_bail;
@@ -216,12 +217,10 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2)
     tv[ly][lane] = tav[h];
   }
   const int tid = ty * 32 + lane;
-  for (int i = tid; i < EH + 1; i += 32 * NT) tv[i][EW] = 0.0f;
   for (int i = tid; i < EW; i += 32 * NT) {
     tv[EH][i] = 0.0f;
     q2s[0][i] = 0.0f;
   }
-  for (int i = tid; i < EH; i += 32 * NT) q1s[i][0] = 0.0f;
   const int sx0 = gx0 & ~7;  // the staged box's first column
   auto issue = [&](int it, int b) {  // thread 0: the tape slot of reversed iteration it
     const uint32_t mb = tma::smem_u32(&s_mb[b]);
@@ -299,9 +298,13 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2)
     for (int h = 0; h < 2; ++h) {
       const int ly = 2 * ty + h;
       float b1 = a1[h], b2 = a2[h], b3 = a3[h];
+      // tau a_v of the x + 1 neighbour: the lane to the right (lane 31, a halo column
+      // whose value is inexact after the first reversed iteration whatever it reads,
+      // takes its own)
+      const float tvx = __shfl_down_sync(0xffffffffu, tav[h], 1);
       if (!(A.first && it == 0)) {
         const float tyn = h == 0 ? tav[1] : tv[ly + 1][lane];
-        const float dx = tv[ly][lane + 1] - tav[h], dy = tyn - tav[h];
+        const float dx = tvx - tav[h], dy = tyn - tav[h];
         b1 -= fmaf(E4[h], dy, E1[h] * dx);
         b2 -= fmaf(E5[h], dy, E2[h] * dx);
         b3 -= fmaf(E6[h], dy, E3[h] * dx);
@@ -328,7 +331,6 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2)
       // number, so a pixel's result does not depend on its place in the tile
       q1o[h] = __fmul_rn(sigma, fmaf(E3[h], b3, fmaf(E2[h], b2, E1[h] * b1)));
       q2o[h] = __fmul_rn(sigma, fmaf(E6[h], b3, fmaf(E5[h], b2, E4[h] * b1)));
-      q1s[ly][lane + 1] = q1o[h];
       if (h == 1) q2s[ly + 1][lane] = q2o[h];  // read by the thread row below
     }
     __syncthreads();
@@ -337,7 +339,9 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2)
     for (int h = 0; h < 2; ++h) {
       const int ly = 2 * ty + h;
       const float q2m = h == 0 ? q2s[ly][lane] : q2o[0];
-      const float div = (q1o[h] - q1s[ly][lane]) + (q2o[h] - q2m);
+      // x - 1 neighbour: the lane to the left (lane 0, a halo column, takes its own)
+      const float q1m = __shfl_up_sync(0xffffffffu, q1o[h], 1);
+      const float div = (q1o[h] - q1m) + (q2o[h] - q2m);
       const float aub = -div;
       float av = 0.0f;  // outside the image: no data term (and no 0/0)
       if (in[h]) {
@@ -357,7 +361,7 @@ __global__ void __launch_bounds__(32 * kRevNTY, 2)
       }
       au[h] = av - aub;
       tav[h] = __fmul_rn(tau, av);
-      tv[ly][lane] = tav[h];
+      if (h == 0) tv[ly][lane] = tav[h];  // the y + 1 neighbour of the thread row above
     }
     // the tile's lambda sum of the iteration, in FP32 in a fixed order (within each warp,
     // then over the warps by warp 0)
